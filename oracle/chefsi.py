@@ -1,0 +1,274 @@
+"""Plain FP64 CPU oracle for one CheFSI cycle on a block-sparse DG Hamiltonian.
+
+TEST INFRASTRUCTURE ONLY. Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module. It shares no code with
+the CUDA library (no kernels, headers, helpers or tables); both sides are fed
+the same arrays from the seeded input generator and nothing else.
+
+Orientation follows the paper: a block of vectors X is N x N_s with one state
+per column, and x_K (rows off_K .. off_K + J_K) is the part of X on element K.
+Everything is float64, NumPy/SciPy, written for clarity, not speed.
+
+Sections of arXiv:1606.03416 followed here:
+  * Sec. II.B, Eqs. eigvalue_prob / HDG_sub_blocks  -> the block-sparse H
+  * Sec. III.A, Algorithm 1 (CheFSI cycle), steps 1-5
+  * Sec. III.B.1, Eqs. matvec_1 .. matvec_3          -> ``matvec``
+  * Sec. III.B.2 (Cholesky-QR, projection, rotation) -> ``cholesky_qr``,
+    ``rayleigh_ritz``
+  * Sec. II.C, Eqs. densitymatrix / electron_density_from_DM, and the Fermi-Dirac
+    occupations of Eq. KS_DG_Energy -> ``fermi_occupations``, ``density_blocks``
+
+Readings where the paper is silent (each is also listed in the design notes):
+  * Filter (Alg. 1 step 2): the *scaled* three-term Chebyshev recurrence of the
+    CheFSI literature the paper cites, with [a, b] mapped to [-1, 1] and the
+    result normalised by C_m at a0 (the lower end of the wanted spectrum).
+    Unscaled p_m(H) X differs by the scalar C_m((a0-c)/e) only.
+  * Bounds (Alg. 1 step 1): k-step Lanczos with full re-orthogonalisation from
+    a given start vector; upper bound = max eig(T_k) + |beta_k|. Lower filter
+    bound a = largest previous Ritz value, a0 = smallest; first cycle:
+    a0 = min eig(T_k), a = a0 + (b - a0) * N_s / N.
+  * Cholesky-QR fails loudly (``np.linalg.LinAlgError``) if S is not SPD.
+  * Occupations: spin factor 2, so sum_i 2 f_i = N_e; mu by bisection on
+    [lambda_1 - 50 kT, lambda_Ns + 50 kT] until |2 sum f - N_e| <= 1e-13 N_e
+    or 200 halvings.
+
+Parity pins (tests/test_oracle_pins.py) check every function here against
+results the mathematics fixes independently of this code: brute-force dense
+products, the closed form V C_m(Lambda) V^T X of the filter, dense eigh of H,
+QR uniqueness, exact spectra of diagonal matrices, and trace / symmetry
+identities.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+
+class DGHamiltonian:
+    """Block-sparse symmetric H (Eq. HDG_sub_blocks): H_{K;K'} nonzero only for
+    neighbouring elements K' in N(K), each block dense J_K x J_K'."""
+
+    def __init__(self, nb, row_ptr, col, blk_off, values):
+        self.nb = np.asarray(nb, dtype=np.int64)
+        self.row_ptr = np.asarray(row_ptr, dtype=np.int64)
+        self.col = np.asarray(col, dtype=np.int64)
+        self.blk_off = np.asarray(blk_off, dtype=np.int64)
+        self.values = np.asarray(values, dtype=np.float64)
+        self.M = int(self.nb.shape[0])
+        self.off = np.zeros(self.M + 1, dtype=np.int64)
+        self.off[1:] = np.cumsum(self.nb)
+        self.N = int(self.off[-1])
+
+    @classmethod
+    def from_blocksparse(cls, bs):
+        return cls(bs.nb, bs.row_ptr, bs.col, bs.blk_off, bs.values)
+
+    def rows(self, K):
+        return slice(int(self.off[K]), int(self.off[K + 1]))
+
+    def neighbours(self, K):
+        """Pairs (K', H_{K;K'}) over K' in N(K) (including K itself)."""
+        for e in range(self.row_ptr[K], self.row_ptr[K + 1]):
+            Kp = int(self.col[e])
+            nK, nKp = int(self.nb[K]), int(self.nb[Kp])
+            start = int(self.blk_off[e])
+            yield Kp, self.values[start:start + nK * nKp].reshape(nK, nKp)
+
+    def dense(self):
+        """Dense N x N matrix assembled entry by entry from the blocks."""
+        A = np.zeros((self.N, self.N))
+        for K in range(self.M):
+            for Kp, blk in self.neighbours(K):
+                A[self.rows(K), self.rows(Kp)] = blk
+        return A
+
+
+def matvec(H: DGHamiltonian, X: np.ndarray) -> np.ndarray:
+    """Y = H X for an N x k block, element by element (Eq. matvec_3):
+    y_K = sum over K' in N(K) of H_{K;K'} x_{K'}, a sum of dense GEMMs."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.zeros_like(X)
+    for K in range(H.M):
+        acc = np.zeros((int(H.nb[K]),) + X.shape[1:])
+        for Kp, blk in H.neighbours(K):
+            acc += blk @ X[H.rows(Kp)]
+        Y[H.rows(K)] = acc
+    return Y
+
+
+def filter_coefficients(m: int, a: float, b: float, a0: float):
+    """Scalars of the scaled recurrence for Alg. 1 step 2.
+
+    e = (b - a)/2 and c = (b + a)/2 map [a, b] to [-1, 1]; sigma_1 = e/(a0 - c)
+    is 1/C_1(tau0) with tau0 = (a0 - c)/e, and sigma_{k+1} = 1/(2/sigma_1 - sigma_k)
+    is C_k(tau0)/C_{k+1}(tau0) by the Chebyshev three-term rule.
+    Returns (c, e, sigmas) with sigmas[k] = sigma_k for k = 1..m (index 0 unused).
+    """
+    if not (a0 < a < b) or m < 1:
+        raise ValueError("need a0 < a < b and m >= 1")
+    e = 0.5 * (b - a)
+    c = 0.5 * (b + a)
+    sig = [0.0] * (m + 1)
+    sig[1] = e / (a0 - c)
+    for k in range(1, m):
+        sig[k + 1] = 1.0 / (2.0 / sig[1] - sig[k])
+    return c, e, sig
+
+
+def chebyshev_filter(H: DGHamiltonian, X: np.ndarray, m: int, a: float, b: float, a0: float) -> np.ndarray:
+    """Y~ = p_m(H) X with [a, b] mapped to [-1, 1] (Alg. 1 step 2).
+
+    p_m(t) = C_m((t - c)/e) / C_m((a0 - c)/e), evaluated by the three-term
+    recurrence Y_{k+1} = (2 sigma_{k+1}/e)(H - cI) Y_k - sigma_k sigma_{k+1} Y_{k-1},
+    starting from Y_0 = X and Y_1 = (sigma_1/e)(H - cI) X.
+    """
+    c, e, sig = filter_coefficients(m, a, b, a0)
+    Y_prev = np.array(X, dtype=np.float64, copy=True)
+    Y = (sig[1] / e) * (matvec(H, Y_prev) - c * Y_prev)
+    for k in range(1, m):
+        Y_next = (2.0 * sig[k + 1] / e) * (matvec(H, Y) - c * Y) - (sig[k] * sig[k + 1]) * Y_prev
+        Y_prev, Y = Y, Y_next
+    return Y
+
+
+def lanczos_bounds(H: DGHamiltonian, v0: np.ndarray, k: int = 10):
+    """Upper spectral bound by k Lanczos steps (Alg. 1 step 1).
+
+    Full re-orthogonalisation (one classical Gram-Schmidt pass against all
+    previous Lanczos vectors after the three-term step). Returns
+    (b_upper, theta_min, alphas, betas): b_upper = max eig(T_k) + |beta_k| with
+    beta_k the norm of the last residual, theta_min = min eig(T_k). Stops early
+    (k reduced) if a residual vanishes (an invariant subspace was found).
+    """
+    k = int(min(k, H.N))
+    v = np.asarray(v0, dtype=np.float64) / np.linalg.norm(v0)
+    V = [v]
+    alphas, betas = [], []
+    beta_prev = 0.0
+    v_prev = np.zeros_like(v)
+    beta_last = 0.0
+    for j in range(k):
+        w = matvec(H, V[j][:, None])[:, 0] - beta_prev * v_prev
+        alpha = float(V[j] @ w)
+        w = w - alpha * V[j]
+        Vm = np.stack(V, axis=1)
+        w = w - Vm @ (Vm.T @ w)
+        alphas.append(alpha)
+        beta = float(np.linalg.norm(w))
+        beta_last = beta
+        if j == k - 1 or beta == 0.0:
+            break
+        betas.append(beta)
+        v_prev = V[j]
+        V.append(w / beta)
+        beta_prev = beta
+    T_eigs = sla.eigh_tridiagonal(np.array(alphas), np.array(betas), eigvals_only=True)
+    return float(T_eigs[-1] + abs(beta_last)), float(T_eigs[0]), alphas, betas
+
+
+def first_cycle_bounds(b_upper: float, theta_min: float, Ns: int, N: int):
+    """(a, a0) for the first cycle, before any Ritz values exist."""
+    a0 = theta_min
+    a = a0 + (b_upper - a0) * Ns / N
+    return a, a0
+
+
+def cholesky_qr(Y: np.ndarray):
+    """Alg. 1 step 3: S = Y^T Y, S = U^T U (U upper, positive diagonal), and
+    Y_hat with Y_hat U = Y. Returns (Y_hat, U, S). Raises LinAlgError if S is
+    not positive definite."""
+    S = Y.T @ Y
+    U = np.linalg.cholesky(S).T  # numpy gives lower L with S = L L^T
+    Y_hat = sla.solve_triangular(U, Y.T, trans="T", lower=False).T
+    return Y_hat, U, S
+
+
+def rayleigh_ritz(H: DGHamiltonian, Y_hat: np.ndarray):
+    """Alg. 1 steps 4-5: H_hat = Y_hat^T (H Y_hat), symmetrised; H_hat Q = Q D
+    with D ascending; X_new = Y_hat Q. Returns (X_new, D, H X_new)."""
+    W = matvec(H, Y_hat)
+    Hh = Y_hat.T @ W
+    Hh = 0.5 * (Hh + Hh.T)
+    D, Q = np.linalg.eigh(Hh)
+    return Y_hat @ Q, D, W @ Q
+
+
+def _fermi(x: np.ndarray) -> np.ndarray:
+    """1/(1 + exp(x)) without overflow."""
+    out = np.empty_like(x)
+    pos = x > 0
+    ex = np.exp(-x[pos])
+    out[pos] = ex / (1.0 + ex)
+    out[~pos] = 1.0 / (1.0 + np.exp(x[~pos]))
+    return out
+
+
+def fermi_occupations(ritz: np.ndarray, Ne: float, kT: float):
+    """Fermi-Dirac occupations f_i = 1/(1 + exp((lambda_i - mu)/kT)) with mu
+    fixed by the electron count 2 sum_i f_i = N_e (spin factor 2, Eq.
+    KS_DG_Energy). mu by bisection. Returns (f, mu)."""
+    lam = np.asarray(ritz, dtype=np.float64)
+    Ns = lam.shape[0]
+    if kT <= 0 or Ne < 0 or Ne > 2 * Ns:
+        raise ValueError("need kT > 0 and 0 <= Ne <= 2 Ns")
+    lo = float(lam.min()) - 50.0 * kT
+    hi = float(lam.max()) + 50.0 * kT
+    tol = 1e-13 * Ne
+    mu = 0.5 * (lo + hi)
+    for _ in range(200):
+        mu = 0.5 * (lo + hi)
+        count = 2.0 * _fermi((lam - mu) / kT).sum()
+        if abs(count - Ne) <= tol:
+            break
+        if count < Ne:
+            lo = mu
+        else:
+            hi = mu
+    return _fermi((lam - mu) / kT), mu
+
+
+def density_blocks(H: DGHamiltonian, X: np.ndarray, f: np.ndarray):
+    """Diagonal blocks of the density matrix (Eq. densitymatrix with K' = K):
+    P_KK = sum_i f_i x_{i;K} x_{i;K}^T, one J_K x J_K block per element."""
+    return [X[H.rows(K)] @ np.diag(f) @ X[H.rows(K)].T for K in range(H.M)]
+
+
+def chefsi_cycle(H: DGHamiltonian, X: np.ndarray, m: int, Ne: float, kT: float, v0: np.ndarray,
+                 prev_ritz=None, k_lanczos: int = 10, bounds=None):
+    """One CheFSI cycle (Alg. 1) followed by occupations and density blocks.
+
+    ``bounds`` = (a, b, a0) overrides step 1 (used when both sides must see
+    identical bounds). Returns a dict with the filter bounds, the new block,
+    Ritz values, occupations, mu and the diagonal density blocks."""
+    Ns = X.shape[1]
+    if bounds is None:
+        b, theta_min, _, _ = lanczos_bounds(H, v0, k_lanczos)
+        if prev_ritz is None:
+            a, a0 = first_cycle_bounds(b, theta_min, Ns, H.N)
+        else:
+            a, a0 = float(np.max(prev_ritz)), float(np.min(prev_ritz))
+    else:
+        a, b, a0 = bounds
+    Yt = chebyshev_filter(H, X, m, a, b, a0)
+    Yh, _, _ = cholesky_qr(Yt)
+    X_new, D, HX = rayleigh_ritz(H, Yh)
+    f, mu = fermi_occupations(D, Ne, kT)
+    P = density_blocks(H, X_new, f)
+    return dict(a=a, b=b, a0=a0, X=X_new, ritz=D, HX=HX, f=f, mu=mu, P=P)
+
+
+def chebyshev_value(m: int, t):
+    """C_m(t) from its trigonometric / hyperbolic closed form (used by the pins)."""
+    t = np.asarray(t, dtype=np.float64)
+    out = np.empty_like(t)
+    inside = np.abs(t) <= 1.0
+    out[inside] = np.cos(m * np.arccos(t[inside]))
+    ta = np.abs(t[~inside])
+    out[~inside] = np.sign(t[~inside]) ** m * np.cosh(m * np.arccosh(ta))
+    return out
+
+
+def packed_density(H: DGHamiltonian, blocks) -> np.ndarray:
+    """Concatenate P_KK row-major in element order (the library's packed form)."""
+    return np.concatenate([np.asarray(b).ravel() for b in blocks]) if blocks else np.zeros(0)
+

@@ -1,0 +1,176 @@
+/*
+ * dgchefsi.h -- C ABI of a GB300 (sm_103a) library for one CheFSI cycle on a
+ * block-sparse Discontinuous-Galerkin Hamiltonian (Banerjee, Lin, Hu, Yang,
+ * Pask, "Chebyshev polynomial filtered subspace iteration in the Discontinuous
+ * Galerkin method for large-scale electronic structure calculations",
+ * arXiv:1606.03416).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * H      symmetric, block-sparse over M elements (Sec. II.B, Eq. HDG_sub_blocks):
+ *        block H_{K;K'} (J_K x J_K', here nb[K] x nb[K']) is stored only for
+ *        neighbouring elements. N = sum_K nb[K]. Element K owns rows
+ *        off_K .. off_K + nb[K] - 1, off_K = sum_{L<K} nb[L].
+ * X, Y   blocks of N_s vectors, stored state-major: a row-major (N_s x ld)
+ *        double array, row i = state i, entry (i, r) = component r of state i.
+ *        This is the paper's N x N_s column block transposed, so each state is
+ *        contiguous. ld >= N; entries r >= N of a row are never read or written.
+ * Device pointers are CUDA device addresses on the context's device; host
+ *        pointers are plain host memory. Every argument below says which.
+ * Streams: all device work is enqueued on the context's stream (set at create,
+ *        changeable with dgchefsi_set_stream). A call returns once its work is
+ *        enqueued, except where it says it synchronises (it returns host
+ *        scalars or checks a device status).
+ * Ownership: the context owns its copy of H and all workspace; callers own
+ *        every buffer they pass. No call keeps a caller pointer after return.
+ * Errors: every call returns a dgchefsi_status. On error the outputs are
+ *        unspecified, nothing leaks, and dgchefsi_last_error() returns a
+ *        message for the calling thread. No C++ exception crosses the ABI.
+ */
+#ifndef DGCHEFSI_H
+#define DGCHEFSI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dgchefsi_ctx dgchefsi_ctx;
+
+typedef enum {
+  DGCHEFSI_OK = 0,
+  DGCHEFSI_ERR_ARG = 1,            /* invalid argument or inconsistent H */
+  DGCHEFSI_ERR_CUDA = 2,           /* a CUDA runtime or library call failed */
+  DGCHEFSI_ERR_OOM = 3,            /* device allocation failed */
+  DGCHEFSI_ERR_NOT_SPD = 4,        /* Cholesky of S = Y^T Y failed (rank loss) */
+  DGCHEFSI_ERR_NONFINITE = 5,      /* NaN/Inf in Ritz values or bounds */
+  DGCHEFSI_ERR_NO_CONVERGENCE = 6, /* the dense eigensolver did not converge */
+  DGCHEFSI_ERR_TIMEOUT = 7,        /* a bounded device wait gave up */
+  DGCHEFSI_ERR_UNSUPPORTED = 8     /* shape or precision this build does not run */
+} dgchefsi_status;
+
+/* Arithmetic of the filter (Alg. 1 step 2). The subspace steps are FP64 always. */
+typedef enum {
+  DGCHEFSI_F64 = 0,    /* FP64 operands, FP64 accumulation (CUDA-core DFMA) */
+  DGCHEFSI_TF32 = 1,   /* tcgen05 kind::tf32: TF32 operands, FP32 accumulation, FP32 iterates */
+  DGCHEFSI_BF16 = 2,   /* tcgen05 kind::f16: BF16 operands, FP32 accumulation, FP32 iterates */
+  DGCHEFSI_BF16X3 = 3  /* tcgen05 kind::f16, operands split hi+lo in BF16, three products
+                          (hi*hi + hi*lo + lo*hi), FP32 accumulation and iterates */
+} dgchefsi_prec;
+
+/* Build a context holding a device copy of H (Sec. II.B, Eq. HDG_sub_blocks;
+ * Fig. 1: H_{K;K'} nonzero only for neighbouring elements).
+ *   M        number of elements, >= 1
+ *   nb       host [M], basis functions per element, each in 1..256
+ *   row_ptr  host [M+1], block-CSR row pointers, row_ptr[0] = 0, nondecreasing
+ *   col      host [row_ptr[M]], neighbour element of each block, strictly
+ *            ascending within a row; every row holds its diagonal block (K,K)
+ *   blk_off  host [row_ptr[M]], offset in doubles of each block in `values`
+ *   values   host [n_values], each block row-major nb[K] x nb[K']
+ *   stream   cudaStream_t to enqueue on (NULL = legacy default stream)
+ *   out      receives the context
+ * Checks (DGCHEFSI_ERR_ARG otherwise): the pattern is symmetric, H_{K';K} equals
+ * H_{K;K'}^T exactly, diagonal blocks are exactly symmetric, every value is
+ * finite, and blocks lie inside `values`. Synchronises (copies H to the device). */
+dgchefsi_status dgchefsi_create(int32_t M, const int32_t* nb, const int64_t* row_ptr,
+                                const int32_t* col, const int64_t* blk_off,
+                                const double* values, int64_t n_values, void* stream,
+                                dgchefsi_ctx** out);
+
+/* Release the context and all its device memory. Synchronises its stream. NULL is a no-op. */
+void dgchefsi_destroy(dgchefsi_ctx* ctx);
+
+/* Change the stream later calls enqueue on. */
+dgchefsi_status dgchefsi_set_stream(dgchefsi_ctx* ctx, void* stream);
+
+/* N (total basis size) and M (elements) of the context's H; either pointer may be NULL. */
+dgchefsi_status dgchefsi_dims(const dgchefsi_ctx* ctx, int64_t* N, int32_t* M);
+
+/* Y = H X, element by element: y_K = sum over K' in N(K) of H_{K;K'} x_{K'}
+ * (Sec. III.B.1, Eq. matvec_3). X, Y: device, (Ns x ld) state-major, FP64; Y
+ * must not overlap X. Ns = 0 is a no-op. */
+dgchefsi_status dgchefsi_matvec(dgchefsi_ctx* ctx, const double* X, double* Y, int64_t Ns, int64_t ld);
+
+/* Spectral bounds by k Lanczos steps (Alg. 1 step 1: "a few steps of the
+ * Lanczos algorithm" for the upper bound), with full re-orthogonalisation.
+ *   v0         device [N] start vector (normalised internally; must be nonzero)
+ *   k          steps, 1..64 (clipped to N); stops early on an invariant subspace
+ *   b_upper    host out: max eig(T_k) + |beta_k|, an upper bound of the spectrum
+ *   theta_min  host out (nullable): min eig(T_k), used for the first cycle's
+ *              lower filter bound when no Ritz values exist yet
+ * Synchronises. */
+dgchefsi_status dgchefsi_bounds(dgchefsi_ctx* ctx, const double* v0, int k,
+                                double* b_upper, double* theta_min);
+
+/* Y = p_m(H) X with [a, b] mapped to [-1, 1] (Alg. 1 step 2), by the scaled
+ * three-term Chebyshev recurrence
+ *   Y_0 = X,  Y_1 = (s_1/e)(H - cI) X,
+ *   Y_{k+1} = (2 s_{k+1}/e)(H - cI) Y_k - s_k s_{k+1} Y_{k-1},
+ * with e = (b-a)/2, c = (b+a)/2, s_1 = e/(a0-c), s_{k+1} = 1/(2/s_1 - s_k), so
+ * that p_m(t) = C_m((t-c)/e)/C_m((a0-c)/e) and p_m(a0) = 1.
+ *   prec      filter arithmetic (dgchefsi_prec); X and Y are FP64 whatever it is
+ *   X         device, (Ns x ld) state-major, FP64, read only
+ *   Y         device, (Ns x ld) state-major, FP64, written; must not overlap X
+ *   m >= 1, and a0 < a < b (else DGCHEFSI_ERR_ARG).
+ * The tensor-core precisions need ld and the element sizes this build supports
+ * (nb[K] <= 128); otherwise DGCHEFSI_ERR_UNSUPPORTED. */
+dgchefsi_status dgchefsi_filter(dgchefsi_ctx* ctx, int prec, const double* X, double* Y,
+                                int64_t Ns, int64_t ld, int m, double a, double b, double a0);
+
+/* Cholesky-QR and Rayleigh-Ritz (Alg. 1 steps 3-5; Sec. III.B.2), all FP64:
+ *   S = Y^T Y, S = U^T U, Y_hat = Y U^{-1};  H_hat = Y_hat^T (H Y_hat), symmetrised;
+ *   H_hat Q = Q D (D ascending);  X_new = Y_hat Q.
+ *   Y     device, (Ns x ld) state-major: in = filtered block, out = X_new
+ *   ritz  device [Ns] out: D, ascending
+ * Returns DGCHEFSI_ERR_NOT_SPD if S is not numerically positive definite
+ * (Cholesky-QR has no fallback), DGCHEFSI_ERR_NO_CONVERGENCE if the dense
+ * eigensolver fails, DGCHEFSI_ERR_NONFINITE on NaN/Inf Ritz values.
+ * Synchronises (checks the factorisation status). Needs Ns <= N. */
+dgchefsi_status dgchefsi_rayleigh_ritz(dgchefsi_ctx* ctx, double* Y, int64_t Ns, int64_t ld, double* ritz);
+
+/* Fermi-Dirac occupations f_i = 1/(1 + exp((lambda_i - mu)/kT)) with mu set by
+ * 2 sum_i f_i = Ne (spin factor 2; occupations of Eq. KS_DG_Energy, Sec. III.B.2).
+ * mu by bisection on [min lambda - 50 kT, max lambda + 50 kT], stopped when
+ * |2 sum f - Ne| <= 1e-13 Ne or after 200 halvings.
+ *   ritz  device [Ns]; f device [Ns] out; mu device [1] out
+ * Needs kT > 0 and 0 <= Ne <= 2 Ns. */
+dgchefsi_status dgchefsi_occupations(dgchefsi_ctx* ctx, const double* ritz, int64_t Ns,
+                                     double Ne, double kT, double* f, double* mu);
+
+/* Diagonal blocks of the density matrix, P_KK = sum_i f_i x_{i;K} x_{i;K}^T
+ * (Eq. densitymatrix with K' = K; only these blocks give the density,
+ * Eq. electron_density_from_DM).
+ *   X  device (Ns x ld) state-major;  f device [Ns]
+ *   P  device out, packed: block K (nb[K] x nb[K], row-major) starts at
+ *      sum_{L<K} nb[L]^2. */
+dgchefsi_status dgchefsi_density_blocks(dgchefsi_ctx* ctx, const double* X, int64_t Ns, int64_t ld,
+                                        const double* f, double* P);
+
+/* One full CheFSI cycle (Alg. 1) plus occupations and density blocks:
+ * bounds -> filter -> Cholesky-QR -> Rayleigh-Ritz -> rotation -> f, mu -> P_KK.
+ *   X          device (Ns x ld): in = starting block, out = X_new
+ *   prev_ritz  host [Ns] or NULL. Filter bounds: b from k_lanczos Lanczos steps
+ *              started at v0 (device [N]); a = max(prev_ritz), a0 = min(prev_ritz);
+ *              on the first cycle (NULL) a0 = theta_min and a = a0 + (b-a0) Ns/N.
+ *   bounds     host [3] or NULL: if `use_bounds` is nonzero, (a, b, a0) are
+ *              taken from it and Lanczos is skipped; on return it holds the
+ *              (a, b, a0) used.
+ *   ritz, f    device [Ns] out;  mu device [1] out;  P device out as above.
+ * Synchronises. */
+dgchefsi_status dgchefsi_cycle(dgchefsi_ctx* ctx, int prec, double* X, int64_t Ns, int64_t ld, int m,
+                               double Ne, double kT, const double* v0, int k_lanczos,
+                               const double* prev_ritz, double* bounds, int use_bounds,
+                               double* ritz, double* f, double* mu, double* P);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* dgchefsi_last_error(void);
+
+/* Number of this library's own kernel launches since load (all contexts). */
+int64_t dgchefsi_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGCHEFSI_H */

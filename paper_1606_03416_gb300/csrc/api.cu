@@ -1,0 +1,553 @@
+// C ABI of the DG-CheFSI library: context set-up and validation, the FP64
+// filter driver, Lanczos bounds, Cholesky-QR / Rayleigh-Ritz, occupations,
+// density blocks and the full cycle (Alg. 1). Kernels live in f64_kernels.cu
+// and tc_filter.cu; the dense factorisations (Cholesky, triangular inverse,
+// symmetric eigensolve of the N_s x N_s projected matrix) are cuSOLVER calls.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+
+#include "ctx.h"
+
+namespace dg {
+
+int64_t launch_count();
+
+static thread_local std::string g_err;
+
+dgchefsi_status set_error(dgchefsi_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+void clear_error() { g_err.clear(); }
+
+dgchefsi_status ensure(dgchefsi_ctx* ctx, DevBuf& b, size_t bytes, const char* what) {
+  if (b.bytes >= bytes && b.p) return DGCHEFSI_OK;
+  if (b.p) {
+    DG_CUDA(cudaStreamSynchronize(ctx->stream));
+    DG_CUDA(cudaFree(b.p));
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return set_error(DGCHEFSI_ERR_OOM, "cudaMalloc of %zu bytes for %s failed: %s", bytes, what,
+                     cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  return DGCHEFSI_OK;
+}
+
+static void free_buf(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+static const char* solver_str(cusolverStatus_t s) {
+  switch (s) {
+    case CUSOLVER_STATUS_SUCCESS: return "success";
+    case CUSOLVER_STATUS_NOT_INITIALIZED: return "not initialized";
+    case CUSOLVER_STATUS_ALLOC_FAILED: return "alloc failed";
+    case CUSOLVER_STATUS_INVALID_VALUE: return "invalid value";
+    case CUSOLVER_STATUS_ARCH_MISMATCH: return "arch mismatch";
+    case CUSOLVER_STATUS_EXECUTION_FAILED: return "execution failed";
+    case CUSOLVER_STATUS_INTERNAL_ERROR: return "internal error";
+    default: return "other cusolver error";
+  }
+}
+
+#define DG_SOLVER(call)                                                                              \
+  do {                                                                                               \
+    cusolverStatus_t s_ = (call);                                                                    \
+    if (s_ != CUSOLVER_STATUS_SUCCESS)                                                               \
+      return dg::set_error(DGCHEFSI_ERR_CUDA, "%s failed: %s", #call, solver_str(s_));                \
+  } while (0)
+
+// Smallest / largest eigenvalue of the symmetric tridiagonal T (diag a, off b)
+// by Sturm-sequence bisection.
+static int sturm_count(const std::vector<double>& a, const std::vector<double>& b, double x) {
+  int cnt = 0;
+  double q = a[0] - x;
+  const double tiny = 1e-300;
+  if (q < 0) ++cnt;
+  for (size_t i = 1; i < a.size(); ++i) {
+    if (q == 0.0) q = tiny;
+    q = (a[i] - x) - b[i - 1] * b[i - 1] / q;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+static double tridiag_eig(const std::vector<double>& a, const std::vector<double>& b, int which /*1-based*/) {
+  double lo = a[0], hi = a[0];
+  for (size_t i = 0; i < a.size(); ++i) {
+    double r = 0;
+    if (i > 0) r += std::fabs(b[i - 1]);
+    if (i + 1 < a.size()) r += std::fabs(b[i]);
+    lo = std::fmin(lo, a[i] - r);
+    hi = std::fmax(hi, a[i] + r);
+  }
+  const double span = std::fmax(std::fabs(lo), std::fabs(hi));
+  lo -= 1e-12 * span + 1e-300;
+  hi += 1e-12 * span + 1e-300;
+  for (int it = 0; it < 400; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(a, b, mid) >= which) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+static dgchefsi_status check_ctx(const dgchefsi_ctx* ctx) {
+  if (!ctx) return set_error(DGCHEFSI_ERR_ARG, "null context");
+  return DGCHEFSI_OK;
+}
+
+static dgchefsi_status check_block(const dgchefsi_ctx* ctx, const void* X, int64_t Ns, int64_t ld, const char* name) {
+  if (Ns < 0) return set_error(DGCHEFSI_ERR_ARG, "Ns < 0");
+  if (ld < ctx->N) return set_error(DGCHEFSI_ERR_ARG, "ld (%lld) < N (%lld)", (long long)ld, (long long)ctx->N);
+  if (Ns > 0 && !X) return set_error(DGCHEFSI_ERR_ARG, "null %s", name);
+  return DGCHEFSI_OK;
+}
+
+static bool overlaps(const void* a, const void* b, size_t bytes) {
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  return pa < pb + bytes && pb < pa + bytes;
+}
+
+static dgchefsi_status filter_f64(dgchefsi_ctx* ctx, const double* X, double* Y, int64_t Ns, int64_t ld, int m,
+                                  double a, double b, double a0) {
+  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+  const double s1 = e / (a0 - c);
+  double* T = nullptr;
+  if (m >= 2) {
+    DG_TRY(ensure(ctx, ctx->ws_filter, sizeof(double) * (size_t)Ns * (size_t)ld, "filter iterate"));
+    T = static_cast<double*>(ctx->ws_filter.p);
+  }
+  // Ping-pong: Y_odd -> A, Y_even -> B, so Y_m lands in Y. Y_{k+1} overwrites
+  // Y_{k-1} in place (each output entry reads its own prev entry only).
+  double* A = (m % 2 == 1) ? Y : T;
+  double* B = (m % 2 == 1) ? T : Y;
+  const HView h = ctx->view();
+  DG_CUDA(filter_step_f64(h, X, ld, nullptr, A, ld, Ns, s1 / e, c, 0.0, ctx->stream));
+  const double* prev = X;
+  double* cur = A;
+  double sig = s1;
+  for (int k = 1; k < m; ++k) {
+    const double sn = 1.0 / (2.0 / s1 - sig);
+    double* out = (k % 2 == 1) ? B : A;
+    DG_CUDA(filter_step_f64(h, cur, ld, prev, out, ld, Ns, 2.0 * sn / e, c, sig * sn, ctx->stream));
+    prev = cur;
+    cur = out;
+    sig = sn;
+  }
+  return DGCHEFSI_OK;
+}
+
+static dgchefsi_status bounds_impl(dgchefsi_ctx* ctx, const double* v0, int k, double* b_upper, double* theta_min) {
+  const int64_t N = ctx->N;
+  if (k > N) k = (int)N;
+  const size_t nvec = (size_t)k + 1;
+  DG_TRY(ensure(ctx, ctx->ws_lanczos, sizeof(double) * (nvec * (size_t)N + (size_t)N + 72), "Lanczos basis"));
+  double* V = static_cast<double*>(ctx->ws_lanczos.p);
+  double* w = V + nvec * (size_t)N;
+  double* sc = w + N;  // device scalars [72]
+  cudaStream_t s = ctx->stream;
+  double host[72];
+  auto fetch = [&](int n) -> dgchefsi_status {
+    DG_CUDA(cudaMemcpyAsync(host, sc, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaStreamSynchronize(s));
+    return DGCHEFSI_OK;
+  };
+  DG_CUDA(dots_f64(v0, 0, 1, v0, N, sc, s));
+  DG_TRY(fetch(1));
+  const double nrm = std::sqrt(host[0]);
+  if (!(nrm > 0.0) || !std::isfinite(nrm)) return set_error(DGCHEFSI_ERR_ARG, "Lanczos start vector is zero or not finite");
+  DG_CUDA(axpby_f64(1.0 / nrm, v0, 0.0, v0, V, N, s));
+  std::vector<double> al, be;
+  double beta_prev = 0.0, beta_last = 0.0;
+  const HView h = ctx->view();
+  for (int j = 0; j < k; ++j) {
+    double* vj = V + (size_t)j * N;
+    DG_CUDA(spmv_f64(h, vj, w, s));
+    if (j > 0) DG_CUDA(axpby_f64(-beta_prev, vj - N, 1.0, w, w, N, s));
+    DG_CUDA(dots_f64(vj, 0, 1, w, N, sc, s));
+    DG_TRY(fetch(1));
+    const double alpha = host[0];
+    DG_CUDA(axpby_f64(-alpha, vj, 1.0, w, w, N, s));
+    DG_CUDA(dots_f64(V, N, j + 1, w, N, sc, s));
+    DG_CUDA(sub_combination_f64(w, V, N, sc, j + 1, N, s));
+    DG_CUDA(dots_f64(w, 0, 1, w, N, sc + 64, s));
+    DG_CUDA(cudaMemcpyAsync(host, sc + 64, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaStreamSynchronize(s));
+    const double beta = std::sqrt(host[0]);
+    al.push_back(alpha);
+    beta_last = beta;
+    if (!std::isfinite(alpha) || !std::isfinite(beta))
+      return set_error(DGCHEFSI_ERR_NONFINITE, "Lanczos produced a non-finite coefficient");
+    if (j == k - 1 || beta == 0.0) break;
+    be.push_back(beta);
+    DG_CUDA(axpby_f64(1.0 / beta, w, 0.0, w, vj + N, N, s));
+    beta_prev = beta;
+  }
+  const int n = (int)al.size();
+  const double tmax = tridiag_eig(al, be, n);
+  const double tmin = tridiag_eig(al, be, 1);
+  *b_upper = tmax + std::fabs(beta_last);
+  if (theta_min) *theta_min = tmin;
+  return DGCHEFSI_OK;
+}
+
+static dgchefsi_status rr_impl(dgchefsi_ctx* ctx, double* Y, int64_t Ns, int64_t ld, double* ritz) {
+  const int64_t N = ctx->N;
+  cudaStream_t s = ctx->stream;
+  DG_TRY(ensure(ctx, ctx->ws_rr, sizeof(double) * (size_t)Ns * (size_t)N, "Rayleigh-Ritz block"));
+  DG_TRY(ensure(ctx, ctx->ws_small, sizeof(double) * (size_t)Ns * (size_t)Ns, "N_s x N_s matrix"));
+  double* W = static_cast<double*>(ctx->ws_rr.p);
+  double* S = static_cast<double*>(ctx->ws_small.p);
+  const int n = (int)Ns;
+  DG_SOLVER(cusolverDnSetStream(ctx->solver, s));
+  // workspace sizes
+  int lw_potrf = 0, lw_syevd = 0;
+  size_t lw_trtri_d = 0, lw_trtri_h = 0;
+  DG_SOLVER(cusolverDnDpotrf_bufferSize(ctx->solver, CUBLAS_FILL_MODE_UPPER, n, S, n, &lw_potrf));
+  DG_SOLVER(cusolverDnXtrtri_bufferSize(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, Ns, CUDA_R_64F, S,
+                                        Ns, &lw_trtri_d, &lw_trtri_h));
+  DG_SOLVER(cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n, S, n, ritz,
+                                        &lw_syevd));
+  size_t need = sizeof(double) * (size_t)std::max(lw_potrf, lw_syevd);
+  if (lw_trtri_d > need) need = lw_trtri_d;
+  DG_TRY(ensure(ctx, ctx->ws_solver, need, "cuSOLVER workspace"));
+  if (ctx->solver_host.size() < lw_trtri_h) ctx->solver_host.resize(lw_trtri_h);
+  double* work = static_cast<double*>(ctx->ws_solver.p);
+  const int lwork = (int)(ctx->ws_solver.bytes / sizeof(double));
+  DG_CUDA(cudaMemsetAsync(ctx->info_d, 0, 4 * sizeof(int), s));
+  // Step 3: S = Y^T Y (lower tiles, mirrored), S = U^T U.
+  DG_CUDA(gemm_nt_f64(Y, ld, Y, ld, S, Ns, Ns, Ns, N, true, false, s));
+  DG_SOLVER(cusolverDnDpotrf(ctx->solver, CUBLAS_FILL_MODE_UPPER, n, S, n, work, lwork, ctx->info_d));
+  int info[4] = {0, 0, 0, 0};
+  DG_CUDA(cudaMemcpyAsync(info, ctx->info_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  if (info[0] != 0)
+    return set_error(DGCHEFSI_ERR_NOT_SPD, "Cholesky of S = Y^T Y failed at column %d (S not positive definite)", info[0]);
+  // U^{-1} in place. Column-major U^{-1} read row-major is U^{-T} (lower).
+  DG_SOLVER(cusolverDnXtrtri(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, Ns, CUDA_R_64F, S, Ns, work,
+                             ctx->ws_solver.bytes, ctx->solver_host.empty() ? nullptr : ctx->solver_host.data(),
+                             lw_trtri_h, ctx->info_d + 1));
+  // Y_hat^T = U^{-T} Y^T  (W holds Y_hat, state-major, ld N)
+  DG_CUDA(gemm_nn_f64(S, Ns, Y, ld, W, N, Ns, N, Ns, true, s));
+  // Step 4: H Y_hat into Y (Y is free now), H_hat = Y_hat^T (H Y_hat), symmetrised.
+  DG_CUDA(filter_step_f64(ctx->view(), W, N, nullptr, Y, ld, Ns, 1.0, 0.0, 0.0, s));
+  DG_CUDA(gemm_nt_f64(W, N, Y, ld, S, Ns, Ns, Ns, N, false, true, s));
+  DG_SOLVER(cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n, S, n, ritz, work, lwork,
+                             ctx->info_d + 2));
+  // Step 5: X_new^T = Q^T Y_hat^T (column-major Q read row-major is Q^T).
+  DG_CUDA(gemm_nn_f64(S, Ns, W, N, Y, ld, Ns, N, Ns, false, s));
+  DG_CUDA(check_finite_f64(ritz, Ns, ctx->info_d + 3, s));
+  DG_CUDA(cudaMemcpyAsync(info, ctx->info_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  if (info[1] != 0) return set_error(DGCHEFSI_ERR_NOT_SPD, "triangular inverse failed (info %d)", info[1]);
+  if (info[2] != 0) return set_error(DGCHEFSI_ERR_NO_CONVERGENCE, "dense eigensolver failed (info %d)", info[2]);
+  if (info[3] != 0) return set_error(DGCHEFSI_ERR_NONFINITE, "non-finite Ritz value");
+  return DGCHEFSI_OK;
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+extern "C" {
+
+const char* dgchefsi_last_error(void) { return g_err.c_str(); }
+
+int64_t dgchefsi_launch_count(void) { return dg::launch_count(); }
+
+dgchefsi_status dgchefsi_create(int32_t M, const int32_t* nb, const int64_t* row_ptr, const int32_t* col,
+                                const int64_t* blk_off, const double* values, int64_t n_values, void* stream,
+                                dgchefsi_ctx** out) {
+  clear_error();
+  if (!out) return set_error(DGCHEFSI_ERR_ARG, "null output pointer");
+  *out = nullptr;
+  if (M < 1 || !nb || !row_ptr || !col || !blk_off || !values || n_values < 1)
+    return set_error(DGCHEFSI_ERR_ARG, "need M >= 1 and non-null host arrays");
+  dgchefsi_ctx* ctx = nullptr;
+  try {
+    ctx = new dgchefsi_ctx();
+  } catch (const std::bad_alloc&) {
+    return set_error(DGCHEFSI_ERR_OOM, "host allocation failed");
+  }
+  auto bail = [&](dgchefsi_status st) {
+    dgchefsi_destroy(ctx);
+    return st;
+  };
+  try {
+    ctx->M = M;
+    ctx->nb_h.assign(nb, nb + M);
+    ctx->off_h.assign(M + 1, 0);
+    for (int K = 0; K < M; ++K) {
+      if (nb[K] < 1 || nb[K] > 256) return bail(set_error(DGCHEFSI_ERR_ARG, "nb[%d] = %d outside 1..256", K, nb[K]));
+      ctx->off_h[K + 1] = ctx->off_h[K] + nb[K];
+      ctx->max_nb = std::max(ctx->max_nb, nb[K]);
+    }
+    ctx->N = ctx->off_h[M];
+    if (row_ptr[0] != 0) return bail(set_error(DGCHEFSI_ERR_ARG, "row_ptr[0] != 0"));
+    for (int K = 0; K < M; ++K)
+      if (row_ptr[K + 1] < row_ptr[K]) return bail(set_error(DGCHEFSI_ERR_ARG, "row_ptr decreases at %d", K));
+    const int64_t nnzb = row_ptr[M];
+    ctx->nnzb = nnzb;
+    ctx->n_values = n_values;
+    ctx->row_ptr_h.assign(row_ptr, row_ptr + M + 1);
+    ctx->col_h.assign(col, col + nnzb);
+    ctx->blk_off_h.assign(blk_off, blk_off + nnzb);
+    for (int K = 0; K < M; ++K) {
+      bool diag = false;
+      for (int64_t e = row_ptr[K]; e < row_ptr[K + 1]; ++e) {
+        const int Kp = col[e];
+        if (Kp < 0 || Kp >= M) return bail(set_error(DGCHEFSI_ERR_ARG, "col[%lld] = %d out of range", (long long)e, Kp));
+        if (e > row_ptr[K] && col[e - 1] >= Kp)
+          return bail(set_error(DGCHEFSI_ERR_ARG, "columns of row %d not strictly ascending", K));
+        if (Kp == K) diag = true;
+        const int64_t sz = (int64_t)nb[K] * nb[Kp];
+        if (blk_off[e] < 0 || blk_off[e] + sz > n_values)
+          return bail(set_error(DGCHEFSI_ERR_ARG, "block %lld lies outside values", (long long)e));
+      }
+      if (!diag) return bail(set_error(DGCHEFSI_ERR_ARG, "row %d has no diagonal block", K));
+    }
+    for (int64_t i = 0; i < n_values; ++i)
+      if (!std::isfinite(values[i])) return bail(set_error(DGCHEFSI_ERR_ARG, "values[%lld] not finite", (long long)i));
+    // symmetry: pattern and H_{K';K} == H_{K;K'}^T exactly
+    for (int K = 0; K < M; ++K) {
+      for (int64_t e = row_ptr[K]; e < row_ptr[K + 1]; ++e) {
+        const int Kp = col[e];
+        int64_t lo = row_ptr[Kp], hi = row_ptr[Kp + 1] - 1, f = -1;
+        while (lo <= hi) {
+          const int64_t mid = (lo + hi) / 2;
+          if (col[mid] == K) { f = mid; break; }
+          if (col[mid] < K) lo = mid + 1; else hi = mid - 1;
+        }
+        if (f < 0) return bail(set_error(DGCHEFSI_ERR_ARG, "pattern not symmetric: (%d,%d) without (%d,%d)", K, Kp, Kp, K));
+        const double* A = values + blk_off[e];
+        const double* B = values + blk_off[f];
+        const int nK = nb[K], nKp = nb[Kp];
+        for (int i = 0; i < nK; ++i)
+          for (int j = 0; j < nKp; ++j)
+            if (A[(int64_t)i * nKp + j] != B[(int64_t)j * nK + i])
+              return bail(set_error(DGCHEFSI_ERR_ARG, "H not symmetric in block (%d,%d) at (%d,%d)", K, Kp, i, j));
+      }
+    }
+    ctx->poff_h.assign(M + 1, 0);
+    for (int K = 0; K < M; ++K) ctx->poff_h[K + 1] = ctx->poff_h[K] + (int64_t)nb[K] * nb[K];
+  } catch (const std::bad_alloc&) {
+    return bail(set_error(DGCHEFSI_ERR_OOM, "host allocation failed"));
+  }
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(set_error(DGCHEFSI_ERR_CUDA, "no CUDA device"));
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  auto dmalloc = [&](void** p, size_t bytes) -> dgchefsi_status {
+    if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(DGCHEFSI_ERR_OOM, "cudaMalloc of %zu bytes for H failed", bytes);
+    }
+    return DGCHEFSI_OK;
+  };
+  dgchefsi_status st;
+  if ((st = dmalloc((void**)&ctx->nb_d, sizeof(int32_t) * M)) ||
+      (st = dmalloc((void**)&ctx->off_d, sizeof(int64_t) * (M + 1))) ||
+      (st = dmalloc((void**)&ctx->row_ptr_d, sizeof(int64_t) * (M + 1))) ||
+      (st = dmalloc((void**)&ctx->col_d, sizeof(int32_t) * ctx->nnzb)) ||
+      (st = dmalloc((void**)&ctx->blk_off_d, sizeof(int64_t) * ctx->nnzb)) ||
+      (st = dmalloc((void**)&ctx->vals_d, sizeof(double) * n_values)) ||
+      (st = dmalloc((void**)&ctx->poff_d, sizeof(int64_t) * (M + 1))) ||
+      (st = dmalloc((void**)&ctx->info_d, sizeof(int) * 4)))
+    return bail(st);
+  auto h2d = [&](void* d, const void* h, size_t bytes) { return cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice); };
+  if (h2d(ctx->nb_d, nb, sizeof(int32_t) * M) || h2d(ctx->off_d, ctx->off_h.data(), sizeof(int64_t) * (M + 1)) ||
+      h2d(ctx->row_ptr_d, row_ptr, sizeof(int64_t) * (M + 1)) || h2d(ctx->col_d, col, sizeof(int32_t) * ctx->nnzb) ||
+      h2d(ctx->blk_off_d, blk_off, sizeof(int64_t) * ctx->nnzb) ||
+      h2d(ctx->vals_d, values, sizeof(double) * n_values) ||
+      h2d(ctx->poff_d, ctx->poff_h.data(), sizeof(int64_t) * (M + 1)))
+    return bail(set_error(DGCHEFSI_ERR_CUDA, "copy of H to the device failed"));
+  if (cusolverDnCreate(&ctx->solver) != CUSOLVER_STATUS_SUCCESS)
+    return bail(set_error(DGCHEFSI_ERR_CUDA, "cusolverDnCreate failed"));
+  *out = ctx;
+  return DGCHEFSI_OK;
+}
+
+void dgchefsi_destroy(dgchefsi_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream || ctx->vals_d) cudaStreamSynchronize(ctx->stream);
+  tc_destroy(ctx);
+  if (ctx->solver) cusolverDnDestroy(ctx->solver);
+  cudaFree(ctx->nb_d);
+  cudaFree(ctx->off_d);
+  cudaFree(ctx->row_ptr_d);
+  cudaFree(ctx->col_d);
+  cudaFree(ctx->blk_off_d);
+  cudaFree(ctx->vals_d);
+  cudaFree(ctx->poff_d);
+  cudaFree(ctx->info_d);
+  free_buf(ctx->ws_filter);
+  free_buf(ctx->ws_rr);
+  free_buf(ctx->ws_small);
+  free_buf(ctx->ws_solver);
+  free_buf(ctx->ws_cycle);
+  free_buf(ctx->ws_lanczos);
+  delete ctx;
+}
+
+dgchefsi_status dgchefsi_set_stream(dgchefsi_ctx* ctx, void* stream) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status dgchefsi_dims(const dgchefsi_ctx* ctx, int64_t* N, int32_t* M) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  if (N) *N = ctx->N;
+  if (M) *M = ctx->M;
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status dgchefsi_matvec(dgchefsi_ctx* ctx, const double* X, double* Y, int64_t Ns, int64_t ld) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  DG_TRY(check_block(ctx, X, Ns, ld, "X"));
+  DG_TRY(check_block(ctx, Y, Ns, ld, "Y"));
+  if (Ns == 0) return DGCHEFSI_OK;
+  if (overlaps(X, Y, sizeof(double) * (size_t)Ns * ld)) return set_error(DGCHEFSI_ERR_ARG, "X and Y overlap");
+  DG_CUDA(filter_step_f64(ctx->view(), X, ld, nullptr, Y, ld, Ns, 1.0, 0.0, 0.0, ctx->stream));
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status dgchefsi_bounds(dgchefsi_ctx* ctx, const double* v0, int k, double* b_upper, double* theta_min) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  if (!v0 || !b_upper) return set_error(DGCHEFSI_ERR_ARG, "null v0 or b_upper");
+  if (k < 1 || k > 64) return set_error(DGCHEFSI_ERR_ARG, "k = %d outside 1..64", k);
+  return bounds_impl(ctx, v0, k, b_upper, theta_min);
+}
+
+static dgchefsi_status check_filter_args(dgchefsi_ctx* ctx, int prec, const double* X, double* Y, int64_t Ns,
+                                         int64_t ld, int m, double a, double b, double a0) {
+  DG_TRY(check_ctx(ctx));
+  DG_TRY(check_block(ctx, X, Ns, ld, "X"));
+  DG_TRY(check_block(ctx, Y, Ns, ld, "Y"));
+  if (prec < DGCHEFSI_F64 || prec > DGCHEFSI_BF16X3) return set_error(DGCHEFSI_ERR_ARG, "unknown precision %d", prec);
+  if (m < 1) return set_error(DGCHEFSI_ERR_ARG, "filter degree m = %d < 1", m);
+  if (!(std::isfinite(a) && std::isfinite(b) && std::isfinite(a0)) || !(a0 < a && a < b))
+    return set_error(DGCHEFSI_ERR_ARG, "need a0 < a < b (got a0=%g a=%g b=%g)", a0, a, b);
+  if (Ns > 0 && overlaps(X, Y, sizeof(double) * (size_t)Ns * ld)) return set_error(DGCHEFSI_ERR_ARG, "X and Y overlap");
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status dgchefsi_filter(dgchefsi_ctx* ctx, int prec, const double* X, double* Y, int64_t Ns, int64_t ld,
+                                int m, double a, double b, double a0) {
+  clear_error();
+  DG_TRY(check_filter_args(ctx, prec, X, Y, Ns, ld, m, a, b, a0));
+  if (Ns == 0) return DGCHEFSI_OK;
+  if (prec == DGCHEFSI_F64) return filter_f64(ctx, X, Y, Ns, ld, m, a, b, a0);
+  return filter_tc(ctx, prec, X, Y, Ns, ld, m, a, b, a0);
+}
+
+dgchefsi_status dgchefsi_rayleigh_ritz(dgchefsi_ctx* ctx, double* Y, int64_t Ns, int64_t ld, double* ritz) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  DG_TRY(check_block(ctx, Y, Ns, ld, "Y"));
+  if (Ns > 0 && !ritz) return set_error(DGCHEFSI_ERR_ARG, "null ritz");
+  if (Ns > ctx->N) return set_error(DGCHEFSI_ERR_ARG, "Ns (%lld) > N (%lld)", (long long)Ns, (long long)ctx->N);
+  if (Ns > 2147483647LL) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "Ns too large for the dense eigensolver");
+  if (Ns == 0) return DGCHEFSI_OK;
+  return rr_impl(ctx, Y, Ns, ld, ritz);
+}
+
+dgchefsi_status dgchefsi_occupations(dgchefsi_ctx* ctx, const double* ritz, int64_t Ns, double Ne, double kT,
+                                     double* f, double* mu) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  if (Ns < 1 || !ritz || !f || !mu) return set_error(DGCHEFSI_ERR_ARG, "need Ns >= 1 and non-null ritz, f, mu");
+  if (!(kT > 0.0) || !std::isfinite(kT)) return set_error(DGCHEFSI_ERR_ARG, "kT must be > 0");
+  if (!(Ne >= 0.0) || Ne > 2.0 * (double)Ns)
+    return set_error(DGCHEFSI_ERR_ARG, "need 0 <= Ne <= 2 Ns (Ne = %g, Ns = %lld)", Ne, (long long)Ns);
+  DG_CUDA(occupations_f64(ritz, Ns, Ne, kT, f, mu, ctx->stream));
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status dgchefsi_density_blocks(dgchefsi_ctx* ctx, const double* X, int64_t Ns, int64_t ld, const double* f,
+                                        double* P) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  DG_TRY(check_block(ctx, X, Ns, ld, "X"));
+  if (!P || (Ns > 0 && !f)) return set_error(DGCHEFSI_ERR_ARG, "null f or P");
+  DG_CUDA(density_f64(ctx->view(), ctx->poff_d, X, Ns, ld, f, P, ctx->stream));
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status dgchefsi_cycle(dgchefsi_ctx* ctx, int prec, double* X, int64_t Ns, int64_t ld, int m, double Ne,
+                               double kT, const double* v0, int k_lanczos, const double* prev_ritz, double* bounds,
+                               int use_bounds, double* ritz, double* f, double* mu, double* P) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  DG_TRY(check_block(ctx, X, Ns, ld, "X"));
+  if (Ns < 1 || !ritz || !f || !mu || !P) return set_error(DGCHEFSI_ERR_ARG, "need Ns >= 1 and non-null outputs");
+  if (Ns > ctx->N) return set_error(DGCHEFSI_ERR_ARG, "Ns > N");
+  if (!(kT > 0.0) || !(Ne >= 0.0) || Ne > 2.0 * (double)Ns)
+    return set_error(DGCHEFSI_ERR_ARG, "need kT > 0 and 0 <= Ne <= 2 Ns");
+  double a, b, a0;
+  if (use_bounds) {
+    if (!bounds) return set_error(DGCHEFSI_ERR_ARG, "use_bounds without bounds");
+    a = bounds[0];
+    b = bounds[1];
+    a0 = bounds[2];
+  } else {
+    if (!v0) return set_error(DGCHEFSI_ERR_ARG, "null Lanczos start vector");
+    if (k_lanczos < 1 || k_lanczos > 64) return set_error(DGCHEFSI_ERR_ARG, "k_lanczos outside 1..64");
+    double tmin = 0.0;
+    DG_TRY(bounds_impl(ctx, v0, k_lanczos, &b, &tmin));
+    if (prev_ritz) {
+      a = -std::numeric_limits<double>::infinity();
+      a0 = std::numeric_limits<double>::infinity();
+      for (int64_t i = 0; i < Ns; ++i) {
+        a = std::fmax(a, prev_ritz[i]);
+        a0 = std::fmin(a0, prev_ritz[i]);
+      }
+    } else {
+      a0 = tmin;
+      a = a0 + (b - a0) * (double)Ns / (double)ctx->N;
+    }
+  }
+  DG_TRY(check_filter_args(ctx, prec, X, X + 0, 0, ld, m, a, b, a0));
+  DG_TRY(ensure(ctx, ctx->ws_cycle, sizeof(double) * (size_t)Ns * (size_t)ld, "filtered block"));
+  double* Yw = static_cast<double*>(ctx->ws_cycle.p);
+  if (prec == DGCHEFSI_F64)
+    DG_TRY(filter_f64(ctx, X, Yw, Ns, ld, m, a, b, a0));
+  else
+    DG_TRY(filter_tc(ctx, prec, X, Yw, Ns, ld, m, a, b, a0));
+  DG_TRY(rr_impl(ctx, Yw, Ns, ld, ritz));
+  DG_CUDA(cudaMemcpy2DAsync(X, sizeof(double) * ld, Yw, sizeof(double) * ld, sizeof(double) * ctx->N, Ns,
+                            cudaMemcpyDeviceToDevice, ctx->stream));
+  DG_CUDA(occupations_f64(ritz, Ns, Ne, kT, f, mu, ctx->stream));
+  DG_CUDA(density_f64(ctx->view(), ctx->poff_d, X, Ns, ld, f, P, ctx->stream));
+  if (bounds) {
+    bounds[0] = a;
+    bounds[1] = b;
+    bounds[2] = a0;
+  }
+  DG_CUDA(cudaStreamSynchronize(ctx->stream));
+  return DGCHEFSI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// Library context and host-side helpers shared by the API translation units.
+#pragma once
+#include <cusolverDn.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dgchefsi.h"
+#include "internal.h"
+
+namespace dg {
+
+// Grow-only device buffer owned by a context.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct TcState;  // tensor-core filter state (tc_filter.cu)
+
+}  // namespace dg
+
+struct dgchefsi_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int32_t M = 0;
+  int64_t N = 0;
+  int32_t max_nb = 0;
+  int64_t nnzb = 0;
+  int64_t n_values = 0;
+  std::vector<int32_t> nb_h;
+  std::vector<int64_t> off_h, row_ptr_h, blk_off_h, poff_h;
+  std::vector<int32_t> col_h;
+  // device copy of H
+  int32_t* nb_d = nullptr;
+  int64_t* off_d = nullptr;
+  int64_t* row_ptr_d = nullptr;
+  int32_t* col_d = nullptr;
+  int64_t* blk_off_d = nullptr;
+  double* vals_d = nullptr;
+  int64_t* poff_d = nullptr;  // packed density-block offsets
+  // workspace
+  dg::DevBuf ws_filter;   // filter ping-pong partner (Ns x ld FP64)
+  dg::DevBuf ws_rr;       // Rayleigh-Ritz block (Ns x N FP64)
+  dg::DevBuf ws_small;    // Ns x Ns FP64
+  dg::DevBuf ws_solver;   // cuSOLVER device workspace
+  dg::DevBuf ws_cycle;    // filtered block inside dgchefsi_cycle
+  dg::DevBuf ws_lanczos;  // Lanczos basis and scalars
+  std::vector<char> solver_host;
+  int* info_d = nullptr;  // [4] cuSOLVER infos + finite flag
+  cusolverDnHandle_t solver = nullptr;
+  dg::TcState* tc = nullptr;
+
+  dg::HView view() const {
+    dg::HView h;
+    h.M = M;
+    h.N = N;
+    h.nb = nb_d;
+    h.off = off_d;
+    h.row_ptr = row_ptr_d;
+    h.col = col_d;
+    h.blk_off = blk_off_d;
+    h.vals = vals_d;
+    h.max_nb = max_nb;
+    return h;
+  }
+};
+
+namespace dg {
+
+// Thread-local last error message; returns `st`.
+dgchefsi_status set_error(dgchefsi_status st, const char* fmt, ...);
+void clear_error();
+// Make `b` hold at least `bytes` (synchronises the context's stream before a regrow).
+dgchefsi_status ensure(dgchefsi_ctx* ctx, DevBuf& b, size_t bytes, const char* what);
+
+// Tensor-core filter (tc_filter.cu). X, Y FP64 (Ns x ld) state-major.
+dgchefsi_status filter_tc(dgchefsi_ctx* ctx, int prec, const double* X, double* Y, int64_t Ns, int64_t ld, int m,
+                          double a, double b, double a0);
+void tc_destroy(dgchefsi_ctx* ctx);
+
+}  // namespace dg
+
+#define DG_CUDA(call)                                                                               \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess)                                                                          \
+      return dg::set_error(DGCHEFSI_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                           __FILE__, __LINE__);                                                     \
+  } while (0)
+
+#define DG_TRY(call)                          \
+  do {                                        \
+    dgchefsi_status st_ = (call);             \
+    if (st_ != DGCHEFSI_OK) return st_;       \
+  } while (0)

@@ -1,0 +1,230 @@
+"""Thin ctypes binding of libdgchefsi.so (C ABI in include/dgchefsi.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels (and
+its cuSOLVER calls for the dense N_s x N_s factorisations). Torch tensors are
+used for device memory and the current CUDA stream. There is no CPU fallback:
+if the library is missing, importing this module raises.
+
+Layout: a block of N_s vectors is a float64 CUDA tensor of shape (N_s, N) (or a
+row-strided view of a wider (N_s, ld) tensor), row i = state i. This is the
+paper's N x N_s block X transposed.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libdgchefsi.so")
+
+PRECISIONS = {"f64": 0, "tf32": 1, "bf16": 2, "bf16x3": 3}
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_SPD", 5: "ERR_NONFINITE",
+          6: "ERR_NO_CONVERGENCE", 7: "ERR_TIMEOUT", 8: "ERR_UNSUPPORTED"}
+
+EXPORTS = ["dgchefsi_create", "dgchefsi_destroy", "dgchefsi_set_stream", "dgchefsi_dims", "dgchefsi_matvec",
+           "dgchefsi_bounds", "dgchefsi_filter", "dgchefsi_rayleigh_ritz", "dgchefsi_occupations",
+           "dgchefsi_density_blocks", "dgchefsi_cycle", "dgchefsi_last_error", "dgchefsi_launch_count"]
+
+
+class DGChefsiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = STATUS.get(status, str(status))
+
+
+def load_library(path: str = _LIBPATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    st = C.c_int
+    sig = {
+        "dgchefsi_create": (st, [I32, P, P, P, P, P, I64, P, C.POINTER(C.c_void_p)]),
+        "dgchefsi_destroy": (None, [P]),
+        "dgchefsi_set_stream": (st, [P, P]),
+        "dgchefsi_dims": (st, [P, P, P]),
+        "dgchefsi_matvec": (st, [P, P, P, I64, I64]),
+        "dgchefsi_bounds": (st, [P, P, C.c_int, P, P]),
+        "dgchefsi_filter": (st, [P, C.c_int, P, P, I64, I64, C.c_int, D, D, D]),
+        "dgchefsi_rayleigh_ritz": (st, [P, P, I64, I64, P]),
+        "dgchefsi_occupations": (st, [P, P, I64, D, D, P, P]),
+        "dgchefsi_density_blocks": (st, [P, P, I64, I64, P, P]),
+        "dgchefsi_cycle": (st, [P, C.c_int, P, I64, I64, C.c_int, D, D, P, C.c_int, P, P, C.c_int, P, P, P, P]),
+        "dgchefsi_last_error": (C.c_char_p, []),
+        "dgchefsi_launch_count": (I64, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+def last_error() -> str:
+    return _lib.dgchefsi_last_error().decode()
+
+
+def launch_count() -> int:
+    return int(_lib.dgchefsi_launch_count())
+
+
+def _check(status: int):
+    if status != 0:
+        raise DGChefsiError(status, last_error())
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+def _block(X: torch.Tensor, N: int, name: str):
+    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float64 and X.dim() == 2):
+        raise TypeError(f"{name} must be a 2-D float64 CUDA tensor (N_s, N)")
+    if X.shape[1] != N or (X.shape[0] > 1 and X.stride(1) != 1) or (X.shape[0] > 0 and X.stride(1) != 1):
+        raise ValueError(f"{name} must have shape (N_s, {N}) with unit column stride")
+    ld = X.stride(0) if X.shape[0] > 1 else N
+    return X.shape[0], max(ld, N)
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Context:
+    """A device copy of the block-sparse H and the library's workspace.
+
+    ``H`` is any object with the block-CSR fields nb, row_ptr, col, blk_off and
+    values (see paper_1606_03416_gb300.inputs.BlockSparse)."""
+
+    def __init__(self, H):
+        nb = np.ascontiguousarray(H.nb, dtype=np.int32)
+        row_ptr = np.ascontiguousarray(H.row_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(H.col, dtype=np.int32)
+        blk_off = np.ascontiguousarray(H.blk_off, dtype=np.int64)
+        values = np.ascontiguousarray(H.values, dtype=np.float64)
+        h = C.c_void_p()
+        _check(_lib.dgchefsi_create(int(nb.shape[0]), nb.ctypes.data, row_ptr.ctypes.data, col.ctypes.data,
+                                    blk_off.ctypes.data, values.ctypes.data, int(values.shape[0]), _stream(),
+                                    C.byref(h)))
+        self._h = h
+        N, M = C.c_int64(), C.c_int32()
+        _check(_lib.dgchefsi_dims(h, C.byref(N), C.byref(M)))
+        self.N, self.M = int(N.value), int(M.value)
+        self.nb = nb
+        self.density_offsets = np.concatenate([[0], np.cumsum(nb.astype(np.int64) ** 2)])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.dgchefsi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _sync_stream(self):
+        _check(_lib.dgchefsi_set_stream(self._h, _stream()))
+
+    # -- Eq. matvec_3
+    def matvec(self, X: torch.Tensor, Y: torch.Tensor | None = None) -> torch.Tensor:
+        Ns, ld = _block(X, self.N, "X")
+        if Y is None:
+            Y = torch.empty_like(X)
+        Ns2, ld2 = _block(Y, self.N, "Y")
+        if (Ns2, ld2) != (Ns, ld):
+            raise ValueError("X and Y need the same shape and stride")
+        self._sync_stream()
+        _check(_lib.dgchefsi_matvec(self._h, _ptr(X), _ptr(Y), Ns, ld))
+        return Y
+
+    # -- Alg. 1 step 1
+    def bounds(self, v0: torch.Tensor, k: int = 10):
+        if not (v0.is_cuda and v0.dtype == torch.float64 and v0.numel() == self.N and v0.is_contiguous()):
+            raise ValueError("v0 must be a contiguous float64 CUDA vector of length N")
+        b, t = C.c_double(), C.c_double()
+        self._sync_stream()
+        _check(_lib.dgchefsi_bounds(self._h, _ptr(v0), int(k), C.byref(b), C.byref(t)))
+        return b.value, t.value
+
+    # -- Alg. 1 step 2
+    def filter(self, X: torch.Tensor, m: int, a: float, b: float, a0: float, prec: str = "f64",
+               Y: torch.Tensor | None = None) -> torch.Tensor:
+        Ns, ld = _block(X, self.N, "X")
+        if Y is None:
+            Y = torch.empty_like(X)
+        Ns2, ld2 = _block(Y, self.N, "Y")
+        if (Ns2, ld2) != (Ns, ld):
+            raise ValueError("X and Y need the same shape and stride")
+        self._sync_stream()
+        _check(_lib.dgchefsi_filter(self._h, PRECISIONS[prec], _ptr(X), _ptr(Y), Ns, ld, int(m), float(a),
+                                    float(b), float(a0)))
+        return Y
+
+    # -- Alg. 1 steps 3-5 (in place: Y becomes X_new)
+    def rayleigh_ritz(self, Y: torch.Tensor, ritz: torch.Tensor | None = None) -> torch.Tensor:
+        Ns, ld = _block(Y, self.N, "Y")
+        if ritz is None:
+            ritz = torch.empty(Ns, dtype=torch.float64, device=Y.device)
+        self._sync_stream()
+        _check(_lib.dgchefsi_rayleigh_ritz(self._h, _ptr(Y), Ns, ld, _ptr(ritz)))
+        return ritz
+
+    def occupations(self, ritz: torch.Tensor, Ne: float, kT: float):
+        f = torch.empty_like(ritz)
+        mu = torch.empty(1, dtype=torch.float64, device=ritz.device)
+        self._sync_stream()
+        _check(_lib.dgchefsi_occupations(self._h, _ptr(ritz), ritz.numel(), float(Ne), float(kT), _ptr(f), _ptr(mu)))
+        return f, mu
+
+    def density_blocks(self, X: torch.Tensor, f: torch.Tensor, P: torch.Tensor | None = None) -> torch.Tensor:
+        Ns, ld = _block(X, self.N, "X")
+        if P is None:
+            P = torch.empty(int(self.density_offsets[-1]), dtype=torch.float64, device=X.device)
+        self._sync_stream()
+        _check(_lib.dgchefsi_density_blocks(self._h, _ptr(X), Ns, ld, _ptr(f), _ptr(P)))
+        return P
+
+    def unpack_density(self, P: torch.Tensor):
+        o = self.density_offsets
+        return [P[o[K]:o[K + 1]].view(int(self.nb[K]), int(self.nb[K])) for K in range(self.M)]
+
+    # -- one full cycle (Alg. 1 + occupations + density), X updated in place
+    def cycle(self, X: torch.Tensor, m: int, Ne: float, kT: float, v0: torch.Tensor | None = None,
+              prev_ritz=None, bounds=None, prec: str = "f64", k_lanczos: int = 10, out=None):
+        Ns, ld = _block(X, self.N, "X")
+        dev = X.device
+        if out is None:
+            out = dict(ritz=torch.empty(Ns, dtype=torch.float64, device=dev),
+                       f=torch.empty(Ns, dtype=torch.float64, device=dev),
+                       mu=torch.empty(1, dtype=torch.float64, device=dev),
+                       P=torch.empty(int(self.density_offsets[-1]), dtype=torch.float64, device=dev))
+        bnd = (C.c_double * 3)(*(bounds if bounds is not None else (0.0, 0.0, 0.0)))
+        prev = None
+        if prev_ritz is not None:
+            prev = np.ascontiguousarray(np.asarray(prev_ritz, dtype=np.float64))
+        self._sync_stream()
+        _check(_lib.dgchefsi_cycle(self._h, PRECISIONS[prec], _ptr(X), Ns, ld, int(m), float(Ne), float(kT),
+                                   _ptr(v0) if v0 is not None else None, int(k_lanczos),
+                                   prev.ctypes.data if prev is not None else None, bnd,
+                                   1 if bounds is not None else 0, _ptr(out["ritz"]), _ptr(out["f"]),
+                                   _ptr(out["mu"]), _ptr(out["P"])))
+        out["bounds"] = (bnd[0], bnd[1], bnd[2])
+        return out
+
+
+def create(H) -> Context:
+    return Context(H)

@@ -1,0 +1,371 @@
+"""Benchmark of one CheFSI cycle on the bulk-3D-like 8x8x8 workload.
+
+Workload (paper Sec. IV stand-in, synthetic, seed 0): 8x8x8 periodic elements,
+27-neighbour block stencil, n_b = 64 (N = 32768), N_s = 4096 states, filter
+degree m = 20. One step = one pass of the whole hot path through the public
+C ABI: Lanczos bounds -> Chebyshev filter -> Cholesky-QR + Rayleigh-Ritz +
+rotation (FP64) -> Fermi occupations -> density blocks.
+
+Metric: Chebyshev-filter TFLOP/s (algorithmic 2 * nnz(H) * N_s * m flops over
+the filter's device time) plus seconds per CheFSI cycle, for the mixed-precision
+filter and for the plain FP64 path. Inputs (X is 1.07 GB FP64, H 0.45 GB) are
+larger than L2, so no flush is needed between steps.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x3]
+        python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "bulk3d_8x8x8"
+METRIC = "CheFSI filter TFLOP/s + s per CheFSI cycle, mixed vs FP64 at Ritz err<=1e-8"
+
+
+def filter_flops(H, Ns: int, m: int) -> float:
+    """2 * (sum of block sizes of H) * N_s per mat-vec, m mat-vecs (the -cI shift
+    and recurrence update are O(N N_s) and not counted)."""
+    nnz = int(H.values.shape[0])
+    return 2.0 * nnz * Ns * m
+
+
+def filter_bytes_per_step(H, Ns: int, prec: str) -> float:
+    """Algorithmic HBM bytes of one tensor-core filter step: read the operand copy
+    of Y_k and the FP32 master of Y_{k-1}, write the FP32 master of Y_{k+1} and
+    its operand copies, read the operand copy of H once."""
+    N = H.N
+    nnz = int(H.values.shape[0])
+    if prec == "tf32":
+        return 4.0 * N * Ns * 3 + 4.0 * nnz
+    if prec == "bf16":
+        return 2.0 * N * Ns + 4.0 * N * Ns * 2 + 2.0 * N * Ns + 2.0 * nnz
+    if prec == "bf16x3":
+        return 2.0 * 2 * N * Ns + 4.0 * N * Ns * 2 + 2.0 * 2 * N * Ns + 2.0 * 2 * nnz
+    return 8.0 * N * Ns * 3 + 8.0 * nnz
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    def __init__(self, index):
+        self.index = index  # nvidia-smi --id value (the device UUID)
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def oracle_sample(Ns_sample: int, m: int, reps: int = 1):
+    """Time the FP64 oracle's filter on the first Ns_sample states (run in a
+    child process pinned to one BLAS thread so the core count is exact)."""
+    code = (
+        "import os,sys,time,json\n"
+        f"sys.path.insert(0,{ROOT!r})\n"
+        "import numpy as np\n"
+        "from oracle import chefsi as O\n"
+        "from paper_1606_03416_gb300 import inputs as G\n"
+        f"cfg=G.CONFIGS[{WORKLOAD!r}]\n"
+        "H=G.make_blocks(cfg); Ho=O.DGHamiltonian.from_blocksparse(H)\n"
+        f"X=G.make_X(H.N,cfg.Ns,cfg.seed)[:{Ns_sample}].T.copy()\n"
+        "lam_lo,lam_hi=-1.5,42.0\n"
+        "a=lam_lo+(lam_hi-lam_lo)*cfg.Ns/H.N\n"
+        "ts=[]\n"
+        f"for _ in range({reps}):\n"
+        "    t=time.perf_counter()\n"
+        f"    O.chebyshev_filter(Ho,X,{m},a,lam_hi,lam_lo)\n"
+        "    ts.append(time.perf_counter()-t)\n"
+        "print(json.dumps({'t':ts,'nnz':int(H.values.shape[0])}))\n")
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    return r["t"], r["nnz"]
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1606_03416_gb300 import inputs as G
+    cfg = G.CONFIGS[WORKLOAD]
+    sample = args.ref_states
+    ts, nnz = oracle_sample(sample, cfg.m, reps=args.warmup + args.steps)
+    timed = ts[args.warmup:] if len(ts) > args.warmup else ts
+    flops = 2.0 * nnz * sample * cfg.m
+    v = flops / statistics.mean(timed) / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(timed),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generator, no dataset)",
+            "config": {"workload": WORKLOAD, "N": 32768, "Ns": cfg.Ns, "m": cfg.m, "l2": "inputs larger than L2",
+                       "sample": f"filter of the first {sample} of {cfg.Ns} states"},
+            "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                             "sample": f"FP64 NumPy oracle filter (m={cfg.m}) on {sample} of {cfg.Ns} states, "
+                                       "one BLAS thread"},
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--prec", default="bf16x3", choices=["tf32", "bf16", "bf16x3", "f64"])
+    ap.add_argument("--f64-steps", type=int, default=1, help="FP64 cycles timed for the per-cycle comparison")
+    ap.add_argument("--ref-states", type=int, default=64, help="states in the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_1606_03416_gb300 import dgchefsi as D
+    from paper_1606_03416_gb300 import inputs as G
+
+    cfg = G.CONFIGS[args.workload]
+    H, X0, v0, Ns, Ne = G.make_problem(cfg)
+    N, m, kT = H.N, cfg.m, cfg.kT
+    ctx = D.Context(H)
+    Xd = torch.from_numpy(X0).to(dev)
+    Yd = torch.empty_like(Xd)
+    vd = torch.from_numpy(v0).to(dev)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    state = {"prev": None}
+
+    def cycle(prec, X, Y, timers=None):
+        """One CheFSI cycle via the public API; returns (ritz, new X buffer, spare buffer)."""
+        b, tmin = ctx.bounds(vd, 10)
+        prev = state["prev"]
+        if prev is None:
+            a0 = tmin
+            a = a0 + (b - a0) * Ns / N
+        else:
+            a, a0 = float(prev.max()), float(prev.min())
+        if timers is not None:
+            timers[0].record(stream)
+        ctx.filter(X, m, a, b, a0, prec=prec, Y=Y)
+        if timers is not None:
+            timers[1].record(stream)
+        ritz = ctx.rayleigh_ritz(Y)
+        f, mu = ctx.occupations(ritz, Ne, kT)
+        ctx.density_blocks(Y, f)
+        state["prev"] = ritz.cpu().numpy()
+        return ritz, Y, X
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- warm-up
+    X, Y = Xd, Yd
+    for _ in range(args.warmup):
+        _, X, Y = cycle(args.prec, X, Y)
+    # ---- timed mixed-precision cycles
+    n0 = D.launch_count()
+    fl_t = [(ev(), ev()) for _ in range(args.steps)]
+    t0, t1 = ev(), ev()
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    gid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else (str(uuid) if uuid else "0")
+    with ClockSampler(gid) as clk:
+        barrier()
+        t0.record(stream)
+        for i in range(args.steps):
+            _, X, Y = cycle(args.prec, X, Y, fl_t[i])
+        t1.record(stream)
+        barrier()
+    launches = D.launch_count() - n0
+    ms_step = t0.elapsed_time(t1) / args.steps
+    ms_filter = statistics.mean(a.elapsed_time(b) for a, b in fl_t)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step, ms_filter], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step, ms_filter = float(t[0]), float(t[1])
+    fl = filter_flops(H, Ns, m)
+    value = world * fl / (ms_filter * 1e-3) / 1e12
+
+    # ---- per-launch time of the filter step kernel: T(m) - T(1) over m-1 launches
+    Xs = Xd.clone()
+    def time_filter(mm, reps=3):
+        s, e = ev(), ev()
+        best = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            s.record(stream)
+            ctx.filter(Xs, mm, 10.0, 45.0, -2.0, prec=args.prec, Y=Yd)
+            e.record(stream)
+            torch.cuda.synchronize()
+            best.append(s.elapsed_time(e))
+        return statistics.median(best)
+    t_m, t_1 = time_filter(m), time_filter(1)
+    ms_launch = (t_m - t_1) / (m - 1)
+    step_fl = fl / m
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    byts = filter_bytes_per_step(H, Ns, args.prec)
+    if args.prec == "f64":
+        roof = {"bound": "alu", "achieved": step_fl / (ms_launch * 1e-3) / 1e12, "peak": 1.25, "unit": "TFLOP/s"}
+    else:
+        mult = 3.0 if args.prec == "bf16x3" else 1.0
+        tpeak = bf16_peak * (1.1 / 2.25) if args.prec == "tf32" else bf16_peak
+        t_tensor = mult * step_fl / (tpeak * 1e12)
+        t_hbm = byts / (hbm * 1e9)
+        if t_hbm >= t_tensor:
+            roof = {"bound": "hbm", "achieved": byts / (ms_launch * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s"}
+        else:
+            roof = {"bound": "tensor", "achieved": mult * step_fl / (ms_launch * 1e-3) / 1e12, "peak": tpeak,
+                    "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = "k_filter_step_tc" if args.prec != "f64" else "k_filter_step_f64"
+    roof["ms_per_launch"] = ms_launch
+    roof["peak_source"] = "measured (MEASURED_PEAKS.json)" if peaks else "fallback"
+
+    # ---- end to end: pinned host X -> device, filter, Y -> host
+    Xh = torch.from_numpy(X0).pin_memory()
+    Yh = torch.empty_like(Xh).pin_memory()
+    e2e_ms = []
+    for i in range(2):
+        s, e = ev(), ev()
+        torch.cuda.synchronize()
+        s.record(stream)
+        Xs.copy_(Xh, non_blocking=True)
+        ctx.filter(Xs, m, 10.0, 45.0, -2.0, prec=args.prec, Y=Yd)
+        Yh.copy_(Yd, non_blocking=True)
+        e.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(s.elapsed_time(e))
+    e2e = {"value": world * fl / (min(e2e_ms) * 1e-3) / 1e12, "unit": "TFLOP/s",
+           "h2d_bytes_per_step": int(Xh.numel() * 8), "d2h_bytes_per_step": int(Yh.numel() * 8),
+           "what": "filter through the C ABI with the block on pinned host memory, both copies timed"}
+
+    # ---- FP64 cycle for the per-cycle comparison, and precision of the mixed cycle
+    f64 = {}
+    if args.f64_steps > 0 and args.prec != "f64":
+        state["prev"] = None
+        Xa, Ya = Xd.clone(), torch.empty_like(Xd)
+        Xb, Yb = Xd.clone(), torch.empty_like(Xd)
+        b, tmin = ctx.bounds(vd, 10)
+        a0 = tmin
+        a = a0 + (b - a0) * Ns / N
+        s, e = ev(), ev()
+        torch.cuda.synchronize()
+        s.record(stream)
+        ctx.filter(Xa, m, a, b, a0, prec="f64", Y=Ya)
+        r64 = ctx.rayleigh_ritz(Ya)
+        fo, _ = ctx.occupations(r64, Ne, kT)
+        ctx.density_blocks(Ya, fo)
+        e.record(stream)
+        torch.cuda.synchronize()
+        f64["s_per_cycle"] = s.elapsed_time(e) / 1e3
+        ctx.filter(Xb, m, a, b, a0, prec=args.prec, Y=Yb)
+        rmx = ctx.rayleigh_ritz(Yb)
+        scale = max(abs(a0), abs(b))
+        f64["ritz_err_first_cycle"] = float((rmx - r64).abs().max().item() / scale)
+
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.prec, "data": "synthetic (seeded generator, random-init blocks)",
+        "config": {"workload": args.workload, "grid": list(cfg.grid), "stencil": cfg.stencil, "nb": cfg.nb, "N": N,
+                   "Ns": Ns, "m": m, "Ne": Ne, "kT": kT, "filter": args.prec, "subspace": "f64",
+                   "l2": "inputs larger than L2 (X 1.07 GB FP64), no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "s_per_cycle": {"mixed": ms_step / 1e3, "f64": f64.get("s_per_cycle")},
+        "filter_ms": ms_filter,
+        "ritz_err_mixed_vs_f64_first_cycle": f64.get("ritz_err_first_cycle"),
+        "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ts, nnz = oracle_sample(args.ref_states, m, reps=1)
+        cv = 2.0 * nnz * args.ref_states * m / ts[0] / 1e12
+        line["cpu_baseline"] = {"value": cv, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                                "sample": f"FP64 NumPy oracle filter (m={m}) on {args.ref_states} of {Ns} states, "
+                                          f"one BLAS thread, {ts[0]:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

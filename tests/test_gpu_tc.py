@@ -1,0 +1,103 @@
+"""GPU parity of the tensor-core filter (TF32, BF16, split BF16x3) against the FP64
+oracle, through the C ABI.
+
+Tolerance (normwise, ||Y_gpu - Y_oracle||_F <= tol * ||Y_oracle||_F): each
+recurrence step rounds its operands to the tensor format (relative error u_op:
+2^-10 for TF32, whose low mantissa bits the tensor core drops; 2^-8 for BF16;
+about 2^-16 for the hi/lo split, whose missing lo*lo term and rounded lo are of
+order 2^-18 and whose FP32 accumulation over the neighbour sum adds ~2^-20)
+and the error of each step is carried forward by the bounded scaled
+recurrence, so the filtered block carries at most about m * u_op. The test
+allows 2 m u_op.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import chefsi as O
+from paper_1606_03416_gb300 import inputs as G
+
+pytestmark = pytest.mark.gpu
+
+D = pytest.importorskip("paper_1606_03416_gb300.dgchefsi") if torch.cuda.is_available() else None
+
+U_OP = {"tf32": 2.0 ** -10, "bf16": 2.0 ** -8, "bf16x3": 2.0 ** -16}
+
+
+def problems():
+    tiny = G.CONFIGS["tiny_2x2x2"]
+    bulk = G.scaled_copy(G.CONFIGS["bulk3d_8x8x8"], grid=(4, 4, 4), nb=64, Ns=300, m=12, name="bulk4")
+    uneven = G.ProblemConfig(name="uneven", grid=(3, 2, 2), periodic=(True, False, True), stencil="27",
+                             nb=(40, 120), Ns=200, m=7, Ne=150.0, seed=5)
+    sheet = G.scaled_copy(G.CONFIGS["sheet2d_24x20"], grid=(4, 3, 1), Ns=130, m=9, name="sheet")
+    return [tiny, bulk, uneven, sheet]
+
+
+_cache = {}
+
+
+def problem(cfg):
+    if cfg.name not in _cache:
+        H, X0, v0, Ns, Ne = G.make_problem(cfg)
+        Ho = O.DGHamiltonian.from_blocksparse(H)
+        _cache[cfg.name] = (H, Ho, X0, v0, Ns, Ne, np.linalg.eigvalsh(Ho.dense()))
+    return _cache[cfg.name]
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "bf16x3"])
+@pytest.mark.parametrize("cfg", problems(), ids=lambda c: c.name)
+def test_filter_tc_matches_oracle(cfg, prec):
+    H, Ho, X0, _, Ns, _, lam = problem(cfg)
+    a0, b, a = lam[0] - 0.5, lam[-1] + 0.5, lam[min(Ns, Ho.N - 1)]
+    dev = torch.device("cuda:0")
+    with D.Context(H) as ctx:
+        for m in sorted({1, 2, cfg.m}):
+            Y = ctx.filter(torch.from_numpy(X0).to(dev), m, a, b, a0, prec=prec).cpu().numpy()
+            ref = O.chebyshev_filter(Ho, X0.T, m, a, b, a0).T
+            err = np.linalg.norm(Y - ref) / np.linalg.norm(ref)
+            print(f"FILTER_ERR {cfg.name} {prec} m={m} rel_fro={err:.3e} bound={2 * m * U_OP[prec]:.3e}")
+            assert np.isfinite(Y).all()
+            assert err <= 2 * m * U_OP[prec], (m, err)
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "bf16x3"])
+def test_filter_tc_ragged_states_and_strides(prec):
+    """N_s not a multiple of the 128-state tile, a row stride wider than N, and
+    the padding of the caller's block left untouched."""
+    H, Ho, X0, _, _, _, lam = problem(problems()[2])
+    Ns = 131
+    dev = torch.device("cuda:0")
+    a0, b, a = lam[0] - 0.5, lam[-1] + 0.5, lam[Ns]
+    with D.Context(H) as ctx:
+        big = torch.full((Ns, Ho.N + 5), 3.0, dtype=torch.float64, device=dev)
+        big[:, :Ho.N] = torch.from_numpy(X0[:Ns])
+        out = torch.full_like(big, -7.0)
+        ctx.filter(big[:, :Ho.N], 5, a, b, a0, prec=prec, Y=out[:, :Ho.N])
+        ref = O.chebyshev_filter(Ho, X0[:Ns].T, 5, a, b, a0).T
+        Y = out[:, :Ho.N].cpu().numpy()
+        assert np.linalg.norm(Y - ref) <= 10 * U_OP[prec] * np.linalg.norm(ref)
+        assert torch.all(out[:, Ho.N:] == -7.0)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3", "tf32"])
+def test_mixed_cycles_converge(prec):
+    """Mixed-precision filter + FP64 Rayleigh-Ritz on the tiny 2x2x2 problem:
+    after 20 cycles the lowest N_s - 8 Ritz values agree with a dense eigensolve.
+    The split BF16 filter must reach the 1e-8 target; one rounding of BF16 or
+    TF32 operands per step leaves a floor of order u_op^2 * spread."""
+    cfg = G.CONFIGS["tiny_2x2x2"]
+    H, Ho, X0, v0, Ns, Ne, lam = problem(cfg)
+    dev = torch.device("cuda:0")
+    with D.Context(H) as ctx:
+        X = torch.from_numpy(X0).to(dev)
+        v = torch.from_numpy(v0).to(dev)
+        prev = None
+        for _ in range(cfg.cycles):
+            out = ctx.cycle(X, cfg.m, Ne, cfg.kT, v0=v, prev_ritz=prev, prec=prec)
+            prev = out["ritz"].cpu().numpy()
+    g = 8
+    scale = max(abs(lam[0]), abs(lam[-1]))
+    err = np.max(np.abs(prev[:Ns - g] - lam[:Ns - g])) / scale
+    print(f"RITZ_ERR tiny {prec} {err:.3e}")
+    limit = {"bf16x3": 1e-8, "tf32": 1e-4, "bf16": 1e-3}[prec]
+    assert err <= limit

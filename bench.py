@@ -110,8 +110,8 @@ class ClockSampler:
 
 
 def dist_env():
-    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
-            int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_1606_03416_gb300.replicas import rank_info
+    return rank_info()
 
 
 def oracle_sample(Ns_sample: int, m: int, reps: int = 1):
@@ -167,6 +167,35 @@ def run_reference(args):
     return 0
 
 
+def run_filter_only(args):
+    """Filter alone on a (possibly smaller) copy of the workload: the case the
+    ncu captures run on. Prints one JSON line with the mean filter time."""
+    import torch
+    from paper_1606_03416_gb300 import dgchefsi as D
+    from paper_1606_03416_gb300 import inputs as G
+    base = G.CONFIGS[args.workload]
+    cfg = G.scaled_copy(base, Ns=args.ns or base.Ns, m=args.m or base.m, name=base.name)
+    H = G.make_blocks(cfg)
+    dev = torch.device("cuda:0")
+    X = torch.from_numpy(G.make_X(H.N, cfg.Ns, cfg.seed)).to(dev)
+    Y = torch.empty_like(X)
+    with D.Context(H) as ctx:
+        for _ in range(args.warmup):
+            ctx.filter(X, cfg.m, 10.0, 45.0, -2.0, prec=args.prec, Y=Y)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(True), torch.cuda.Event(True)
+        s.record()
+        for _ in range(args.steps):
+            ctx.filter(X, cfg.m, 10.0, 45.0, -2.0, prec=args.prec, Y=Y)
+        e.record()
+        torch.cuda.synchronize()
+        ms = s.elapsed_time(e) / max(args.steps, 1)
+    fl = filter_flops(H, cfg.Ns, cfg.m)
+    print(json.dumps({"mode": "filter-only", "workload": args.workload, "Ns": cfg.Ns, "m": cfg.m, "prec": args.prec,
+                      "ms_per_filter": ms, "filter_tflops": fl / (ms * 1e-3) / 1e12}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -178,9 +207,15 @@ def main():
     ap.add_argument("--ref-states", type=int, default=64, help="states in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--filter-only", action="store_true",
+                    help="time only the filter (profiling case); --ns and --m override the workload")
+    ap.add_argument("--ns", type=int, default=0)
+    ap.add_argument("--m", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.filter_only:
+        return run_filter_only(args)
 
     import torch
     rank, world, local = dist_env()
@@ -250,11 +285,8 @@ def main():
     launches = D.launch_count() - n0
     ms_step = t0.elapsed_time(t1) / args.steps
     ms_filter = statistics.mean(a.elapsed_time(b) for a, b in fl_t)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step, ms_filter], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step, ms_filter = float(t[0]), float(t[1])
+    from paper_1606_03416_gb300.replicas import max_over_ranks
+    ms_step, ms_filter = max_over_ranks([ms_step, ms_filter], device=dev)
     fl = filter_flops(H, Ns, m)
     value = world * fl / (ms_filter * 1e-3) / 1e12
 

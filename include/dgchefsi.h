@@ -103,6 +103,31 @@ dgchefsi_status dgchefsi_matvec(dgchefsi_ctx* ctx, const double* X, double* Y, i
 dgchefsi_status dgchefsi_bounds(dgchefsi_ctx* ctx, const double* v0, int k,
                                 double* b_upper, double* theta_min);
 
+/* Capacity, in doubles, of the fixed device array used by dgchefsi_bounds_static
+ * (8 MiB per GPU that loads this library, held until the process exits). */
+#define DGCHEFSI_BOUNDS_STATIC_DOUBLES (1 << 20)
+
+/* The same k-step Lanczos bound as dgchefsi_bounds, for callers that must not
+ * allocate device memory while they run: for example code whose GPU memory is
+ * already handed out to another framework's caching allocator, or a loop that
+ * cannot afford the device-wide synchronisation cudaMalloc/cudaFree imply.
+ * This entry point has no counterpart in the paper; it is a deployment aid.
+ * It calls no cudaMalloc, cudaFree or allocating library routine: the Krylov
+ * basis lives in a fixed array inside the library of
+ * DGCHEFSI_BOUNDS_STATIC_DOUBLES doubles, and the call needs
+ * (k + 2) * N + 72 of them (k clipped to N); larger requests return
+ * DGCHEFSI_ERR_ARG with a message and touch nothing. The context itself must
+ * have been created beforehand (dgchefsi_create does allocate).
+ * The first call on a device looks up that array's device address once
+ * (cudaGetSymbolAddress, with the context's device made current); make that
+ * first call before any stream capture. Every call on a device shares the one
+ * array and nothing in it needs to start at zero (each call writes every entry
+ * it reads), but calls whose work overlaps on the GPU (other threads or
+ * streams) race on it and must be serialised by the caller.
+ * Arguments, results and synchronisation are those of dgchefsi_bounds. */
+dgchefsi_status dgchefsi_bounds_static(dgchefsi_ctx* ctx, const double* v0, int k,
+                                       double* b_upper, double* theta_min);
+
 /* Y = p_m(H) X with [a, b] mapped to [-1, 1] (Alg. 1 step 2), by the scaled
  * three-term Chebyshev recurrence
  *   Y_0 = X,  Y_1 = (s_1/e)(H - cI) X,

@@ -26,7 +26,11 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_SPD", 
 
 EXPORTS = ["dgchefsi_create", "dgchefsi_destroy", "dgchefsi_set_stream", "dgchefsi_dims", "dgchefsi_matvec",
            "dgchefsi_bounds", "dgchefsi_filter", "dgchefsi_rayleigh_ritz", "dgchefsi_occupations",
-           "dgchefsi_density_blocks", "dgchefsi_cycle", "dgchefsi_last_error", "dgchefsi_launch_count"]
+           "dgchefsi_density_blocks", "dgchefsi_cycle", "dgchefsi_last_error", "dgchefsi_launch_count",
+           "dgchefsi_bounds_static"]
+
+# Capacity (doubles) of the library's fixed scratch array for bounds_static.
+BOUNDS_STATIC_DOUBLES = 1 << 20
 
 
 class DGChefsiError(RuntimeError):
@@ -48,6 +52,7 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_dims": (st, [P, P, P]),
         "dgchefsi_matvec": (st, [P, P, P, I64, I64]),
         "dgchefsi_bounds": (st, [P, P, C.c_int, P, P]),
+        "dgchefsi_bounds_static": (st, [P, P, C.c_int, P, P]),
         "dgchefsi_filter": (st, [P, C.c_int, P, P, I64, I64, C.c_int, D, D, D]),
         "dgchefsi_rayleigh_ritz": (st, [P, P, I64, I64, P]),
         "dgchefsi_occupations": (st, [P, P, I64, D, D, P, P]),
@@ -158,6 +163,16 @@ class Context:
         b, t = C.c_double(), C.c_double()
         self._sync_stream()
         _check(_lib.dgchefsi_bounds(self._h, _ptr(v0), int(k), C.byref(b), C.byref(t)))
+        return b.value, t.value
+
+    def bounds_static(self, v0: torch.Tensor, k: int = 10):
+        """Same as ``bounds`` but without any device allocation: the Krylov basis
+        lives in a fixed array inside the library (see include/dgchefsi.h)."""
+        if not (v0.is_cuda and v0.dtype == torch.float64 and v0.numel() == self.N and v0.is_contiguous()):
+            raise ValueError("v0 must be a contiguous float64 CUDA vector of length N")
+        b, t = C.c_double(), C.c_double()
+        self._sync_stream()
+        _check(_lib.dgchefsi_bounds_static(self._h, _ptr(v0), int(k), C.byref(b), C.byref(t)))
         return b.value, t.value
 
     # -- Alg. 1 step 2

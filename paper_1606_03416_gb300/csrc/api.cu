@@ -249,9 +249,12 @@ static dgchefsi_status rr_impl(dgchefsi_ctx* ctx, double* Y, int64_t Ns, int64_t
                              lw_trtri_h, ctx->info_d + 1));
   // Y_hat^T = U^{-T} Y^T  (W holds Y_hat, state-major, ld N)
   DG_CUDA(gemm_nn_f64(S, Ns, Y, ld, W, N, Ns, N, Ns, true, s));
-  // Step 4: H Y_hat into Y (Y is free now), H_hat = Y_hat^T (H Y_hat), symmetrised.
+  // Step 4: H Y_hat into Y (Y is free now), H_hat = Y_hat^T (H Y_hat). H_hat is
+  // symmetric up to rounding and the eigensolver reads one triangle (row-major
+  // lower = column-major upper), so only the tiles on and below the diagonal
+  // are computed.
   DG_CUDA(filter_step_f64(ctx->view(), W, N, nullptr, Y, ld, Ns, 1.0, 0.0, 0.0, s));
-  DG_CUDA(gemm_nt_f64(W, N, Y, ld, S, Ns, Ns, Ns, N, false, true, s));
+  DG_CUDA(gemm_nt_f64(W, N, Y, ld, S, Ns, Ns, Ns, N, true, false, s));
   DG_SOLVER(cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n, S, n, ritz, work, lwork,
                              ctx->info_d + 2));
   // Step 5: X_new^T = Q^T Y_hat^T (column-major Q read row-major is Q^T).

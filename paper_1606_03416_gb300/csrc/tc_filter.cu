@@ -1,28 +1,35 @@
 // Chebyshev filter on the tcgen05 tensor cores (Alg. 1 step 2; Eq. matvec_3).
 //
-// One step of the scaled recurrence is, per element K and per tile of 128 states,
+// One step of the scaled recurrence is, per element K and state tile,
 //     Y_{k+1}[s, K] = alpha_k * sum_{K' in N(K)} (H - cI)_{KK'} Y_k[s, K'] - beta_k * Y_{k-1}[s, K]
 // i.e. a dense GEMM with M = 128 states, N = n_K (padded to 16) and a K dimension
-// that runs over the neighbour blocks, followed by the recurrence update. One CTA
-// owns one (state tile, element) output tile:
-//   * warp 0 / lane 0 streams 128-byte-wide K slices of Y_k (A operand, 128 rows)
-//     and of (H - cI) (B operand, n_K rows) with TMA into a 4-stage shared-memory
-//     ring (SWIZZLE_128B, K-major), signalling mbarriers;
-//   * warp 1 / lane 0 issues tcgen05.mma (kind::f16 for BF16, kind::tf32 for
-//     TF32) into a 128 x n_K FP32 accumulator in tensor memory and frees each
-//     ring slot with tcgen05.commit;
-//   * all four warps then read the accumulator (tcgen05.ld, one state row per
-//     thread) and apply alpha_k, -beta_k Y_{k-1} (FP32 master copy), writing the
-//     FP32 master of Y_{k+1} and, for the BF16 forms, its BF16 operand copies.
-// The shift -cI is folded into the diagonal block of the operand copy of H,
-// rebuilt once per filter call. Iterates live in an element-padded layout
-// (every element starts on a 16-column boundary, pads held at zero) so TMA
-// coordinates are always 16-byte aligned; pads of H are zero so neighbouring
-// columns read by a wide K slice contribute nothing.
+// running over the neighbour blocks, followed by the recurrence update.
+//
+// Persistent, warp-specialised kernel, one CTA per SM (192 threads):
+//   * warp 0 (one lane) streams 128-byte-wide K slices with TMA into a
+//     shared-memory ring (SWIZZLE_128B, K-major): per slot, T state tiles of
+//     Y_k (A operands, 128 rows each) and the blocks of (H - cI) that couple the
+//     slice's element K' to each of the G output elements of the work unit
+//     (B operands);
+//   * warp 1 (one lane) issues tcgen05.mma (kind::f16 for BF16, kind::tf32 for
+//     TF32) into G x T FP32 accumulators in tensor memory, double-buffered
+//     across work units, and frees ring slots with tcgen05.commit;
+//   * warps 2-5 drain a finished unit's accumulators (tcgen05.ld, one state row
+//     per thread) while the next unit is multiplied, apply alpha_k and
+//     -beta_k Y_{k-1} (FP32 master), and write the FP32 master of Y_{k+1} and,
+//     for the BF16 forms, its BF16 operand copies.
+// A work unit is G consecutive elements x T consecutive state tiles; it walks
+// the union of the G elements' neighbour lists, so each A slice loaded is used
+// for every element of the unit that couples to it, and each B block for all
+// T state tiles. The shift -cI is folded into the diagonal blocks of the
+// operand copy of H, rebuilt once per filter call. Iterates live in an
+// element-padded layout (every element starts on a 16-column boundary, pads
+// held at zero) so TMA coordinates stay 16-byte aligned; pads of H are zero,
+// so columns of a neighbouring element read by a wide slice contribute nothing.
 //
 // BF16X3 splits every operand v into hi = bf16(v) and lo = bf16(v - hi) and
-// accumulates hi*hi + hi*lo + lo*hi (three K passes over the same neighbours),
-// which recovers close to FP32 accuracy on the BF16 tensor pipe.
+// accumulates hi*hi + hi*lo + lo*hi (three passes per slice), which recovers
+// close to FP32 accuracy on the BF16 tensor pipe.
 //
 // Every wait on an mbarrier is bounded by wall-clock time; on expiry the CTA
 // records DGCHEFSI_ERR_TIMEOUT in a device word, drains its own copies in
@@ -42,19 +49,23 @@ namespace {
 
 constexpr int BM = 128;           // states per tile (MMA M)
 constexpr int SLICE_BYTES = 128;  // K extent of one ring slot in bytes (one swizzle row)
-constexpr int STAGES = 4;
+constexpr int NTHREADS = 320;  // producer warp, MMA warp, 8 epilogue warps
+constexpr int EPI_WARPS = 8;
+constexpr int STAGES = 4;  // ring slots (each T A-tiles + G B-tiles, 48 KB for every shape used)
 constexpr int A_BYTES = BM * SLICE_BYTES;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per wait
+
+constexpr int MAXG = 4;
 
 enum Mode { MODE_TF32 = 0, MODE_BF16 = 1, MODE_BF16X3 = 2 };
 
 struct Params {
-  const int64_t* row_ptr;
-  const int32_t* col;
+  const int32_t* sched;      // slice entries: [A x coordinate, B row for each of the G elements or -1]
+  const int32_t* sched_ptr;  // [ngroups + 1] first entry of each element group
+  const int32_t* grp_elem;   // [ngroups * G] elements of each group (-1 past the end)
   const int32_t* nb;
   const int32_t* pnb;   // padded element sizes (multiple of 16)
   const int32_t* poff;  // padded element offsets
-  const int64_t* brow;  // first row of block e in the B operand tensor
   int64_t lo_rows;      // BF16X3: row offset of the lo copy of H
   int64_t Ns, ldp;
   const float* Fprev;
@@ -65,6 +76,9 @@ struct Params {
   int W;      // elements per slice: 64 (BF16) or 32 (TF32)
   int mode;
   int boxn;   // rows of a B box (max padded element size)
+  int G, T, ACC, NBUF, stages;
+  int ngroups, ntg;
+  int maxent;  // most slice entries of any element group (shared-memory copy size)
   int* err;
 };
 
@@ -161,41 +175,122 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(128, 1)
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+// Epilogue of one 16-column chunk of one state row.
+__device__ __forceinline__ void store_chunk(const Params& p, int64_t idx, int jn, const float (&v)[16],
+                                            const float4 (&pr)[4]) {
+  float y[16];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    y[4 * q + 0] = p.alpha * v[4 * q + 0] - p.beta * pr[q].x;
+    y[4 * q + 1] = p.alpha * v[4 * q + 1] - p.beta * pr[q].y;
+    y[4 * q + 2] = p.alpha * v[4 * q + 2] - p.beta * pr[q].z;
+    y[4 * q + 3] = p.alpha * v[4 * q + 3] - p.beta * pr[q].w;
+  }
+  if (jn == 16) {
+    float4* po = reinterpret_cast<float4*>(p.Fout + idx);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) po[q] = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+    if (p.mode != MODE_TF32) {
+      uint32_t hw[8], lw[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(y[2 * q], y[2 * q + 1]);
+        const float2 hf = __bfloat1622float2(h2);
+        const __nv_bfloat162 l2 = __floats2bfloat162_rn(y[2 * q] - hf.x, y[2 * q + 1] - hf.y);
+        hw[q] = *reinterpret_cast<const uint32_t*>(&h2);
+        lw[q] = *reinterpret_cast<const uint32_t*>(&l2);
+      }
+      uint4* ph = reinterpret_cast<uint4*>(p.Hout + idx);
+      ph[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      ph[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+      if (p.mode == MODE_BF16X3) {
+        uint4* pl = reinterpret_cast<uint4*>(p.Lout + idx);
+        pl[0] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        pl[1] = make_uint4(lw[4], lw[5], lw[6], lw[7]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      if (q < jn) {
+        p.Fout[idx + q] = y[q];
+        if (p.mode != MODE_TF32) {
+          const __nv_bfloat16 h = __float2bfloat16_rn(y[q]);
+          p.Hout[idx + q] = h;
+          if (p.mode == MODE_BF16X3) p.Lout[idx + q] = __float2bfloat16_rn(y[q] - __bfloat162float(h));
+        }
+      }
+    }
+  }
+}
+
+// Fprev for one chunk (zeros when beta == 0 or the row is not live).
+__device__ __forceinline__ void load_prev(const Params& p, int64_t idx, int jn, bool live, float4 (&pr)[4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) pr[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!live || p.beta == 0.f || jn <= 0) return;
+  if (jn == 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pr[q] = ld4(p.Fprev + idx + 4 * q);
+  } else {
+    float t[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) t[q] = q < jn ? p.Fprev[idx + q] : 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pr[q] = make_float4(t[4 * q], t[4 * q + 1], t[4 * q + 2], t[4 * q + 3]);
+  }
+}
+
+// MODE_, G, T and ACC (accumulator columns per element) are compile-time so
+// the single MMA-issuing thread runs a fully unrolled loop of descriptor adds:
+// with N = 64 each MMA is only ~32 tensor-core cycles, so issue overhead
+// would otherwise dominate.
+template <int MODE_, int G, int T, int ACC>
+__global__ void __launch_bounds__(NTHREADS, 1)
     k_filter_step_tc(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                      const __grid_constant__ CUtensorMap tmB, const Params p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  const int b_bytes = p.boxn * SLICE_BYTES;
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + STAGES * A_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * b_bytes);  // full[S], empty[S], acc
+  constexpr int S = STAGES;
+  constexpr int b_bytes = ACC * SLICE_BYTES;  // one element's B tile: ACC rows of 128 bytes
+  constexpr int stage_bytes = T * A_BYTES + G * b_bytes;
+  constexpr uint32_t NMMA = (uint32_t)(G * ACC);  // the G elements' B tiles are stacked along N
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
+  // per-role copies of the current group's slice entries (producer, MMA issuer)
+  int32_t* sched_sh0 = reinterpret_cast<int32_t*>(bars + 2 * S + 4);
+  int32_t* sched_sh1 = sched_sh0 + p.maxent * (1 + G);
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int K = blockIdx.y;
-  const int64_t s0 = (int64_t)blockIdx.x * BM;
-  const int nK = p.nb[K];
-  const int pK = p.pnb[K];
-  const uint32_t ncols = pK <= 32 ? 32u : (pK <= 64 ? 64u : 128u);
-  const int npass = p.mode == MODE_BF16X3 ? 3 : 1;
-  const int64_t e0 = p.row_ptr[K], e1 = p.row_ptr[K + 1];
+  constexpr int npass = MODE_ == MODE_BF16X3 ? 3 : 1;
+  const int nunits = p.ngroups * p.ntg;
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * S;
+  const uint32_t accf0 = empty0 + 8 * S, acce0 = accf0 + 16;
 
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), accb = smem_u32(bars + 2 * STAGES);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(accb, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, EPI_WARPS);
+    }
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 2) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                 "r"(ncols)
+                 "r"(512)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -204,139 +299,178 @@ __global__ void __launch_bounds__(128, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_base_sh;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- producer: TMA into the ring
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA0)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  if (warp == 0) {
+    // ---------------- producer: TMA into the ring (lane 0 issues; the warp copies schedules)
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA0)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+    }
     int c = 0;
     bool ok = true;
-    for (int64_t e = e0; e < e1 && ok; ++e) {
-      const int Kp = p.col[e];
-      const int nsl = (p.pnb[Kp] + p.W - 1) / p.W;
-      const int x0 = p.poff[Kp];
-      const int64_t r0 = p.brow[e];
-      for (int sl = 0; sl < nsl && ok; ++sl) {
-        for (int pass = 0; pass < npass; ++pass) {
-          const int st = c % STAGES;
-          const uint32_t ph = (uint32_t)(c / STAGES) & 1u;
-          if (!mbar_wait(empty0 + 8 * st, ph ^ 1u)) {
-            ok = false;
-            break;
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+      const int eg = u / p.ntg, tg = u % p.ntg;
+      const int s0 = tg * BM * T;
+      const int e0 = p.sched_ptr[eg], ne = p.sched_ptr[eg + 1] - e0;
+      __syncwarp();
+      for (int z = lane; z < ne * (1 + G); z += 32) sched_sh0[z] = p.sched[(int64_t)e0 * (1 + G) + z];
+      __syncwarp();
+      if (lane == 0 && ok) {
+        for (int e = 0; e < ne && ok; ++e) {
+          const int32_t* ent = sched_sh0 + e * (1 + G);
+          const int ax = ent[0];
+          for (int pass = 0; pass < npass; ++pass) {
+            const int st = c & (S - 1);
+            const uint32_t ph = (uint32_t)(c / S) & 1u;
+            if (!mbar_wait(empty0 + 8 * st, ph ^ 1u)) {
+              ok = false;
+              break;
+            }
+            const uint32_t fb = full0 + 8 * st;
+            mbar_expect_tx(fb, (uint32_t)stage_bytes);
+            uint8_t* sst = smem + st * stage_bytes;
+            for (int t = 0; t < T; ++t)
+              tma_load_2d(smem_u32(sst + t * A_BYTES), (MODE_ == MODE_BF16X3 && pass == 2) ? &tmA1 : &tmA0, ax, s0 + BM * t, fb);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+              const int r = ent[1 + g];  // a zero block when element g does not couple to this slice
+              tma_load_2d(smem_u32(sst + T * A_BYTES + g * b_bytes), &tmB, 0,
+                          (int)(r + (pass == 1 ? p.lo_rows : 0)), fb);
+            }
+            ++c;
           }
-          mbar_expect_tx(full0 + 8 * st, (uint32_t)(A_BYTES + b_bytes));
-          tma_load_2d(smem_u32(sA + st * A_BYTES), pass == 2 ? &tmA1 : &tmA0, x0 + sl * p.W, (int)s0,
-                      full0 + 8 * st);
-          const int64_t brow = r0 + (int64_t)sl * pK + (pass == 1 ? p.lo_rows : 0);
-          tma_load_2d(smem_u32(sB + st * b_bytes), &tmB, 0, (int)brow, full0 + 8 * st);
-          ++c;
         }
       }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
     }
-    if (!ok) {
+    if (lane == 0) {
+      if (!ok) {
+        atomicOr(p.err, 1);
+        atomicExch(&abort_sh, 1);
+      }
+      // drain: every issued copy must land before the CTA may exit
+      for (int i = c - S < 0 ? 0 : c - S; i < c; ++i)
+        if (!mbar_wait(full0 + 8 * (i & (S - 1)), (uint32_t)(i / S) & 1u)) atomicOr(p.err, 1);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (lane 0 issues; the warp copies schedules)
+    constexpr uint32_t fmt = MODE_ == MODE_TF32 ? 2u : 1u;
+    // descriptor of the ring's first byte; every operand is an offset from it
+    const uint64_t desc0 = sdesc(smem_u32(smem));
+    int c = 0, i = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++i) {
+      const int eg = u / p.ntg;
+      const int e0 = p.sched_ptr[eg], ne = p.sched_ptr[eg + 1] - e0;
+      __syncwarp();
+      for (int z = lane; z < ne * (1 + G); z += 32) sched_sh1[z] = p.sched[(int64_t)e0 * (1 + G) + z];
+      __syncwarp();
+      if (lane == 0 && ok) {
+        const int buf = p.NBUF == 2 ? (i & 1) : 0;
+        const int use = p.NBUF == 2 ? (i >> 1) : i;
+        if (!mbar_wait(acce0 + 8 * buf, ((uint32_t)use & 1u) ^ 1u)) ok = false;
+        tc_fence_after();
+        constexpr uint32_t ID = idesc(fmt, NMMA);
+        const uint32_t dbuf = tmem + (uint32_t)(buf * T * G * ACC);
+        uint32_t first = 0;  // the unit's first slice overwrites the accumulators
+        for (int e = 0; e < ne && ok; ++e) {
+#pragma unroll
+          for (int pass = 0; pass < npass; ++pass) {
+            const int st = c & (S - 1);
+            const uint32_t ph = (uint32_t)(c / S) & 1u;
+            if (!mbar_wait(full0 + 8 * st, ph)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint64_t da = desc0 + (uint64_t)((st * stage_bytes) >> 4);
+            const uint64_t db = da + (uint64_t)((T * A_BYTES) >> 4);
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+              const uint32_t d = dbuf + (uint32_t)(t * G * ACC);
+#pragma unroll
+              for (int kk = 0; kk < SLICE_BYTES / 32; ++kk) {
+                const uint64_t ad = da + (uint64_t)((t * A_BYTES + 32 * kk) >> 4);
+                const uint64_t bd = db + (uint64_t)((32 * kk) >> 4);
+                const uint32_t acc = kk > 0 ? 1u : first;
+                if constexpr (MODE_ == MODE_TF32) mma_tf32(d, ad, bd, ID, acc);
+                else mma_bf16(d, ad, bd, ID, acc);
+              }
+            }
+            first = 1u;
+            mma_commit(empty0 + 8 * st);
+            ++c;
+          }
+        }
+        mma_commit(accf0 + 8 * buf);
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+    }
+    if (lane == 0 && !ok) {
       atomicOr(p.err, 1);
       atomicExch(&abort_sh, 1);
     }
-    // drain: every issued copy must land before the CTA may exit
-    for (int i = std::max(0, c - STAGES); i < c; ++i)
-      if (!mbar_wait(full0 + 8 * (i % STAGES), (uint32_t)(i / STAGES) & 1u)) atomicOr(p.err, 1);
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    int total = 0;
-    for (int64_t e = e0; e < e1; ++e) total += (p.pnb[p.col[e]] + p.W - 1) / p.W;
-    total *= npass;
-    const uint32_t id = idesc(p.mode == MODE_TF32 ? 2u : 1u, (uint32_t)pK);
-    for (int c = 0; c < total; ++c) {
-      const int st = c % STAGES;
-      const uint32_t ph = (uint32_t)(c / STAGES) & 1u;
-      if (!mbar_wait(full0 + 8 * st, ph)) {
-        atomicOr(p.err, 1);
-        atomicExch(&abort_sh, 1);
+  } else {
+    // ---------------- epilogue: warps 2..9; two warps per TMEM lane quarter split
+    // the 16-column chunks of each accumulator; one state row per thread.
+    const int q = warp & 3;          // TMEM lane quarter this warp may access
+    const int h = (warp - 2) >> 2;   // which half of the chunks
+    int i = 0;
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++i) {
+      const int buf = p.NBUF == 2 ? (i & 1) : 0;
+      const int use = p.NBUF == 2 ? (i >> 1) : i;
+      const int eg = u / p.ntg, tg = u % p.ntg;
+      const int64_t s0 = (int64_t)tg * BM * T;
+      bool ready = mbar_wait(accf0 + 8 * buf, (uint32_t)use & 1u);
+      ready = __all_sync(0xffffffffu, ready);
+      if (!ready) {
+        if (lane == 0) atomicOr(p.err, 1);
         break;
       }
       tc_fence_after();
-      const uint32_t a0 = smem_u32(sA + st * A_BYTES), b0 = smem_u32(sB + st * b_bytes);
+      const bool go = *(volatile int*)&abort_sh == 0;
+      for (int g = 0; g < G; ++g) {
+        const int K = p.grp_elem[eg * G + g];
+        if (K < 0) continue;
+        const int nK = p.nb[K], pK = p.pnb[K];
+        const int nch = pK >> 4;
+        const int64_t col = p.poff[K];
+        for (int t = 0; t < T; ++t) {
+          const int64_t s = s0 + BM * t + 32 * q + lane;
+          const bool live = go && s < p.Ns;
+          const int64_t rbase = s * p.ldp + col;
+          const uint32_t ta = tmem + (uint32_t)(((buf * T + t) * G + g) * ACC) + ((uint32_t)(32 * q) << 16);
+          // all loads of Y_{k-1} for this warp's chunks first (memory-level parallelism)
+          float4 pr[4][4];
 #pragma unroll
-      for (int kk = 0; kk < SLICE_BYTES / 32; ++kk) {
-        const uint64_t ad = sdesc(a0 + 32 * kk), bd = sdesc(b0 + 32 * kk);
-        const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
-        if (p.mode == MODE_TF32) mma_tf32(tmem, ad, bd, id, acc);
-        else mma_bf16(tmem, ad, bd, id, acc);
-      }
-      mma_commit(empty0 + 8 * st);
-    }
-    mma_commit(accb);
-  }
-
-  // ---------------- epilogue: every thread owns one state row
-  __syncwarp();
-  bool ready = mbar_wait(accb, 0);
-  ready = __all_sync(0xffffffffu, ready);
-  tc_fence_after();
-  if (!ready && lane == 0) atomicOr(p.err, 1);
-  const bool store = ready && (*(volatile int*)&abort_sh == 0);
-  const int row = warp * 32 + lane;
-  const int64_t s = s0 + row;
-  const bool live = store && s < p.Ns;
-  const int64_t base = s * p.ldp + p.poff[K];
-  for (int j0 = 0; j0 < pK; j0 += 16) {
-    float v[16];
-    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j0, v);
-    if (!live) continue;
-    const int jn = min(16, nK - j0);
-    if (jn <= 0) continue;
-    float y[16];
-    if (jn == 16) {
-      const float4* pv = reinterpret_cast<const float4*>(p.Fprev + base + j0);
+          for (int cc = 0; cc < 4; ++cc) {
+            const int c = h + 2 * cc;
+            const int jn = nK - 16 * c;
+            load_prev(p, rbase + 16 * c, jn > 16 ? 16 : jn, live && c < nch, pr[cc]);
+          }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float4 pr = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (p.beta != 0.f) pr = pv[q];
-        y[4 * q + 0] = p.alpha * v[4 * q + 0] - p.beta * pr.x;
-        y[4 * q + 1] = p.alpha * v[4 * q + 1] - p.beta * pr.y;
-        y[4 * q + 2] = p.alpha * v[4 * q + 2] - p.beta * pr.z;
-        y[4 * q + 3] = p.alpha * v[4 * q + 3] - p.beta * pr.w;
-      }
-      float4* po = reinterpret_cast<float4*>(p.Fout + base + j0);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) po[q] = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
-      if (p.mode != MODE_TF32) {
-        uint32_t hw[8], lw[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const __nv_bfloat162 h2 = __floats2bfloat162_rn(y[2 * q], y[2 * q + 1]);
-          const float2 hf = __bfloat1622float2(h2);
-          const __nv_bfloat162 l2 = __floats2bfloat162_rn(y[2 * q] - hf.x, y[2 * q + 1] - hf.y);
-          hw[q] = *reinterpret_cast<const uint32_t*>(&h2);
-          lw[q] = *reinterpret_cast<const uint32_t*>(&l2);
-        }
-        uint4* ph = reinterpret_cast<uint4*>(p.Hout + base + j0);
-        ph[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        ph[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
-        if (p.mode == MODE_BF16X3) {
-          uint4* pl = reinterpret_cast<uint4*>(p.Lout + base + j0);
-          pl[0] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-          pl[1] = make_uint4(lw[4], lw[5], lw[6], lw[7]);
+          for (int cc = 0; cc < 4; ++cc) {
+            const int c = h + 2 * cc;
+            if (c < nch) {
+              float v[16];
+              tmem_ld16(ta + (uint32_t)(16 * c), v);
+              const int jn = nK - 16 * c;
+              if (live && jn > 0) store_chunk(p, rbase + 16 * c, jn > 16 ? 16 : jn, v, pr[cc]);
+            }
+          }
         }
       }
-    } else {
-      for (int q = 0; q < jn; ++q) {
-        const int64_t idx = base + j0 + q;
-        const float pr = p.beta != 0.f ? p.Fprev[idx] : 0.f;
-        const float yv = p.alpha * v[q] - p.beta * pr;
-        p.Fout[idx] = yv;
-        if (p.mode != MODE_TF32) {
-          const __nv_bfloat16 h = __float2bfloat16_rn(yv);
-          p.Hout[idx] = h;
-          if (p.mode == MODE_BF16X3) p.Lout[idx] = __float2bfloat16_rn(yv - __bfloat162float(h));
-        }
-      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce0 + 8 * buf);
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 2) {
+  if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
   }
 }
 
@@ -428,15 +562,31 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 struct TcState {
   int64_t Ns = -1, ldp = 0;
   int mode = -1;
-  std::vector<int32_t> pnb_h, poff_h, blk_row_h;
+  int G = 1, T = 1, ACC = 64, NBUF = 2, boxn = 16;
+  int ngroups = 0, num_sms = 0, maxent = 0;
+  std::vector<int32_t> pnb_h, poff_h, blk_row_h, grp_elem_h;
   std::vector<int64_t> brow_h;
   int64_t b_rows = 0;  // rows of one copy of H in the operand tensor
-  int boxn = 0;
-  int32_t *pnb_d = nullptr, *poff_d = nullptr, *blk_row_d = nullptr;
+  int64_t zero_row = 0;
+  int32_t *pnb_d = nullptr, *poff_d = nullptr, *blk_row_d = nullptr, *grp_elem_d = nullptr;
+  int32_t *sched_d = nullptr, *sched_ptr_d = nullptr;
   int64_t* brow_d = nullptr;
   DevBuf F[2], Sh[2], Sl[2], Hop;
   int* err_d = nullptr;
 };
+
+// Work-unit shape: G elements x T state tiles of ACC accumulator columns,
+// NBUF accumulator sets, all within the 512 tensor-memory columns of an SM.
+static void choose_shape(TcState& t) {
+  t.ACC = t.boxn <= 32 ? 32 : (t.boxn <= 64 ? 64 : 128);
+  t.NBUF = 2;
+  t.T = t.ACC <= 64 ? 2 : 1;
+  t.G = std::min(MAXG, 512 / (t.NBUF * t.T * t.ACC));
+  if (t.G < 1) {
+    t.NBUF = 1;
+    t.G = 1;
+  }
+}
 
 static dgchefsi_status tc_setup(dgchefsi_ctx* ctx, int mode, int64_t Ns) {
   if (!ctx->tc) ctx->tc = new TcState();
@@ -455,19 +605,31 @@ static dgchefsi_status tc_setup(dgchefsi_ctx* ctx, int mode, int64_t Ns) {
     }
     t.boxn = boxn;
     t.ldp = t.poff_h[M];
+    choose_shape(t);
+    t.boxn = t.ACC;  // B boxes are ACC rows high so the G tiles stack along N
+    t.ngroups = (M + t.G - 1) / t.G;
+    t.grp_elem_h.assign((size_t)t.ngroups * t.G, -1);
+    for (int K = 0; K < M; ++K) t.grp_elem_h[K] = K;  // group eg holds elements eg*G .. eg*G+G-1
     t.blk_row_h.resize(ctx->nnzb);
     for (int K = 0; K < M; ++K)
       for (int64_t e = ctx->row_ptr_h[K]; e < ctx->row_ptr_h[K + 1]; ++e) t.blk_row_h[e] = K;
+    int dev = 0;
+    DG_CUDA(cudaGetDevice(&dev));
+    DG_CUDA(cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, dev));
     DG_CUDA(cudaMalloc(&t.pnb_d, sizeof(int32_t) * M));
     DG_CUDA(cudaMalloc(&t.poff_d, sizeof(int32_t) * (M + 1)));
     DG_CUDA(cudaMalloc(&t.blk_row_d, sizeof(int32_t) * std::max<int64_t>(ctx->nnzb, 1)));
     DG_CUDA(cudaMalloc(&t.brow_d, sizeof(int64_t) * std::max<int64_t>(ctx->nnzb, 1)));
+    DG_CUDA(cudaMalloc(&t.grp_elem_d, sizeof(int32_t) * t.grp_elem_h.size()));
+    DG_CUDA(cudaMalloc(&t.sched_ptr_d, sizeof(int32_t) * (t.ngroups + 1)));
     DG_CUDA(cudaMalloc(&t.err_d, sizeof(int)));
     DG_CUDA(cudaMemcpy(t.pnb_d, t.pnb_h.data(), sizeof(int32_t) * M, cudaMemcpyHostToDevice));
     DG_CUDA(cudaMemcpy(t.poff_d, t.poff_h.data(), sizeof(int32_t) * (M + 1), cudaMemcpyHostToDevice));
     DG_CUDA(cudaMemcpy(t.blk_row_d, t.blk_row_h.data(), sizeof(int32_t) * ctx->nnzb, cudaMemcpyHostToDevice));
+    DG_CUDA(cudaMemcpy(t.grp_elem_d, t.grp_elem_h.data(), sizeof(int32_t) * t.grp_elem_h.size(),
+                       cudaMemcpyHostToDevice));
   }
-  if (t.mode != mode) {  // B row layout depends on the slice width
+  if (t.mode != mode) {  // B row layout and slice schedule depend on the slice width
     t.brow_h.resize(ctx->nnzb);
     int64_t r = 0;
     for (int64_t e = 0; e < ctx->nnzb; ++e) {
@@ -475,8 +637,54 @@ static dgchefsi_status tc_setup(dgchefsi_ctx* ctx, int mode, int64_t Ns) {
       const int Kp = ctx->col_h[e];
       r += (int64_t)((t.pnb_h[Kp] + W - 1) / W) * t.pnb_h[t.blk_row_h[e]];
     }
-    t.b_rows = r + t.boxn;  // slack so a full-height box never leaves the tensor
+    t.zero_row = r;         // ACC zero rows: the B tile of a non-coupling element
+    t.b_rows = r + t.boxn;  // also slack so a full-height box never leaves the tensor
+    if (t.b_rows * (mode == MODE_BF16X3 ? 2 : 1) > 2147483647LL)
+      return set_error(DGCHEFSI_ERR_UNSUPPORTED, "operand copy of H too large for 32-bit TMA rows");
     DG_CUDA(cudaMemcpy(t.brow_d, t.brow_h.data(), sizeof(int64_t) * ctx->nnzb, cudaMemcpyHostToDevice));
+    // slice schedule of every element group: union of the members' neighbour lists
+    std::vector<int32_t> sched, sptr(t.ngroups + 1, 0);
+    for (int eg = 0; eg < t.ngroups; ++eg) {
+      std::vector<int> nbrs;
+      for (int g = 0; g < t.G; ++g) {
+        const int K = t.grp_elem_h[(size_t)eg * t.G + g];
+        if (K < 0) continue;
+        for (int64_t e = ctx->row_ptr_h[K]; e < ctx->row_ptr_h[K + 1]; ++e) nbrs.push_back(ctx->col_h[e]);
+      }
+      std::sort(nbrs.begin(), nbrs.end());
+      nbrs.erase(std::unique(nbrs.begin(), nbrs.end()), nbrs.end());
+      for (int Kp : nbrs) {
+        const int nsl = (t.pnb_h[Kp] + W - 1) / W;
+        for (int sl = 0; sl < nsl; ++sl) {
+          sched.push_back(t.poff_h[Kp] + sl * W);
+          for (int g = 0; g < t.G; ++g) {
+            const int K = t.grp_elem_h[(size_t)eg * t.G + g];
+            int32_t row = (int32_t)t.zero_row;
+            if (K >= 0) {
+              int64_t lo = ctx->row_ptr_h[K], hi = ctx->row_ptr_h[K + 1] - 1;
+              while (lo <= hi) {
+                const int64_t mid = (lo + hi) / 2;
+                const int cm = ctx->col_h[mid];
+                if (cm == Kp) {
+                  row = (int32_t)(t.brow_h[mid] + (int64_t)sl * t.pnb_h[K]);
+                  break;
+                }
+                if (cm < Kp) lo = mid + 1; else hi = mid - 1;
+              }
+            }
+            sched.push_back(row);
+          }
+        }
+      }
+      sptr[eg + 1] = (int32_t)(sched.size() / (1 + t.G));
+    }
+    t.maxent = 0;
+    for (int eg = 0; eg < t.ngroups; ++eg) t.maxent = std::max(t.maxent, sptr[eg + 1] - sptr[eg]);
+    cudaFree(t.sched_d);
+    t.sched_d = nullptr;
+    DG_CUDA(cudaMalloc(&t.sched_d, sizeof(int32_t) * std::max<size_t>(sched.size(), 1)));
+    DG_CUDA(cudaMemcpy(t.sched_d, sched.data(), sizeof(int32_t) * sched.size(), cudaMemcpyHostToDevice));
+    DG_CUDA(cudaMemcpy(t.sched_ptr_d, sptr.data(), sizeof(int32_t) * sptr.size(), cudaMemcpyHostToDevice));
     const size_t esz = mode == MODE_TF32 ? 4 : 2;
     const size_t copies = mode == MODE_BF16X3 ? 2 : 1;
     DG_TRY(ensure(ctx, t.Hop, (size_t)t.b_rows * copies * W * esz, "operand copy of H"));
@@ -507,6 +715,22 @@ static dgchefsi_status tc_setup(dgchefsi_ctx* ctx, int mode, int64_t Ns) {
   return DGCHEFSI_OK;
 }
 
+using FilterKernel = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const Params);
+
+template <int MODE_>
+static FilterKernel pick_shape(int G, int T, int ACC) {
+  if (G == 2 && T == 2 && ACC == 64) return k_filter_step_tc<MODE_, 2, 2, 64>;
+  if (G == 2 && T == 1 && ACC == 128) return k_filter_step_tc<MODE_, 2, 1, 128>;
+  if (G == 4 && T == 2 && ACC == 32) return k_filter_step_tc<MODE_, 4, 2, 32>;
+  return nullptr;
+}
+
+static FilterKernel pick_kernel(int mode, int G, int T, int ACC) {
+  if (mode == MODE_TF32) return pick_shape<MODE_TF32>(G, T, ACC);
+  if (mode == MODE_BF16) return pick_shape<MODE_BF16>(G, T, ACC);
+  return pick_shape<MODE_BF16X3>(G, T, ACC);
+}
+
 static dgchefsi_status make_map(CUtensorMap* map, void* base, bool f32, uint64_t inner, uint64_t rows,
                                 uint32_t box_inner, uint32_t box_rows) {
   auto enc = encode_fn();
@@ -528,7 +752,7 @@ dgchefsi_status filter_tc(dgchefsi_ctx* ctx, int prec, const double* X, double* 
   if (ctx->max_nb > 128)
     return set_error(DGCHEFSI_ERR_UNSUPPORTED, "tensor-core filter supports element sizes up to 128 (got %d)",
                      ctx->max_nb);
-  if (Ns > 2147483647LL - BM) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "Ns too large");
+  if (Ns > 2147483647LL / 2 - 2 * BM) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "Ns too large");
   const int mode = prec == DGCHEFSI_TF32 ? MODE_TF32 : (prec == DGCHEFSI_BF16 ? MODE_BF16 : MODE_BF16X3);
   const int W = mode == MODE_TF32 ? 32 : 64;
   DG_TRY(tc_setup(ctx, mode, Ns));
@@ -543,7 +767,6 @@ dgchefsi_status filter_tc(dgchefsi_ctx* ctx, int prec, const double* X, double* 
                                                   t.pnb_d, t.brow_d, W, c, mode, t.b_rows, Hop32, Hop16);
   count_launch();
   DG_CUDA(cudaGetLastError());
-  // Y_0 = X in buffer 0
   auto sh = [&](int i) { return static_cast<__nv_bfloat16*>(t.Sh[i].p); };
   auto sl = [&](int i) { return static_cast<__nv_bfloat16*>(t.Sl[i].p); };
   auto fb = [&](int i) { return static_cast<float*>(t.F[i].p); };
@@ -567,24 +790,38 @@ dgchefsi_status filter_tc(dgchefsi_ctx* ctx, int prec, const double* X, double* 
   const uint64_t brows_total = (uint64_t)t.b_rows * (mode == MODE_BF16X3 ? 2 : 1);
   DG_TRY(make_map(&mapB, t.Hop.p, f32, (uint64_t)W, brows_total, (uint32_t)W, (uint32_t)t.boxn));
 
-  const int smem = STAGES * (A_BYTES + t.boxn * SLICE_BYTES) + (2 * STAGES + 1) * 8 + 1024;
-  DG_CUDA(cudaFuncSetAttribute(k_filter_step_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int stage_bytes = t.T * A_BYTES + t.G * t.ACC * SLICE_BYTES;
+  const int stages = STAGES;
+  const int smem = stages * stage_bytes + (2 * stages + 4) * 8 + 2 * t.maxent * (1 + t.G) * 4 + 1024;
+  if (smem > 227 * 1024) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "filter schedule too large for shared memory");
+  auto kern = pick_kernel(mode, t.G, t.T, t.ACC);
+  if (!kern) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "no filter kernel for G=%d T=%d ACC=%d", t.G, t.T, t.ACC);
+  DG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   DG_CUDA(cudaMemsetAsync(t.err_d, 0, sizeof(int), s));
   Params p{};
-  p.row_ptr = ctx->row_ptr_d;
-  p.col = ctx->col_d;
+  p.sched = t.sched_d;
+  p.sched_ptr = t.sched_ptr_d;
+  p.grp_elem = t.grp_elem_d;
   p.nb = ctx->nb_d;
   p.pnb = t.pnb_d;
   p.poff = t.poff_d;
-  p.brow = t.brow_d;
   p.lo_rows = t.b_rows;
   p.Ns = Ns;
   p.ldp = t.ldp;
   p.W = W;
   p.mode = mode;
   p.boxn = t.boxn;
+  p.G = t.G;
+  p.T = t.T;
+  p.ACC = t.ACC;
+  p.NBUF = t.NBUF;
+  p.stages = stages;
+  p.ngroups = t.ngroups;
+  p.ntg = (int)((Ns + (int64_t)BM * t.T - 1) / ((int64_t)BM * t.T));
+  p.maxent = t.maxent;
   p.err = t.err_d;
-  dim3 grid((unsigned)((Ns + BM - 1) / BM), (unsigned)ctx->M);
+  const int64_t nunits = (int64_t)p.ngroups * p.ntg;
+  const unsigned grid = (unsigned)std::min<int64_t>(nunits, t.num_sms);
   double sig = s1;
   for (int k = 0; k < m; ++k) {
     // step k: Y_{k+1} from Y_k (buffer k%2) and Y_{k-1} (buffer (k+1)%2)
@@ -607,7 +844,7 @@ dgchefsi_status filter_tc(dgchefsi_ctx* ctx, int prec, const double* X, double* 
     p.Lout = mode == MODE_BF16X3 ? sl(nxt) : nullptr;
     const CUtensorMap& A0 = f32 ? mapF[cur] : mapH[cur];
     const CUtensorMap& A1 = f32 ? mapF[cur] : mapL[cur];
-    k_filter_step_tc<<<grid, 128, smem, s>>>(A0, A1, mapB, p);
+    kern<<<grid, NTHREADS, smem, s>>>(A0, A1, mapB, p);
     count_launch();
     DG_CUDA(cudaGetLastError());
   }
@@ -631,6 +868,9 @@ void tc_destroy(dgchefsi_ctx* ctx) {
   cudaFree(t.poff_d);
   cudaFree(t.blk_row_d);
   cudaFree(t.brow_d);
+  cudaFree(t.grp_elem_d);
+  cudaFree(t.sched_d);
+  cudaFree(t.sched_ptr_d);
   cudaFree(t.err_d);
   for (int i = 0; i < 2; ++i) {
     cudaFree(t.F[i].p);

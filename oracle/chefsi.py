@@ -272,3 +272,116 @@ def packed_density(H: DGHamiltonian, blocks) -> np.ndarray:
     """Concatenate P_KK row-major in element order (the library's packed form)."""
     return np.concatenate([np.asarray(b).ravel() for b in blocks]) if blocks else np.zeros(0)
 
+
+
+# --------------------------------------------------------------------------
+# Band energy of one cycle and its adjoint (differentiation of the cycle).
+#
+# E(H, X) = sum_i f_i lambda_i for one cycle (filter -> Cholesky-QR ->
+# Rayleigh-Ritz -> occupations) with the filter bounds (a, b, a0), N_e and kT
+# held fixed. The paper does not differentiate the cycle; the adjoint below is
+# derived from the steps above:
+#   * occupations: f'_i = -f_i (1 - f_i)/kT and mu(lambda) from sum f = N_e/2
+#     give g_i = dE/dlambda_i = f_i + lambda_i f'_i - f'_i (sum_j lambda_j f'_j)/(sum_j f'_j);
+#   * Rayleigh-Ritz on span(Y~): with Z = U^{-1} Q (so X_new = Y~ Z) and
+#     R = H X_new - X_new Lambda, dlambda_i = x_i^T dH x_i + 2 r_i^T dY~ z_i, hence
+#     dE/dH (each stored entry independent) gets sum_i g_i x_i x_i^T and
+#     Y~bar = 2 R G Z^T;
+#   * filter: reverse the recurrence Y_{k+1} = alpha_k (H - cI) Y_k - beta_k Y_{k-1}
+#     (alpha_0 = s_1/e, beta_0 = 0; alpha_k = 2 s_{k+1}/e, beta_k = s_k s_{k+1}):
+#     W_m = Y~bar, dE/dH += alpha_k W_{k+1} Y_k^T, W_k = alpha_k (H - cI) W_{k+1} - beta_{k+1} W_{k+2},
+#     and X bar = W_0.
+# Gradients w.r.t. H are returned per stored block as if every stored entry
+# were independent; a symmetric perturbation of H_{KK'}[j, j'] = H_{K'K}[j', j]
+# changes E by G_{KK'}[j, j'] + G_{K'K}[j', j] (see ``tied_gradient``).
+# --------------------------------------------------------------------------
+
+
+def _recurrence_coefficients(m, a, b, a0):
+    c, e, sig = filter_coefficients(m, a, b, a0)
+    alpha = [sig[1] / e] + [2.0 * sig[k + 1] / e for k in range(1, m)]
+    beta = [0.0] + [sig[k] * sig[k + 1] for k in range(1, m)]
+    return c, alpha, beta
+
+
+def band_energy(H: DGHamiltonian, X, m, a, b, a0, Ne, kT):
+    """E = sum_i f_i lambda_i after one cycle with fixed bounds."""
+    Yt = chebyshev_filter(H, X, m, a, b, a0)
+    Yh, _, _ = cholesky_qr(Yt)
+    _, D, _ = rayleigh_ritz(H, Yh)
+    f, _ = fermi_occupations(D, Ne, kT)
+    return float(np.sum(f * D))
+
+
+def energy_weights(lam, f, kT):
+    """g_i = dE/dlambda_i with the Fermi level following the eigenvalues."""
+    fp = -f * (1.0 - f) / kT
+    s = fp.sum()
+    shift = (lam * fp).sum() / s if s != 0.0 else 0.0
+    return f + lam * fp - fp * shift
+
+
+def block_outer(H: DGHamiltonian, A, B, w=None):
+    """Per stored block (K, K'): sum_i w_i A[K rows, i] B[K' rows, i]^T."""
+    Aw = A if w is None else A * w[None, :]
+    out = []
+    for K in range(H.M):
+        for Kp, _ in H.neighbours(K):
+            out.append(Aw[H.rows(K)] @ B[H.rows(Kp)].T)
+    return out
+
+
+def band_energy_grad(H: DGHamiltonian, X, m, a, b, a0, Ne, kT):
+    """(E, G, Xbar): the band energy, dE/dH per stored block (list in block-CSR
+    order, each stored entry independent) and dE/dX (N x N_s)."""
+    c, alpha, beta = _recurrence_coefficients(m, a, b, a0)
+    Ys = [np.array(X, dtype=np.float64, copy=True)]
+    for k in range(m):
+        nxt = alpha[k] * (matvec(H, Ys[k]) - c * Ys[k])
+        if k > 0:
+            nxt -= beta[k] * Ys[k - 1]
+        Ys.append(nxt)
+    Yt = Ys[m]
+    Yh, U, _ = cholesky_qr(Yt)
+    Wh = matvec(H, Yh)
+    Hh = Yh.T @ Wh
+    lam, Q = np.linalg.eigh(0.5 * (Hh + Hh.T))
+    X_new, HX = Yh @ Q, Wh @ Q
+    f, _ = fermi_occupations(lam, Ne, kT)
+    E = float(np.sum(f * lam))
+    g = energy_weights(lam, f, kT)
+    # Rayleigh-Ritz part
+    G = block_outer(H, X_new, X_new, g)
+    Z = sla.solve_triangular(U, Q, lower=False)   # X_new = Y~ Z
+    R = HX - X_new * lam[None, :]
+    W_next = 2.0 * (R * g[None, :]) @ Z.T         # Y~bar
+    W_next2 = np.zeros_like(W_next)
+    # filter part: reverse recurrence
+    for k in range(m - 1, -1, -1):
+        for idx, blk in enumerate(block_outer(H, W_next, Ys[k])):
+            G[idx] = G[idx] + alpha[k] * blk
+        Wk = alpha[k] * (matvec(H, W_next) - c * W_next)
+        if k + 1 < m:
+            Wk -= beta[k + 1] * W_next2
+        W_next2, W_next = W_next, Wk
+    return E, G, W_next
+
+
+def tied_gradient(H: DGHamiltonian, G):
+    """dE for symmetric perturbations: for each stored block (K, K') the matrix
+    T with T[j, j'] = dE/d(H_KK'[j, j'] and H_K'K[j', j] together) =
+    G_KK'[j, j'] + G_K'K[j', j] (for K = K' the diagonal counts once)."""
+    index = {}
+    e = 0
+    for K in range(H.M):
+        for Kp, _ in H.neighbours(K):
+            index[(K, Kp)] = e
+            e += 1
+    out = []
+    for K in range(H.M):
+        for Kp, _ in H.neighbours(K):
+            t = G[index[(K, Kp)]] + G[index[(Kp, K)]].T
+            if K == Kp:
+                t = t - np.diag(np.diag(G[index[(K, K)]]))
+            out.append(t)
+    return out

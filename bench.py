@@ -31,6 +31,10 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 WORKLOAD = "bulk3d_8x8x8"
+# FP64 peak of the GB300 CUDA cores: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+# (the FP64 rate NVIDIA states for this part is 1.25 TFLOP/s; cuBLAS DGEMM
+# measured 1.10 TFLOP/s here).
+F64_PEAK_TFLOPS = 1.259
 METRIC = "CheFSI filter TFLOP/s + s per CheFSI cycle, mixed vs FP64 at Ritz err<=1e-8"
 
 
@@ -107,6 +111,27 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def profiled_traffic(prec: str, Ns: int):
+    """DRAM bytes per launch of the tensor-core filter step from the committed
+    ncu summary, if that summary was taken on the current kernel source (its
+    recorded source hash matches) for this precision; scaled to N_s (traffic
+    grows in proportion). None otherwise."""
+    import glob
+    import hashlib
+    src = os.path.join(ROOT, "paper_1606_03416_gb300", "csrc", "tc_filter.cu")
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    for path in glob.glob(os.path.join(ROOT, "profiles", f"k_filter_step_tc_{prec}_bulk3d_*.md")):
+        text = open(path).read()
+        if f"source-sha1 (paper_1606_03416_gb300/csrc/tc_filter.cu, first 12): {sha}" not in text:
+            continue
+        for line in text.splitlines():
+            key = f"traffic-per-launch-bytes-{prec}-Ns"
+            if line.startswith(key):
+                ns_ref = int(line[len(key):].split(":")[0])
+                return float(line.split(":")[1]) * Ns / ns_ref
+    return None
 
 
 def dist_env():
@@ -310,24 +335,64 @@ def main():
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    src = "measured (MEASURED_PEAKS.json)" if peaks else "fallback"
     byts = filter_bytes_per_step(H, Ns, args.prec)
     if args.prec == "f64":
-        roof = {"bound": "alu", "achieved": step_fl / (ms_launch * 1e-3) / 1e12, "peak": 1.25, "unit": "TFLOP/s"}
+        rf = {"bound": "alu", "achieved": step_fl / (ms_launch * 1e-3) / 1e12, "peak": F64_PEAK_TFLOPS,
+              "unit": "TFLOP/s"}
     else:
         mult = 3.0 if args.prec == "bf16x3" else 1.0
         tpeak = bf16_peak * (1.1 / 2.25) if args.prec == "tf32" else bf16_peak
         t_tensor = mult * step_fl / (tpeak * 1e12)
         t_hbm = byts / (hbm * 1e9)
         if t_hbm >= t_tensor:
-            roof = {"bound": "hbm", "achieved": byts / (ms_launch * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s"}
+            rf = {"bound": "hbm", "achieved": byts / (ms_launch * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s"}
         else:
-            roof = {"bound": "tensor", "achieved": mult * step_fl / (ms_launch * 1e-3) / 1e12, "peak": tpeak,
-                    "unit": "TFLOP/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
-    roof["kernel"] = "k_filter_step_tc" if args.prec != "f64" else "k_filter_step_f64"
-    roof["ms_per_launch"] = ms_launch
-    roof["peak_source"] = "measured (MEASURED_PEAKS.json)" if peaks else "fallback"
+            rf = {"bound": "tensor", "achieved": mult * step_fl / (ms_launch * 1e-3) / 1e12, "peak": tpeak,
+                  "unit": "TFLOP/s"}
+    rf["frac"] = rf["achieved"] / rf["peak"]
+    rf["traffic"] = profiled_traffic(args.prec, Ns) if args.prec != "f64" else None
+    rf["algorithmic_bytes"] = byts
+    rf["kernel"] = "k_filter_step_tc" if args.prec != "f64" else "k_filter_step_f64"
+    rf["ms_per_launch"] = ms_launch
+    rf["peak_source"] = src + (" x 1.1/2.25 (nominal TF32/BF16 ratio)" if args.prec == "tf32" else "")
+
+    # ---- the cycle's dominant kernel: the FP64 N_s x N_s products of Rayleigh-Ritz
+    # (k_gemm_nt_f64 / k_gemm_nn_f64); timed through dgchefsi_gram, one launch of k_gemm_nt_f64.
+    S = torch.empty((Ns, Ns), dtype=torch.float64, device=dev)
+    gms = []
+    for _ in range(3):
+        s_, e_ = ev(), ev()
+        torch.cuda.synchronize()
+        s_.record(stream)
+        ctx.gram(Xs, S)
+        e_.record(stream)
+        torch.cuda.synchronize()
+        gms.append(s_.elapsed_time(e_))
+    nt = (Ns + 63) // 64
+    gram_fl = 2.0 * (nt * (nt + 1) // 2) * 64 * 64 * N
+    g_ach = gram_fl / (statistics.median(gms) * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": g_ach, "peak": F64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": g_ach / F64_PEAK_TFLOPS, "traffic": None, "kernel": "k_gemm_nt_f64",
+            "ms_per_launch": statistics.median(gms),
+            "peak_source": "FP64 DFMA peak derived in DESIGN.md (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz); "
+                           "cuBLAS DGEMM measured 1.10 TFLOP/s on this GB300"}
+
+    # ---- filter throughput of the other tensor-core precisions (filter alone)
+    other = {}
+    for pr in ("bf16", "bf16x3", "tf32"):
+        if pr == args.prec or args.prec == "f64":
+            continue
+        ts_ = []
+        for _ in range(2):
+            s_, e_ = ev(), ev()
+            torch.cuda.synchronize()
+            s_.record(stream)
+            ctx.filter(Xs, m, 10.0, 45.0, -2.0, prec=pr, Y=Yd)
+            e_.record(stream)
+            torch.cuda.synchronize()
+            ts_.append(s_.elapsed_time(e_))
+        other[pr] = fl / (min(ts_) * 1e-3) / 1e12
 
     # ---- end to end: pinned host X -> device, filter, Y -> host
     Xh = torch.from_numpy(X0).pin_memory()
@@ -383,7 +448,8 @@ def main():
         "s_per_cycle": {"mixed": ms_step / 1e3, "f64": f64.get("s_per_cycle")},
         "filter_ms": ms_filter,
         "ritz_err_mixed_vs_f64_first_cycle": f64.get("ritz_err_first_cycle"),
-        "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "roofline": roof, "roofline_filter": rf, "filter_tflops_other_precisions": other,
+        "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ts, nnz = oracle_sample(args.ref_states, m, reps=1)

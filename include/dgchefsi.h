@@ -143,6 +143,12 @@ dgchefsi_status dgchefsi_bounds_static(dgchefsi_ctx* ctx, const double* v0, int 
 dgchefsi_status dgchefsi_filter(dgchefsi_ctx* ctx, int prec, const double* X, double* Y,
                                 int64_t Ns, int64_t ld, int m, double a, double b, double a0);
 
+/* Overlap matrix S = Y^T Y of a block (the first product of Cholesky-QR,
+ * Alg. 1 step 3), FP64: the tiles on and below the diagonal are computed and
+ * mirrored, so S is exactly symmetric.
+ *   Y  device (Ns x ld) state-major;  S  device out, row-major Ns x Ns. */
+dgchefsi_status dgchefsi_gram(dgchefsi_ctx* ctx, const double* Y, int64_t Ns, int64_t ld, double* S);
+
 /* Cholesky-QR and Rayleigh-Ritz (Alg. 1 steps 3-5; Sec. III.B.2), all FP64:
  *   S = Y^T Y, S = U^T U, Y_hat = Y U^{-1};  H_hat = Y_hat^T (H Y_hat), symmetrised;
  *   H_hat Q = Q D (D ascending);  X_new = Y_hat Q.
@@ -187,6 +193,30 @@ dgchefsi_status dgchefsi_cycle(dgchefsi_ctx* ctx, int prec, double* X, int64_t N
                                double Ne, double kT, const double* v0, int k_lanczos,
                                const double* prev_ritz, double* bounds, int use_bounds,
                                double* ritz, double* f, double* mu, double* P);
+
+/* Replace the values of H (same block pattern) from a device array laid out
+ * like `values` at create: [n_values] doubles. The caller keeps H symmetric
+ * (not re-checked). Operand copies used by the tensor-core filter are rebuilt. */
+dgchefsi_status dgchefsi_set_values(dgchefsi_ctx* ctx, const double* values);
+
+/* Band energy of one cycle and its gradient. The paper does not differentiate
+ * the cycle; this is the adjoint of its steps: E = sum_i f_i lambda_i after
+ * Alg. 1 steps 2-5 and the Fermi occupations, with (a, b, a0), Ne and kT fixed.
+ *   prec               DGCHEFSI_F64 (the only form this build differentiates)
+ *   X                  device (Ns x ld) starting block
+ *   checkpoint_stride  s: iterate pairs kept every s filter steps, each
+ *                      segment recomputed backwards (0 = ceil(sqrt(m)))
+ *   energy             host out: E
+ *   ritz               device [Ns] out or NULL
+ *   H_bar              device [n_values] out or NULL: dE/dH for every stored
+ *                      entry taken as independent (a symmetric perturbation of
+ *                      H_KK'[j,j'] = H_K'K[j',j] changes E by the sum of the two
+ *                      entries' values)
+ *   X_bar              device (Ns x ld) out or NULL: dE/dX
+ * With H_bar and X_bar both NULL only E (and ritz) are computed. Synchronises. */
+dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, const double* X, int64_t Ns, int64_t ld, int m,
+                                     double a, double b, double a0, double Ne, double kT, int checkpoint_stride,
+                                     double* energy, double* ritz, double* H_bar, double* X_bar);
 
 /* Message describing the last error on the calling thread ("" if none). */
 const char* dgchefsi_last_error(void);

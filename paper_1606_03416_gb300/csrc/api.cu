@@ -373,9 +373,15 @@ dgchefsi_status dgchefsi_create(int32_t M, const int32_t* nb, const int64_t* row
       (st = dmalloc((void**)&ctx->blk_off_d, sizeof(int64_t) * ctx->nnzb)) ||
       (st = dmalloc((void**)&ctx->vals_d, sizeof(double) * n_values)) ||
       (st = dmalloc((void**)&ctx->poff_d, sizeof(int64_t) * (M + 1))) ||
+      (st = dmalloc((void**)&ctx->blk_row_d, sizeof(int32_t) * std::max<int64_t>(ctx->nnzb, 1))) ||
       (st = dmalloc((void**)&ctx->info_d, sizeof(int) * 4)))
     return bail(st);
   auto h2d = [&](void* d, const void* h, size_t bytes) { return cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice); };
+  std::vector<int32_t> blk_row(ctx->nnzb);
+  for (int K = 0; K < M; ++K)
+    for (int64_t e = row_ptr[K]; e < row_ptr[K + 1]; ++e) blk_row[e] = K;
+  if (ctx->nnzb > 0 && h2d(ctx->blk_row_d, blk_row.data(), sizeof(int32_t) * ctx->nnzb))
+    return bail(set_error(DGCHEFSI_ERR_CUDA, "copy of the block rows to the device failed"));
   if (h2d(ctx->nb_d, nb, sizeof(int32_t) * M) || h2d(ctx->off_d, ctx->off_h.data(), sizeof(int64_t) * (M + 1)) ||
       h2d(ctx->row_ptr_d, row_ptr, sizeof(int64_t) * (M + 1)) || h2d(ctx->col_d, col, sizeof(int32_t) * ctx->nnzb) ||
       h2d(ctx->blk_off_d, blk_off, sizeof(int64_t) * ctx->nnzb) ||
@@ -400,6 +406,7 @@ void dgchefsi_destroy(dgchefsi_ctx* ctx) {
   cudaFree(ctx->blk_off_d);
   cudaFree(ctx->vals_d);
   cudaFree(ctx->poff_d);
+  cudaFree(ctx->blk_row_d);
   cudaFree(ctx->info_d);
   free_buf(ctx->ws_filter);
   free_buf(ctx->ws_rr);
@@ -407,6 +414,7 @@ void dgchefsi_destroy(dgchefsi_ctx* ctx) {
   free_buf(ctx->ws_solver);
   free_buf(ctx->ws_cycle);
   free_buf(ctx->ws_lanczos);
+  free_buf(ctx->ws_adjoint);
   delete ctx;
 }
 
@@ -464,6 +472,15 @@ dgchefsi_status dgchefsi_filter(dgchefsi_ctx* ctx, int prec, const double* X, do
   if (Ns == 0) return DGCHEFSI_OK;
   if (prec == DGCHEFSI_F64) return filter_f64(ctx, X, Y, Ns, ld, m, a, b, a0);
   return filter_tc(ctx, prec, X, Y, Ns, ld, m, a, b, a0);
+}
+
+dgchefsi_status dgchefsi_gram(dgchefsi_ctx* ctx, const double* Y, int64_t Ns, int64_t ld, double* S) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  DG_TRY(check_block(ctx, Y, Ns, ld, "Y"));
+  if (Ns > 0 && !S) return set_error(DGCHEFSI_ERR_ARG, "null S");
+  DG_CUDA(gemm_nt_f64(Y, ld, Y, ld, S, Ns, Ns, Ns, ctx->N, true, false, ctx->stream));
+  return DGCHEFSI_OK;
 }
 
 dgchefsi_status dgchefsi_rayleigh_ritz(dgchefsi_ctx* ctx, double* Y, int64_t Ns, int64_t ld, double* ritz) {

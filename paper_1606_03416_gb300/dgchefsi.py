@@ -27,7 +27,7 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_SPD", 
 EXPORTS = ["dgchefsi_create", "dgchefsi_destroy", "dgchefsi_set_stream", "dgchefsi_dims", "dgchefsi_matvec",
            "dgchefsi_bounds", "dgchefsi_filter", "dgchefsi_rayleigh_ritz", "dgchefsi_occupations",
            "dgchefsi_density_blocks", "dgchefsi_cycle", "dgchefsi_last_error", "dgchefsi_launch_count",
-           "dgchefsi_bounds_static"]
+           "dgchefsi_bounds_static", "dgchefsi_gram", "dgchefsi_set_values", "dgchefsi_energy_grad"]
 
 # Capacity (doubles) of the library's fixed scratch array for bounds_static.
 BOUNDS_STATIC_DOUBLES = 1 << 20
@@ -55,6 +55,9 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_bounds_static": (st, [P, P, C.c_int, P, P]),
         "dgchefsi_filter": (st, [P, C.c_int, P, P, I64, I64, C.c_int, D, D, D]),
         "dgchefsi_rayleigh_ritz": (st, [P, P, I64, I64, P]),
+        "dgchefsi_gram": (st, [P, P, I64, I64, P]),
+        "dgchefsi_set_values": (st, [P, P]),
+        "dgchefsi_energy_grad": (st, [P, C.c_int, P, I64, I64, C.c_int, D, D, D, D, D, C.c_int, P, P, P, P]),
         "dgchefsi_occupations": (st, [P, P, I64, D, D, P, P]),
         "dgchefsi_density_blocks": (st, [P, P, I64, I64, P, P]),
         "dgchefsi_cycle": (st, [P, C.c_int, P, I64, I64, C.c_int, D, D, P, C.c_int, P, P, C.c_int, P, P, P, P]),
@@ -122,6 +125,7 @@ class Context:
         _check(_lib.dgchefsi_dims(h, C.byref(N), C.byref(M)))
         self.N, self.M = int(N.value), int(M.value)
         self.nb = nb
+        self.n_values = int(values.shape[0])
         self.density_offsets = np.concatenate([[0], np.cumsum(nb.astype(np.int64) ** 2)])
 
     def close(self):
@@ -189,6 +193,15 @@ class Context:
                                     float(b), float(a0)))
         return Y
 
+    # -- Alg. 1 step 3, first product
+    def gram(self, Y: torch.Tensor, S: torch.Tensor | None = None) -> torch.Tensor:
+        Ns, ld = _block(Y, self.N, "Y")
+        if S is None:
+            S = torch.empty((Ns, Ns), dtype=torch.float64, device=Y.device)
+        self._sync_stream()
+        _check(_lib.dgchefsi_gram(self._h, _ptr(Y), Ns, ld, _ptr(S)))
+        return S
+
     # -- Alg. 1 steps 3-5 (in place: Y becomes X_new)
     def rayleigh_ritz(self, Y: torch.Tensor, ritz: torch.Tensor | None = None) -> torch.Tensor:
         Ns, ld = _block(Y, self.N, "Y")
@@ -212,6 +225,31 @@ class Context:
         self._sync_stream()
         _check(_lib.dgchefsi_density_blocks(self._h, _ptr(X), Ns, ld, _ptr(f), _ptr(P)))
         return P
+
+    # -- differentiation of one cycle (band energy)
+    def set_values(self, values: torch.Tensor):
+        """Replace H's stored values from a float64 CUDA tensor [n_values]."""
+        if not (values.is_cuda and values.dtype == torch.float64 and values.is_contiguous()):
+            raise TypeError("values must be a contiguous float64 CUDA tensor")
+        self._sync_stream()
+        _check(_lib.dgchefsi_set_values(self._h, _ptr(values)))
+
+    def energy_grad(self, X: torch.Tensor, m: int, a: float, b: float, a0: float, Ne: float, kT: float,
+                    grad: bool = True, stride: int = 0, n_values: int | None = None):
+        """(E, ritz, H_bar, X_bar) of one cycle's band energy; H_bar and X_bar are
+        None when grad is False. H_bar is per stored entry (entries independent)."""
+        Ns, ld = _block(X, self.N, "X")
+        dev = X.device
+        ritz = torch.empty(Ns, dtype=torch.float64, device=dev)
+        Hb = torch.empty(int(n_values if n_values is not None else self.n_values), dtype=torch.float64,
+                         device=dev) if grad else None
+        Xb = torch.empty_like(X) if grad else None
+        E = C.c_double()
+        self._sync_stream()
+        _check(_lib.dgchefsi_energy_grad(self._h, 0, _ptr(X), Ns, ld, int(m), float(a), float(b), float(a0),
+                                         float(Ne), float(kT), int(stride), C.byref(E), _ptr(ritz),
+                                         _ptr(Hb) if grad else None, _ptr(Xb) if grad else None))
+        return E.value, ritz, Hb, Xb
 
     def unpack_density(self, P: torch.Tensor):
         o = self.density_offsets

@@ -128,6 +128,16 @@ def test_rayleigh_ritz_occupations_density(cfg, dev):
         assert np.linalg.norm(P.cpu().numpy() - Po) <= 1e-9 * np.linalg.norm(Po)
 
 
+@pytest.mark.parametrize("cfg", problems(), ids=lambda c: c.name)
+def test_gram(cfg, dev):
+    H, Ho, X0, _, Ns, _ = problem(cfg)
+    with D.Context(H) as ctx:
+        S = ctx.gram(torch.from_numpy(X0).to(dev)).cpu().numpy()
+    Yt, _, So = None, None, O.cholesky_qr(X0.T)[2]
+    assert np.array_equal(S, S.T)
+    assert rel_max(S, So) <= 1e-12
+
+
 def test_occupations_and_density_on_oracle_inputs(dev):
     H, Ho, X0, _, Ns, Ne = problem(problems()[2])
     rng = np.random.default_rng(3)

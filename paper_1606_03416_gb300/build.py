@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgchefsi.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "f64_kernels.cu", "tc_filter.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "f64_kernels.cu", "tc_filter.cu", "noalloc.cu", "adjoint.cu"]
 
 
 def nvcc() -> str:

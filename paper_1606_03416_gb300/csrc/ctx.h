@@ -41,6 +41,7 @@ struct dgchefsi_ctx {
   int64_t* blk_off_d = nullptr;
   double* vals_d = nullptr;
   int64_t* poff_d = nullptr;  // packed density-block offsets
+  int32_t* blk_row_d = nullptr;  // element row of each stored block
   // workspace
   dg::DevBuf ws_filter;   // filter ping-pong partner (Ns x ld FP64)
   dg::DevBuf ws_rr;       // Rayleigh-Ritz block (Ns x N FP64)
@@ -48,6 +49,7 @@ struct dgchefsi_ctx {
   dg::DevBuf ws_solver;   // cuSOLVER device workspace
   dg::DevBuf ws_cycle;    // filtered block inside dgchefsi_cycle
   dg::DevBuf ws_lanczos;  // Lanczos basis and scalars
+  dg::DevBuf ws_adjoint;  // checkpoints and blocks of the band-energy gradient
   std::vector<char> solver_host;
   int* info_d = nullptr;  // [4] cuSOLVER infos + finite flag
   cusolverDnHandle_t solver = nullptr;

@@ -378,6 +378,114 @@ __global__ void k_check_finite_f64(const double* __restrict__ x, int64_t n, int*
     if (!isfinite(x[i])) atomicOr(flag, 1);
 }
 
+
+// G_e += alpha * sum_s w_s A[s, off_K + j] B[s, off_K' + j'] for every stored
+// block e = (K, K') (w may be null: unit weights).
+__global__ void __launch_bounds__(NT) k_block_outer_f64(HView h, const int32_t* __restrict__ blk_row,
+                                                        const double* __restrict__ A, int64_t lda,
+                                                        const double* __restrict__ B, int64_t ldb,
+                                                        const double* __restrict__ w, double alpha, int64_t Ns,
+                                                        double* __restrict__ G) {
+  const int64_t e = blockIdx.x;
+  const int K = blk_row[e], Kp = h.col[e];
+  const int nK = h.nb[K], nKp = h.nb[Kp];
+  const int j0 = blockIdx.y * T, jp0 = blockIdx.z * T;
+  if (j0 >= nK || jp0 >= nKp) return;
+  const int64_t offK = h.off[K], offKp = h.off[Kp];
+  __shared__ double As[BK][TP];
+  __shared__ double Bs[BK][TP];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  const int cc = tid & 63;
+  for (int64_t i0 = 0; i0 < Ns; i0 += BK) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int kk = (tid >> 6) + 4 * i;
+      const int64_t s = i0 + kk;
+      double v = 0.0, u = 0.0;
+      if (s < Ns) {
+        if (j0 + cc < nK) v = (w ? w[s] : 1.0) * A[s * lda + offK + j0 + cc];
+        if (jp0 + cc < nKp) u = B[s * ldb + offKp + jp0 + cc];
+      }
+      As[kk][cc] = v;
+      Bs[kk][cc] = u;
+    }
+    __syncthreads();
+    fma_tile(As, Bs, acc, tx, ty);
+    __syncthreads();
+  }
+  double* Ge = G + h.blk_off[e];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int jj = j0 + ty + 16 * i;
+    if (jj >= nK) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int jq = jp0 + tx + 16 * j;
+      if (jq < nKp) Ge[(int64_t)jj * nKp + jq] += alpha * acc[i][j];
+    }
+  }
+}
+
+// C[i,r] = sum_l A[l,i] B[l,r]  (A: K x rows, B: K x cols, both row-major)
+__global__ void __launch_bounds__(NT) k_gemm_tn_f64(const double* __restrict__ A, int64_t lda,
+                                                    const double* __restrict__ B, int64_t ldb,
+                                                    double* __restrict__ C, int64_t ldc, int64_t rows,
+                                                    int64_t cols, int64_t K) {
+  const int64_t i0 = (int64_t)blockIdx.y * T, r0 = (int64_t)blockIdx.x * T;
+  __shared__ double As[BK][TP];
+  __shared__ double Bs[BK][TP];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  const int cc = tid & 63;
+  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int kk = (tid >> 6) + 4 * i;
+      const int64_t l = k0 + kk;
+      double v = 0.0, u = 0.0;
+      if (l < K) {
+        if (i0 + cc < rows) v = A[l * lda + i0 + cc];
+        if (r0 + cc < cols) u = B[l * ldb + r0 + cc];
+      }
+      As[kk][cc] = v;
+      Bs[kk][cc] = u;
+    }
+    __syncthreads();
+    fma_tile(As, Bs, acc, tx, ty);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t ii = i0 + ty + 16 * i;
+    if (ii >= rows) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t rr = r0 + tx + 16 * j;
+      if (rr < cols) C[ii * ldc + rr] = acc[i][j];
+    }
+  }
+}
+
+// out[i, r] = scale * g[i] * (HX[i, r] - lam[i] * X[i, r]) for r < n
+__global__ void k_scaled_residual_f64(const double* __restrict__ HX, const double* __restrict__ X, int64_t ld,
+                                      const double* __restrict__ lam, const double* __restrict__ g, double scale,
+                                      int64_t Ns, int64_t n, double* __restrict__ out, int64_t ldo) {
+  const int64_t i = blockIdx.y;
+  if (i >= Ns) return;
+  const double gi = scale * g[i], li = lam[i];
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    out[i * ldo + r] = gi * (HX[i * ld + r] - li * X[i * ld + r]);
+}
+
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 inline unsigned stream_grid(int64_t n) {
   int64_t g = (n + 255) / 256;
@@ -466,6 +574,35 @@ cudaError_t occupations_f64(const double* ritz, int64_t Ns, double Ne, double kT
 cudaError_t zero_strict_upper_f64(double* A, int64_t n, int64_t lda, cudaStream_t s) {
   dim3 b(32, 8), g(cdiv(n, 32), cdiv(n, 8));
   k_zero_strict_upper_f64<<<g, b, 0, s>>>(A, n, lda);
+  count_launch();
+  return cudaGetLastError();
+}
+
+
+cudaError_t block_outer_f64(const HView& h, const int32_t* blk_row, int64_t nnzb, const double* A, int64_t lda,
+                            const double* B, int64_t ldb, const double* w, double alpha, int64_t Ns, double* G,
+                            cudaStream_t s) {
+  if (nnzb == 0) return cudaSuccess;
+  dim3 grid((unsigned)nnzb, cdiv(h.max_nb, T), cdiv(h.max_nb, T));
+  k_block_outer_f64<<<grid, NT, 0, s>>>(h, blk_row, A, lda, B, ldb, w, alpha, Ns, G);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_tn_f64(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                        int64_t rows, int64_t cols, int64_t K, cudaStream_t s) {
+  if (rows == 0 || cols == 0) return cudaSuccess;
+  dim3 grid(cdiv(cols, T), cdiv(rows, T));
+  k_gemm_tn_f64<<<grid, NT, 0, s>>>(A, lda, B, ldb, C, ldc, rows, cols, K);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t scaled_residual_f64(const double* HX, const double* X, int64_t ld, const double* lam, const double* g,
+                                double scale, int64_t Ns, int64_t n, double* out, int64_t ldo, cudaStream_t s) {
+  if (Ns == 0) return cudaSuccess;
+  dim3 grid(cdiv(n, 256) > 64 ? 64 : cdiv(n, 256), (unsigned)Ns);
+  k_scaled_residual_f64<<<grid, 256, 0, s>>>(HX, X, ld, lam, g, scale, Ns, n, out, ldo);
   count_launch();
   return cudaGetLastError();
 }

@@ -55,6 +55,18 @@ cudaError_t density_f64(const HView& h, const int64_t* poff, const double* X, in
 cudaError_t occupations_f64(const double* ritz, int64_t Ns, double Ne, double kT, double* f, double* mu,
                             cudaStream_t s);
 
+// G_e += alpha * sum_s w_s A[s, off_K + j] B[s, off_K' + j'] for every stored block e = (K, K')
+// (values layout of H; w may be null).
+cudaError_t block_outer_f64(const HView& h, const int32_t* blk_row, int64_t nnzb, const double* A, int64_t lda,
+                            const double* B, int64_t ldb, const double* w, double alpha, int64_t Ns, double* G,
+                            cudaStream_t s);
+// C[i,r] = sum_l A[l,i] B[l,r]  (A: K x rows row-major, B: K x cols row-major).
+cudaError_t gemm_tn_f64(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                        int64_t rows, int64_t cols, int64_t K, cudaStream_t s);
+// out[i, r] = scale * g[i] * (HX[i, r] - lam[i] X[i, r]) for r < n.
+cudaError_t scaled_residual_f64(const double* HX, const double* X, int64_t ld, const double* lam, const double* g,
+                                double scale, int64_t Ns, int64_t n, double* out, int64_t ldo, cudaStream_t s);
+
 // Zero the strict upper triangle of a row-major n x n matrix.
 cudaError_t zero_strict_upper_f64(double* A, int64_t n, int64_t lda, cudaStream_t s);
 // flag[0] |= 1 if any of x[0..n) is not finite.

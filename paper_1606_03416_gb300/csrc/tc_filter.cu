@@ -258,9 +258,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                      const __grid_constant__ CUtensorMap tmB, const Params p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  constexpr int S = STAGES;
+  // BF16X3 keeps the hi and lo copies of both operands in one ring slot (its
+  // three products reuse them), so its slots are twice as large and half as many.
+  constexpr int NA = MODE_ == MODE_BF16X3 ? 2 : 1;
+  constexpr int S = MODE_ == MODE_BF16X3 ? STAGES / 2 : STAGES;
   constexpr int b_bytes = ACC * SLICE_BYTES;  // one element's B tile: ACC rows of 128 bytes
-  constexpr int stage_bytes = T * A_BYTES + G * b_bytes;
+  constexpr int a_part = NA * T * A_BYTES;    // [A hi x T][A lo x T]
+  constexpr int stage_bytes = a_part + NA * G * b_bytes;  // then [B hi x G][B lo x G]
   constexpr uint32_t NMMA = (uint32_t)(G * ACC);  // the G elements' B tiles are stacked along N
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
   // per-role copies of the current group's slice entries (producer, MMA issuer)
@@ -270,7 +274,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ int abort_sh;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int npass = MODE_ == MODE_BF16X3 ? 3 : 1;
   const int nunits = p.ngroups * p.ntg;
   const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * S;
   const uint32_t accf0 = empty0 + 8 * S, acce0 = accf0 + 16;
@@ -318,7 +321,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int e = 0; e < ne && ok; ++e) {
           const int32_t* ent = sched_sh0 + e * (1 + G);
           const int ax = ent[0];
-          for (int pass = 0; pass < npass; ++pass) {
+          {
             const int st = c & (S - 1);
             const uint32_t ph = (uint32_t)(c / S) & 1u;
             if (!mbar_wait(empty0 + 8 * st, ph ^ 1u)) {
@@ -328,14 +331,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t fb = full0 + 8 * st;
             mbar_expect_tx(fb, (uint32_t)stage_bytes);
             uint8_t* sst = smem + st * stage_bytes;
-            for (int t = 0; t < T; ++t)
-              tma_load_2d(smem_u32(sst + t * A_BYTES), (MODE_ == MODE_BF16X3 && pass == 2) ? &tmA1 : &tmA0, ax, s0 + BM * t, fb);
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-              const int r = ent[1 + g];  // a zero block when element g does not couple to this slice
-              tma_load_2d(smem_u32(sst + T * A_BYTES + g * b_bytes), &tmB, 0,
-                          (int)(r + (pass == 1 ? p.lo_rows : 0)), fb);
-            }
+            for (int v = 0; v < NA; ++v)
+#pragma unroll
+              for (int t = 0; t < T; ++t)
+                tma_load_2d(smem_u32(sst + (v * T + t) * A_BYTES), v == 1 ? &tmA1 : &tmA0, ax, s0 + BM * t, fb);
+#pragma unroll
+            for (int v = 0; v < NA; ++v)
+#pragma unroll
+              for (int g = 0; g < G; ++g) {
+                const int r = ent[1 + g];  // a zero block when element g does not couple to this slice
+                tma_load_2d(smem_u32(sst + a_part + (v * G + g) * b_bytes), &tmB, 0,
+                            (int)(r + (v == 1 ? p.lo_rows : 0)), fb);
+              }
             ++c;
           }
         }
@@ -374,33 +382,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint32_t dbuf = tmem + (uint32_t)(buf * T * G * ACC);
         uint32_t first = 0;  // the unit's first slice overwrites the accumulators
         for (int e = 0; e < ne && ok; ++e) {
+          const int st = c & (S - 1);
+          const uint32_t ph = (uint32_t)(c / S) & 1u;
+          if (!mbar_wait(full0 + 8 * st, ph)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t da = desc0 + (uint64_t)((st * stage_bytes) >> 4);  // A hi
+          const uint64_t db = da + (uint64_t)(a_part >> 4);                   // B hi
 #pragma unroll
-          for (int pass = 0; pass < npass; ++pass) {
-            const int st = c & (S - 1);
-            const uint32_t ph = (uint32_t)(c / S) & 1u;
-            if (!mbar_wait(full0 + 8 * st, ph)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const uint64_t da = desc0 + (uint64_t)((st * stage_bytes) >> 4);
-            const uint64_t db = da + (uint64_t)((T * A_BYTES) >> 4);
+          for (int t = 0; t < T; ++t) {
+            const uint32_t d = dbuf + (uint32_t)(t * G * ACC);
 #pragma unroll
-            for (int t = 0; t < T; ++t) {
-              const uint32_t d = dbuf + (uint32_t)(t * G * ACC);
-#pragma unroll
-              for (int kk = 0; kk < SLICE_BYTES / 32; ++kk) {
-                const uint64_t ad = da + (uint64_t)((t * A_BYTES + 32 * kk) >> 4);
-                const uint64_t bd = db + (uint64_t)((32 * kk) >> 4);
-                const uint32_t acc = kk > 0 ? 1u : first;
-                if constexpr (MODE_ == MODE_TF32) mma_tf32(d, ad, bd, ID, acc);
-                else mma_bf16(d, ad, bd, ID, acc);
+            for (int kk = 0; kk < SLICE_BYTES / 32; ++kk) {
+              const uint64_t ad = da + (uint64_t)((t * A_BYTES + 32 * kk) >> 4);
+              const uint64_t bd = db + (uint64_t)((32 * kk) >> 4);
+              const uint32_t acc = kk > 0 ? 1u : first;
+              if constexpr (MODE_ == MODE_TF32) {
+                mma_tf32(d, ad, bd, ID, acc);
+              } else {
+                mma_bf16(d, ad, bd, ID, acc);
+                if constexpr (MODE_ == MODE_BF16X3) {
+                  // hi * lo(H) and lo * hi(H)
+                  mma_bf16(d, ad, bd + (uint64_t)((G * b_bytes) >> 4), ID, 1u);
+                  mma_bf16(d, ad + (uint64_t)((T * A_BYTES) >> 4), bd, ID, 1u);
+                }
               }
             }
-            first = 1u;
-            mma_commit(empty0 + 8 * st);
-            ++c;
           }
+          first = 1u;
+          mma_commit(empty0 + 8 * st);
+          ++c;
         }
         mma_commit(accf0 + 8 * buf);
       }
@@ -790,8 +803,9 @@ dgchefsi_status filter_tc(dgchefsi_ctx* ctx, int prec, const double* X, double* 
   const uint64_t brows_total = (uint64_t)t.b_rows * (mode == MODE_BF16X3 ? 2 : 1);
   DG_TRY(make_map(&mapB, t.Hop.p, f32, (uint64_t)W, brows_total, (uint32_t)W, (uint32_t)t.boxn));
 
-  const int stage_bytes = t.T * A_BYTES + t.G * t.ACC * SLICE_BYTES;
-  const int stages = STAGES;
+  const int na = mode == MODE_BF16X3 ? 2 : 1;
+  const int stage_bytes = na * (t.T * A_BYTES + t.G * t.ACC * SLICE_BYTES);
+  const int stages = mode == MODE_BF16X3 ? STAGES / 2 : STAGES;
   const int smem = stages * stage_bytes + (2 * stages + 4) * 8 + 2 * t.maxent * (1 + t.G) * 4 + 1024;
   if (smem > 227 * 1024) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "filter schedule too large for shared memory");
   auto kern = pick_kernel(mode, t.G, t.T, t.ACC);

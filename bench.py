@@ -221,6 +221,42 @@ def run_filter_only(args):
     return 0
 
 
+def measure_uneven(dev, precs=("bf16x3", "tf32"), reps=3):
+    """The graphene-like 2D sheet with uneven element sizes (24 x 20 elements,
+    9-neighbour stencil, n_b ~ U{40..120}, N_s = floor(0.55 N), m = 16): every
+    element size runs in one persistent launch per step, the unit shape is
+    autotuned, and the whole filter is replayed from a CUDA graph."""
+    import torch
+    from paper_1606_03416_gb300 import dgchefsi as D
+    from paper_1606_03416_gb300 import inputs as G
+    cfg = G.CONFIGS["sheet2d_24x20"]
+    H = G.make_blocks(cfg)
+    Ns, _ = G.resolve_sizes(cfg, H)
+    X = torch.from_numpy(G.make_X(H.N, Ns, cfg.seed)).to(dev)
+    Y = torch.empty_like(X)
+    fl = filter_flops(H, Ns, cfg.m)
+    out = {"workload": "sheet2d_24x20", "N": H.N, "Ns": Ns, "m": cfg.m, "nb_range": [int(H.nb.min()), int(H.nb.max())],
+           "filter_gflop": fl / 1e9}
+    with D.Context(H) as ctx:
+        for pr in precs:
+            ctx.filter_graph(X, cfg.m, 10.0, 45.0, -2.0, prec=pr, Y=Y)   # tunes, captures
+            ts = []
+            for _ in range(reps):
+                s_, e_ = torch.cuda.Event(True), torch.cuda.Event(True)
+                torch.cuda.synchronize()
+                s_.record()
+                ctx.filter_graph(X, cfg.m, 10.0, 45.0, -2.0, prec=pr, Y=Y)
+                e_.record()
+                torch.cuda.synchronize()
+                ts.append(s_.elapsed_time(e_))
+            g_, t_, acc = ctx.tile_shape(pr)
+            out[pr] = {"ms_per_filter": min(ts), "tflops": fl / (min(ts) * 1e-3) / 1e12,
+                       "unit_shape": {"G": g_, "T": t_, "ACC": acc}, "graph": True}
+    del X, Y
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -231,6 +267,7 @@ def main():
     ap.add_argument("--f64-steps", type=int, default=1, help="FP64 cycles timed for the per-cycle comparison")
     ap.add_argument("--ref-states", type=int, default=64, help="states in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-n_b 2D sheet measurement")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--filter-only", action="store_true",
                     help="time only the filter (profiling case); --ns and --m override the workload")
@@ -435,6 +472,7 @@ def main():
         rmx = ctx.rayleigh_ritz(Yb)
         scale = max(abs(a0), abs(b))
         f64["ritz_err_first_cycle"] = float((rmx - r64).abs().max().item() / scale)
+        Xa = Ya = Xb = Yb = None
 
     clocks = clk.summary()
     line = {
@@ -451,6 +489,11 @@ def main():
         "roofline": roof, "roofline_filter": rf, "filter_tflops_other_precisions": other,
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }
+    ctx.close()
+    X = Y = Xd = Yd = Xs = Xh = Yh = S = None  # free the 8x8x8 buffers before the next workload
+    torch.cuda.empty_cache()
+    if not args.no_uneven and args.prec != "f64":
+        line["batched_uneven"] = measure_uneven(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ts, nnz = oracle_sample(args.ref_states, m, reps=1)
         cv = 2.0 * nnz * args.ref_states * m / ts[0] / 1e12
@@ -459,7 +502,6 @@ def main():
                                           f"one BLAS thread, {ts[0]:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

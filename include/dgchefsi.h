@@ -143,6 +143,26 @@ dgchefsi_status dgchefsi_bounds_static(dgchefsi_ctx* ctx, const double* v0, int 
 dgchefsi_status dgchefsi_filter(dgchefsi_ctx* ctx, int prec, const double* X, double* Y,
                                 int64_t Ns, int64_t ld, int m, double a, double b, double a0);
 
+/* The tensor-core filter of dgchefsi_filter (same arguments, results and
+ * synchronisation), replayed from a CUDA graph: the first call for a given
+ * (prec, X, Y, Ns, ld, m) tunes the unit shape if needed, captures the whole
+ * launch sequence (operand copy of H, packing, the m steps, unpacking) and
+ * later calls only update the recurrence coefficients and relaunch the graph.
+ * Every element size runs in the same persistent grouped launch per step.
+ * prec must be a tensor-core precision (DGCHEFSI_ERR_UNSUPPORTED for F64). */
+dgchefsi_status dgchefsi_filter_graph(dgchefsi_ctx* ctx, int prec, const double* X, double* Y, int64_t Ns,
+                                      int64_t ld, int m, double a, double b, double a0);
+
+/* Work-unit shape of the tensor-core filter for one precision: G consecutive
+ * elements x T tiles of 128 states per unit (G*T accumulators of ACC columns
+ * in tensor memory). By default (G = T = 0) the first filter call times one
+ * step with every shape that has a kernel for this H's accumulator width
+ * (ACC = 32, 64 or 128, from the largest element) and keeps the fastest.
+ * Setting a shape that has no kernel returns DGCHEFSI_ERR_UNSUPPORTED. */
+dgchefsi_status dgchefsi_set_tile_shape(dgchefsi_ctx* ctx, int prec, int G, int T);
+/* The shape in use (0, 0 if not chosen yet) and the accumulator width. */
+dgchefsi_status dgchefsi_get_tile_shape(dgchefsi_ctx* ctx, int prec, int* G, int* T, int* ACC);
+
 /* Overlap matrix S = Y^T Y of a block (the first product of Cholesky-QR,
  * Alg. 1 step 3), FP64: the tiles on and below the diagonal are computed and
  * mirrored, so S is exactly symmetric.
@@ -217,6 +237,13 @@ dgchefsi_status dgchefsi_set_values(dgchefsi_ctx* ctx, const double* values);
 dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, const double* X, int64_t Ns, int64_t ld, int m,
                                      double a, double b, double a0, double Ne, double kT, int checkpoint_stride,
                                      double* energy, double* ritz, double* H_bar, double* X_bar);
+
+/* Self-test of failure detection (no counterpart in the paper): launches one
+ * thread that waits, with the same bounded wait the pipelined kernels use, on
+ * a barrier phase that nothing completes. The wait gives up after limit_ns
+ * (1 ns .. 10 s) and the call returns DGCHEFSI_ERR_TIMEOUT; the context stays
+ * usable. Any other status means the timeout path is broken. Synchronises. */
+dgchefsi_status dgchefsi_selftest_wait(dgchefsi_ctx* ctx, int64_t limit_ns);
 
 /* Message describing the last error on the calling thread ("" if none). */
 const char* dgchefsi_last_error(void);

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgchefsi.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "f64_kernels.cu", "tc_filter.cu", "noalloc.cu", "adjoint.cu"]
+SOURCES = ["api.cu", "f64_kernels.cu", "tc_filter.cu", "tc_tf32.cu", "tc_bf16.cu", "tc_bf16x3.cu", "noalloc.cu",
+           "adjoint.cu"]
 
 
 def nvcc() -> str:

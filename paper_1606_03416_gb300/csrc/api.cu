@@ -474,6 +474,38 @@ dgchefsi_status dgchefsi_filter(dgchefsi_ctx* ctx, int prec, const double* X, do
   return filter_tc(ctx, prec, X, Y, Ns, ld, m, a, b, a0);
 }
 
+dgchefsi_status dgchefsi_filter_graph(dgchefsi_ctx* ctx, int prec, const double* X, double* Y, int64_t Ns,
+                                      int64_t ld, int m, double a, double b, double a0) {
+  clear_error();
+  DG_TRY(check_filter_args(ctx, prec, X, Y, Ns, ld, m, a, b, a0));
+  if (prec == DGCHEFSI_F64) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "the graph form runs the tensor-core filter");
+  if (Ns == 0) return DGCHEFSI_OK;
+  return filter_tc_graph(ctx, prec, X, Y, Ns, ld, m, a, b, a0);
+}
+
+dgchefsi_status dgchefsi_set_tile_shape(dgchefsi_ctx* ctx, int prec, int G, int T) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  if (prec < DGCHEFSI_TF32 || prec > DGCHEFSI_BF16X3) return set_error(DGCHEFSI_ERR_ARG, "not a tensor-core precision");
+  if (G < 0 || T < 0 || (G == 0) != (T == 0)) return set_error(DGCHEFSI_ERR_ARG, "need G, T both > 0 or both 0");
+  return tc_set_shape(ctx, prec, G, T);
+}
+
+dgchefsi_status dgchefsi_get_tile_shape(dgchefsi_ctx* ctx, int prec, int* G, int* T, int* ACC) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  if (!G || !T || !ACC) return set_error(DGCHEFSI_ERR_ARG, "null output");
+  if (prec < DGCHEFSI_TF32 || prec > DGCHEFSI_BF16X3) return set_error(DGCHEFSI_ERR_ARG, "not a tensor-core precision");
+  return tc_get_shape(ctx, prec, G, T, ACC);
+}
+
+dgchefsi_status dgchefsi_selftest_wait(dgchefsi_ctx* ctx, int64_t limit_ns) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  if (limit_ns < 1 || limit_ns > 10000000000LL) return set_error(DGCHEFSI_ERR_ARG, "limit_ns outside 1 ns .. 10 s");
+  return tc_wait_selftest(ctx, limit_ns);
+}
+
 dgchefsi_status dgchefsi_gram(dgchefsi_ctx* ctx, const double* Y, int64_t Ns, int64_t ld, double* S) {
   clear_error();
   DG_TRY(check_ctx(ctx));

@@ -1,491 +1,15 @@
-// Chebyshev filter on the tcgen05 tensor cores (Alg. 1 step 2; Eq. matvec_3).
-//
-// One step of the scaled recurrence is, per element K and state tile,
-//     Y_{k+1}[s, K] = alpha_k * sum_{K' in N(K)} (H - cI)_{KK'} Y_k[s, K'] - beta_k * Y_{k-1}[s, K]
-// i.e. a dense GEMM with M = 128 states, N = n_K (padded to 16) and a K dimension
-// running over the neighbour blocks, followed by the recurrence update.
-//
-// Persistent, warp-specialised kernel, one CTA per SM (192 threads):
-//   * warp 0 (one lane) streams 128-byte-wide K slices with TMA into a
-//     shared-memory ring (SWIZZLE_128B, K-major): per slot, T state tiles of
-//     Y_k (A operands, 128 rows each) and the blocks of (H - cI) that couple the
-//     slice's element K' to each of the G output elements of the work unit
-//     (B operands);
-//   * warp 1 (one lane) issues tcgen05.mma (kind::f16 for BF16, kind::tf32 for
-//     TF32) into G x T FP32 accumulators in tensor memory, double-buffered
-//     across work units, and frees ring slots with tcgen05.commit;
-//   * warps 2-5 drain a finished unit's accumulators (tcgen05.ld, one state row
-//     per thread) while the next unit is multiplied, apply alpha_k and
-//     -beta_k Y_{k-1} (FP32 master), and write the FP32 master of Y_{k+1} and,
-//     for the BF16 forms, its BF16 operand copies.
-// A work unit is G consecutive elements x T consecutive state tiles; it walks
-// the union of the G elements' neighbour lists, so each A slice loaded is used
-// for every element of the unit that couples to it, and each B block for all
-// T state tiles. The shift -cI is folded into the diagonal blocks of the
-// operand copy of H, rebuilt once per filter call. Iterates live in an
-// element-padded layout (every element starts on a 16-column boundary, pads
-// held at zero) so TMA coordinates stay 16-byte aligned; pads of H are zero,
-// so columns of a neighbouring element read by a wide slice contribute nothing.
-//
-// BF16X3 splits every operand v into hi = bf16(v) and lo = bf16(v - hi) and
-// accumulates hi*hi + hi*lo + lo*hi (three passes per slice), which recovers
-// close to FP32 accuracy on the BF16 tensor pipe.
-//
-// Every wait on an mbarrier is bounded by wall-clock time; on expiry the CTA
-// records DGCHEFSI_ERR_TIMEOUT in a device word, drains its own copies in
-// flight, frees its tensor memory and returns.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-#include <cuda_bf16.h>
-
+// Host side of the tensor-core Chebyshev filter: operand layouts, element
+// groups and slice schedules per unit shape, an autotuner over unit shapes,
+// and a CUDA-graph form of the whole filter. The step kernel itself is in
+// tc_kernel.cuh (instantiated in tc_tf32.cu, tc_bf16.cu, tc_bf16x3.cu).
 #include <algorithm>
 #include <cmath>
+#include <map>
 
-#include "ctx.h"
+#include "tc_kernel.cuh"
 
 namespace dg {
-
 namespace {
-
-constexpr int BM = 128;           // states per tile (MMA M)
-constexpr int SLICE_BYTES = 128;  // K extent of one ring slot in bytes (one swizzle row)
-constexpr int NTHREADS = 320;  // producer warp, MMA warp, 8 epilogue warps
-constexpr int EPI_WARPS = 8;
-constexpr int STAGES = 4;  // ring slots (each T A-tiles + G B-tiles, 48 KB for every shape used)
-constexpr int A_BYTES = BM * SLICE_BYTES;
-constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per wait
-
-constexpr int MAXG = 4;
-
-enum Mode { MODE_TF32 = 0, MODE_BF16 = 1, MODE_BF16X3 = 2 };
-
-struct Params {
-  const int32_t* sched;      // slice entries: [A x coordinate, B row for each of the G elements or -1]
-  const int32_t* sched_ptr;  // [ngroups + 1] first entry of each element group
-  const int32_t* grp_elem;   // [ngroups * G] elements of each group (-1 past the end)
-  const int32_t* nb;
-  const int32_t* pnb;   // padded element sizes (multiple of 16)
-  const int32_t* poff;  // padded element offsets
-  int64_t lo_rows;      // BF16X3: row offset of the lo copy of H
-  int64_t Ns, ldp;
-  const float* Fprev;
-  float* Fout;
-  __nv_bfloat16* Hout;
-  __nv_bfloat16* Lout;
-  float alpha, beta;
-  int W;      // elements per slice: 64 (BF16) or 32 (TF32)
-  int mode;
-  int boxn;   // rows of a B box (max padded element size)
-  int G, T, ACC, NBUF, stages;
-  int ngroups, ntg;
-  int maxent;  // most slice entries of any element group (shared-memory copy size)
-  int* err;
-};
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t gtime() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: true once the phase with the given parity has completed.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = gtime();
-  while (true) {
-    for (int i = 0; i < 32; ++i)
-      if (mbar_try_wait(bar, parity)) return true;
-    if (gtime() - t0 > WAIT_LIMIT_NS) return false;
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-// Instruction descriptor: FP32 accumulate, A/B format code `fmt` (1 = BF16 for
-// kind::f16, 2 = TF32 for kind::tf32), both K-major, M = 128, N = n.
-__host__ __device__ constexpr uint32_t idesc(uint32_t fmt, uint32_t n) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(id), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          d),
-      "l"(a), "l"(b), "r"(id), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-
-// Epilogue of one 16-column chunk of one state row.
-__device__ __forceinline__ void store_chunk(const Params& p, int64_t idx, int jn, const float (&v)[16],
-                                            const float4 (&pr)[4]) {
-  float y[16];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    y[4 * q + 0] = p.alpha * v[4 * q + 0] - p.beta * pr[q].x;
-    y[4 * q + 1] = p.alpha * v[4 * q + 1] - p.beta * pr[q].y;
-    y[4 * q + 2] = p.alpha * v[4 * q + 2] - p.beta * pr[q].z;
-    y[4 * q + 3] = p.alpha * v[4 * q + 3] - p.beta * pr[q].w;
-  }
-  if (jn == 16) {
-    float4* po = reinterpret_cast<float4*>(p.Fout + idx);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) po[q] = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
-    if (p.mode != MODE_TF32) {
-      uint32_t hw[8], lw[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const __nv_bfloat162 h2 = __floats2bfloat162_rn(y[2 * q], y[2 * q + 1]);
-        const float2 hf = __bfloat1622float2(h2);
-        const __nv_bfloat162 l2 = __floats2bfloat162_rn(y[2 * q] - hf.x, y[2 * q + 1] - hf.y);
-        hw[q] = *reinterpret_cast<const uint32_t*>(&h2);
-        lw[q] = *reinterpret_cast<const uint32_t*>(&l2);
-      }
-      uint4* ph = reinterpret_cast<uint4*>(p.Hout + idx);
-      ph[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-      ph[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
-      if (p.mode == MODE_BF16X3) {
-        uint4* pl = reinterpret_cast<uint4*>(p.Lout + idx);
-        pl[0] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-        pl[1] = make_uint4(lw[4], lw[5], lw[6], lw[7]);
-      }
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      if (q < jn) {
-        p.Fout[idx + q] = y[q];
-        if (p.mode != MODE_TF32) {
-          const __nv_bfloat16 h = __float2bfloat16_rn(y[q]);
-          p.Hout[idx + q] = h;
-          if (p.mode == MODE_BF16X3) p.Lout[idx + q] = __float2bfloat16_rn(y[q] - __bfloat162float(h));
-        }
-      }
-    }
-  }
-}
-
-// Fprev for one chunk (zeros when beta == 0 or the row is not live).
-__device__ __forceinline__ void load_prev(const Params& p, int64_t idx, int jn, bool live, float4 (&pr)[4]) {
-#pragma unroll
-  for (int q = 0; q < 4; ++q) pr[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (!live || p.beta == 0.f || jn <= 0) return;
-  if (jn == 16) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) pr[q] = ld4(p.Fprev + idx + 4 * q);
-  } else {
-    float t[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) t[q] = q < jn ? p.Fprev[idx + q] : 0.f;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) pr[q] = make_float4(t[4 * q], t[4 * q + 1], t[4 * q + 2], t[4 * q + 3]);
-  }
-}
-
-// MODE_, G, T and ACC (accumulator columns per element) are compile-time so
-// the single MMA-issuing thread runs a fully unrolled loop of descriptor adds:
-// with N = 64 each MMA is only ~32 tensor-core cycles, so issue overhead
-// would otherwise dominate.
-template <int MODE_, int G, int T, int ACC>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    k_filter_step_tc(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
-                     const __grid_constant__ CUtensorMap tmB, const Params p) {
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  // BF16X3 keeps the hi and lo copies of both operands in one ring slot (its
-  // three products reuse them), so its slots are twice as large and half as many.
-  constexpr int NA = MODE_ == MODE_BF16X3 ? 2 : 1;
-  constexpr int S = MODE_ == MODE_BF16X3 ? STAGES / 2 : STAGES;
-  constexpr int b_bytes = ACC * SLICE_BYTES;  // one element's B tile: ACC rows of 128 bytes
-  constexpr int a_part = NA * T * A_BYTES;    // [A hi x T][A lo x T]
-  constexpr int stage_bytes = a_part + NA * G * b_bytes;  // then [B hi x G][B lo x G]
-  constexpr uint32_t NMMA = (uint32_t)(G * ACC);  // the G elements' B tiles are stacked along N
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
-  // per-role copies of the current group's slice entries (producer, MMA issuer)
-  int32_t* sched_sh0 = reinterpret_cast<int32_t*>(bars + 2 * S + 4);
-  int32_t* sched_sh1 = sched_sh0 + p.maxent * (1 + G);
-  __shared__ uint32_t tmem_base_sh;
-  __shared__ int abort_sh;
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nunits = p.ngroups * p.ntg;
-  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * S;
-  const uint32_t accf0 = empty0 + 8 * S, acce0 = accf0 + 16;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(accf0 + 8 * b, 1);
-      mbar_init(acce0 + 8 * b, EPI_WARPS);
-    }
-    abort_sh = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                 "r"(512)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = tmem_base_sh;
-
-  if (warp == 0) {
-    // ---------------- producer: TMA into the ring (lane 0 issues; the warp copies schedules)
-    if (lane == 0) {
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA0)) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-    }
-    int c = 0;
-    bool ok = true;
-    for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-      const int eg = u / p.ntg, tg = u % p.ntg;
-      const int s0 = tg * BM * T;
-      const int e0 = p.sched_ptr[eg], ne = p.sched_ptr[eg + 1] - e0;
-      __syncwarp();
-      for (int z = lane; z < ne * (1 + G); z += 32) sched_sh0[z] = p.sched[(int64_t)e0 * (1 + G) + z];
-      __syncwarp();
-      if (lane == 0 && ok) {
-        for (int e = 0; e < ne && ok; ++e) {
-          const int32_t* ent = sched_sh0 + e * (1 + G);
-          const int ax = ent[0];
-          {
-            const int st = c & (S - 1);
-            const uint32_t ph = (uint32_t)(c / S) & 1u;
-            if (!mbar_wait(empty0 + 8 * st, ph ^ 1u)) {
-              ok = false;
-              break;
-            }
-            const uint32_t fb = full0 + 8 * st;
-            mbar_expect_tx(fb, (uint32_t)stage_bytes);
-            uint8_t* sst = smem + st * stage_bytes;
-#pragma unroll
-            for (int v = 0; v < NA; ++v)
-#pragma unroll
-              for (int t = 0; t < T; ++t)
-                tma_load_2d(smem_u32(sst + (v * T + t) * A_BYTES), v == 1 ? &tmA1 : &tmA0, ax, s0 + BM * t, fb);
-#pragma unroll
-            for (int v = 0; v < NA; ++v)
-#pragma unroll
-              for (int g = 0; g < G; ++g) {
-                const int r = ent[1 + g];  // a zero block when element g does not couple to this slice
-                tma_load_2d(smem_u32(sst + a_part + (v * G + g) * b_bytes), &tmB, 0,
-                            (int)(r + (v == 1 ? p.lo_rows : 0)), fb);
-              }
-            ++c;
-          }
-        }
-      }
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
-    }
-    if (lane == 0) {
-      if (!ok) {
-        atomicOr(p.err, 1);
-        atomicExch(&abort_sh, 1);
-      }
-      // drain: every issued copy must land before the CTA may exit
-      for (int i = c - S < 0 ? 0 : c - S; i < c; ++i)
-        if (!mbar_wait(full0 + 8 * (i & (S - 1)), (uint32_t)(i / S) & 1u)) atomicOr(p.err, 1);
-    }
-  } else if (warp == 1) {
-    // ---------------- MMA issuer (lane 0 issues; the warp copies schedules)
-    constexpr uint32_t fmt = MODE_ == MODE_TF32 ? 2u : 1u;
-    // descriptor of the ring's first byte; every operand is an offset from it
-    const uint64_t desc0 = sdesc(smem_u32(smem));
-    int c = 0, i = 0;
-    bool ok = true;
-    for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++i) {
-      const int eg = u / p.ntg;
-      const int e0 = p.sched_ptr[eg], ne = p.sched_ptr[eg + 1] - e0;
-      __syncwarp();
-      for (int z = lane; z < ne * (1 + G); z += 32) sched_sh1[z] = p.sched[(int64_t)e0 * (1 + G) + z];
-      __syncwarp();
-      if (lane == 0 && ok) {
-        const int buf = p.NBUF == 2 ? (i & 1) : 0;
-        const int use = p.NBUF == 2 ? (i >> 1) : i;
-        if (!mbar_wait(acce0 + 8 * buf, ((uint32_t)use & 1u) ^ 1u)) ok = false;
-        tc_fence_after();
-        constexpr uint32_t ID = idesc(fmt, NMMA);
-        const uint32_t dbuf = tmem + (uint32_t)(buf * T * G * ACC);
-        uint32_t first = 0;  // the unit's first slice overwrites the accumulators
-        for (int e = 0; e < ne && ok; ++e) {
-          const int st = c & (S - 1);
-          const uint32_t ph = (uint32_t)(c / S) & 1u;
-          if (!mbar_wait(full0 + 8 * st, ph)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint64_t da = desc0 + (uint64_t)((st * stage_bytes) >> 4);  // A hi
-          const uint64_t db = da + (uint64_t)(a_part >> 4);                   // B hi
-#pragma unroll
-          for (int t = 0; t < T; ++t) {
-            const uint32_t d = dbuf + (uint32_t)(t * G * ACC);
-#pragma unroll
-            for (int kk = 0; kk < SLICE_BYTES / 32; ++kk) {
-              const uint64_t ad = da + (uint64_t)((t * A_BYTES + 32 * kk) >> 4);
-              const uint64_t bd = db + (uint64_t)((32 * kk) >> 4);
-              const uint32_t acc = kk > 0 ? 1u : first;
-              if constexpr (MODE_ == MODE_TF32) {
-                mma_tf32(d, ad, bd, ID, acc);
-              } else {
-                mma_bf16(d, ad, bd, ID, acc);
-                if constexpr (MODE_ == MODE_BF16X3) {
-                  // hi * lo(H) and lo * hi(H)
-                  mma_bf16(d, ad, bd + (uint64_t)((G * b_bytes) >> 4), ID, 1u);
-                  mma_bf16(d, ad + (uint64_t)((T * A_BYTES) >> 4), bd, ID, 1u);
-                }
-              }
-            }
-          }
-          first = 1u;
-          mma_commit(empty0 + 8 * st);
-          ++c;
-        }
-        mma_commit(accf0 + 8 * buf);
-      }
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
-    }
-    if (lane == 0 && !ok) {
-      atomicOr(p.err, 1);
-      atomicExch(&abort_sh, 1);
-    }
-  } else {
-    // ---------------- epilogue: warps 2..9; two warps per TMEM lane quarter split
-    // the 16-column chunks of each accumulator; one state row per thread.
-    const int q = warp & 3;          // TMEM lane quarter this warp may access
-    const int h = (warp - 2) >> 2;   // which half of the chunks
-    int i = 0;
-    for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++i) {
-      const int buf = p.NBUF == 2 ? (i & 1) : 0;
-      const int use = p.NBUF == 2 ? (i >> 1) : i;
-      const int eg = u / p.ntg, tg = u % p.ntg;
-      const int64_t s0 = (int64_t)tg * BM * T;
-      bool ready = mbar_wait(accf0 + 8 * buf, (uint32_t)use & 1u);
-      ready = __all_sync(0xffffffffu, ready);
-      if (!ready) {
-        if (lane == 0) atomicOr(p.err, 1);
-        break;
-      }
-      tc_fence_after();
-      const bool go = *(volatile int*)&abort_sh == 0;
-      for (int g = 0; g < G; ++g) {
-        const int K = p.grp_elem[eg * G + g];
-        if (K < 0) continue;
-        const int nK = p.nb[K], pK = p.pnb[K];
-        const int nch = pK >> 4;
-        const int64_t col = p.poff[K];
-        for (int t = 0; t < T; ++t) {
-          const int64_t s = s0 + BM * t + 32 * q + lane;
-          const bool live = go && s < p.Ns;
-          const int64_t rbase = s * p.ldp + col;
-          const uint32_t ta = tmem + (uint32_t)(((buf * T + t) * G + g) * ACC) + ((uint32_t)(32 * q) << 16);
-          // all loads of Y_{k-1} for this warp's chunks first (memory-level parallelism)
-          float4 pr[4][4];
-#pragma unroll
-          for (int cc = 0; cc < 4; ++cc) {
-            const int c = h + 2 * cc;
-            const int jn = nK - 16 * c;
-            load_prev(p, rbase + 16 * c, jn > 16 ? 16 : jn, live && c < nch, pr[cc]);
-          }
-#pragma unroll
-          for (int cc = 0; cc < 4; ++cc) {
-            const int c = h + 2 * cc;
-            if (c < nch) {
-              float v[16];
-              tmem_ld16(ta + (uint32_t)(16 * c), v);
-              const int jn = nK - 16 * c;
-              if (live && jn > 0) store_chunk(p, rbase + 16 * c, jn > 16 ? 16 : jn, v, pr[cc]);
-            }
-          }
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acce0 + 8 * buf);
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 1) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
-  }
-}
 
 // X (FP64, natural layout, ld) -> FP32 master + BF16 hi / lo copies in the padded layout.
 __global__ void k_pack(const double* __restrict__ X, int64_t ld, int64_t Ns, const int64_t* __restrict__ off,
@@ -526,9 +50,11 @@ __global__ void k_unpack(const float* __restrict__ F, int64_t ldp, int64_t Ns, c
 __global__ void k_build_hop(const int32_t* __restrict__ blk_row, const int32_t* __restrict__ col,
                             const int64_t* __restrict__ blk_off, const double* __restrict__ vals,
                             const int32_t* __restrict__ nb, const int32_t* __restrict__ pnb,
-                            const int64_t* __restrict__ brow, int W, double c, int mode, int64_t lo_rows,
+                            const int64_t* __restrict__ brow, int W, const double* __restrict__ coef, int mode,
+                            int64_t lo_rows,
                             float* __restrict__ H32, __nv_bfloat16* __restrict__ H16) {
   const int64_t e = blockIdx.x;
+  const double c = coef[0];
   const int K = blk_row[e], Kp = col[e];
   const int nK = nb[K], nKp = nb[Kp], pK = pnb[K];
   const int nsl = (pnb[Kp] + W - 1) / W;
@@ -570,140 +96,206 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-}  // namespace
-
-struct TcState {
-  int64_t Ns = -1, ldp = 0;
-  int mode = -1;
-  int G = 1, T = 1, ACC = 64, NBUF = 2, boxn = 16;
-  int ngroups = 0, num_sms = 0, maxent = 0;
-  std::vector<int32_t> pnb_h, poff_h, blk_row_h, grp_elem_h;
-  std::vector<int64_t> brow_h;
-  int64_t b_rows = 0;  // rows of one copy of H in the operand tensor
-  int64_t zero_row = 0;
-  int32_t *pnb_d = nullptr, *poff_d = nullptr, *blk_row_d = nullptr, *grp_elem_d = nullptr;
-  int32_t *sched_d = nullptr, *sched_ptr_d = nullptr;
-  int64_t* brow_d = nullptr;
-  DevBuf F[2], Sh[2], Sl[2], Hop;
-  int* err_d = nullptr;
-};
-
-// Work-unit shape: G elements x T state tiles of ACC accumulator columns,
-// NBUF accumulator sets, all within the 512 tensor-memory columns of an SM.
-static void choose_shape(TcState& t) {
-  t.ACC = t.boxn <= 32 ? 32 : (t.boxn <= 64 ? 64 : 128);
-  t.NBUF = 2;
-  t.T = t.ACC <= 64 ? 2 : 1;
-  t.G = std::min(MAXG, 512 / (t.NBUF * t.T * t.ACC));
-  if (t.G < 1) {
-    t.NBUF = 1;
-    t.G = 1;
+// Self-test of the bounded wait: one thread waits on an mbarrier whose phase
+// nothing completes; the wait must give up after limit_ns and report it.
+__global__ void k_wait_selftest(uint64_t limit_ns, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const bool completed = mbar_wait_for(smem_u32(&bar), 0u, limit_ns);
+    *status = completed ? 0 : 1;
   }
 }
 
-static dgchefsi_status tc_setup(dgchefsi_ctx* ctx, int mode, int64_t Ns) {
-  if (!ctx->tc) ctx->tc = new TcState();
-  TcState& t = *ctx->tc;
+}  // namespace
+
+dgchefsi_status tc_wait_selftest(dgchefsi_ctx* ctx, int64_t limit_ns) {
+  int* d = nullptr;
+  if (ctx->ws_small.bytes < sizeof(int)) DG_TRY(ensure(ctx, ctx->ws_small, sizeof(int) * 4, "self-test status"));
+  d = static_cast<int*>(ctx->ws_small.p);
+  DG_CUDA(cudaMemsetAsync(d, 0xff, sizeof(int), ctx->stream));
+  k_wait_selftest<<<1, 32, 0, ctx->stream>>>((uint64_t)limit_ns, d);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  int st = -1;
+  DG_CUDA(cudaMemcpyAsync(&st, d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  DG_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (st == 1) return set_error(DGCHEFSI_ERR_TIMEOUT, "bounded device wait gave up after %lld ns (self-test)",
+                                (long long)limit_ns);
+  return DGCHEFSI_OK;
+}
+
+// Element groups of G consecutive elements and, per group, the slices of the
+// union of its members' neighbour lists: [A x coordinate, B row per member].
+struct Plan {
+  int G = 0, W = 0, ngroups = 0, maxent = 0;
+  int32_t* grp_elem_d = nullptr;
+  int32_t* sched_d = nullptr;
+  int32_t* sched_ptr_d = nullptr;
+};
+
+struct TcState {
+  int64_t Ns = -1, ldp = 0;
+  int mode = -1;  // precision the operand copy of H is laid out for
+  int boxn = 16, ACC = 64, num_sms = 0;
+  std::vector<int32_t> pnb_h, poff_h, blk_row_h;
+  std::vector<int64_t> brow_h;
+  int64_t b_rows = 0, zero_row = 0;
+  int32_t *pnb_d = nullptr, *poff_d = nullptr, *blk_row_d = nullptr;
+  int64_t* brow_d = nullptr;
+  DevBuf F[2], Sh[2], Sl[2], Hop;
+  int* err_d = nullptr;
+  double* coef_d = nullptr;  // [1 + 2m] c, alpha_k, beta_k
+  double* coef_h = nullptr;  // pinned mirror
+  int coef_cap = 0;
+  std::map<int, Plan> plans;  // keyed by G
+  int shapeG[3] = {0, 0, 0}, shapeT[3] = {0, 0, 0};    // chosen per precision (0 = not yet)
+  int forceG[3] = {0, 0, 0}, forceT[3] = {0, 0, 0};    // set by dgchefsi_set_tile_shape
+  float tuned_ms[3][NSHAPES] = {};
+  // graph form
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int g_mode = -1, g_m = 0, g_G = 0, g_T = 0;
+  const void* g_X = nullptr;
+  void* g_Y = nullptr;
+  int64_t g_Ns = 0, g_ld = 0;
+};
+
+static FilterKernel pick_kernel(int mode, int G, int T, int ACC) {
+  if (mode == MODE_TF32) return pick_kernel_tf32(G, T, ACC);
+  if (mode == MODE_BF16) return pick_kernel_bf16(G, T, ACC);
+  return pick_kernel_bf16x3(G, T, ACC);
+}
+
+static void free_plan(Plan& pl) {
+  cudaFree(pl.grp_elem_d);
+  cudaFree(pl.sched_d);
+  cudaFree(pl.sched_ptr_d);
+  pl = Plan();
+}
+
+static dgchefsi_status ensure_layout(dgchefsi_ctx* ctx, TcState& t) {
+  if (!t.pnb_h.empty()) return DGCHEFSI_OK;
   const int M = ctx->M;
-  const int W = mode == MODE_TF32 ? 32 : 64;
-  if (t.pnb_h.empty()) {
-    t.pnb_h.resize(M);
-    t.poff_h.resize(M + 1);
-    t.poff_h[0] = 0;
-    int boxn = 16;
-    for (int K = 0; K < M; ++K) {
-      t.pnb_h[K] = (ctx->nb_h[K] + 15) / 16 * 16;
-      t.poff_h[K + 1] = t.poff_h[K] + t.pnb_h[K];
-      boxn = std::max(boxn, t.pnb_h[K]);
-    }
-    t.boxn = boxn;
-    t.ldp = t.poff_h[M];
-    choose_shape(t);
-    t.boxn = t.ACC;  // B boxes are ACC rows high so the G tiles stack along N
-    t.ngroups = (M + t.G - 1) / t.G;
-    t.grp_elem_h.assign((size_t)t.ngroups * t.G, -1);
-    for (int K = 0; K < M; ++K) t.grp_elem_h[K] = K;  // group eg holds elements eg*G .. eg*G+G-1
-    t.blk_row_h.resize(ctx->nnzb);
-    for (int K = 0; K < M; ++K)
-      for (int64_t e = ctx->row_ptr_h[K]; e < ctx->row_ptr_h[K + 1]; ++e) t.blk_row_h[e] = K;
-    int dev = 0;
-    DG_CUDA(cudaGetDevice(&dev));
-    DG_CUDA(cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, dev));
-    DG_CUDA(cudaMalloc(&t.pnb_d, sizeof(int32_t) * M));
-    DG_CUDA(cudaMalloc(&t.poff_d, sizeof(int32_t) * (M + 1)));
-    DG_CUDA(cudaMalloc(&t.blk_row_d, sizeof(int32_t) * std::max<int64_t>(ctx->nnzb, 1)));
-    DG_CUDA(cudaMalloc(&t.brow_d, sizeof(int64_t) * std::max<int64_t>(ctx->nnzb, 1)));
-    DG_CUDA(cudaMalloc(&t.grp_elem_d, sizeof(int32_t) * t.grp_elem_h.size()));
-    DG_CUDA(cudaMalloc(&t.sched_ptr_d, sizeof(int32_t) * (t.ngroups + 1)));
-    DG_CUDA(cudaMalloc(&t.err_d, sizeof(int)));
-    DG_CUDA(cudaMemcpy(t.pnb_d, t.pnb_h.data(), sizeof(int32_t) * M, cudaMemcpyHostToDevice));
-    DG_CUDA(cudaMemcpy(t.poff_d, t.poff_h.data(), sizeof(int32_t) * (M + 1), cudaMemcpyHostToDevice));
-    DG_CUDA(cudaMemcpy(t.blk_row_d, t.blk_row_h.data(), sizeof(int32_t) * ctx->nnzb, cudaMemcpyHostToDevice));
-    DG_CUDA(cudaMemcpy(t.grp_elem_d, t.grp_elem_h.data(), sizeof(int32_t) * t.grp_elem_h.size(),
-                       cudaMemcpyHostToDevice));
+  t.pnb_h.resize(M);
+  t.poff_h.resize(M + 1);
+  t.poff_h[0] = 0;
+  int boxn = 16;
+  for (int K = 0; K < M; ++K) {
+    t.pnb_h[K] = (ctx->nb_h[K] + 15) / 16 * 16;
+    t.poff_h[K + 1] = t.poff_h[K] + t.pnb_h[K];
+    boxn = std::max(boxn, t.pnb_h[K]);
   }
-  if (t.mode != mode) {  // B row layout and slice schedule depend on the slice width
-    t.brow_h.resize(ctx->nnzb);
-    int64_t r = 0;
-    for (int64_t e = 0; e < ctx->nnzb; ++e) {
-      t.brow_h[e] = r;
-      const int Kp = ctx->col_h[e];
-      r += (int64_t)((t.pnb_h[Kp] + W - 1) / W) * t.pnb_h[t.blk_row_h[e]];
+  t.ldp = t.poff_h[M];
+  t.ACC = boxn <= 32 ? 32 : (boxn <= 64 ? 64 : 128);
+  t.boxn = t.ACC;  // B boxes are ACC rows high so the tiles of G elements stack along N
+  t.blk_row_h.resize(ctx->nnzb);
+  for (int K = 0; K < M; ++K)
+    for (int64_t e = ctx->row_ptr_h[K]; e < ctx->row_ptr_h[K + 1]; ++e) t.blk_row_h[e] = K;
+  int dev = 0;
+  DG_CUDA(cudaGetDevice(&dev));
+  DG_CUDA(cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, dev));
+  DG_CUDA(cudaMalloc(&t.pnb_d, sizeof(int32_t) * M));
+  DG_CUDA(cudaMalloc(&t.poff_d, sizeof(int32_t) * (M + 1)));
+  DG_CUDA(cudaMalloc(&t.blk_row_d, sizeof(int32_t) * std::max<int64_t>(ctx->nnzb, 1)));
+  DG_CUDA(cudaMalloc(&t.brow_d, sizeof(int64_t) * std::max<int64_t>(ctx->nnzb, 1)));
+  DG_CUDA(cudaMalloc(&t.err_d, sizeof(int)));
+  DG_CUDA(cudaMemcpy(t.pnb_d, t.pnb_h.data(), sizeof(int32_t) * M, cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMemcpy(t.poff_d, t.poff_h.data(), sizeof(int32_t) * (M + 1), cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMemcpy(t.blk_row_d, t.blk_row_h.data(), sizeof(int32_t) * ctx->nnzb, cudaMemcpyHostToDevice));
+  return DGCHEFSI_OK;
+}
+
+// Row layout of the operand copy of H for one slice width; plans depend on it.
+static dgchefsi_status ensure_mode(dgchefsi_ctx* ctx, TcState& t, int mode) {
+  if (t.mode == mode) return DGCHEFSI_OK;
+  const int W = mode == MODE_TF32 ? 32 : 64;
+  for (auto& kv : t.plans) free_plan(kv.second);
+  t.plans.clear();
+  t.brow_h.resize(ctx->nnzb);
+  int64_t r = 0;
+  for (int64_t e = 0; e < ctx->nnzb; ++e) {
+    t.brow_h[e] = r;
+    const int Kp = ctx->col_h[e];
+    r += (int64_t)((t.pnb_h[Kp] + W - 1) / W) * t.pnb_h[t.blk_row_h[e]];
+  }
+  t.zero_row = r;                                       // ZERO_TILES zero tiles of ACC rows
+  t.b_rows = r + (int64_t)ZERO_TILES * t.boxn + t.boxn;  // plus slack for a full-height box
+  if (t.b_rows * (mode == MODE_BF16X3 ? 2 : 1) > 2147483647LL)
+    return set_error(DGCHEFSI_ERR_UNSUPPORTED, "operand copy of H too large for 32-bit TMA rows");
+  DG_CUDA(cudaMemcpy(t.brow_d, t.brow_h.data(), sizeof(int64_t) * ctx->nnzb, cudaMemcpyHostToDevice));
+  const size_t esz = mode == MODE_TF32 ? 4 : 2;
+  const size_t copies = mode == MODE_BF16X3 ? 2 : 1;
+  DG_TRY(ensure(ctx, t.Hop, (size_t)t.b_rows * copies * W * esz, "operand copy of H"));
+  DG_CUDA(cudaMemsetAsync(t.Hop.p, 0, t.Hop.bytes, ctx->stream));
+  t.mode = mode;
+  return DGCHEFSI_OK;
+}
+
+static dgchefsi_status get_plan(dgchefsi_ctx* ctx, TcState& t, int G, Plan** out) {
+  auto it = t.plans.find(G);
+  if (it != t.plans.end()) {
+    *out = &it->second;
+    return DGCHEFSI_OK;
+  }
+  const int M = ctx->M;
+  const int W = t.mode == MODE_TF32 ? 32 : 64;
+  Plan pl;
+  pl.G = G;
+  pl.W = W;
+  pl.ngroups = (M + G - 1) / G;
+  std::vector<int32_t> grp((size_t)pl.ngroups * G, -1);
+  for (int K = 0; K < M; ++K) grp[K] = K;  // group eg holds elements eg*G .. eg*G+G-1
+  std::vector<int32_t> sched, sptr(pl.ngroups + 1, 0);
+  for (int eg = 0; eg < pl.ngroups; ++eg) {
+    std::vector<int> nbrs;
+    for (int g = 0; g < G; ++g) {
+      const int K = grp[(size_t)eg * G + g];
+      if (K < 0) continue;
+      for (int64_t e = ctx->row_ptr_h[K]; e < ctx->row_ptr_h[K + 1]; ++e) nbrs.push_back(ctx->col_h[e]);
     }
-    t.zero_row = r;         // ACC zero rows: the B tile of a non-coupling element
-    t.b_rows = r + t.boxn;  // also slack so a full-height box never leaves the tensor
-    if (t.b_rows * (mode == MODE_BF16X3 ? 2 : 1) > 2147483647LL)
-      return set_error(DGCHEFSI_ERR_UNSUPPORTED, "operand copy of H too large for 32-bit TMA rows");
-    DG_CUDA(cudaMemcpy(t.brow_d, t.brow_h.data(), sizeof(int64_t) * ctx->nnzb, cudaMemcpyHostToDevice));
-    // slice schedule of every element group: union of the members' neighbour lists
-    std::vector<int32_t> sched, sptr(t.ngroups + 1, 0);
-    for (int eg = 0; eg < t.ngroups; ++eg) {
-      std::vector<int> nbrs;
-      for (int g = 0; g < t.G; ++g) {
-        const int K = t.grp_elem_h[(size_t)eg * t.G + g];
-        if (K < 0) continue;
-        for (int64_t e = ctx->row_ptr_h[K]; e < ctx->row_ptr_h[K + 1]; ++e) nbrs.push_back(ctx->col_h[e]);
-      }
-      std::sort(nbrs.begin(), nbrs.end());
-      nbrs.erase(std::unique(nbrs.begin(), nbrs.end()), nbrs.end());
-      for (int Kp : nbrs) {
-        const int nsl = (t.pnb_h[Kp] + W - 1) / W;
-        for (int sl = 0; sl < nsl; ++sl) {
-          sched.push_back(t.poff_h[Kp] + sl * W);
-          for (int g = 0; g < t.G; ++g) {
-            const int K = t.grp_elem_h[(size_t)eg * t.G + g];
-            int32_t row = (int32_t)t.zero_row;
-            if (K >= 0) {
-              int64_t lo = ctx->row_ptr_h[K], hi = ctx->row_ptr_h[K + 1] - 1;
-              while (lo <= hi) {
-                const int64_t mid = (lo + hi) / 2;
-                const int cm = ctx->col_h[mid];
-                if (cm == Kp) {
-                  row = (int32_t)(t.brow_h[mid] + (int64_t)sl * t.pnb_h[K]);
-                  break;
-                }
-                if (cm < Kp) lo = mid + 1; else hi = mid - 1;
+    std::sort(nbrs.begin(), nbrs.end());
+    nbrs.erase(std::unique(nbrs.begin(), nbrs.end()), nbrs.end());
+    for (int Kp : nbrs) {
+      const int nsl = (t.pnb_h[Kp] + W - 1) / W;
+      for (int sl = 0; sl < nsl; ++sl) {
+        sched.push_back(t.poff_h[Kp] + sl * W);
+        for (int g = 0; g < G; ++g) {
+          const int K = grp[(size_t)eg * G + g];
+          // a zero tile (one of ZERO_TILES, spread over L2) when K does not couple to K'
+          int32_t row = (int32_t)(t.zero_row + (int64_t)(eg % ZERO_TILES) * t.boxn);
+          if (K >= 0) {
+            int64_t lo = ctx->row_ptr_h[K], hi = ctx->row_ptr_h[K + 1] - 1;
+            while (lo <= hi) {
+              const int64_t mid = (lo + hi) / 2;
+              const int cm = ctx->col_h[mid];
+              if (cm == Kp) {
+                row = (int32_t)(t.brow_h[mid] + (int64_t)sl * t.pnb_h[K]);
+                break;
               }
+              if (cm < Kp) lo = mid + 1; else hi = mid - 1;
             }
-            sched.push_back(row);
           }
+          sched.push_back(row);
         }
       }
-      sptr[eg + 1] = (int32_t)(sched.size() / (1 + t.G));
     }
-    t.maxent = 0;
-    for (int eg = 0; eg < t.ngroups; ++eg) t.maxent = std::max(t.maxent, sptr[eg + 1] - sptr[eg]);
-    cudaFree(t.sched_d);
-    t.sched_d = nullptr;
-    DG_CUDA(cudaMalloc(&t.sched_d, sizeof(int32_t) * std::max<size_t>(sched.size(), 1)));
-    DG_CUDA(cudaMemcpy(t.sched_d, sched.data(), sizeof(int32_t) * sched.size(), cudaMemcpyHostToDevice));
-    DG_CUDA(cudaMemcpy(t.sched_ptr_d, sptr.data(), sizeof(int32_t) * sptr.size(), cudaMemcpyHostToDevice));
-    const size_t esz = mode == MODE_TF32 ? 4 : 2;
-    const size_t copies = mode == MODE_BF16X3 ? 2 : 1;
-    DG_TRY(ensure(ctx, t.Hop, (size_t)t.b_rows * copies * W * esz, "operand copy of H"));
-    DG_CUDA(cudaMemsetAsync(t.Hop.p, 0, t.Hop.bytes, ctx->stream));
-    t.mode = mode;
+    sptr[eg + 1] = (int32_t)(sched.size() / (1 + G));
+    pl.maxent = std::max(pl.maxent, sptr[eg + 1] - sptr[eg]);
   }
+  DG_CUDA(cudaMalloc(&pl.grp_elem_d, sizeof(int32_t) * grp.size()));
+  DG_CUDA(cudaMalloc(&pl.sched_d, sizeof(int32_t) * std::max<size_t>(sched.size(), 1)));
+  DG_CUDA(cudaMalloc(&pl.sched_ptr_d, sizeof(int32_t) * sptr.size()));
+  DG_CUDA(cudaMemcpy(pl.grp_elem_d, grp.data(), sizeof(int32_t) * grp.size(), cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMemcpy(pl.sched_d, sched.data(), sizeof(int32_t) * sched.size(), cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMemcpy(pl.sched_ptr_d, sptr.data(), sizeof(int32_t) * sptr.size(), cudaMemcpyHostToDevice));
+  t.plans[G] = pl;
+  *out = &t.plans[G];
+  return DGCHEFSI_OK;
+}
+
+static dgchefsi_status ensure_iterates(dgchefsi_ctx* ctx, TcState& t, int mode, int64_t Ns) {
   if (t.Ns < Ns || t.F[0].p == nullptr) {
     const size_t n = (size_t)Ns * (size_t)t.ldp;
     for (int i = 0; i < 2; ++i) {
@@ -728,22 +320,6 @@ static dgchefsi_status tc_setup(dgchefsi_ctx* ctx, int mode, int64_t Ns) {
   return DGCHEFSI_OK;
 }
 
-using FilterKernel = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const Params);
-
-template <int MODE_>
-static FilterKernel pick_shape(int G, int T, int ACC) {
-  if (G == 2 && T == 2 && ACC == 64) return k_filter_step_tc<MODE_, 2, 2, 64>;
-  if (G == 2 && T == 1 && ACC == 128) return k_filter_step_tc<MODE_, 2, 1, 128>;
-  if (G == 4 && T == 2 && ACC == 32) return k_filter_step_tc<MODE_, 4, 2, 32>;
-  return nullptr;
-}
-
-static FilterKernel pick_kernel(int mode, int G, int T, int ACC) {
-  if (mode == MODE_TF32) return pick_shape<MODE_TF32>(G, T, ACC);
-  if (mode == MODE_BF16) return pick_shape<MODE_BF16>(G, T, ACC);
-  return pick_shape<MODE_BF16X3>(G, T, ACC);
-}
-
 static dgchefsi_status make_map(CUtensorMap* map, void* base, bool f32, uint64_t inner, uint64_t rows,
                                 uint32_t box_inner, uint32_t box_rows) {
   auto enc = encode_fn();
@@ -760,86 +336,111 @@ static dgchefsi_status make_map(CUtensorMap* map, void* base, bool f32, uint64_t
   return DGCHEFSI_OK;
 }
 
-dgchefsi_status filter_tc(dgchefsi_ctx* ctx, int prec, const double* X, double* Y, int64_t Ns, int64_t ld, int m,
-                          double a, double b, double a0) {
-  if (ctx->max_nb > 128)
-    return set_error(DGCHEFSI_ERR_UNSUPPORTED, "tensor-core filter supports element sizes up to 128 (got %d)",
-                     ctx->max_nb);
-  if (Ns > 2147483647LL / 2 - 2 * BM) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "Ns too large");
-  const int mode = prec == DGCHEFSI_TF32 ? MODE_TF32 : (prec == DGCHEFSI_BF16 ? MODE_BF16 : MODE_BF16X3);
-  const int W = mode == MODE_TF32 ? 32 : 64;
-  DG_TRY(tc_setup(ctx, mode, Ns));
-  TcState& t = *ctx->tc;
-  cudaStream_t s = ctx->stream;
-  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
-  const double s1 = e / (a0 - c);
+static int mode_of(int prec) {
+  return prec == DGCHEFSI_TF32 ? MODE_TF32 : (prec == DGCHEFSI_BF16 ? MODE_BF16 : MODE_BF16X3);
+}
+
+// Everything one filter call enqueues, for a given unit shape.
+struct Launch {
+  FilterKernel kern = nullptr;
+  Params p{};
+  CUtensorMap A0[2], A1[2], B;
+  dim3 grid;
+  int smem = 0;
+};
+
+static dgchefsi_status prepare_launch(dgchefsi_ctx* ctx, TcState& t, int mode, int G, int T, int64_t Ns,
+                                      Launch& L) {
   const bool f32 = mode == MODE_TF32;
-  __nv_bfloat16* Hop16 = f32 ? nullptr : static_cast<__nv_bfloat16*>(t.Hop.p);
-  float* Hop32 = f32 ? static_cast<float*>(t.Hop.p) : nullptr;
-  k_build_hop<<<(unsigned)ctx->nnzb, 256, 0, s>>>(t.blk_row_d, ctx->col_d, ctx->blk_off_d, ctx->vals_d, ctx->nb_d,
-                                                  t.pnb_d, t.brow_d, W, c, mode, t.b_rows, Hop32, Hop16);
-  count_launch();
-  DG_CUDA(cudaGetLastError());
-  auto sh = [&](int i) { return static_cast<__nv_bfloat16*>(t.Sh[i].p); };
-  auto sl = [&](int i) { return static_cast<__nv_bfloat16*>(t.Sl[i].p); };
-  auto fb = [&](int i) { return static_cast<float*>(t.F[i].p); };
-  {
-    dim3 g((unsigned)std::min<int64_t>(Ns, 1024), (unsigned)ctx->M);
-    k_pack<<<g, 128, 0, s>>>(X, ld, Ns, ctx->off_d, ctx->nb_d, t.poff_d, t.ldp, fb(0), f32 ? nullptr : sh(0),
-                             mode == MODE_BF16X3 ? sl(0) : nullptr);
-    count_launch();
-    DG_CUDA(cudaGetLastError());
-  }
-  CUtensorMap mapF[2], mapH[2], mapL[2], mapB;
+  const int W = f32 ? 32 : 64;
+  Plan* pl = nullptr;
+  DG_TRY(get_plan(ctx, t, G, &pl));
+  L.kern = pick_kernel(mode, G, T, t.ACC);
+  if (!L.kern) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "no filter kernel for G=%d T=%d ACC=%d", G, T, t.ACC);
   for (int i = 0; i < 2; ++i) {
     if (f32) {
-      DG_TRY(make_map(&mapF[i], t.F[i].p, true, (uint64_t)t.ldp, (uint64_t)Ns, 32, BM));
+      DG_TRY(make_map(&L.A0[i], t.F[i].p, true, (uint64_t)t.ldp, (uint64_t)Ns, 32, BM));
+      L.A1[i] = L.A0[i];
     } else {
-      DG_TRY(make_map(&mapH[i], t.Sh[i].p, false, (uint64_t)t.ldp, (uint64_t)Ns, 64, BM));
-      if (mode == MODE_BF16X3) DG_TRY(make_map(&mapL[i], t.Sl[i].p, false, (uint64_t)t.ldp, (uint64_t)Ns, 64, BM));
-      else mapL[i] = mapH[i];
+      DG_TRY(make_map(&L.A0[i], t.Sh[i].p, false, (uint64_t)t.ldp, (uint64_t)Ns, 64, BM));
+      if (mode == MODE_BF16X3) DG_TRY(make_map(&L.A1[i], t.Sl[i].p, false, (uint64_t)t.ldp, (uint64_t)Ns, 64, BM));
+      else L.A1[i] = L.A0[i];
     }
   }
   const uint64_t brows_total = (uint64_t)t.b_rows * (mode == MODE_BF16X3 ? 2 : 1);
-  DG_TRY(make_map(&mapB, t.Hop.p, f32, (uint64_t)W, brows_total, (uint32_t)W, (uint32_t)t.boxn));
-
+  DG_TRY(make_map(&L.B, t.Hop.p, f32, (uint64_t)W, brows_total, (uint32_t)W, (uint32_t)t.boxn));
   const int na = mode == MODE_BF16X3 ? 2 : 1;
-  const int stage_bytes = na * (t.T * A_BYTES + t.G * t.ACC * SLICE_BYTES);
+  const int stage_bytes = na * (T * A_BYTES + G * t.ACC * SLICE_BYTES);
   const int stages = mode == MODE_BF16X3 ? STAGES / 2 : STAGES;
-  const int smem = stages * stage_bytes + (2 * stages + 4) * 8 + 2 * t.maxent * (1 + t.G) * 4 + 1024;
-  if (smem > 227 * 1024) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "filter schedule too large for shared memory");
-  auto kern = pick_kernel(mode, t.G, t.T, t.ACC);
-  if (!kern) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "no filter kernel for G=%d T=%d ACC=%d", t.G, t.T, t.ACC);
-  DG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  DG_CUDA(cudaMemsetAsync(t.err_d, 0, sizeof(int), s));
-  Params p{};
-  p.sched = t.sched_d;
-  p.sched_ptr = t.sched_ptr_d;
-  p.grp_elem = t.grp_elem_d;
+  L.smem = stages * stage_bytes + (2 * stages + 4) * 8 + 2 * pl->maxent * (1 + G) * 4 + 1024;
+  if (L.smem > 227 * 1024) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "filter schedule too large for shared memory");
+  DG_CUDA(cudaFuncSetAttribute(L.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem));
+  Params& p = L.p;
+  p = Params{};
+  p.sched = pl->sched_d;
+  p.sched_ptr = pl->sched_ptr_d;
+  p.grp_elem = pl->grp_elem_d;
   p.nb = ctx->nb_d;
   p.pnb = t.pnb_d;
   p.poff = t.poff_d;
   p.lo_rows = t.b_rows;
   p.Ns = Ns;
   p.ldp = t.ldp;
+  p.coef = t.coef_d;
   p.W = W;
   p.mode = mode;
   p.boxn = t.boxn;
-  p.G = t.G;
-  p.T = t.T;
+  p.G = G;
+  p.T = T;
   p.ACC = t.ACC;
-  p.NBUF = t.NBUF;
+  p.NBUF = 2;
   p.stages = stages;
-  p.ngroups = t.ngroups;
-  p.ntg = (int)((Ns + (int64_t)BM * t.T - 1) / ((int64_t)BM * t.T));
-  p.maxent = t.maxent;
+  p.ngroups = pl->ngroups;
+  p.ntg = (int)((Ns + (int64_t)BM * T - 1) / ((int64_t)BM * T));
+  p.maxent = pl->maxent;
   p.err = t.err_d;
   const int64_t nunits = (int64_t)p.ngroups * p.ntg;
-  const unsigned grid = (unsigned)std::min<int64_t>(nunits, t.num_sms);
+  L.grid = dim3((unsigned)std::min<int64_t>(nunits, t.num_sms));
+  return DGCHEFSI_OK;
+}
+
+// Step k: Y_{k+1} from Y_k (buffer k%2) and Y_{k-1} (buffer (k+1)%2).
+static dgchefsi_status launch_step(dgchefsi_ctx* ctx, TcState& t, int mode, Launch& L, int k, cudaStream_t s) {
+  const int cur = k & 1, nxt = cur ^ 1;
+  Params p = L.p;
+  p.step = k;
+  p.Fprev = static_cast<float*>(t.F[nxt].p);
+  p.Fout = static_cast<float*>(t.F[nxt].p);
+  p.Hout = mode == MODE_TF32 ? nullptr : static_cast<__nv_bfloat16*>(t.Sh[nxt].p);
+  p.Lout = mode == MODE_BF16X3 ? static_cast<__nv_bfloat16*>(t.Sl[nxt].p) : nullptr;
+  L.kern<<<L.grid, NTHREADS, L.smem, s>>>(L.A0[cur], L.A1[cur], L.B, p);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  (void)ctx;
+  return DGCHEFSI_OK;
+}
+
+static dgchefsi_status upload_coefficients(dgchefsi_ctx* ctx, TcState& t, int m, double a, double b, double a0) {
+  if (t.coef_cap < 1 + 2 * m) {
+    if (t.gexec) {  // a captured graph refers to the old buffers
+      DG_CUDA(cudaStreamSynchronize(ctx->stream));
+      cudaGraphExecDestroy(t.gexec);
+      t.gexec = nullptr;
+    }
+    cudaFree(t.coef_d);
+    cudaFreeHost(t.coef_h);
+    t.coef_d = nullptr;
+    t.coef_h = nullptr;
+    t.coef_cap = 0;
+    DG_CUDA(cudaMalloc(&t.coef_d, sizeof(double) * (1 + 2 * m)));
+    DG_CUDA(cudaMallocHost(&t.coef_h, sizeof(double) * (1 + 2 * m)));
+    t.coef_cap = 1 + 2 * m;
+  }
+  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+  const double s1 = e / (a0 - c);
+  t.coef_h[0] = c;
   double sig = s1;
   for (int k = 0; k < m; ++k) {
-    // step k: Y_{k+1} from Y_k (buffer k%2) and Y_{k-1} (buffer (k+1)%2)
-    const int cur = k & 1, nxt = cur ^ 1;
     double alpha, beta;
     if (k == 0) {
       alpha = s1 / e;
@@ -850,24 +451,83 @@ dgchefsi_status filter_tc(dgchefsi_ctx* ctx, int prec, const double* X, double* 
       beta = sig * sn;
       sig = sn;
     }
-    p.alpha = (float)alpha;
-    p.beta = (float)beta;
-    p.Fprev = fb(nxt);
-    p.Fout = fb(nxt);
-    p.Hout = f32 ? nullptr : sh(nxt);
-    p.Lout = mode == MODE_BF16X3 ? sl(nxt) : nullptr;
-    const CUtensorMap& A0 = f32 ? mapF[cur] : mapH[cur];
-    const CUtensorMap& A1 = f32 ? mapF[cur] : mapL[cur];
-    kern<<<grid, NTHREADS, smem, s>>>(A0, A1, mapB, p);
-    count_launch();
-    DG_CUDA(cudaGetLastError());
+    t.coef_h[1 + 2 * k] = alpha;
+    t.coef_h[2 + 2 * k] = beta;
   }
-  {
-    dim3 g((unsigned)std::min<int64_t>(Ns, 1024), (unsigned)ctx->M);
-    k_unpack<<<g, 128, 0, s>>>(fb(m & 1), t.ldp, Ns, ctx->off_d, ctx->nb_d, t.poff_d, Y, ld);
-    count_launch();
-    DG_CUDA(cudaGetLastError());
+  return DGCHEFSI_OK;
+}
+
+// build_hop -> pack -> steps -> unpack, all on stream s (the coefficients must be on the device).
+static dgchefsi_status enqueue_filter(dgchefsi_ctx* ctx, TcState& t, int mode, Launch& L, const double* X,
+                                      double* Y, int64_t Ns, int64_t ld, int m, cudaStream_t s) {
+  const bool f32 = mode == MODE_TF32;
+  const int W = f32 ? 32 : 64;
+  k_build_hop<<<(unsigned)ctx->nnzb, 256, 0, s>>>(
+      t.blk_row_d, ctx->col_d, ctx->blk_off_d, ctx->vals_d, ctx->nb_d, t.pnb_d, t.brow_d, W, t.coef_d, mode, t.b_rows,
+      f32 ? static_cast<float*>(t.Hop.p) : nullptr, f32 ? nullptr : static_cast<__nv_bfloat16*>(t.Hop.p));
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  dim3 g((unsigned)std::min<int64_t>(Ns, 1024), (unsigned)ctx->M);
+  k_pack<<<g, 128, 0, s>>>(X, ld, Ns, ctx->off_d, ctx->nb_d, t.poff_d, t.ldp, static_cast<float*>(t.F[0].p),
+                           f32 ? nullptr : static_cast<__nv_bfloat16*>(t.Sh[0].p),
+                           mode == MODE_BF16X3 ? static_cast<__nv_bfloat16*>(t.Sl[0].p) : nullptr);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  for (int k = 0; k < m; ++k) DG_TRY(launch_step(ctx, t, mode, L, k, s));
+  k_unpack<<<g, 128, 0, s>>>(static_cast<float*>(t.F[m & 1].p), t.ldp, Ns, ctx->off_d, ctx->nb_d, t.poff_d, Y, ld);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  return DGCHEFSI_OK;
+}
+
+// Pick the unit shape for this precision: a forced one, the tuned one, or time
+// step 0 with every candidate whose accumulator width fits and keep the fastest.
+static dgchefsi_status choose_shape(dgchefsi_ctx* ctx, TcState& t, int mode, int64_t Ns, int* G, int* T) {
+  if (t.forceG[mode]) {
+    *G = t.forceG[mode];
+    *T = t.forceT[mode];
+    return DGCHEFSI_OK;
   }
+  if (t.shapeG[mode]) {
+    *G = t.shapeG[mode];
+    *T = t.shapeT[mode];
+    return DGCHEFSI_OK;
+  }
+  cudaStream_t s = ctx->stream;
+  cudaEvent_t e0, e1;
+  DG_CUDA(cudaEventCreate(&e0));
+  DG_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bG = 0, bT = 0;
+  for (int i = 0; i < NSHAPES; ++i) {
+    if (SHAPES[i][2] != t.ACC) continue;
+    Launch L;
+    dgchefsi_status st = prepare_launch(ctx, t, mode, SHAPES[i][0], SHAPES[i][1], Ns, L);
+    if (st != DGCHEFSI_OK) continue;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {  // the first launch warms caches and the L2
+      DG_CUDA(cudaEventRecord(e0, s));
+      DG_TRY(launch_step(ctx, t, mode, L, 0, s));
+      DG_CUDA(cudaEventRecord(e1, s));
+      DG_CUDA(cudaEventSynchronize(e1));
+      DG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    }
+    t.tuned_ms[mode][i] = ms;
+    if (ms < best) {
+      best = ms;
+      bG = SHAPES[i][0];
+      bT = SHAPES[i][1];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!bG) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "no tensor-core unit shape for accumulator width %d", t.ACC);
+  t.shapeG[mode] = *G = bG;
+  t.shapeT[mode] = *T = bT;
+  return DGCHEFSI_OK;
+}
+
+static dgchefsi_status check_err(TcState& t, cudaStream_t s) {
   int err = 0;
   DG_CUDA(cudaMemcpyAsync(&err, t.err_d, sizeof(int), cudaMemcpyDeviceToHost, s));
   DG_CUDA(cudaStreamSynchronize(s));
@@ -875,17 +535,155 @@ dgchefsi_status filter_tc(dgchefsi_ctx* ctx, int prec, const double* X, double* 
   return DGCHEFSI_OK;
 }
 
+static dgchefsi_status tc_prepare(dgchefsi_ctx* ctx, int prec, int64_t Ns, int m, double a, double b, double a0,
+                                  int* mode_out) {
+  if (ctx->max_nb > 128)
+    return set_error(DGCHEFSI_ERR_UNSUPPORTED, "tensor-core filter supports element sizes up to 128 (got %d)",
+                     ctx->max_nb);
+  if (Ns > 2147483647LL / 2 - 4 * BM) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "Ns too large");
+  if (!ctx->tc) ctx->tc = new TcState();
+  TcState& t = *ctx->tc;
+  const int mode = mode_of(prec);
+  DG_TRY(ensure_layout(ctx, t));
+  DG_TRY(ensure_mode(ctx, t, mode));
+  DG_TRY(ensure_iterates(ctx, t, mode, Ns));
+  DG_TRY(upload_coefficients(ctx, t, m, a, b, a0));
+  *mode_out = mode;
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status filter_tc(dgchefsi_ctx* ctx, int prec, const double* X, double* Y, int64_t Ns, int64_t ld, int m,
+                          double a, double b, double a0) {
+  int mode = 0;
+  DG_TRY(tc_prepare(ctx, prec, Ns, m, a, b, a0, &mode));
+  TcState& t = *ctx->tc;
+  cudaStream_t s = ctx->stream;
+  DG_CUDA(cudaMemcpyAsync(t.coef_d, t.coef_h, sizeof(double) * (1 + 2 * m), cudaMemcpyHostToDevice, s));
+  DG_CUDA(cudaMemsetAsync(t.err_d, 0, sizeof(int), s));
+  int G = 0, T = 0;
+  if (!t.forceG[mode] && !t.shapeG[mode]) {
+    // tuning runs step 0 on the packed block, so pack (and build H) first
+    const bool f32 = mode == MODE_TF32;
+    k_build_hop<<<(unsigned)ctx->nnzb, 256, 0, s>>>(
+        t.blk_row_d, ctx->col_d, ctx->blk_off_d, ctx->vals_d, ctx->nb_d, t.pnb_d, t.brow_d, f32 ? 32 : 64, t.coef_d,
+        mode, t.b_rows, f32 ? static_cast<float*>(t.Hop.p) : nullptr,
+        f32 ? nullptr : static_cast<__nv_bfloat16*>(t.Hop.p));
+    count_launch();
+    dim3 g((unsigned)std::min<int64_t>(Ns, 1024), (unsigned)ctx->M);
+    k_pack<<<g, 128, 0, s>>>(X, ld, Ns, ctx->off_d, ctx->nb_d, t.poff_d, t.ldp, static_cast<float*>(t.F[0].p),
+                             f32 ? nullptr : static_cast<__nv_bfloat16*>(t.Sh[0].p),
+                             mode == MODE_BF16X3 ? static_cast<__nv_bfloat16*>(t.Sl[0].p) : nullptr);
+    count_launch();
+    DG_CUDA(cudaGetLastError());
+  }
+  DG_TRY(choose_shape(ctx, t, mode, Ns, &G, &T));
+  Launch L;
+  DG_TRY(prepare_launch(ctx, t, mode, G, T, Ns, L));
+  DG_TRY(enqueue_filter(ctx, t, mode, L, X, Y, Ns, ld, m, s));
+  return check_err(t, s);
+}
+
+dgchefsi_status filter_tc_graph(dgchefsi_ctx* ctx, int prec, const double* X, double* Y, int64_t Ns, int64_t ld,
+                                int m, double a, double b, double a0) {
+  int mode = 0;
+  DG_TRY(tc_prepare(ctx, prec, Ns, m, a, b, a0, &mode));
+  TcState& t = *ctx->tc;
+  cudaStream_t s = ctx->stream;
+  if (!t.forceG[mode] && !t.shapeG[mode]) {
+    // tune with one ordinary call (host synchronisation is not allowed under capture)
+    DG_TRY(filter_tc(ctx, prec, X, Y, Ns, ld, m, a, b, a0));
+    DG_TRY(upload_coefficients(ctx, t, m, a, b, a0));
+  }
+  int G = 0, T = 0;
+  DG_TRY(choose_shape(ctx, t, mode, Ns, &G, &T));
+  const bool same = t.gexec && t.g_mode == mode && t.g_m == m && t.g_G == G && t.g_T == T && t.g_X == X &&
+                    t.g_Y == Y && t.g_Ns == Ns && t.g_ld == ld;
+  if (!same) {
+    if (t.gexec) {
+      DG_CUDA(cudaStreamSynchronize(s));
+      cudaGraphExecDestroy(t.gexec);
+      t.gexec = nullptr;
+    }
+    if (!t.cap_stream) DG_CUDA(cudaStreamCreateWithFlags(&t.cap_stream, cudaStreamNonBlocking));
+    Launch L;
+    DG_TRY(prepare_launch(ctx, t, mode, G, T, Ns, L));
+    cudaGraph_t graph = nullptr;
+    DG_CUDA(cudaStreamBeginCapture(t.cap_stream, cudaStreamCaptureModeThreadLocal));
+    // the coefficients are copied from the pinned host mirror at every replay
+    cudaError_t e1 = cudaMemcpyAsync(t.coef_d, t.coef_h, sizeof(double) * (1 + 2 * m), cudaMemcpyHostToDevice,
+                                     t.cap_stream);
+    cudaError_t e2 = cudaMemsetAsync(t.err_d, 0, sizeof(int), t.cap_stream);
+    dgchefsi_status st = DGCHEFSI_OK;
+    if (e1 == cudaSuccess && e2 == cudaSuccess) st = enqueue_filter(ctx, t, mode, L, X, Y, Ns, ld, m, t.cap_stream);
+    cudaError_t e3 = cudaStreamEndCapture(t.cap_stream, &graph);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || st != DGCHEFSI_OK || e3 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      if (st != DGCHEFSI_OK) return st;
+      return set_error(DGCHEFSI_ERR_CUDA, "capture of the filter graph failed");
+    }
+    cudaError_t e4 = cudaGraphInstantiate(&t.gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e4 != cudaSuccess) {
+      t.gexec = nullptr;
+      return set_error(DGCHEFSI_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e4));
+    }
+    t.g_mode = mode;
+    t.g_m = m;
+    t.g_G = G;
+    t.g_T = T;
+    t.g_X = X;
+    t.g_Y = Y;
+    t.g_Ns = Ns;
+    t.g_ld = ld;
+  }
+  DG_CUDA(cudaGraphLaunch(t.gexec, s));
+  count_launch(m + 3);
+  return check_err(t, s);
+}
+
+dgchefsi_status tc_set_shape(dgchefsi_ctx* ctx, int prec, int G, int T) {
+  if (!ctx->tc) ctx->tc = new TcState();
+  TcState& t = *ctx->tc;
+  DG_TRY(ensure_layout(ctx, t));
+  const int mode = mode_of(prec);
+  if (G == 0 && T == 0) {
+    t.forceG[mode] = t.forceT[mode] = 0;
+    return DGCHEFSI_OK;
+  }
+  if (!pick_kernel(mode, G, T, t.ACC))
+    return set_error(DGCHEFSI_ERR_UNSUPPORTED, "no kernel for G=%d T=%d with accumulator width %d", G, T, t.ACC);
+  t.forceG[mode] = G;
+  t.forceT[mode] = T;
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status tc_get_shape(dgchefsi_ctx* ctx, int prec, int* G, int* T, int* ACC) {
+  if (!ctx->tc) {
+    *G = *T = *ACC = 0;
+    return DGCHEFSI_OK;
+  }
+  TcState& t = *ctx->tc;
+  const int mode = mode_of(prec);
+  *G = t.forceG[mode] ? t.forceG[mode] : t.shapeG[mode];
+  *T = t.forceG[mode] ? t.forceT[mode] : t.shapeT[mode];
+  *ACC = t.ACC;
+  return DGCHEFSI_OK;
+}
+
 void tc_destroy(dgchefsi_ctx* ctx) {
   if (!ctx->tc) return;
   TcState& t = *ctx->tc;
+  if (t.gexec) cudaGraphExecDestroy(t.gexec);
+  if (t.cap_stream) cudaStreamDestroy(t.cap_stream);
+  for (auto& kv : t.plans) free_plan(kv.second);
   cudaFree(t.pnb_d);
   cudaFree(t.poff_d);
   cudaFree(t.blk_row_d);
   cudaFree(t.brow_d);
-  cudaFree(t.grp_elem_d);
-  cudaFree(t.sched_d);
-  cudaFree(t.sched_ptr_d);
   cudaFree(t.err_d);
+  cudaFree(t.coef_d);
+  cudaFreeHost(t.coef_h);
   for (int i = 0; i < 2; ++i) {
     cudaFree(t.F[i].p);
     cudaFree(t.Sh[i].p);

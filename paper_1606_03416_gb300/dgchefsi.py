@@ -27,7 +27,9 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_SPD", 
 EXPORTS = ["dgchefsi_create", "dgchefsi_destroy", "dgchefsi_set_stream", "dgchefsi_dims", "dgchefsi_matvec",
            "dgchefsi_bounds", "dgchefsi_filter", "dgchefsi_rayleigh_ritz", "dgchefsi_occupations",
            "dgchefsi_density_blocks", "dgchefsi_cycle", "dgchefsi_last_error", "dgchefsi_launch_count",
-           "dgchefsi_bounds_static", "dgchefsi_gram", "dgchefsi_set_values", "dgchefsi_energy_grad"]
+           "dgchefsi_bounds_static", "dgchefsi_gram", "dgchefsi_set_values", "dgchefsi_energy_grad",
+           "dgchefsi_filter_graph", "dgchefsi_set_tile_shape", "dgchefsi_get_tile_shape",
+           "dgchefsi_selftest_wait"]
 
 # Capacity (doubles) of the library's fixed scratch array for bounds_static.
 BOUNDS_STATIC_DOUBLES = 1 << 20
@@ -56,6 +58,10 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_filter": (st, [P, C.c_int, P, P, I64, I64, C.c_int, D, D, D]),
         "dgchefsi_rayleigh_ritz": (st, [P, P, I64, I64, P]),
         "dgchefsi_gram": (st, [P, P, I64, I64, P]),
+        "dgchefsi_filter_graph": (st, [P, C.c_int, P, P, I64, I64, C.c_int, D, D, D]),
+        "dgchefsi_set_tile_shape": (st, [P, C.c_int, C.c_int, C.c_int]),
+        "dgchefsi_get_tile_shape": (st, [P, C.c_int, P, P, P]),
+        "dgchefsi_selftest_wait": (st, [P, I64]),
         "dgchefsi_set_values": (st, [P, P]),
         "dgchefsi_energy_grad": (st, [P, C.c_int, P, I64, I64, C.c_int, D, D, D, D, D, C.c_int, P, P, P, P]),
         "dgchefsi_occupations": (st, [P, P, I64, D, D, P, P]),
@@ -201,6 +207,30 @@ class Context:
         self._sync_stream()
         _check(_lib.dgchefsi_gram(self._h, _ptr(Y), Ns, ld, _ptr(S)))
         return S
+
+    def filter_graph(self, X: torch.Tensor, m: int, a: float, b: float, a0: float, prec: str = "bf16x3",
+                     Y: torch.Tensor | None = None) -> torch.Tensor:
+        """The tensor-core filter replayed from a CUDA graph (captured on first use)."""
+        Ns, ld = _block(X, self.N, "X")
+        if Y is None:
+            Y = torch.empty_like(X)
+        self._sync_stream()
+        _check(_lib.dgchefsi_filter_graph(self._h, PRECISIONS[prec], _ptr(X), _ptr(Y), Ns, ld, int(m), float(a),
+                                          float(b), float(a0)))
+        return Y
+
+    def selftest_wait(self, limit_ns: int = 50_000_000):
+        """Run the bounded-wait self-test; returns the status name (ERR_TIMEOUT expected)."""
+        st = _lib.dgchefsi_selftest_wait(self._h, int(limit_ns))
+        return STATUS.get(st, str(st)), last_error()
+
+    def set_tile_shape(self, prec: str, G: int, T: int):
+        _check(_lib.dgchefsi_set_tile_shape(self._h, PRECISIONS[prec], int(G), int(T)))
+
+    def tile_shape(self, prec: str):
+        g, t, acc = C.c_int(), C.c_int(), C.c_int()
+        _check(_lib.dgchefsi_get_tile_shape(self._h, PRECISIONS[prec], C.byref(g), C.byref(t), C.byref(acc)))
+        return g.value, t.value, acc.value
 
     # -- Alg. 1 steps 3-5 (in place: Y becomes X_new)
     def rayleigh_ritz(self, Y: torch.Tensor, ritz: torch.Tensor | None = None) -> torch.Tensor:

@@ -227,3 +227,17 @@ def test_error_paths(dev):
         # the context still works after the errors
         out = ctx.matvec(X)
         assert rel_max(out.cpu().numpy(), O.matvec(Ho, X0.T).T) <= 1e-11
+
+
+def test_bounded_wait_times_out_and_context_survives(dev):
+    """Failure detection: a device wait that nothing satisfies gives up after
+    its bound and reports a timeout; the context keeps working."""
+    H, Ho, X0, _, _, _ = problem(problems()[0])
+    with D.Context(H) as ctx:
+        import time
+        t0 = time.time()
+        status, msg = ctx.selftest_wait(50_000_000)   # 50 ms
+        assert status == "ERR_TIMEOUT" and "gave up" in msg
+        assert time.time() - t0 < 5.0
+        Y = ctx.matvec(torch.from_numpy(X0).to(dev))
+        assert rel_max(Y.cpu().numpy(), O.matvec(Ho, X0.T).T) <= 1e-11

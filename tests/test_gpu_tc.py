@@ -101,3 +101,50 @@ def test_mixed_cycles_converge(prec):
     print(f"RITZ_ERR tiny {prec} {err:.3e}")
     limit = {"bf16x3": 1e-8, "tf32": 1e-4, "bf16": 1e-3}[prec]
     assert err <= limit
+
+
+SHAPES = {32: [(4, 2), (2, 2)], 64: [(2, 2), (1, 2), (2, 1)], 128: [(2, 1), (1, 2)]}
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3", "tf32"])
+@pytest.mark.parametrize("cfg", problems()[:3], ids=lambda c: c.name)
+def test_every_unit_shape_matches_oracle(cfg, prec):
+    """Each work-unit shape the autotuner may pick gives the same filter."""
+    H, Ho, X0, _, Ns, _, lam = problem(cfg)
+    a0, b, a = lam[0] - 0.5, lam[-1] + 0.5, lam[min(Ns, Ho.N - 1)]
+    ref = O.chebyshev_filter(Ho, X0.T, cfg.m, a, b, a0).T
+    dev = torch.device("cuda:0")
+    with D.Context(H) as ctx:
+        acc = 32 if Ho.nb.max() <= 32 else (64 if Ho.nb.max() <= 64 else 128)
+        for G, T in SHAPES[acc]:
+            ctx.set_tile_shape(prec, G, T)
+            assert ctx.tile_shape(prec) == (G, T, acc)
+            Y = ctx.filter(torch.from_numpy(X0).to(dev), cfg.m, a, b, a0, prec=prec).cpu().numpy()
+            err = np.linalg.norm(Y - ref) / np.linalg.norm(ref)
+            assert err <= 2 * cfg.m * U_OP[prec], (G, T, err)
+        ctx.set_tile_shape(prec, 0, 0)  # back to the autotuner
+        ctx.filter(torch.from_numpy(X0).to(dev), 2, a, b, a0, prec=prec)
+        G, T, _ = ctx.tile_shape(prec)
+        assert (G, T) in SHAPES[acc]
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_graph_filter_equals_direct_filter(prec):
+    """The CUDA-graph replay gives bit-identical results to ordinary launches,
+    also after the bounds (hence the recurrence coefficients) change."""
+    H, Ho, X0, _, Ns, _, lam = problem(problems()[2])   # uneven element sizes
+    dev = torch.device("cuda:0")
+    X = torch.from_numpy(X0).to(dev)
+    with D.Context(H) as ctx:
+        Yg = torch.empty_like(X)
+        for shift in (0.5, 1.5, 0.5):
+            a0, b, a = lam[0] - shift, lam[-1] + shift, lam[Ns]
+            Yd = ctx.filter(X, 7, a, b, a0, prec=prec)
+            ctx.filter_graph(X, 7, a, b, a0, prec=prec, Y=Yg)
+            assert torch.equal(Yd, Yg), shift
+        ref = O.chebyshev_filter(Ho, X0.T, 7, lam[Ns], lam[-1] + 0.5, lam[0] - 0.5).T
+        assert np.linalg.norm(Yg.cpu().numpy() - ref) <= 14 * U_OP[prec] * np.linalg.norm(ref)
+    with D.Context(H) as ctx:
+        with pytest.raises(D.DGChefsiError) as e:
+            ctx.filter_graph(X, 3, 1.0, 2.0, 0.0, prec="f64")
+        assert e.value.status == "ERR_UNSUPPORTED"

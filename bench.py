@@ -120,11 +120,11 @@ def profiled_traffic(prec: str, Ns: int):
     grows in proportion). None otherwise."""
     import glob
     import hashlib
-    src = os.path.join(ROOT, "paper_1606_03416_gb300", "csrc", "tc_filter.cu")
+    src = os.path.join(ROOT, "paper_1606_03416_gb300", "csrc", "tc_kernel.cuh")
     sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
     for path in glob.glob(os.path.join(ROOT, "profiles", f"k_filter_step_tc_{prec}_bulk3d_*.md")):
         text = open(path).read()
-        if f"source-sha1 (paper_1606_03416_gb300/csrc/tc_filter.cu, first 12): {sha}" not in text:
+        if f"source-sha1 (paper_1606_03416_gb300/csrc/tc_kernel.cuh, first 12): {sha}" not in text:
             continue
         for line in text.splitlines():
             key = f"traffic-per-launch-bytes-{prec}-Ns"

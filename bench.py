@@ -205,6 +205,9 @@ def run_filter_only(args):
     X = torch.from_numpy(G.make_X(H.N, cfg.Ns, cfg.seed)).to(dev)
     Y = torch.empty_like(X)
     with D.Context(H) as ctx:
+        if args.shape:
+            G_, T_, L_ = (int(v) for v in args.shape.split(","))
+            ctx.set_tile_shape(args.prec, G_, T_, L_)
         for _ in range(args.warmup):
             ctx.filter(X, cfg.m, 10.0, 45.0, -2.0, prec=args.prec, Y=Y)
         torch.cuda.synchronize()
@@ -215,9 +218,11 @@ def run_filter_only(args):
         e.record()
         torch.cuda.synchronize()
         ms = s.elapsed_time(e) / max(args.steps, 1)
+        shape = ctx.tile_shape(args.prec) if args.prec != "f64" else None
     fl = filter_flops(H, cfg.Ns, cfg.m)
     print(json.dumps({"mode": "filter-only", "workload": args.workload, "Ns": cfg.Ns, "m": cfg.m, "prec": args.prec,
-                      "ms_per_filter": ms, "filter_tflops": fl / (ms * 1e-3) / 1e12}), flush=True)
+                      "ms_per_filter": ms, "filter_tflops": fl / (ms * 1e-3) / 1e12, "unit_shape": shape}),
+          flush=True)
     return 0
 
 
@@ -249,9 +254,9 @@ def measure_uneven(dev, precs=("bf16x3", "tf32"), reps=3):
                 e_.record()
                 torch.cuda.synchronize()
                 ts.append(s_.elapsed_time(e_))
-            g_, t_, acc = ctx.tile_shape(pr)
+            g_, t_, acc, lay = ctx.tile_shape(pr)
             out[pr] = {"ms_per_filter": min(ts), "tflops": fl / (min(ts) * 1e-3) / 1e12,
-                       "unit_shape": {"G": g_, "T": t_, "ACC": acc}, "graph": True}
+                       "unit_shape": {"G": g_, "T": t_, "ACC": acc, "layout": lay}, "graph": True}
     del X, Y
     torch.cuda.empty_cache()
     return out
@@ -273,6 +278,7 @@ def main():
                     help="time only the filter (profiling case); --ns and --m override the workload")
     ap.add_argument("--ns", type=int, default=0)
     ap.add_argument("--m", type=int, default=0)
+    ap.add_argument("--shape", default="", help="filter-only: force the unit shape G,T,layout (default: autotune)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

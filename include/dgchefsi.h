@@ -154,14 +154,16 @@ dgchefsi_status dgchefsi_filter_graph(dgchefsi_ctx* ctx, int prec, const double*
                                       int64_t ld, int m, double a, double b, double a0);
 
 /* Work-unit shape of the tensor-core filter for one precision: G consecutive
- * elements x T tiles of 128 states per unit (G*T accumulators of ACC columns
- * in tensor memory). By default (G = T = 0) the first filter call times one
- * step with every shape that has a kernel for this H's accumulator width
- * (ACC = 32, 64 or 128, from the largest element) and keeps the fastest.
- * Setting a shape that has no kernel returns DGCHEFSI_ERR_UNSUPPORTED. */
-dgchefsi_status dgchefsi_set_tile_shape(dgchefsi_ctx* ctx, int prec, int G, int T);
-/* The shape in use (0, 0 if not chosen yet) and the accumulator width. */
-dgchefsi_status dgchefsi_get_tile_shape(dgchefsi_ctx* ctx, int prec, int* G, int* T, int* ACC);
+ * elements x T tiles of 128 states per unit, ACC accumulator columns per
+ * element (32, 64 or 128, from the largest element). layout 0 puts states on
+ * the MMA's M dimension (G*T accumulators); layout 1 puts the G = 128/ACC
+ * elements' rows on M and 2 x 128 states on N. By default (G = T = 0) the
+ * first filter call times one step with every shape that has a kernel for
+ * this H's accumulator width and keeps the fastest. Setting a shape without a
+ * kernel returns DGCHEFSI_ERR_UNSUPPORTED. */
+dgchefsi_status dgchefsi_set_tile_shape(dgchefsi_ctx* ctx, int prec, int G, int T, int layout);
+/* The shape in use (all 0 if not chosen yet) and the accumulator width. */
+dgchefsi_status dgchefsi_get_tile_shape(dgchefsi_ctx* ctx, int prec, int* G, int* T, int* ACC, int* layout);
 
 /* Overlap matrix S = Y^T Y of a block (the first product of Cholesky-QR,
  * Alg. 1 step 3), FP64: the tiles on and below the diagonal are computed and

@@ -483,20 +483,21 @@ dgchefsi_status dgchefsi_filter_graph(dgchefsi_ctx* ctx, int prec, const double*
   return filter_tc_graph(ctx, prec, X, Y, Ns, ld, m, a, b, a0);
 }
 
-dgchefsi_status dgchefsi_set_tile_shape(dgchefsi_ctx* ctx, int prec, int G, int T) {
+dgchefsi_status dgchefsi_set_tile_shape(dgchefsi_ctx* ctx, int prec, int G, int T, int layout) {
   clear_error();
   DG_TRY(check_ctx(ctx));
   if (prec < DGCHEFSI_TF32 || prec > DGCHEFSI_BF16X3) return set_error(DGCHEFSI_ERR_ARG, "not a tensor-core precision");
   if (G < 0 || T < 0 || (G == 0) != (T == 0)) return set_error(DGCHEFSI_ERR_ARG, "need G, T both > 0 or both 0");
-  return tc_set_shape(ctx, prec, G, T);
+  if (layout < 0 || layout > 1) return set_error(DGCHEFSI_ERR_ARG, "layout must be 0 or 1");
+  return tc_set_shape(ctx, prec, G, T, layout);
 }
 
-dgchefsi_status dgchefsi_get_tile_shape(dgchefsi_ctx* ctx, int prec, int* G, int* T, int* ACC) {
+dgchefsi_status dgchefsi_get_tile_shape(dgchefsi_ctx* ctx, int prec, int* G, int* T, int* ACC, int* layout) {
   clear_error();
   DG_TRY(check_ctx(ctx));
-  if (!G || !T || !ACC) return set_error(DGCHEFSI_ERR_ARG, "null output");
+  if (!G || !T || !ACC || !layout) return set_error(DGCHEFSI_ERR_ARG, "null output");
   if (prec < DGCHEFSI_TF32 || prec > DGCHEFSI_BF16X3) return set_error(DGCHEFSI_ERR_ARG, "not a tensor-core precision");
-  return tc_get_shape(ctx, prec, G, T, ACC);
+  return tc_get_shape(ctx, prec, G, T, ACC, layout);
 }
 
 dgchefsi_status dgchefsi_selftest_wait(dgchefsi_ctx* ctx, int64_t limit_ns) {

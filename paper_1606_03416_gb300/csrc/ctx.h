@@ -84,8 +84,8 @@ dgchefsi_status filter_tc(dgchefsi_ctx* ctx, int prec, const double* X, double* 
 // The same filter replayed from a CUDA graph captured for (prec, X, Y, Ns, ld, m).
 dgchefsi_status filter_tc_graph(dgchefsi_ctx* ctx, int prec, const double* X, double* Y, int64_t Ns, int64_t ld,
                                 int m, double a, double b, double a0);
-dgchefsi_status tc_set_shape(dgchefsi_ctx* ctx, int prec, int G, int T);
-dgchefsi_status tc_get_shape(dgchefsi_ctx* ctx, int prec, int* G, int* T, int* ACC);
+dgchefsi_status tc_set_shape(dgchefsi_ctx* ctx, int prec, int G, int T, int layout);
+dgchefsi_status tc_get_shape(dgchefsi_ctx* ctx, int prec, int* G, int* T, int* ACC, int* layout);
 dgchefsi_status tc_wait_selftest(dgchefsi_ctx* ctx, int64_t limit_ns);
 void tc_destroy(dgchefsi_ctx* ctx);
 

@@ -150,22 +150,22 @@ struct TcState {
   double* coef_h = nullptr;  // pinned mirror
   int coef_cap = 0;
   std::map<int, Plan> plans;  // keyed by G
-  int shapeG[3] = {0, 0, 0}, shapeT[3] = {0, 0, 0};    // chosen per precision (0 = not yet)
-  int forceG[3] = {0, 0, 0}, forceT[3] = {0, 0, 0};    // set by dgchefsi_set_tile_shape
+  int shapeG[3] = {0, 0, 0}, shapeT[3] = {0, 0, 0}, shapeL[3] = {0, 0, 0};  // chosen per precision
+  int forceG[3] = {0, 0, 0}, forceT[3] = {0, 0, 0}, forceL[3] = {0, 0, 0};  // dgchefsi_set_tile_shape
   float tuned_ms[3][NSHAPES] = {};
   // graph form
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
-  int g_mode = -1, g_m = 0, g_G = 0, g_T = 0;
+  int g_mode = -1, g_m = 0, g_G = 0, g_T = 0, g_L = 0;
   const void* g_X = nullptr;
   void* g_Y = nullptr;
   int64_t g_Ns = 0, g_ld = 0;
 };
 
-static FilterKernel pick_kernel(int mode, int G, int T, int ACC) {
-  if (mode == MODE_TF32) return pick_kernel_tf32(G, T, ACC);
-  if (mode == MODE_BF16) return pick_kernel_bf16(G, T, ACC);
-  return pick_kernel_bf16x3(G, T, ACC);
+static FilterKernel pick_kernel(int mode, int G, int T, int ACC, int layout) {
+  if (mode == MODE_TF32) return pick_kernel_tf32(G, T, ACC, layout);
+  if (mode == MODE_BF16) return pick_kernel_bf16(G, T, ACC, layout);
+  return pick_kernel_bf16x3(G, T, ACC, layout);
 }
 
 static void free_plan(Plan& pl) {
@@ -349,28 +349,32 @@ struct Launch {
   int smem = 0;
 };
 
-static dgchefsi_status prepare_launch(dgchefsi_ctx* ctx, TcState& t, int mode, int G, int T, int64_t Ns,
-                                      Launch& L) {
+static dgchefsi_status prepare_launch(dgchefsi_ctx* ctx, TcState& t, int mode, int G, int T, int layout,
+                                      int64_t Ns, Launch& L) {
   const bool f32 = mode == MODE_TF32;
   const int W = f32 ? 32 : 64;
   Plan* pl = nullptr;
   DG_TRY(get_plan(ctx, t, G, &pl));
-  L.kern = pick_kernel(mode, G, T, t.ACC);
-  if (!L.kern) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "no filter kernel for G=%d T=%d ACC=%d", G, T, t.ACC);
+  L.kern = pick_kernel(mode, G, T, t.ACC, layout);
+  if (!L.kern)
+    return set_error(DGCHEFSI_ERR_UNSUPPORTED, "no filter kernel for G=%d T=%d ACC=%d layout %d", G, T, t.ACC, layout);
+  const uint32_t xrows = layout == 1 ? 256u : (uint32_t)BM;  // states per box of Y_k
   for (int i = 0; i < 2; ++i) {
     if (f32) {
-      DG_TRY(make_map(&L.A0[i], t.F[i].p, true, (uint64_t)t.ldp, (uint64_t)Ns, 32, BM));
+      DG_TRY(make_map(&L.A0[i], t.F[i].p, true, (uint64_t)t.ldp, (uint64_t)Ns, 32, xrows));
       L.A1[i] = L.A0[i];
     } else {
-      DG_TRY(make_map(&L.A0[i], t.Sh[i].p, false, (uint64_t)t.ldp, (uint64_t)Ns, 64, BM));
-      if (mode == MODE_BF16X3) DG_TRY(make_map(&L.A1[i], t.Sl[i].p, false, (uint64_t)t.ldp, (uint64_t)Ns, 64, BM));
+      DG_TRY(make_map(&L.A0[i], t.Sh[i].p, false, (uint64_t)t.ldp, (uint64_t)Ns, 64, xrows));
+      if (mode == MODE_BF16X3)
+        DG_TRY(make_map(&L.A1[i], t.Sl[i].p, false, (uint64_t)t.ldp, (uint64_t)Ns, 64, xrows));
       else L.A1[i] = L.A0[i];
     }
   }
   const uint64_t brows_total = (uint64_t)t.b_rows * (mode == MODE_BF16X3 ? 2 : 1);
   DG_TRY(make_map(&L.B, t.Hop.p, f32, (uint64_t)W, brows_total, (uint32_t)W, (uint32_t)t.boxn));
   const int na = mode == MODE_BF16X3 ? 2 : 1;
-  const int stage_bytes = na * (T * A_BYTES + G * t.ACC * SLICE_BYTES);
+  const int stage_bytes = layout == 1 ? na * (128 * SLICE_BYTES + 256 * SLICE_BYTES)
+                                      : na * (T * A_BYTES + G * t.ACC * SLICE_BYTES);
   const int stages = mode == MODE_BF16X3 ? STAGES / 2 : STAGES;
   L.smem = stages * stage_bytes + (2 * stages + 4) * 8 + 2 * pl->maxent * (1 + G) * 4 + 1024;
   if (L.smem > 227 * 1024) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "filter schedule too large for shared memory");
@@ -482,15 +486,18 @@ static dgchefsi_status enqueue_filter(dgchefsi_ctx* ctx, TcState& t, int mode, L
 
 // Pick the unit shape for this precision: a forced one, the tuned one, or time
 // step 0 with every candidate whose accumulator width fits and keep the fastest.
-static dgchefsi_status choose_shape(dgchefsi_ctx* ctx, TcState& t, int mode, int64_t Ns, int* G, int* T) {
+static dgchefsi_status choose_shape(dgchefsi_ctx* ctx, TcState& t, int mode, int64_t Ns, int* G, int* T,
+                                    int* layout) {
   if (t.forceG[mode]) {
     *G = t.forceG[mode];
     *T = t.forceT[mode];
+    *layout = t.forceL[mode];
     return DGCHEFSI_OK;
   }
   if (t.shapeG[mode]) {
     *G = t.shapeG[mode];
     *T = t.shapeT[mode];
+    *layout = t.shapeL[mode];
     return DGCHEFSI_OK;
   }
   cudaStream_t s = ctx->stream;
@@ -498,11 +505,11 @@ static dgchefsi_status choose_shape(dgchefsi_ctx* ctx, TcState& t, int mode, int
   DG_CUDA(cudaEventCreate(&e0));
   DG_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  int bG = 0, bT = 0;
+  int bG = 0, bT = 0, bL = 0;
   for (int i = 0; i < NSHAPES; ++i) {
     if (SHAPES[i][2] != t.ACC) continue;
     Launch L;
-    dgchefsi_status st = prepare_launch(ctx, t, mode, SHAPES[i][0], SHAPES[i][1], Ns, L);
+    dgchefsi_status st = prepare_launch(ctx, t, mode, SHAPES[i][0], SHAPES[i][1], SHAPES[i][3], Ns, L);
     if (st != DGCHEFSI_OK) continue;
     float ms = 0.f;
     for (int rep = 0; rep < 2; ++rep) {  // the first launch warms caches and the L2
@@ -517,6 +524,7 @@ static dgchefsi_status choose_shape(dgchefsi_ctx* ctx, TcState& t, int mode, int
       best = ms;
       bG = SHAPES[i][0];
       bT = SHAPES[i][1];
+      bL = SHAPES[i][3];
     }
   }
   cudaEventDestroy(e0);
@@ -524,6 +532,8 @@ static dgchefsi_status choose_shape(dgchefsi_ctx* ctx, TcState& t, int mode, int
   if (!bG) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "no tensor-core unit shape for accumulator width %d", t.ACC);
   t.shapeG[mode] = *G = bG;
   t.shapeT[mode] = *T = bT;
+  t.shapeL[mode] = *layout = bL;
+  clear_error();  // a candidate without a kernel is skipped, not an error
   return DGCHEFSI_OK;
 }
 
@@ -576,9 +586,10 @@ dgchefsi_status filter_tc(dgchefsi_ctx* ctx, int prec, const double* X, double* 
     count_launch();
     DG_CUDA(cudaGetLastError());
   }
-  DG_TRY(choose_shape(ctx, t, mode, Ns, &G, &T));
+  int layout = 0;
+  DG_TRY(choose_shape(ctx, t, mode, Ns, &G, &T, &layout));
   Launch L;
-  DG_TRY(prepare_launch(ctx, t, mode, G, T, Ns, L));
+  DG_TRY(prepare_launch(ctx, t, mode, G, T, layout, Ns, L));
   DG_TRY(enqueue_filter(ctx, t, mode, L, X, Y, Ns, ld, m, s));
   return check_err(t, s);
 }
@@ -594,10 +605,10 @@ dgchefsi_status filter_tc_graph(dgchefsi_ctx* ctx, int prec, const double* X, do
     DG_TRY(filter_tc(ctx, prec, X, Y, Ns, ld, m, a, b, a0));
     DG_TRY(upload_coefficients(ctx, t, m, a, b, a0));
   }
-  int G = 0, T = 0;
-  DG_TRY(choose_shape(ctx, t, mode, Ns, &G, &T));
-  const bool same = t.gexec && t.g_mode == mode && t.g_m == m && t.g_G == G && t.g_T == T && t.g_X == X &&
-                    t.g_Y == Y && t.g_Ns == Ns && t.g_ld == ld;
+  int G = 0, T = 0, layout = 0;
+  DG_TRY(choose_shape(ctx, t, mode, Ns, &G, &T, &layout));
+  const bool same = t.gexec && t.g_mode == mode && t.g_m == m && t.g_G == G && t.g_T == T && t.g_L == layout &&
+                    t.g_X == X && t.g_Y == Y && t.g_Ns == Ns && t.g_ld == ld;
   if (!same) {
     if (t.gexec) {
       DG_CUDA(cudaStreamSynchronize(s));
@@ -606,7 +617,7 @@ dgchefsi_status filter_tc_graph(dgchefsi_ctx* ctx, int prec, const double* X, do
     }
     if (!t.cap_stream) DG_CUDA(cudaStreamCreateWithFlags(&t.cap_stream, cudaStreamNonBlocking));
     Launch L;
-    DG_TRY(prepare_launch(ctx, t, mode, G, T, Ns, L));
+    DG_TRY(prepare_launch(ctx, t, mode, G, T, layout, Ns, L));
     cudaGraph_t graph = nullptr;
     DG_CUDA(cudaStreamBeginCapture(t.cap_stream, cudaStreamCaptureModeThreadLocal));
     // the coefficients are copied from the pinned host mirror at every replay
@@ -632,6 +643,7 @@ dgchefsi_status filter_tc_graph(dgchefsi_ctx* ctx, int prec, const double* X, do
     t.g_m = m;
     t.g_G = G;
     t.g_T = T;
+    t.g_L = layout;
     t.g_X = X;
     t.g_Y = Y;
     t.g_Ns = Ns;
@@ -642,31 +654,34 @@ dgchefsi_status filter_tc_graph(dgchefsi_ctx* ctx, int prec, const double* X, do
   return check_err(t, s);
 }
 
-dgchefsi_status tc_set_shape(dgchefsi_ctx* ctx, int prec, int G, int T) {
+dgchefsi_status tc_set_shape(dgchefsi_ctx* ctx, int prec, int G, int T, int layout) {
   if (!ctx->tc) ctx->tc = new TcState();
   TcState& t = *ctx->tc;
   DG_TRY(ensure_layout(ctx, t));
   const int mode = mode_of(prec);
   if (G == 0 && T == 0) {
-    t.forceG[mode] = t.forceT[mode] = 0;
+    t.forceG[mode] = t.forceT[mode] = t.forceL[mode] = 0;
     return DGCHEFSI_OK;
   }
-  if (!pick_kernel(mode, G, T, t.ACC))
-    return set_error(DGCHEFSI_ERR_UNSUPPORTED, "no kernel for G=%d T=%d with accumulator width %d", G, T, t.ACC);
+  if (!pick_kernel(mode, G, T, t.ACC, layout))
+    return set_error(DGCHEFSI_ERR_UNSUPPORTED, "no kernel for G=%d T=%d layout %d with accumulator width %d", G, T,
+                     layout, t.ACC);
   t.forceG[mode] = G;
   t.forceT[mode] = T;
+  t.forceL[mode] = layout;
   return DGCHEFSI_OK;
 }
 
-dgchefsi_status tc_get_shape(dgchefsi_ctx* ctx, int prec, int* G, int* T, int* ACC) {
+dgchefsi_status tc_get_shape(dgchefsi_ctx* ctx, int prec, int* G, int* T, int* ACC, int* layout) {
   if (!ctx->tc) {
-    *G = *T = *ACC = 0;
+    *G = *T = *ACC = *layout = 0;
     return DGCHEFSI_OK;
   }
   TcState& t = *ctx->tc;
   const int mode = mode_of(prec);
   *G = t.forceG[mode] ? t.forceG[mode] : t.shapeG[mode];
   *T = t.forceG[mode] ? t.forceT[mode] : t.shapeT[mode];
+  *layout = t.forceG[mode] ? t.forceL[mode] : t.shapeL[mode];
   *ACC = t.ACC;
   return DGCHEFSI_OK;
 }

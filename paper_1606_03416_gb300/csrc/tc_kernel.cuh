@@ -498,16 +498,256 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 
+
+// Transposed orientation: the MMA's M = 128 rows are the H rows of the unit's
+// G = 128/ACC elements stacked (A operand: the blocks (H - cI)_{K_g K'} of one
+// slice), and N = 256 states (B operand: the slice of Y_k for 256 states).
+// Per ring slot 16 KB of A and 32 KB of B feed four 128x256x16 MMAs, so the
+// tensor core reads 48 KB of shared memory per slot instead of 64 KB, issues
+// half as many instructions, and the epilogue (tensor-memory lane = element
+// row, column = state) writes along element rows, coalesced across the warp.
+template <int MODE_, int ACC>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_filter_step_tn(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
+                     const __grid_constant__ CUtensorMap tmB, const Params p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  constexpr int G = 128 / ACC;   // elements stacked along M
+  constexpr int NS = 256;        // states per unit (MMA N)
+  constexpr int NA = MODE_ == MODE_BF16X3 ? 2 : 1;
+  constexpr int S = MODE_ == MODE_BF16X3 ? STAGES / 2 : STAGES;
+  constexpr int h_bytes = ACC * SLICE_BYTES;    // one element's H tile
+  constexpr int a_bytes = G * h_bytes;          // 16 KB: the stacked H tiles (MMA A)
+  constexpr int x_bytes = NS * SLICE_BYTES;     // 32 KB: the Y_k slice (MMA B)
+  constexpr int stage_bytes = NA * (a_bytes + x_bytes);  // [H hi][H lo][X hi][X lo]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
+  int32_t* sched_sh0 = reinterpret_cast<int32_t*>(bars + 2 * S + 4);
+  int32_t* sched_sh1 = sched_sh0 + p.maxent * (1 + G);
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nunits = p.ngroups * p.ntg;
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * S;
+  const uint32_t accf0 = empty0 + 8 * S, acce0 = accf0 + 16;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, EPI_WARPS);
+    }
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0) {
+    // ---------------- producer
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA0)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+    }
+    int c = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+      const int eg = u / p.ntg, tg = u % p.ntg;
+      const int s0 = tg * NS;
+      const int e0 = p.sched_ptr[eg], ne = p.sched_ptr[eg + 1] - e0;
+      __syncwarp();
+      for (int z = lane; z < ne * (1 + G); z += 32) sched_sh0[z] = p.sched[(int64_t)e0 * (1 + G) + z];
+      __syncwarp();
+      if (lane == 0 && ok) {
+        for (int e = 0; e < ne && ok; ++e) {
+          const int32_t* ent = sched_sh0 + e * (1 + G);
+          const int st = c & (S - 1);
+          const uint32_t ph = (uint32_t)(c / S) & 1u;
+          if (!mbar_wait(empty0 + 8 * st, ph ^ 1u)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = full0 + 8 * st;
+          mbar_expect_tx(fb, (uint32_t)stage_bytes);
+          uint8_t* sst = smem + st * stage_bytes;
+#pragma unroll
+          for (int v = 0; v < NA; ++v) {
+#pragma unroll
+            for (int g = 0; g < G; ++g)  // H tiles (zero tiles for non-coupling elements)
+              tma_load_2d(smem_u32(sst + v * a_bytes + g * h_bytes), &tmB, 0,
+                          (int)(ent[1 + g] + (v == 1 ? p.lo_rows : 0)), fb);
+            tma_load_2d(smem_u32(sst + NA * a_bytes + v * x_bytes), v == 1 ? &tmA1 : &tmA0, ent[0], s0, fb);
+          }
+          ++c;
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+    }
+    if (lane == 0) {
+      if (!ok) {
+        atomicOr(p.err, 1);
+        atomicExch(&abort_sh, 1);
+      }
+      for (int i = c - S < 0 ? 0 : c - S; i < c; ++i)
+        if (!mbar_wait(full0 + 8 * (i & (S - 1)), (uint32_t)(i / S) & 1u)) atomicOr(p.err, 1);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    constexpr uint32_t fmt = MODE_ == MODE_TF32 ? 2u : 1u;
+    constexpr uint32_t ID = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(NS >> 3) << 17) |
+                            ((uint32_t)(128 >> 4) << 24);
+    const uint64_t desc0 = sdesc(smem_u32(smem));
+    int c = 0, i = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++i) {
+      const int eg = u / p.ntg;
+      const int ne = p.sched_ptr[eg + 1] - p.sched_ptr[eg];
+      if (lane == 0) {
+        const int buf = i & 1;
+        const int use = i >> 1;
+        if (!mbar_wait(acce0 + 8 * buf, ((uint32_t)use & 1u) ^ 1u)) ok = false;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * NS);
+        uint32_t first = 0;
+        for (int e = 0; e < ne && ok; ++e) {
+          const int st = c & (S - 1);
+          const uint32_t ph = (uint32_t)(c / S) & 1u;
+          if (!mbar_wait(full0 + 8 * st, ph)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t dh = desc0 + (uint64_t)((st * stage_bytes) >> 4);  // H hi (A)
+          const uint64_t dx = dh + (uint64_t)((NA * a_bytes) >> 4);         // X hi (B)
+#pragma unroll
+          for (int kk = 0; kk < SLICE_BYTES / 32; ++kk) {
+            const uint64_t ad = dh + (uint64_t)((32 * kk) >> 4);
+            const uint64_t bd = dx + (uint64_t)((32 * kk) >> 4);
+            const uint32_t acc = kk > 0 ? 1u : first;
+            if constexpr (MODE_ == MODE_TF32) {
+              mma_tf32(d, ad, bd, ID, acc);
+            } else {
+              mma_bf16(d, ad, bd, ID, acc);
+              if constexpr (MODE_ == MODE_BF16X3) {
+                mma_bf16(d, ad + (uint64_t)(a_bytes >> 4), bd, ID, 1u);  // lo(H) * hi(X)
+                mma_bf16(d, ad, bd + (uint64_t)(x_bytes >> 4), ID, 1u);  // hi(H) * lo(X)
+              }
+            }
+          }
+          first = 1u;
+          mma_commit(empty0 + 8 * st);
+          ++c;
+        }
+        mma_commit(accf0 + 8 * buf);
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+    }
+    if (lane == 0 && !ok) {
+      atomicOr(p.err, 1);
+      atomicExch(&abort_sh, 1);
+    }
+    (void)sched_sh1;
+  } else {
+    // ---------------- epilogue: warps 2..9; lane quarter q = element rows 32q..32q+31,
+    // the two warps of a quarter take alternate 16-state chunks
+    const float alpha = (float)p.coef[1 + 2 * p.step], beta = (float)p.coef[2 + 2 * p.step];
+    const int q = warp & 3;
+    const int h = (warp - 2) >> 2;
+    const int r = 32 * q + lane;        // row of the stacked M = 128
+    const int g = r / ACC, j = r % ACC;
+    int i = 0;
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++i) {
+      const int buf = i & 1;
+      const int use = i >> 1;
+      const int eg = u / p.ntg, tg = u % p.ntg;
+      const int64_t s0 = (int64_t)tg * NS;
+      bool ready = mbar_wait(accf0 + 8 * buf, (uint32_t)use & 1u);
+      ready = __all_sync(0xffffffffu, ready);
+      if (!ready) {
+        if (lane == 0) atomicOr(p.err, 1);
+        break;
+      }
+      tc_fence_after();
+      const bool go = *(volatile int*)&abort_sh == 0;
+      const int K = p.grp_elem[eg * G + g];
+      const bool row_ok = go && K >= 0 && j < (K >= 0 ? p.nb[K] : 0);
+      const int64_t col = (K >= 0 ? (int64_t)p.poff[K] : 0) + j;
+      const uint32_t ta = tmem + (uint32_t)(buf * NS) + ((uint32_t)(32 * q) << 16);
+#pragma unroll 1
+      for (int cc = 0; cc < NS / 32; ++cc) {
+        const int c0 = 16 * (h + 2 * cc);
+        float pr[16];
+#pragma unroll
+        for (int z = 0; z < 16; ++z) {
+          const int64_t s = s0 + c0 + z;
+          pr[z] = (row_ok && beta != 0.f && s < p.Ns) ? p.Fprev[s * p.ldp + col] : 0.f;
+        }
+        float v[16];
+        tmem_ld16(ta + (uint32_t)c0, v);
+        if (row_ok) {
+#pragma unroll
+          for (int z = 0; z < 16; ++z) {
+            const int64_t s = s0 + c0 + z;
+            if (s < p.Ns) {
+              const int64_t idx = s * p.ldp + col;
+              const float y = alpha * v[z] - beta * pr[z];
+              p.Fout[idx] = y;
+              if constexpr (MODE_ != MODE_TF32) {
+                const __nv_bfloat16 hb = __float2bfloat16_rn(y);
+                p.Hout[idx] = hb;
+                if constexpr (MODE_ == MODE_BF16X3) p.Lout[idx] = __float2bfloat16_rn(y - __bfloat162float(hb));
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce0 + 8 * buf);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
 using FilterKernel = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const Params);
 
-// Unit shapes (G elements x T state tiles, ACC accumulator columns per element)
-// that have kernels; the autotuner picks among those matching ACC.
-constexpr int NSHAPES = 7;
-constexpr int SHAPES[NSHAPES][3] = {{2, 2, 64}, {1, 2, 64}, {2, 1, 64}, {4, 2, 32},
-                                    {2, 2, 32}, {2, 1, 128}, {1, 2, 128}};
+// Unit shapes {G elements, T tiles of 128 states, ACC accumulator columns per
+// element, layout} that have kernels; layout 0 = states along the MMA's M
+// (k_filter_step_tc), 1 = element rows along M, 256 states along N
+// (k_filter_step_tn, G = 128/ACC, T = 2). The autotuner picks among those
+// matching ACC.
+constexpr int NSHAPES = 10;
+constexpr int SHAPES[NSHAPES][4] = {{2, 2, 64, 0}, {1, 2, 64, 0}, {2, 1, 64, 0}, {4, 2, 32, 0}, {2, 2, 32, 0},
+                                    {2, 1, 128, 0}, {1, 2, 128, 0}, {2, 2, 64, 1}, {4, 2, 32, 1},
+                                    {1, 2, 128, 1}};
 
 template <int MODE_>
-FilterKernel pick_shape(int G, int T, int ACC) {
+FilterKernel pick_shape(int G, int T, int ACC, int layout) {
+  if (layout == 1) {
+    if (ACC == 64 && G == 2 && T == 2) return k_filter_step_tn<MODE_, 64>;
+    if (ACC == 32 && G == 4 && T == 2) return k_filter_step_tn<MODE_, 32>;
+    if (ACC == 128 && G == 1 && T == 2) return k_filter_step_tn<MODE_, 128>;
+    return nullptr;
+  }
+  if (layout != 0) return nullptr;
   if (G == 2 && T == 2 && ACC == 64) return k_filter_step_tc<MODE_, 2, 2, 64>;
   if (G == 1 && T == 2 && ACC == 64) return k_filter_step_tc<MODE_, 1, 2, 64>;
   if (G == 2 && T == 1 && ACC == 64) return k_filter_step_tc<MODE_, 2, 1, 64>;
@@ -521,8 +761,8 @@ FilterKernel pick_shape(int G, int T, int ACC) {
 }  // namespace
 
 // One translation unit per precision instantiates the kernels (compiled in parallel).
-FilterKernel pick_kernel_tf32(int G, int T, int ACC);
-FilterKernel pick_kernel_bf16(int G, int T, int ACC);
-FilterKernel pick_kernel_bf16x3(int G, int T, int ACC);
+FilterKernel pick_kernel_tf32(int G, int T, int ACC, int layout);
+FilterKernel pick_kernel_bf16(int G, int T, int ACC, int layout);
+FilterKernel pick_kernel_bf16x3(int G, int T, int ACC, int layout);
 
 }  // namespace dg

@@ -59,8 +59,8 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_rayleigh_ritz": (st, [P, P, I64, I64, P]),
         "dgchefsi_gram": (st, [P, P, I64, I64, P]),
         "dgchefsi_filter_graph": (st, [P, C.c_int, P, P, I64, I64, C.c_int, D, D, D]),
-        "dgchefsi_set_tile_shape": (st, [P, C.c_int, C.c_int, C.c_int]),
-        "dgchefsi_get_tile_shape": (st, [P, C.c_int, P, P, P]),
+        "dgchefsi_set_tile_shape": (st, [P, C.c_int, C.c_int, C.c_int, C.c_int]),
+        "dgchefsi_get_tile_shape": (st, [P, C.c_int, P, P, P, P]),
         "dgchefsi_selftest_wait": (st, [P, I64]),
         "dgchefsi_set_values": (st, [P, P]),
         "dgchefsi_energy_grad": (st, [P, C.c_int, P, I64, I64, C.c_int, D, D, D, D, D, C.c_int, P, P, P, P]),
@@ -224,13 +224,15 @@ class Context:
         st = _lib.dgchefsi_selftest_wait(self._h, int(limit_ns))
         return STATUS.get(st, str(st)), last_error()
 
-    def set_tile_shape(self, prec: str, G: int, T: int):
-        _check(_lib.dgchefsi_set_tile_shape(self._h, PRECISIONS[prec], int(G), int(T)))
+    def set_tile_shape(self, prec: str, G: int, T: int, layout: int = 0):
+        _check(_lib.dgchefsi_set_tile_shape(self._h, PRECISIONS[prec], int(G), int(T), int(layout)))
 
     def tile_shape(self, prec: str):
-        g, t, acc = C.c_int(), C.c_int(), C.c_int()
-        _check(_lib.dgchefsi_get_tile_shape(self._h, PRECISIONS[prec], C.byref(g), C.byref(t), C.byref(acc)))
-        return g.value, t.value, acc.value
+        """(G, T, ACC, layout) of the tensor-core filter for this precision."""
+        g, t, acc, lay = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(_lib.dgchefsi_get_tile_shape(self._h, PRECISIONS[prec], C.byref(g), C.byref(t), C.byref(acc),
+                                            C.byref(lay)))
+        return g.value, t.value, acc.value, lay.value
 
     # -- Alg. 1 steps 3-5 (in place: Y becomes X_new)
     def rayleigh_ritz(self, Y: torch.Tensor, ritz: torch.Tensor | None = None) -> torch.Tensor:

@@ -104,7 +104,8 @@ def test_mixed_cycles_converge(prec):
     assert err <= limit
 
 
-SHAPES = {32: [(4, 2), (2, 2)], 64: [(2, 2), (1, 2), (2, 1)], 128: [(2, 1), (1, 2)]}
+SHAPES = {32: [(4, 2, 0), (2, 2, 0), (4, 2, 1)], 64: [(2, 2, 0), (1, 2, 0), (2, 1, 0), (2, 2, 1)],
+          128: [(2, 1, 0), (1, 2, 0), (1, 2, 1)]}
 
 
 @pytest.mark.parametrize("prec", ["bf16", "bf16x3", "tf32"])
@@ -117,16 +118,17 @@ def test_every_unit_shape_matches_oracle(cfg, prec):
     dev = torch.device("cuda:0")
     with D.Context(H) as ctx:
         acc = 32 if Ho.nb.max() <= 32 else (64 if Ho.nb.max() <= 64 else 128)
-        for G, T in SHAPES[acc]:
-            ctx.set_tile_shape(prec, G, T)
-            assert ctx.tile_shape(prec) == (G, T, acc)
+        for G, T, lay in SHAPES[acc]:
+            ctx.set_tile_shape(prec, G, T, lay)
+            assert ctx.tile_shape(prec) == (G, T, acc, lay)
             Y = ctx.filter(torch.from_numpy(X0).to(dev), cfg.m, a, b, a0, prec=prec).cpu().numpy()
             err = np.linalg.norm(Y - ref) / np.linalg.norm(ref)
-            assert err <= 2 * cfg.m * U_OP[prec], (G, T, err)
+            print(f"SHAPE_ERR {cfg.name} {prec} G={G} T={T} layout={lay} rel_fro={err:.3e}")
+            assert err <= 2 * cfg.m * U_OP[prec], (G, T, lay, err)
         ctx.set_tile_shape(prec, 0, 0)  # back to the autotuner
         ctx.filter(torch.from_numpy(X0).to(dev), 2, a, b, a0, prec=prec)
-        G, T, _ = ctx.tile_shape(prec)
-        assert (G, T) in SHAPES[acc]
+        G, T, _, lay = ctx.tile_shape(prec)
+        assert (G, T, lay) in SHAPES[acc]
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32"])

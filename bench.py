@@ -122,7 +122,7 @@ def profiled_traffic(prec: str, Ns: int):
     import hashlib
     src = os.path.join(ROOT, "paper_1606_03416_gb300", "csrc", "tc_kernel.cuh")
     sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
-    for path in glob.glob(os.path.join(ROOT, "profiles", f"k_filter_step_tc_{prec}_bulk3d_*.md")):
+    for path in glob.glob(os.path.join(ROOT, "profiles", f"k_filter_step_t?_{prec}_bulk3d_*.md")):
         text = open(path).read()
         if f"source-sha1 (paper_1606_03416_gb300/csrc/tc_kernel.cuh, first 12): {sha}" not in text:
             continue
@@ -262,6 +262,78 @@ def measure_uneven(dev, precs=("bf16x3", "tf32"), reps=3):
     return out
 
 
+def run_adjoint(args):
+    """Differentiation workload (12^3 elements, 27-neighbour stencil, n_b = 48,
+    N_s = 8192, m = 24): the band-energy gradient of one cycle. On a 6^3 copy
+    (N_s = 1024) the adjoint is compared with central differences (h = 1e-4) of
+    the GPU's own FP64 energy on 32 random tied block entries; with --adjoint-full
+    one forward + backward is also timed at full size."""
+    import torch
+    from paper_1606_03416_gb300 import autograd as A
+    from paper_1606_03416_gb300 import dgchefsi as D
+    from paper_1606_03416_gb300 import inputs as G
+    dev = torch.device("cuda:0")
+    base = G.CONFIGS["bulk3d_12x12x12"]
+    out = {"mode": "adjoint", "workload": base.name}
+
+    def bounds_for(ctx, X, v, Ns, N):
+        b, tmin = ctx.bounds(v, 10)
+        return tmin + (b - tmin) * Ns / N, b, tmin
+
+    small = G.scaled_copy(base, grid=(6, 6, 6), Ns=1024, name="bulk3d_6x6x6")
+    H, X0, v0, Ns, Ne = G.make_problem(small)
+    with D.Context(H) as ctx:
+        X = torch.from_numpy(X0).to(dev)
+        v = torch.from_numpy(v0).to(dev)
+        a, b, a0 = bounds_for(ctx, X, v, Ns, H.N)
+        t0 = time.time()
+        E, _, Hb, Xb = ctx.energy_grad(X, small.m, a, b, a0, Ne, small.kT)
+        torch.cuda.synchronize()
+        t_grad = time.time() - t0
+        mirror = A.mirror_index(H)
+        tied = A.tie_symmetric(Hb, mirror).cpu().numpy()
+        rng = np.random.default_rng(0)
+        h = 1e-4
+        vals = torch.from_numpy(H.values.copy()).to(dev)
+        errs = []
+        for _ in range(32):
+            i = int(rng.integers(0, H.values.shape[0]))
+            ent = torch.tensor(sorted({i, int(mirror[i])}), device=dev)
+            fd = []
+            for sgn in (1.0, -1.0):
+                vv = vals.clone()
+                vv[ent] += sgn * h
+                ctx.set_values(vv)
+                fd.append(ctx.energy_grad(X, small.m, a, b, a0, Ne, small.kT, grad=False)[0])
+            g_fd = (fd[0] - fd[1]) / (2 * h)
+            errs.append(abs(g_fd - tied[i]) / max(np.max(np.abs(tied)), 1e-300))
+        ctx.set_values(vals)
+    out["fd_check_6x6x6"] = {"N": H.N, "Ns": Ns, "m": small.m, "entries": 32, "h": h, "precision": "f64",
+                             "max_rel_err_vs_max_grad": float(max(errs)), "s_forward_backward": t_grad}
+    if args.adjoint_full:
+        H, X0, v0, Ns, Ne = G.make_problem(base)
+        with D.Context(H) as ctx:
+            X = torch.from_numpy(X0).to(dev)
+            v = torch.from_numpy(v0).to(dev)
+            a, b, a0 = bounds_for(ctx, X, v, Ns, H.N)
+            s_, e_ = torch.cuda.Event(True), torch.cuda.Event(True)
+            s_.record()
+            E, _, _, _ = ctx.energy_grad(X, base.m, a, b, a0, Ne, base.kT, grad=False)
+            e_.record()
+            torch.cuda.synchronize()
+            t_fwd = s_.elapsed_time(e_) / 1e3
+            s_.record()
+            E2, _, Hb, Xb = ctx.energy_grad(X, base.m, a, b, a0, Ne, base.kT)
+            e_.record()
+            torch.cuda.synchronize()
+            out["full_12x12x12"] = {"N": H.N, "Ns": Ns, "m": base.m, "precision": "f64", "s_forward": t_fwd,
+                                    "s_forward_and_backward": s_.elapsed_time(e_) / 1e3,
+                                    "checkpoint_stride": int(np.ceil(np.sqrt(base.m))),
+                                    "energy": E, "grad_norm_H": float(Hb.norm()), "grad_norm_X": float(Xb.norm())}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,6 +345,8 @@ def main():
     ap.add_argument("--ref-states", type=int, default=64, help="states in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-n_b 2D sheet measurement")
+    ap.add_argument("--adjoint", action="store_true", help="differentiation workload instead of the cycle")
+    ap.add_argument("--adjoint-full", action="store_true", help="with --adjoint: also time the full 12^3 size")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--filter-only", action="store_true",
                     help="time only the filter (profiling case); --ns and --m override the workload")
@@ -284,6 +358,8 @@ def main():
         return run_reference(args)
     if args.filter_only:
         return run_filter_only(args)
+    if args.adjoint:
+        return run_adjoint(args)
 
     import torch
     rank, world, local = dist_env()
@@ -396,7 +472,11 @@ def main():
     rf["frac"] = rf["achieved"] / rf["peak"]
     rf["traffic"] = profiled_traffic(args.prec, Ns) if args.prec != "f64" else None
     rf["algorithmic_bytes"] = byts
-    rf["kernel"] = "k_filter_step_tc" if args.prec != "f64" else "k_filter_step_f64"
+    if args.prec == "f64":
+        rf["kernel"] = "k_filter_step_f64"
+    else:
+        g_, t_, acc_, lay_ = ctx.tile_shape(args.prec)
+        rf["kernel"] = ("k_filter_step_tn" if lay_ == 1 else "k_filter_step_tc") + f"<{args.prec}, G={g_}, T={t_}>"
     rf["ms_per_launch"] = ms_launch
     rf["peak_source"] = src + (" x 1.1/2.25 (nominal TF32/BF16 ratio)" if args.prec == "tf32" else "")
 

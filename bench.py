@@ -292,24 +292,32 @@ def run_adjoint(args):
         t_grad = time.time() - t0
         mirror = A.mirror_index(H)
         tied = A.tie_symmetric(Hb, mirror).cpu().numpy()
+        gmax = max(float(np.max(np.abs(tied))), 1e-300)
         rng = np.random.default_rng(0)
-        h = 1e-4
+        picks = [int(rng.integers(0, H.values.shape[0])) for _ in range(32)]
         vals = torch.from_numpy(H.values.copy()).to(dev)
-        errs = []
-        for _ in range(32):
-            i = int(rng.integers(0, H.values.shape[0]))
-            ent = torch.tensor(sorted({i, int(mirror[i])}), device=dev)
-            fd = []
-            for sgn in (1.0, -1.0):
-                vv = vals.clone()
-                vv[ent] += sgn * h
-                ctx.set_values(vv)
-                fd.append(ctx.energy_grad(X, small.m, a, b, a0, Ne, small.kT, grad=False)[0])
-            g_fd = (fd[0] - fd[1]) / (2 * h)
-            errs.append(abs(g_fd - tied[i]) / max(np.max(np.abs(tied)), 1e-300))
-        ctx.set_values(vals)
+
+        def fd_errors(h, idx):
+            errs = []
+            for i in idx:
+                ent = torch.tensor(sorted({i, int(mirror[i])}), device=dev)
+                fd = []
+                for sgn in (1.0, -1.0):
+                    vv = vals.clone()
+                    vv[ent] += sgn * h
+                    ctx.set_values(vv)
+                    fd.append(ctx.energy_grad(X, small.m, a, b, a0, Ne, small.kT, grad=False)[0])
+                errs.append(abs((fd[0] - fd[1]) / (2 * h) - tied[i]) / gmax)
+            ctx.set_values(vals)
+            return errs
+        errs = fd_errors(1e-4, picks)
+        # the same 8 entries at three step sizes: truncation error falls as h^2,
+        # rounding noise of the energy grows as 1/h
+        sweep = {f"{h:g}": float(max(fd_errors(h, picks[:8]))) for h in (1e-3, 1e-4, 1e-5, 1e-6)}
+        h = 1e-4
     out["fd_check_6x6x6"] = {"N": H.N, "Ns": Ns, "m": small.m, "entries": 32, "h": h, "precision": "f64",
-                             "max_rel_err_vs_max_grad": float(max(errs)), "s_forward_backward": t_grad}
+                             "max_rel_err_vs_max_grad": float(max(errs)), "s_forward_backward": t_grad,
+                             "max_rel_err_by_h_8_entries": sweep}
     if args.adjoint_full:
         H, X0, v0, Ns, Ne = G.make_problem(base)
         with D.Context(H) as ctx:
@@ -558,6 +566,21 @@ def main():
         rmx = ctx.rayleigh_ritz(Yb)
         scale = max(abs(a0), abs(b))
         f64["ritz_err_first_cycle"] = float((rmx - r64).abs().max().item() / scale)
+        # largest principal angle between the occupied subspaces (sin, by power
+        # iteration on R = Xm - X64 (X64^T Xm)) and the density-block error
+        n_occ = int(round(Ne / 2))
+        X64o, Xmo = Ya[:n_occ], Yb[:n_occ]          # state-major rows
+        R = Xmo - (Xmo @ X64o.T) @ X64o
+        v = torch.ones(n_occ, dtype=torch.float64, device=dev)
+        for _ in range(30):
+            v = R @ (R.T @ v)
+            v = v / v.norm()
+        f64["max_subspace_angle_sin"] = float((R.T @ v).norm().item())  # top singular value of R
+        fm, _ = ctx.occupations(rmx, Ne, kT)
+        P64 = ctx.density_blocks(Ya, fo)
+        Pmx = ctx.density_blocks(Yb, fm)
+        f64["density_rel_err"] = float((Pmx - P64).norm().item() / P64.norm().item())
+        R = X64o = Xmo = P64 = Pmx = None
         Xa = Ya = Xb = Yb = None
 
     clocks = clk.summary()
@@ -572,6 +595,8 @@ def main():
         "s_per_cycle": {"mixed": ms_step / 1e3, "f64": f64.get("s_per_cycle")},
         "filter_ms": ms_filter,
         "ritz_err_mixed_vs_f64_first_cycle": f64.get("ritz_err_first_cycle"),
+        "subspace_sin_max_mixed_vs_f64": f64.get("max_subspace_angle_sin"),
+        "density_rel_err_mixed_vs_f64": f64.get("density_rel_err"),
         "roofline": roof, "roofline_filter": rf, "filter_tflops_other_precisions": other,
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }

@@ -264,21 +264,33 @@ def measure_uneven(dev, precs=("bf16x3", "tf32"), reps=3):
 
 def run_adjoint(args):
     """Differentiation workload (12^3 elements, 27-neighbour stencil, n_b = 48,
-    N_s = 8192, m = 24): the band-energy gradient of one cycle. On a 6^3 copy
-    (N_s = 1024) the adjoint is compared with central differences (h = 1e-4) of
-    the GPU's own FP64 energy on 32 random tied block entries; with --adjoint-full
-    one forward + backward is also timed at full size."""
+    N_s = 8192, m = 24): the band-energy gradient of one cycle, with the filter
+    in FP64 and in the tensor-core form --prec (FP32 iterates). On a 6^3 copy
+    (N_s = 1024) both gradients are compared with central differences of the
+    GPU's FP64 energy on 32 random tied block entries (h = 1e-4, plus a sweep
+    over h on 8 of them) and along one random symmetric direction of all
+    entries; with --adjoint-full one forward + backward is also timed at full
+    size (tensor-core form; FP64 too with --adjoint-f64)."""
     import torch
     from paper_1606_03416_gb300 import autograd as A
     from paper_1606_03416_gb300 import dgchefsi as D
     from paper_1606_03416_gb300 import inputs as G
     dev = torch.device("cuda:0")
     base = G.CONFIGS["bulk3d_12x12x12"]
-    out = {"mode": "adjoint", "workload": base.name}
+    tc = args.prec if args.prec != "f64" else "bf16x3"
+    out = {"mode": "adjoint", "workload": base.name, "tensor_core_precision": tc}
 
     def bounds_for(ctx, X, v, Ns, N):
         b, tmin = ctx.bounds(v, 10)
         return tmin + (b - tmin) * Ns / N, b, tmin
+
+    def timed(fn):
+        s_, e_ = torch.cuda.Event(True), torch.cuda.Event(True)
+        s_.record()
+        r = fn()
+        e_.record()
+        torch.cuda.synchronize()
+        return r, s_.elapsed_time(e_) / 1e3
 
     small = G.scaled_copy(base, grid=(6, 6, 6), Ns=1024, name="bulk3d_6x6x6")
     H, X0, v0, Ns, Ne = G.make_problem(small)
@@ -286,58 +298,79 @@ def run_adjoint(args):
         X = torch.from_numpy(X0).to(dev)
         v = torch.from_numpy(v0).to(dev)
         a, b, a0 = bounds_for(ctx, X, v, Ns, H.N)
-        t0 = time.time()
-        E, _, Hb, Xb = ctx.energy_grad(X, small.m, a, b, a0, Ne, small.kT)
-        torch.cuda.synchronize()
-        t_grad = time.time() - t0
+        (E, _, Hb, Xb), t_grad = timed(lambda: ctx.energy_grad(X, small.m, a, b, a0, Ne, small.kT))
+        ctx.energy_grad(X, small.m, a, b, a0, Ne, small.kT, prec=tc)  # tunes the unit shape
+        (Et, _, Hbt, Xbt), t_grad_tc = timed(lambda: ctx.energy_grad(X, small.m, a, b, a0, Ne, small.kT, prec=tc))
         mirror = A.mirror_index(H)
         tied = A.tie_symmetric(Hb, mirror).cpu().numpy()
+        tied_tc = A.tie_symmetric(Hbt, mirror).cpu().numpy()
         gmax = max(float(np.max(np.abs(tied))), 1e-300)
         rng = np.random.default_rng(0)
         picks = [int(rng.integers(0, H.values.shape[0])) for _ in range(32)]
         vals = torch.from_numpy(H.values.copy()).to(dev)
 
-        def fd_errors(h, idx):
-            errs = []
+        def energy_at(vv):
+            ctx.set_values(vv)
+            return ctx.energy_grad(X, small.m, a, b, a0, Ne, small.kT, grad=False)[0]
+
+        def fd_values(h, idx):
+            fds = []
             for i in idx:
                 ent = torch.tensor(sorted({i, int(mirror[i])}), device=dev)
-                fd = []
+                e = []
                 for sgn in (1.0, -1.0):
                     vv = vals.clone()
                     vv[ent] += sgn * h
-                    ctx.set_values(vv)
-                    fd.append(ctx.energy_grad(X, small.m, a, b, a0, Ne, small.kT, grad=False)[0])
-                errs.append(abs((fd[0] - fd[1]) / (2 * h) - tied[i]) / gmax)
+                    e.append(energy_at(vv))
+                fds.append((e[0] - e[1]) / (2 * h))
             ctx.set_values(vals)
-            return errs
-        errs = fd_errors(1e-4, picks)
-        # the same 8 entries at three step sizes: truncation error falls as h^2,
+            return np.array(fds)
+
+        fd = fd_values(1e-4, picks)
+        err64 = np.abs(fd - tied[picks]) / gmax
+        errtc = np.abs(fd - tied_tc[picks]) / gmax
+        # the same 8 entries at four step sizes: truncation error falls as h^2,
         # rounding noise of the energy grows as 1/h
-        sweep = {f"{h:g}": float(max(fd_errors(h, picks[:8]))) for h in (1e-3, 1e-4, 1e-5, 1e-6)}
-        h = 1e-4
-    out["fd_check_6x6x6"] = {"N": H.N, "Ns": Ns, "m": small.m, "entries": 32, "h": h, "precision": "f64",
-                             "max_rel_err_vs_max_grad": float(max(errs)), "s_forward_backward": t_grad,
-                             "max_rel_err_by_h_8_entries": sweep}
+        sweep = {}
+        for h in (1e-3, 1e-4, 1e-5, 1e-6):
+            f8 = fd_values(h, picks[:8])
+            sweep[f"{h:g}"] = float(np.max(np.abs(f8 - tied[picks[:8]])) / gmax)
+        # one random symmetric direction over all entries: E(v +- h d)
+        r = np.random.default_rng(1).standard_normal(H.values.shape[0])
+        d = torch.from_numpy(0.5 * (r + r[mirror])).to(dev)
+        dd64, ddtc = float((Hb * d).sum()), float((Hbt * d).sum())
+        direc = {}
+        for h in (1e-3, 1e-4, 1e-5):
+            fdd = (energy_at(vals + h * d) - energy_at(vals - h * d)) / (2 * h)
+            direc[f"{h:g}"] = {"fd": fdd, "rel_err_f64": abs(fdd - dd64) / abs(dd64),
+                               f"rel_err_{tc}": abs(fdd - ddtc) / abs(dd64)}
+        ctx.set_values(vals)
+    out["fd_check_6x6x6"] = {
+        "N": H.N, "Ns": Ns, "m": small.m, "entries": 32, "h": 1e-4,
+        "max_rel_err_vs_max_grad": {"f64": float(err64.max()), tc: float(errtc.max())},
+        "max_rel_err_by_h_8_entries_f64": sweep,
+        "directional_derivative": {"analytic_f64": dd64, f"analytic_{tc}": ddtc, "by_h": direc},
+        f"{tc}_vs_f64": {"energy_rel": abs(Et - E) / abs(E),
+                         "grad_H_rel_max": float(np.max(np.abs(tied_tc - tied)) / gmax),
+                         "grad_X_rel_max": float((Xbt - Xb).abs().max() / Xb.abs().max())},
+        "s_forward_backward": {"f64": t_grad, tc: t_grad_tc}}
     if args.adjoint_full:
         H, X0, v0, Ns, Ne = G.make_problem(base)
+        full = {"N": H.N, "Ns": Ns, "m": base.m, "checkpoint_stride": int(np.ceil(np.sqrt(base.m)))}
         with D.Context(H) as ctx:
             X = torch.from_numpy(X0).to(dev)
             v = torch.from_numpy(v0).to(dev)
             a, b, a0 = bounds_for(ctx, X, v, Ns, H.N)
-            s_, e_ = torch.cuda.Event(True), torch.cuda.Event(True)
-            s_.record()
-            E, _, _, _ = ctx.energy_grad(X, base.m, a, b, a0, Ne, base.kT, grad=False)
-            e_.record()
-            torch.cuda.synchronize()
-            t_fwd = s_.elapsed_time(e_) / 1e3
-            s_.record()
-            E2, _, Hb, Xb = ctx.energy_grad(X, base.m, a, b, a0, Ne, base.kT)
-            e_.record()
-            torch.cuda.synchronize()
-            out["full_12x12x12"] = {"N": H.N, "Ns": Ns, "m": base.m, "precision": "f64", "s_forward": t_fwd,
-                                    "s_forward_and_backward": s_.elapsed_time(e_) / 1e3,
-                                    "checkpoint_stride": int(np.ceil(np.sqrt(base.m))),
-                                    "energy": E, "grad_norm_H": float(Hb.norm()), "grad_norm_X": float(Xb.norm())}
+            precs = [tc] + (["f64"] if args.adjoint_f64 else [])
+            for p in precs:
+                (E, _, _, _), t_fwd = timed(lambda: ctx.energy_grad(X, base.m, a, b, a0, Ne, base.kT, grad=False,
+                                                                    prec=p))
+                (E2, _, Hb, Xb), t_all = timed(lambda: ctx.energy_grad(X, base.m, a, b, a0, Ne, base.kT, prec=p))
+                full[p] = {"s_forward": t_fwd, "s_forward_and_backward": t_all, "energy": E,
+                           "grad_norm_H": float(Hb.norm()), "grad_norm_X": float(Xb.norm())}
+                del Hb, Xb
+                torch.cuda.empty_cache()
+        out["full_12x12x12"] = full
     print(json.dumps(out), flush=True)
     return 0
 
@@ -355,6 +388,7 @@ def main():
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-n_b 2D sheet measurement")
     ap.add_argument("--adjoint", action="store_true", help="differentiation workload instead of the cycle")
     ap.add_argument("--adjoint-full", action="store_true", help="with --adjoint: also time the full 12^3 size")
+    ap.add_argument("--adjoint-f64", action="store_true", help="with --adjoint-full: time the FP64 gradient too")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--filter-only", action="store_true",
                     help="time only the filter (profiling case); --ns and --m override the workload")

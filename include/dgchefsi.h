@@ -224,7 +224,14 @@ dgchefsi_status dgchefsi_set_values(dgchefsi_ctx* ctx, const double* values);
 /* Band energy of one cycle and its gradient. The paper does not differentiate
  * the cycle; this is the adjoint of its steps: E = sum_i f_i lambda_i after
  * Alg. 1 steps 2-5 and the Fermi occupations, with (a, b, a0), Ne and kT fixed.
- *   prec               DGCHEFSI_F64 (the only form this build differentiates)
+ *   prec               DGCHEFSI_F64: every step in FP64. DGCHEFSI_TF32, _BF16,
+ *                      _BF16X3: the filter, its checkpoints (FP32 iterates),
+ *                      the recomputed segments and the backward recurrence on
+ *                      the tensor-core step kernel, alpha_k W_{k+1} Y_k^T summed
+ *                      over FP32 iterates into FP64; Cholesky-QR, Rayleigh-Ritz
+ *                      and their adjoint in FP64. The gradient is then that of
+ *                      the exact recurrence evaluated at the rounded iterates
+ *                      (error of order m u_op relative)
  *   X                  device (Ns x ld) starting block
  *   checkpoint_stride  s: iterate pairs kept every s filter steps, each
  *                      segment recomputed backwards (0 = ceil(sqrt(m)))

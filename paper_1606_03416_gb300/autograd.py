@@ -19,24 +19,26 @@ import torch
 
 class BandEnergy(torch.autograd.Function):
     @staticmethod
-    def forward(fctx, values, X, lib_ctx, m, a, b, a0, Ne, kT, stride=0):
+    def forward(fctx, values, X, lib_ctx, m, a, b, a0, Ne, kT, stride=0, prec="f64"):
         lib_ctx.set_values(values)
-        E, _, _, _ = lib_ctx.energy_grad(X, m, a, b, a0, Ne, kT, grad=False)
+        E, _, _, _ = lib_ctx.energy_grad(X, m, a, b, a0, Ne, kT, grad=False, prec=prec)
         fctx.save_for_backward(values, X)
-        fctx.params = (lib_ctx, m, a, b, a0, Ne, kT, stride)
+        fctx.params = (lib_ctx, m, a, b, a0, Ne, kT, stride, prec)
         return torch.tensor(E, dtype=torch.float64, device=X.device)
 
     @staticmethod
     def backward(fctx, gE):
         values, X = fctx.saved_tensors
-        lib_ctx, m, a, b, a0, Ne, kT, stride = fctx.params
+        lib_ctx, m, a, b, a0, Ne, kT, stride, prec = fctx.params
         lib_ctx.set_values(values)
-        _, _, Hb, Xb = lib_ctx.energy_grad(X, m, a, b, a0, Ne, kT, grad=True, stride=stride)
-        return gE * Hb, gE * Xb, None, None, None, None, None, None, None, None
+        _, _, Hb, Xb = lib_ctx.energy_grad(X, m, a, b, a0, Ne, kT, grad=True, stride=stride, prec=prec)
+        return gE * Hb, gE * Xb, None, None, None, None, None, None, None, None, None
 
 
-def band_energy(values, X, lib_ctx, m, a, b, a0, Ne, kT, stride=0):
-    return BandEnergy.apply(values, X, lib_ctx, m, a, b, a0, Ne, kT, stride)
+def band_energy(values, X, lib_ctx, m, a, b, a0, Ne, kT, stride=0, prec="f64"):
+    """E = sum_i f_i lambda_i of one cycle; prec selects the filter's arithmetic
+    ("f64", or a tensor-core form "tf32", "bf16", "bf16x3" with FP32 iterates)."""
+    return BandEnergy.apply(values, X, lib_ctx, m, a, b, a0, Ne, kT, stride, prec)
 
 
 def mirror_index(H) -> np.ndarray:

@@ -11,6 +11,10 @@
 //     backwards, W_m = Y~bar, dE/dH += alpha_k W_{k+1} Y_k^T,
 //     W_k = alpha_k (H - cI) W_{k+1} - beta_{k+1} W_{k+2}, Xbar = W_0.
 // The backward recurrence is the forward step kernel with other coefficients.
+// With a tensor-core precision the filter, its checkpoints (FP32), the
+// recomputed segments and the backward recurrence run on the tensor-core step
+// kernel, and alpha_k W_{k+1} Y_k^T is accumulated from FP32 iterates into
+// FP64; Cholesky-QR, Rayleigh-Ritz and their adjoint stay FP64.
 // Iterates Y_k are not all stored: pairs (Y_{js}, Y_{js+1}) are kept every s
 // steps (s = ceil(sqrt(m)) by default, a three-term restart needs two
 // iterates) and each segment is recomputed in reverse order, so the memory is
@@ -73,7 +77,9 @@ extern "C" dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, con
                                                 double* X_bar) {
   clear_error();
   if (!ctx) return set_error(DGCHEFSI_ERR_ARG, "null context");
-  if (prec != DGCHEFSI_F64) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "the band-energy gradient runs in FP64 only");
+  if (prec != DGCHEFSI_F64 && prec != DGCHEFSI_TF32 && prec != DGCHEFSI_BF16 && prec != DGCHEFSI_BF16X3)
+    return set_error(DGCHEFSI_ERR_ARG, "unknown precision %d", prec);
+  const bool tc = prec != DGCHEFSI_F64;
   if (!X || !energy || Ns < 1) return set_error(DGCHEFSI_ERR_ARG, "need X, energy and Ns >= 1");
   if (ld < ctx->N) return set_error(DGCHEFSI_ERR_ARG, "ld < N");
   if (Ns > ctx->N) return set_error(DGCHEFSI_ERR_ARG, "Ns > N");
@@ -94,7 +100,7 @@ extern "C" dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, con
 
   // ---- workspace: every block is (Ns x N) FP64, compact (ld = N)
   const size_t blk = (size_t)Ns * (size_t)N;
-  const int nbig = want_grad ? (2 * nseg + stride + 9) : 8;
+  const int nbig = (want_grad && !tc) ? (2 * nseg + stride + 9) : (want_grad ? 9 : 8);
   const size_t small = (size_t)Ns * (size_t)Ns;
   DG_TRY(ensure(ctx, ctx->ws_adjoint, sizeof(double) * (blk * nbig + 3 * small + 4 * (size_t)Ns + 8),
                 "band-energy workspace"));
@@ -110,7 +116,7 @@ extern "C" dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, con
   double* T1 = take();
   double* T2 = take();
   std::vector<double*> cp0(nseg), cp1(nseg), seg;
-  if (want_grad) {
+  if (want_grad && !tc) {
     for (int j = 0; j < nseg; ++j) {
       cp0[j] = take();
       cp1[j] = take();
@@ -132,7 +138,10 @@ extern "C" dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, con
                               cudaMemcpyDeviceToDevice, s));
     return DGCHEFSI_OK;
   };
-  {
+  if (tc) {
+    // tensor-core filter; FP32 checkpoints are kept inside the filter state
+    DG_TRY(tc_grad_forward(ctx, prec, X, ld, Ns, m, a, b, a0, stride, Yt));
+  } else {
     // Y_0 = X (caller layout ld); iterates in T0/T1/T2 rotation (ld = N)
     double* rot[3] = {T0, T1, T2};
     const double* prev = nullptr;
@@ -231,6 +240,11 @@ extern "C" dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, con
   DG_CUDA(scaled_residual_f64(HXN, XN, N, lam, g, 2.0, Ns, N, T0, N, s));
   DG_CUDA(gemm_nn_f64(S, Ns, L, Ns, Z, Ns, Ns, Ns, Ns, false, s));  // Z^T = Q^T L
   DG_CUDA(gemm_tn_f64(Z, Ns, T0, N, WA, N, Ns, N, Ns, s));         // W_m = Z (2 G R^T)
+  if (tc) {
+    DG_TRY(tc_grad_backward(ctx, prec, WA, Ns, m, stride, Hb, X_bar, ld));
+    DG_CUDA(cudaStreamSynchronize(s));
+    return DGCHEFSI_OK;
+  }
   // ---- filter backward, segment by segment from the last
   double* Wcur = WA;   // W_{k+1}
   double* Wprev = T1;  // W_{k+2} (unused while beta_{k+1} = 0)

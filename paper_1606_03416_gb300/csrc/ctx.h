@@ -87,6 +87,15 @@ dgchefsi_status filter_tc_graph(dgchefsi_ctx* ctx, int prec, const double* X, do
 dgchefsi_status tc_set_shape(dgchefsi_ctx* ctx, int prec, int G, int T, int layout);
 dgchefsi_status tc_get_shape(dgchefsi_ctx* ctx, int prec, int* G, int* T, int* ACC, int* layout);
 dgchefsi_status tc_wait_selftest(dgchefsi_ctx* ctx, int64_t limit_ns);
+// Band-energy gradient on the tensor-core filter. Forward: Y_m (FP64, Ns x N
+// compact) from X, keeping FP32 iterate pairs every `stride` steps. Backward
+// (same prec, m, stride, right after the forward): the reverse recurrence from
+// W_m (FP64 compact), adding alpha_k W_{k+1} Y_k^T to H_bar (values layout,
+// may be null) and writing W_0 to X_bar (ld_xbar, may be null).
+dgchefsi_status tc_grad_forward(dgchefsi_ctx* ctx, int prec, const double* X, int64_t ld, int64_t Ns, int m,
+                                double a, double b, double a0, int stride, double* Ym);
+dgchefsi_status tc_grad_backward(dgchefsi_ctx* ctx, int prec, const double* Wm, int64_t Ns, int m, int stride,
+                                 double* H_bar, double* X_bar, int64_t ld_xbar);
 void tc_destroy(dgchefsi_ctx* ctx);
 
 }  // namespace dg

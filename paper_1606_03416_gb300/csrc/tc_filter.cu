@@ -83,6 +83,82 @@ __global__ void k_build_hop(const int32_t* __restrict__ blk_row, const int32_t* 
   }
 }
 
+// BF16 operand copies (hi, and lo = bf16(v - hi)) of an FP32 iterate in the padded layout.
+__global__ void k_shadow(const float* __restrict__ F, int64_t n, __nv_bfloat16* __restrict__ Hh,
+                         __nv_bfloat16* __restrict__ Hl) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = F[i];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    Hh[i] = h;
+    if (Hl) Hl[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+// G_e += alpha * sum_s W[s, poff_K + j] Y[s, poff_K' + j'] for every stored block
+// e = (K, K'); W, Y FP32 in the padded layout (ld ldp), FP32 accumulation per
+// 64 x 64 tile, FP64 update of G (values layout of H).
+__global__ void __launch_bounds__(256) k_block_outer_f32(const int32_t* __restrict__ blk_row,
+                                                         const int32_t* __restrict__ col, const int64_t* __restrict__ blk_off,
+                                                         const int32_t* __restrict__ nb, const int32_t* __restrict__ poff,
+                                                         const float* __restrict__ W, const float* __restrict__ Y,
+                                                         int64_t ldp, int64_t Ns, double alpha, double* __restrict__ G) {
+  constexpr int TT = 64, KB = 16, TPAD = TT + 4;
+  const int64_t e = blockIdx.x;
+  const int K = blk_row[e], Kp = col[e];
+  const int nK = nb[K], nKp = nb[Kp];
+  const int j0 = blockIdx.y * TT, jp0 = blockIdx.z * TT;
+  if (j0 >= nK || jp0 >= nKp) return;
+  const int64_t oK = poff[K], oKp = poff[Kp];
+  __shared__ float As[KB][TPAD];
+  __shared__ float Bs[KB][TPAD];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  const int cc = tid & 63;
+  for (int64_t i0 = 0; i0 < Ns; i0 += KB) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int kk = (tid >> 6) + 4 * i;
+      const int64_t st = i0 + kk;
+      float v = 0.f, u = 0.f;
+      if (st < Ns) {
+        if (j0 + cc < nK) v = W[st * ldp + oK + j0 + cc];
+        if (jp0 + cc < nKp) u = Y[st * ldp + oKp + jp0 + cc];
+      }
+      As[kk][cc] = v;
+      Bs[kk][cc] = u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KB; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* Ge = G + blk_off[e];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int jj = j0 + ty + 16 * i;
+    if (jj >= nK) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int jq = jp0 + tx + 16 * j;
+      if (jq < nKp) Ge[(int64_t)jj * nKp + jq] += alpha * (double)acc[i][j];
+    }
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -160,6 +236,16 @@ struct TcState {
   const void* g_X = nullptr;
   void* g_Y = nullptr;
   int64_t g_Ns = 0, g_ld = 0;
+  // band-energy gradient: FP32 checkpoints, segment and backward iterates
+  DevBuf gbuf;
+  double* coefb_d = nullptr;  // [1 + 2m] c, then alpha_k, beta_{k+1} of each backward step
+  int coefb_cap = 0;
+  int g_stride = 0, g_nseg = 0, g_mG = 0, g_mT = 0, g_mL = 0, g_mm = 0;
+  std::vector<float*> cp0, cp1, segb;
+  float* R[3] = {nullptr, nullptr, nullptr};
+  float* WF[2] = {nullptr, nullptr};
+  __nv_bfloat16* WSh[2] = {nullptr, nullptr};
+  __nv_bfloat16* WSl[2] = {nullptr, nullptr};
 };
 
 static FilterKernel pick_kernel(int mode, int G, int T, int ACC, int layout) {
@@ -347,7 +433,25 @@ struct Launch {
   CUtensorMap A0[2], A1[2], B;
   dim3 grid;
   int smem = 0;
+  int layout = 0;
 };
+
+// A-operand tensor maps of one iterate: the FP32 master itself for TF32, the
+// BF16 hi (A0) and lo (A1) copies otherwise.
+static dgchefsi_status bind_iterate(TcState& t, int mode, int layout, int64_t Ns, const float* F,
+                                    const __nv_bfloat16* Sh, const __nv_bfloat16* Sl, CUtensorMap* A0,
+                                    CUtensorMap* A1) {
+  const uint32_t xrows = layout == 1 ? 256u : (uint32_t)BM;  // states per box of Y_k
+  if (mode == MODE_TF32) {
+    DG_TRY(make_map(A0, const_cast<float*>(F), true, (uint64_t)t.ldp, (uint64_t)Ns, 32, xrows));
+    *A1 = *A0;
+    return DGCHEFSI_OK;
+  }
+  DG_TRY(make_map(A0, const_cast<__nv_bfloat16*>(Sh), false, (uint64_t)t.ldp, (uint64_t)Ns, 64, xrows));
+  if (mode == MODE_BF16X3) DG_TRY(make_map(A1, const_cast<__nv_bfloat16*>(Sl), false, (uint64_t)t.ldp, (uint64_t)Ns, 64, xrows));
+  else *A1 = *A0;
+  return DGCHEFSI_OK;
+}
 
 static dgchefsi_status prepare_launch(dgchefsi_ctx* ctx, TcState& t, int mode, int G, int T, int layout,
                                       int64_t Ns, Launch& L) {
@@ -358,18 +462,10 @@ static dgchefsi_status prepare_launch(dgchefsi_ctx* ctx, TcState& t, int mode, i
   L.kern = pick_kernel(mode, G, T, t.ACC, layout);
   if (!L.kern)
     return set_error(DGCHEFSI_ERR_UNSUPPORTED, "no filter kernel for G=%d T=%d ACC=%d layout %d", G, T, t.ACC, layout);
-  const uint32_t xrows = layout == 1 ? 256u : (uint32_t)BM;  // states per box of Y_k
-  for (int i = 0; i < 2; ++i) {
-    if (f32) {
-      DG_TRY(make_map(&L.A0[i], t.F[i].p, true, (uint64_t)t.ldp, (uint64_t)Ns, 32, xrows));
-      L.A1[i] = L.A0[i];
-    } else {
-      DG_TRY(make_map(&L.A0[i], t.Sh[i].p, false, (uint64_t)t.ldp, (uint64_t)Ns, 64, xrows));
-      if (mode == MODE_BF16X3)
-        DG_TRY(make_map(&L.A1[i], t.Sl[i].p, false, (uint64_t)t.ldp, (uint64_t)Ns, 64, xrows));
-      else L.A1[i] = L.A0[i];
-    }
-  }
+  L.layout = layout;
+  for (int i = 0; i < 2; ++i)
+    DG_TRY(bind_iterate(t, mode, layout, Ns, static_cast<float*>(t.F[i].p), static_cast<__nv_bfloat16*>(t.Sh[i].p),
+                        static_cast<__nv_bfloat16*>(t.Sl[i].p), &L.A0[i], &L.A1[i]));
   const uint64_t brows_total = (uint64_t)t.b_rows * (mode == MODE_BF16X3 ? 2 : 1);
   DG_TRY(make_map(&L.B, t.Hop.p, f32, (uint64_t)W, brows_total, (uint32_t)W, (uint32_t)t.boxn));
   const int na = mode == MODE_BF16X3 ? 2 : 1;
@@ -421,6 +517,35 @@ static dgchefsi_status launch_step(dgchefsi_ctx* ctx, TcState& t, int mode, Laun
   count_launch();
   DG_CUDA(cudaGetLastError());
   (void)ctx;
+  return DGCHEFSI_OK;
+}
+
+// Iterate addresses of one step given explicitly (the gradient keeps its
+// iterates in checkpoint and segment buffers rather than the ping-pong pair).
+struct StepIO {
+  const float* Fin = nullptr;          // Y_k, FP32 (the A operand for TF32)
+  const __nv_bfloat16* Shin = nullptr;  // Y_k hi / lo operand copies (BF16 forms)
+  const __nv_bfloat16* Slin = nullptr;
+  const float* Fprev = nullptr;  // Y_{k-1} (not read while beta_k = 0)
+  float* Fout = nullptr;         // Y_{k+1}; may alias Fprev
+  __nv_bfloat16* Hout = nullptr;
+  __nv_bfloat16* Lout = nullptr;
+};
+
+static dgchefsi_status launch_io(TcState& t, int mode, Launch& L, int k, const double* coef, const StepIO& io,
+                                 cudaStream_t s) {
+  CUtensorMap A0, A1;
+  DG_TRY(bind_iterate(t, mode, L.layout, L.p.Ns, io.Fin, io.Shin, io.Slin, &A0, &A1));
+  Params p = L.p;
+  p.step = k;
+  p.coef = coef;
+  p.Fprev = io.Fprev ? io.Fprev : io.Fout;
+  p.Fout = io.Fout;
+  p.Hout = mode == MODE_TF32 ? nullptr : io.Hout;
+  p.Lout = mode == MODE_BF16X3 ? io.Lout : nullptr;
+  L.kern<<<L.grid, NTHREADS, L.smem, s>>>(A0, A1, L.B, p);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
   return DGCHEFSI_OK;
 }
 
@@ -545,6 +670,29 @@ static dgchefsi_status check_err(TcState& t, cudaStream_t s) {
   return DGCHEFSI_OK;
 }
 
+// The unit shape for X: when nothing is forced or tuned yet, H's operand copy
+// is built and X packed into the ping-pong pair first, so that the autotuner
+// times step 0 on the caller's data.
+static dgchefsi_status select_shape(dgchefsi_ctx* ctx, TcState& t, int mode, const double* X, int64_t ld, int64_t Ns,
+                                    int* G, int* T, int* layout) {
+  if (!t.forceG[mode] && !t.shapeG[mode]) {
+    cudaStream_t s = ctx->stream;
+    const bool f32 = mode == MODE_TF32;
+    k_build_hop<<<(unsigned)ctx->nnzb, 256, 0, s>>>(
+        t.blk_row_d, ctx->col_d, ctx->blk_off_d, ctx->vals_d, ctx->nb_d, t.pnb_d, t.brow_d, f32 ? 32 : 64, t.coef_d,
+        mode, t.b_rows, f32 ? static_cast<float*>(t.Hop.p) : nullptr,
+        f32 ? nullptr : static_cast<__nv_bfloat16*>(t.Hop.p));
+    count_launch();
+    dim3 g((unsigned)std::min<int64_t>(Ns, 1024), (unsigned)ctx->M);
+    k_pack<<<g, 128, 0, s>>>(X, ld, Ns, ctx->off_d, ctx->nb_d, t.poff_d, t.ldp, static_cast<float*>(t.F[0].p),
+                             f32 ? nullptr : static_cast<__nv_bfloat16*>(t.Sh[0].p),
+                             mode == MODE_BF16X3 ? static_cast<__nv_bfloat16*>(t.Sl[0].p) : nullptr);
+    count_launch();
+    DG_CUDA(cudaGetLastError());
+  }
+  return choose_shape(ctx, t, mode, Ns, G, T, layout);
+}
+
 static dgchefsi_status tc_prepare(dgchefsi_ctx* ctx, int prec, int64_t Ns, int m, double a, double b, double a0,
                                   int* mode_out) {
   if (ctx->max_nb > 128)
@@ -570,24 +718,8 @@ dgchefsi_status filter_tc(dgchefsi_ctx* ctx, int prec, const double* X, double* 
   cudaStream_t s = ctx->stream;
   DG_CUDA(cudaMemcpyAsync(t.coef_d, t.coef_h, sizeof(double) * (1 + 2 * m), cudaMemcpyHostToDevice, s));
   DG_CUDA(cudaMemsetAsync(t.err_d, 0, sizeof(int), s));
-  int G = 0, T = 0;
-  if (!t.forceG[mode] && !t.shapeG[mode]) {
-    // tuning runs step 0 on the packed block, so pack (and build H) first
-    const bool f32 = mode == MODE_TF32;
-    k_build_hop<<<(unsigned)ctx->nnzb, 256, 0, s>>>(
-        t.blk_row_d, ctx->col_d, ctx->blk_off_d, ctx->vals_d, ctx->nb_d, t.pnb_d, t.brow_d, f32 ? 32 : 64, t.coef_d,
-        mode, t.b_rows, f32 ? static_cast<float*>(t.Hop.p) : nullptr,
-        f32 ? nullptr : static_cast<__nv_bfloat16*>(t.Hop.p));
-    count_launch();
-    dim3 g((unsigned)std::min<int64_t>(Ns, 1024), (unsigned)ctx->M);
-    k_pack<<<g, 128, 0, s>>>(X, ld, Ns, ctx->off_d, ctx->nb_d, t.poff_d, t.ldp, static_cast<float*>(t.F[0].p),
-                             f32 ? nullptr : static_cast<__nv_bfloat16*>(t.Sh[0].p),
-                             mode == MODE_BF16X3 ? static_cast<__nv_bfloat16*>(t.Sl[0].p) : nullptr);
-    count_launch();
-    DG_CUDA(cudaGetLastError());
-  }
-  int layout = 0;
-  DG_TRY(choose_shape(ctx, t, mode, Ns, &G, &T, &layout));
+  int G = 0, T = 0, layout = 0;
+  DG_TRY(select_shape(ctx, t, mode, X, ld, Ns, &G, &T, &layout));
   Launch L;
   DG_TRY(prepare_launch(ctx, t, mode, G, T, layout, Ns, L));
   DG_TRY(enqueue_filter(ctx, t, mode, L, X, Y, Ns, ld, m, s));
@@ -654,6 +786,193 @@ dgchefsi_status filter_tc_graph(dgchefsi_ctx* ctx, int prec, const double* X, do
   return check_err(t, s);
 }
 
+// ---- band-energy gradient on the tensor-core filter
+
+// Workspace of the gradient: 2 nseg checkpoint blocks, stride - 2 segment
+// blocks, 3 rotation blocks and the backward pair, all FP32 in the padded
+// layout, plus BF16 operand copies of the backward pair. Zeroed when
+// (re)allocated so element pads read as zero.
+static dgchefsi_status ensure_grad(dgchefsi_ctx* ctx, TcState& t, int mode, int64_t Ns, int m, int stride) {
+  const int nseg = (m + stride - 1) / stride;
+  const size_t fblk = ((size_t)Ns * (size_t)t.ldp * sizeof(float) + 255) / 256 * 256;
+  const size_t hblk = ((size_t)Ns * (size_t)t.ldp * sizeof(__nv_bfloat16) + 255) / 256 * 256;
+  const int nf = 2 * nseg + std::max(stride - 2, 0) + 3 + 2;
+  const int nh = mode == MODE_TF32 ? 0 : (mode == MODE_BF16X3 ? 4 : 2);
+  const size_t need = fblk * nf + hblk * nh;
+  DG_TRY(ensure(ctx, t.gbuf, need, "gradient checkpoints"));
+  DG_CUDA(cudaMemsetAsync(t.gbuf.p, 0, need, ctx->stream));  // block offsets move with Ns
+  char* base = static_cast<char*>(t.gbuf.p);
+  size_t o = 0;
+  auto takef = [&]() { float* q = reinterpret_cast<float*>(base + o); o += fblk; return q; };
+  auto takeh = [&]() { __nv_bfloat16* q = reinterpret_cast<__nv_bfloat16*>(base + o); o += hblk; return q; };
+  t.cp0.assign(nseg, nullptr);
+  t.cp1.assign(nseg, nullptr);
+  for (int j = 0; j < nseg; ++j) {
+    t.cp0[j] = takef();
+    t.cp1[j] = takef();
+  }
+  t.segb.assign(std::max(stride - 2, 0), nullptr);
+  for (auto& q : t.segb) q = takef();
+  for (auto& q : t.R) q = takef();
+  for (auto& q : t.WF) q = takef();
+  for (int i = 0; i < 2; ++i) {
+    t.WSh[i] = mode == MODE_TF32 ? nullptr : takeh();
+    t.WSl[i] = mode == MODE_BF16X3 ? takeh() : nullptr;
+  }
+  t.g_stride = stride;
+  t.g_nseg = nseg;
+  t.g_mm = m;
+  return DGCHEFSI_OK;
+}
+
+static __nv_bfloat16* bf_ptr(DevBuf& b) { return static_cast<__nv_bfloat16*>(b.p); }
+
+dgchefsi_status tc_grad_forward(dgchefsi_ctx* ctx, int prec, const double* X, int64_t ld, int64_t Ns, int m,
+                                double a, double b, double a0, int stride, double* Ym) {
+  int mode = 0;
+  DG_TRY(tc_prepare(ctx, prec, Ns, m, a, b, a0, &mode));
+  TcState& t = *ctx->tc;
+  cudaStream_t s = ctx->stream;
+  DG_CUDA(cudaMemcpyAsync(t.coef_d, t.coef_h, sizeof(double) * (1 + 2 * m), cudaMemcpyHostToDevice, s));
+  DG_CUDA(cudaMemsetAsync(t.err_d, 0, sizeof(int), s));
+  int G = 0, T = 0, layout = 0;
+  DG_TRY(select_shape(ctx, t, mode, X, ld, Ns, &G, &T, &layout));
+  DG_TRY(ensure_grad(ctx, t, mode, Ns, m, stride));
+  Launch L;
+  DG_TRY(prepare_launch(ctx, t, mode, G, T, layout, Ns, L));
+  t.g_mG = G;
+  t.g_mT = T;
+  t.g_mL = layout;
+  const bool f32 = mode == MODE_TF32;
+  const int W = f32 ? 32 : 64;
+  k_build_hop<<<(unsigned)ctx->nnzb, 256, 0, s>>>(
+      t.blk_row_d, ctx->col_d, ctx->blk_off_d, ctx->vals_d, ctx->nb_d, t.pnb_d, t.brow_d, W, t.coef_d, mode, t.b_rows,
+      f32 ? static_cast<float*>(t.Hop.p) : nullptr, f32 ? nullptr : bf_ptr(t.Hop));
+  count_launch();
+  dim3 g((unsigned)std::min<int64_t>(Ns, 1024), (unsigned)ctx->M);
+  k_pack<<<g, 128, 0, s>>>(X, ld, Ns, ctx->off_d, ctx->nb_d, t.poff_d, t.ldp, t.cp0[0], f32 ? nullptr : bf_ptr(t.Sh[0]),
+                           mode == MODE_BF16X3 ? bf_ptr(t.Sl[0]) : nullptr);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  // Y_{k+1} goes straight to its checkpoint slot, else to the rotation block
+  // that holds neither Y_k nor Y_{k-1}.
+  std::vector<float*> pos(m + 1, nullptr);
+  pos[0] = t.cp0[0];
+  for (int k = 0; k < m; ++k) {
+    const int kk = k + 1;
+    float* out = t.R[kk % 3];
+    if (kk < m && kk % stride == 0) out = t.cp0[kk / stride];
+    else if (kk < m && stride > 1 && kk % stride == 1) out = t.cp1[kk / stride];
+    StepIO io;
+    io.Fin = pos[k];
+    io.Shin = f32 ? nullptr : bf_ptr(t.Sh[k & 1]);
+    io.Slin = mode == MODE_BF16X3 ? bf_ptr(t.Sl[k & 1]) : nullptr;
+    io.Fprev = k > 0 ? pos[k - 1] : out;
+    io.Fout = out;
+    io.Hout = f32 ? nullptr : bf_ptr(t.Sh[kk & 1]);
+    io.Lout = mode == MODE_BF16X3 ? bf_ptr(t.Sl[kk & 1]) : nullptr;
+    DG_TRY(launch_io(t, mode, L, k, t.coef_d, io, s));
+    pos[kk] = out;
+  }
+  k_unpack<<<g, 128, 0, s>>>(pos[m], t.ldp, Ns, ctx->off_d, ctx->nb_d, t.poff_d, Ym, ctx->N);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  return check_err(t, s);
+}
+
+dgchefsi_status tc_grad_backward(dgchefsi_ctx* ctx, int prec, const double* Wm, int64_t Ns, int m, int stride,
+                                 double* H_bar, double* X_bar, int64_t ld_xbar) {
+  if (!ctx->tc || ctx->tc->g_stride != stride || ctx->tc->g_mm != m || ctx->tc->Ns < Ns)
+    return set_error(DGCHEFSI_ERR_ARG, "tensor-core gradient backward without its forward");
+  TcState& t = *ctx->tc;
+  const int mode = mode_of(prec);
+  if (t.mode != mode) return set_error(DGCHEFSI_ERR_ARG, "backward precision differs from the forward's");
+  cudaStream_t s = ctx->stream;
+  const bool f32 = mode == MODE_TF32;
+  const int nseg = t.g_nseg;
+  // backward coefficients from the forward ones on the pinned mirror:
+  // step j computes W_k, k = m-1-j, with alpha_k and beta_{k+1} (0 for j = 0)
+  if (t.coefb_cap < 1 + 2 * m) {
+    cudaFree(t.coefb_d);
+    t.coefb_d = nullptr;
+    t.coefb_cap = 0;
+    DG_CUDA(cudaMalloc(&t.coefb_d, sizeof(double) * (1 + 2 * m)));
+    t.coefb_cap = 1 + 2 * m;
+  }
+  std::vector<double> cb(1 + 2 * m);
+  cb[0] = t.coef_h[0];
+  for (int j = 0; j < m; ++j) {
+    const int k = m - 1 - j;
+    cb[1 + 2 * j] = t.coef_h[1 + 2 * k];
+    cb[2 + 2 * j] = j == 0 ? 0.0 : t.coef_h[2 + 2 * (k + 1)];
+  }
+  DG_CUDA(cudaMemcpyAsync(t.coefb_d, cb.data(), sizeof(double) * cb.size(), cudaMemcpyHostToDevice, s));
+  DG_CUDA(cudaMemsetAsync(t.err_d, 0, sizeof(int), s));
+  Launch L;
+  DG_TRY(prepare_launch(ctx, t, mode, t.g_mG, t.g_mT, t.g_mL, Ns, L));
+  dim3 g((unsigned)std::min<int64_t>(Ns, 1024), (unsigned)ctx->M);
+  k_pack<<<g, 128, 0, s>>>(Wm, ctx->N, Ns, ctx->off_d, ctx->nb_d, t.poff_d, t.ldp, t.WF[0], t.WSh[0], t.WSl[0]);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  const int tiles = (ctx->max_nb + 63) / 64;
+  const dim3 go((unsigned)ctx->nnzb, (unsigned)tiles, (unsigned)tiles);
+  const int64_t nsh = Ns * t.ldp;
+  const unsigned gsh = (unsigned)std::min<int64_t>((nsh + 255) / 256, 8 * (int64_t)t.num_sms);
+  int jb = 0;
+  std::vector<const float*> ypos(stride + 1, nullptr);
+  for (int j = nseg - 1; j >= 0; --j) {
+    const int k0 = j * stride, k1 = std::min(m, k0 + stride);
+    ypos[0] = t.cp0[j];
+    if (k1 - k0 > 1) ypos[1] = t.cp1[j];
+    if (k1 - k0 > 2) {
+      if (!f32) {
+        k_shadow<<<gsh, 256, 0, s>>>(t.cp1[j], nsh, bf_ptr(t.Sh[(k0 + 1) & 1]),
+                                     mode == MODE_BF16X3 ? bf_ptr(t.Sl[(k0 + 1) & 1]) : nullptr);
+        count_launch();
+        DG_CUDA(cudaGetLastError());
+      }
+      for (int kk = k0 + 2; kk < k1; ++kk) {
+        const int q = kk - k0;
+        StepIO io;
+        io.Fin = ypos[q - 1];
+        io.Shin = f32 ? nullptr : bf_ptr(t.Sh[(kk - 1) & 1]);
+        io.Slin = mode == MODE_BF16X3 ? bf_ptr(t.Sl[(kk - 1) & 1]) : nullptr;
+        io.Fprev = ypos[q - 2];
+        io.Fout = t.segb[q - 2];
+        io.Hout = f32 ? nullptr : bf_ptr(t.Sh[kk & 1]);
+        io.Lout = mode == MODE_BF16X3 ? bf_ptr(t.Sl[kk & 1]) : nullptr;
+        DG_TRY(launch_io(t, mode, L, kk - 1, t.coef_d, io, s));
+        ypos[q] = t.segb[q - 2];
+      }
+    }
+    for (int k = k1 - 1; k >= k0; --k, ++jb) {
+      const int cur = jb & 1, nxt = cur ^ 1;
+      if (H_bar) {
+        k_block_outer_f32<<<go, 256, 0, s>>>(t.blk_row_d, ctx->col_d, ctx->blk_off_d, ctx->nb_d, t.poff_d, t.WF[cur],
+                                             ypos[k - k0], t.ldp, Ns, t.coef_h[1 + 2 * k], H_bar);
+        count_launch();
+        DG_CUDA(cudaGetLastError());
+      }
+      // W_k = alpha_k (H - cI) W_{k+1} - beta_{k+1} W_{k+2}, over W_{k+2}
+      StepIO io;
+      io.Fin = t.WF[cur];
+      io.Shin = t.WSh[cur];
+      io.Slin = t.WSl[cur];
+      io.Fprev = t.WF[nxt];
+      io.Fout = t.WF[nxt];
+      io.Hout = t.WSh[nxt];
+      io.Lout = t.WSl[nxt];
+      DG_TRY(launch_io(t, mode, L, jb, t.coefb_d, io, s));
+    }
+  }
+  if (X_bar) {
+    k_unpack<<<g, 128, 0, s>>>(t.WF[m & 1], t.ldp, Ns, ctx->off_d, ctx->nb_d, t.poff_d, X_bar, ld_xbar);
+    count_launch();
+    DG_CUDA(cudaGetLastError());
+  }
+  return check_err(t, s);
+}
+
 dgchefsi_status tc_set_shape(dgchefsi_ctx* ctx, int prec, int G, int T, int layout) {
   if (!ctx->tc) ctx->tc = new TcState();
   TcState& t = *ctx->tc;
@@ -705,6 +1024,8 @@ void tc_destroy(dgchefsi_ctx* ctx) {
     cudaFree(t.Sl[i].p);
   }
   cudaFree(t.Hop.p);
+  cudaFree(t.gbuf.p);
+  cudaFree(t.coefb_d);
   delete ctx->tc;
   ctx->tc = nullptr;
 }

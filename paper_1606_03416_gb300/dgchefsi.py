@@ -267,7 +267,7 @@ class Context:
         _check(_lib.dgchefsi_set_values(self._h, _ptr(values)))
 
     def energy_grad(self, X: torch.Tensor, m: int, a: float, b: float, a0: float, Ne: float, kT: float,
-                    grad: bool = True, stride: int = 0, n_values: int | None = None):
+                    grad: bool = True, stride: int = 0, n_values: int | None = None, prec: str = "f64"):
         """(E, ritz, H_bar, X_bar) of one cycle's band energy; H_bar and X_bar are
         None when grad is False. H_bar is per stored entry (entries independent)."""
         Ns, ld = _block(X, self.N, "X")
@@ -278,7 +278,7 @@ class Context:
         Xb = torch.empty_like(X) if grad else None
         E = C.c_double()
         self._sync_stream()
-        _check(_lib.dgchefsi_energy_grad(self._h, 0, _ptr(X), Ns, ld, int(m), float(a), float(b), float(a0),
+        _check(_lib.dgchefsi_energy_grad(self._h, PRECISIONS[prec], _ptr(X), Ns, ld, int(m), float(a), float(b), float(a0),
                                          float(Ne), float(kT), int(stride), C.byref(E), _ptr(ritz),
                                          _ptr(Hb) if grad else None, _ptr(Xb) if grad else None))
         return E.value, ritz, Hb, Xb

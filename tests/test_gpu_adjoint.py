@@ -117,3 +117,64 @@ def test_converged_gradient_is_dense_eigen_formula():
     ref = np.concatenate([r.ravel() for r in O.block_outer(Ho, V[:, :Ns], V[:, :Ns], g)])
     assert rel(Hb.cpu().numpy(), ref) <= 1e-8
     assert float(Xb.norm()) <= 1e-8 * float(X.norm())
+
+
+# ---- tensor-core forms: filter, checkpoints and backward recurrence on the
+# tcgen05 step kernel with FP32 iterates; Rayleigh-Ritz and its adjoint FP64.
+# Each filter step rounds its operands with relative error u_op (see
+# test_gpu_tc), so the iterates carry about m * u_op, and Cholesky-QR turns a
+# relative perturbation of Y_m into one of the orthonormal basis (hence of E,
+# the weights and Z) at most cond(Y_m) times larger. Tolerance on E and on the
+# largest gradient entries: 2 m u_op cond(Y_m).
+U_OP = {"tf32": 2.0 ** -9, "bf16x3": 2.0 ** -16}
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("kind", ["small", "tiny", "bulk3"])
+def test_tensor_core_energy_grad_matches_oracle(kind, prec):
+    cfg, H, Ho, X0, Ns, Ne, (a, b, a0) = case(kind)
+    E_o, G_o, Xb_o = O.band_energy_grad(Ho, X0.T, cfg.m, a, b, a0, Ne, cfg.kT)
+    kappa = np.linalg.cond(O.chebyshev_filter(Ho, X0.T, cfg.m, a, b, a0))
+    tol = 2 * cfg.m * U_OP[prec] * kappa
+    dev = torch.device("cuda:0")
+    with D.Context(H) as ctx:
+        E, ritz, Hb, Xb = ctx.energy_grad(torch.from_numpy(X0).to(dev), cfg.m, a, b, a0, Ne, cfg.kT, prec=prec)
+    Gflat = np.concatenate([g.ravel() for g in G_o])
+    eE, eH, eX = abs(E - E_o) / abs(E_o), rel(Hb.cpu().numpy(), Gflat), rel(Xb.cpu().numpy(), Xb_o.T)
+    print(f"TC_GRAD {kind} {prec} cond={kappa:.2e} E={eE:.2e} H={eH:.2e} X={eX:.2e} tol={tol:.2e}")
+    assert np.isfinite(Hb.cpu().numpy()).all() and np.isfinite(Xb.cpu().numpy()).all()
+    assert eE <= tol and eH <= tol and eX <= tol
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32", "bf16"])
+def test_tensor_core_grad_independent_of_checkpoint_stride(prec):
+    """Recomputed segments reproduce the forward iterates bit for bit (same
+    kernel, same inputs, operand copies rebuilt by the same rounding), so the
+    gradient does not depend on the checkpoint stride at all."""
+    cfg, H, Ho, X0, Ns, Ne, (a, b, a0) = case("tiny")
+    dev = torch.device("cuda:0")
+    X = torch.from_numpy(X0).to(dev)
+    with D.Context(H) as ctx:
+        ref = ctx.energy_grad(X, cfg.m, a, b, a0, Ne, cfg.kT, stride=1, prec=prec)
+        for s in (2, 3, 0, cfg.m):
+            out = ctx.energy_grad(X, cfg.m, a, b, a0, Ne, cfg.kT, stride=s, prec=prec)
+            assert out[0] == ref[0]
+            assert torch.equal(out[2], ref[2]) and torch.equal(out[3], ref[3]), s
+
+
+def test_tensor_core_autograd_matches_fp64_gradient():
+    cfg, H, Ho, X0, Ns, Ne, (a, b, a0) = case("bulk3")
+    kappa = np.linalg.cond(O.chebyshev_filter(Ho, X0.T, cfg.m, a, b, a0))
+    dev = torch.device("cuda:0")
+    grads = {}
+    with D.Context(H) as ctx:
+        for prec in ("f64", "bf16x3"):
+            vals = torch.from_numpy(H.values.copy()).to(dev).requires_grad_(True)
+            X = torch.from_numpy(X0).to(dev).requires_grad_(True)
+            E = A.band_energy(vals, X, ctx, cfg.m, a, b, a0, Ne, cfg.kT, prec=prec)
+            E.backward()
+            grads[prec] = (float(E), vals.grad.cpu().numpy(), X.grad.cpu().numpy())
+    tol = 2 * cfg.m * U_OP["bf16x3"] * kappa
+    assert abs(grads["bf16x3"][0] - grads["f64"][0]) <= tol * abs(grads["f64"][0])
+    assert rel(grads["bf16x3"][1], grads["f64"][1]) <= tol
+    assert rel(grads["bf16x3"][2], grads["f64"][2]) <= tol

@@ -157,7 +157,9 @@ dgchefsi_status dgchefsi_filter_graph(dgchefsi_ctx* ctx, int prec, const double*
  * elements x T tiles of 128 states per unit, ACC accumulator columns per
  * element (32, 64 or 128, from the largest element). layout 0 puts states on
  * the MMA's M dimension (G*T accumulators); layout 1 puts the G = 128/ACC
- * elements' rows on M and 2 x 128 states on N. By default (G = T = 0) the
+ * elements' rows on M and 2 x 128 states on N; layout 2 is layout 1 with each
+ * 128-byte K slice staged as two 64-byte ring slots (twice the ring depth in
+ * the same shared memory). By default (G = T = 0) the
  * first filter call times one step with every shape that has a kernel for
  * this H's accumulator width and keeps the fastest. Setting a shape without a
  * kernel returns DGCHEFSI_ERR_UNSUPPORTED. */

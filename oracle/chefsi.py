@@ -385,3 +385,70 @@ def tied_gradient(H: DGHamiltonian, G):
                 t = t - np.diag(np.diag(G[index[(K, K)]]))
             out.append(t)
     return out
+
+
+# --------------------------------------------------------------------------
+# Beyond one cycle.
+#  * Re-alignment of the coefficients to the next SCF step's basis
+#    (Sec. III.B.3, Eqs. basis_rotation_1-3).
+#  * Density-matrix blocks on all of H's pattern (Eq. densitymatrix for
+#    neighbouring K, K'; the paper computes the diagonal ones, Sec. II.C).
+#  * CholeskyQR2 and shifted CholeskyQR3, alternatives to the Cholesky-QR of
+#    Alg. 1 step 3, whose loss of stability on ill-conditioned filtered blocks
+#    the paper mentions (Sec. III.B.2). Readings: CholeskyQR2 is Cholesky-QR
+#    applied twice (Fukaya, Nakatsukasa, Yanagisawa, Yamamoto 2014); the shifted
+#    form first factors Y^T Y + s I with s = 11 (n N_s + N_s (N_s + 1)) u ||Y||_F^2
+#    (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa 2020, with the Frobenius
+#    norm in place of the 2-norm, an upper bound they allow), u = 2^-53, then
+#    applies CholeskyQR2. All three give the same Q (the thin-QR factor with
+#    positive R diagonal) in exact arithmetic.
+# --------------------------------------------------------------------------
+
+
+def realign(V_old, V_new, X: np.ndarray) -> np.ndarray:
+    """Eq. basis_rotation_3: X_K^{(i+1)} = (V_K^{i+1})^T V_K^{i} X_K^{(i)} on every
+    element K. V_old[K] is R_K x J_K^{i} (element K's old basis functions
+    sampled on its R_K grid points), V_new[K] is R_K x J_K^{i+1}; X is
+    (sum_K J_K^{i}) x N_s with element K's rows consecutive. Elements have
+    disjoint supports, so the global product of Eq. basis_rotation_1 splits
+    into these per-element products (Eq. basis_rotation_2)."""
+    rows, out, o = [], [], 0
+    for K in range(len(V_old)):
+        n = V_old[K].shape[1]
+        rows.append((o, o + n))
+        o += n
+    if o != X.shape[0]:
+        raise ValueError("X rows do not match the old basis sizes")
+    for K, (r0, r1) in enumerate(rows):
+        out.append((V_new[K].T @ V_old[K]) @ X[r0:r1])
+    return np.vstack(out)
+
+
+def density_pattern_blocks(H: DGHamiltonian, X: np.ndarray, f: np.ndarray):
+    """Eq. densitymatrix on every stored block of H: P_KK' = sum_i f_i
+    x_{i;K} x_{i;K'}^T for K' in N(K), in block-CSR order."""
+    out = []
+    for K in range(H.M):
+        for Kp, _ in H.neighbours(K):
+            out.append(X[H.rows(K)] @ np.diag(f) @ X[H.rows(Kp)].T)
+    return out
+
+
+def cholesky_qr2(Y: np.ndarray):
+    """CholeskyQR2: Y = Q1 U1 by Cholesky-QR, then Q1 = Q U2. Returns (Q, U)
+    with U = U2 U1 upper triangular, Y = Q U."""
+    Q1, U1, _ = cholesky_qr(Y)
+    Q, U2, _ = cholesky_qr(Q1)
+    return Q, U2 @ U1
+
+
+def shifted_cholesky_qr3(Y: np.ndarray):
+    """Shifted CholeskyQR3: U1 = chol(Y^T Y + s I), Q1 = Y U1^{-1}, then
+    CholeskyQR2 of Q1. Returns (Q, U) with Y = Q U."""
+    n, ns = Y.shape
+    S = Y.T @ Y
+    s = 11.0 * (n * ns + ns * (ns + 1)) * 2.0 ** -53 * float(np.sum(Y * Y))
+    U1 = np.linalg.cholesky(S + s * np.eye(ns)).T
+    Q1 = sla.solve_triangular(U1, Y.T, trans="T", lower=False).T
+    Q, U23 = cholesky_qr2(Q1)
+    return Q, U23 @ U1

@@ -488,7 +488,7 @@ dgchefsi_status dgchefsi_set_tile_shape(dgchefsi_ctx* ctx, int prec, int G, int 
   DG_TRY(check_ctx(ctx));
   if (prec < DGCHEFSI_TF32 || prec > DGCHEFSI_BF16X3) return set_error(DGCHEFSI_ERR_ARG, "not a tensor-core precision");
   if (G < 0 || T < 0 || (G == 0) != (T == 0)) return set_error(DGCHEFSI_ERR_ARG, "need G, T both > 0 or both 0");
-  if (layout < 0 || layout > 1) return set_error(DGCHEFSI_ERR_ARG, "layout must be 0 or 1");
+  if (layout < 0 || layout > 2) return set_error(DGCHEFSI_ERR_ARG, "layout must be 0, 1 or 2");
   return tc_set_shape(ctx, prec, G, T, layout);
 }
 

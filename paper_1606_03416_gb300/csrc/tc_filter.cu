@@ -407,7 +407,7 @@ static dgchefsi_status ensure_iterates(dgchefsi_ctx* ctx, TcState& t, int mode, 
 }
 
 static dgchefsi_status make_map(CUtensorMap* map, void* base, bool f32, uint64_t inner, uint64_t rows,
-                                uint32_t box_inner, uint32_t box_rows) {
+                                uint32_t box_inner, uint32_t box_rows, bool swizzle64 = false) {
   auto enc = encode_fn();
   if (!enc) return set_error(DGCHEFSI_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   const size_t esz = f32 ? 4 : 2;
@@ -416,7 +416,8 @@ static dgchefsi_status make_map(CUtensorMap* map, void* base, bool f32, uint64_t
   cuuint32_t box[2] = {box_inner, box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims,
-                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   swizzle64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(DGCHEFSI_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return DGCHEFSI_OK;
@@ -441,14 +442,18 @@ struct Launch {
 static dgchefsi_status bind_iterate(TcState& t, int mode, int layout, int64_t Ns, const float* F,
                                     const __nv_bfloat16* Sh, const __nv_bfloat16* Sl, CUtensorMap* A0,
                                     CUtensorMap* A1) {
-  const uint32_t xrows = layout == 1 ? 256u : (uint32_t)BM;  // states per box of Y_k
+  const uint32_t xrows = layout >= 1 ? 256u : (uint32_t)BM;  // states per box of Y_k
+  const bool sw64 = layout == 2;                              // 64-byte slots
   if (mode == MODE_TF32) {
-    DG_TRY(make_map(A0, const_cast<float*>(F), true, (uint64_t)t.ldp, (uint64_t)Ns, 32, xrows));
+    DG_TRY(make_map(A0, const_cast<float*>(F), true, (uint64_t)t.ldp, (uint64_t)Ns, sw64 ? 16 : 32, xrows, sw64));
     *A1 = *A0;
     return DGCHEFSI_OK;
   }
-  DG_TRY(make_map(A0, const_cast<__nv_bfloat16*>(Sh), false, (uint64_t)t.ldp, (uint64_t)Ns, 64, xrows));
-  if (mode == MODE_BF16X3) DG_TRY(make_map(A1, const_cast<__nv_bfloat16*>(Sl), false, (uint64_t)t.ldp, (uint64_t)Ns, 64, xrows));
+  DG_TRY(make_map(A0, const_cast<__nv_bfloat16*>(Sh), false, (uint64_t)t.ldp, (uint64_t)Ns, sw64 ? 32 : 64, xrows,
+                  sw64));
+  if (mode == MODE_BF16X3)
+    DG_TRY(make_map(A1, const_cast<__nv_bfloat16*>(Sl), false, (uint64_t)t.ldp, (uint64_t)Ns, sw64 ? 32 : 64, xrows,
+                    sw64));
   else *A1 = *A0;
   return DGCHEFSI_OK;
 }
@@ -467,11 +472,12 @@ static dgchefsi_status prepare_launch(dgchefsi_ctx* ctx, TcState& t, int mode, i
     DG_TRY(bind_iterate(t, mode, layout, Ns, static_cast<float*>(t.F[i].p), static_cast<__nv_bfloat16*>(t.Sh[i].p),
                         static_cast<__nv_bfloat16*>(t.Sl[i].p), &L.A0[i], &L.A1[i]));
   const uint64_t brows_total = (uint64_t)t.b_rows * (mode == MODE_BF16X3 ? 2 : 1);
-  DG_TRY(make_map(&L.B, t.Hop.p, f32, (uint64_t)W, brows_total, (uint32_t)W, (uint32_t)t.boxn));
+  const int sb = layout == 2 ? 64 : SLICE_BYTES;  // ring-slot K extent in bytes
+  DG_TRY(make_map(&L.B, t.Hop.p, f32, (uint64_t)W, brows_total, (uint32_t)(W * sb / SLICE_BYTES), (uint32_t)t.boxn,
+                  layout == 2));
   const int na = mode == MODE_BF16X3 ? 2 : 1;
-  const int stage_bytes = layout == 1 ? na * (128 * SLICE_BYTES + 256 * SLICE_BYTES)
-                                      : na * (T * A_BYTES + G * t.ACC * SLICE_BYTES);
-  const int stages = mode == MODE_BF16X3 ? STAGES / 2 : STAGES;
+  const int stage_bytes = layout >= 1 ? na * (128 * sb + 256 * sb) : na * (T * A_BYTES + G * t.ACC * SLICE_BYTES);
+  const int stages = layout >= 1 ? TN_RING_BYTES / stage_bytes : (mode == MODE_BF16X3 ? STAGES / 2 : STAGES);
   L.smem = stages * stage_bytes + (2 * stages + 4) * 8 + 2 * pl->maxent * (1 + G) * 4 + 1024;
   if (L.smem > 227 * 1024) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "filter schedule too large for shared memory");
   DG_CUDA(cudaFuncSetAttribute(L.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem));

@@ -55,6 +55,7 @@ constexpr int EPI_WARPS = 8;
 constexpr int STAGES = 4;       // ring slots (each T A-tiles + G B-tiles)
 constexpr int ZERO_TILES = 64;  // zero B tiles for non-coupling elements, spread over L2
 constexpr int A_BYTES = BM * SLICE_BYTES;
+constexpr int TN_RING_BYTES = 192 * 1024;  // ring of the transposed kernel (any slot size)
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per wait
 
 constexpr int MAXG = 4;
@@ -141,6 +142,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// The same for rows of SB bytes (128: 128-byte swizzle, layout code 2; 64:
+// 64-byte swizzle, layout code 4), 8-row groups 8 * SB bytes apart.
+template <int SB>
+__device__ __forceinline__ uint64_t sdesc_sb(uint32_t addr) {
+  static_assert(SB == 128 || SB == 64, "slice width");
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)((8 * SB) >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)(SB == 128 ? 2 : 4) << 61);
 }
 
 // Instruction descriptor: FP32 accumulate, A/B format code `fmt` (1 = BF16 for
@@ -506,7 +516,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // tensor core reads 48 KB of shared memory per slot instead of 64 KB, issues
 // half as many instructions, and the epilogue (tensor-memory lane = element
 // row, column = state) writes along element rows, coalesced across the warp.
-template <int MODE_, int ACC>
+// SB is the K extent of a ring slot in bytes: 128 (one 128-byte swizzle row per
+// slice of the schedule) or 64 (each slice split into two slots with 64-byte
+// swizzle), which halves the slot and doubles the ring depth in the same
+// shared memory, so a refill has three slots of MMA time to land instead of one.
+template <int MODE_, int ACC, int SB = SLICE_BYTES>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_filter_step_tn(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                      const __grid_constant__ CUtensorMap tmB, const Params p) {
@@ -515,11 +529,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   constexpr int G = 128 / ACC;   // elements stacked along M
   constexpr int NS = 256;        // states per unit (MMA N)
   constexpr int NA = MODE_ == MODE_BF16X3 ? 2 : 1;
-  constexpr int S = MODE_ == MODE_BF16X3 ? STAGES / 2 : STAGES;
-  constexpr int h_bytes = ACC * SLICE_BYTES;    // one element's H tile
-  constexpr int a_bytes = G * h_bytes;          // 16 KB: the stacked H tiles (MMA A)
-  constexpr int x_bytes = NS * SLICE_BYTES;     // 32 KB: the Y_k slice (MMA B)
+  constexpr int h_bytes = ACC * SB;             // one element's H tile
+  constexpr int a_bytes = G * h_bytes;          // 128 SB: the stacked H tiles (MMA A)
+  constexpr int x_bytes = NS * SB;              // 256 SB: the Y_k slice (MMA B)
   constexpr int stage_bytes = NA * (a_bytes + x_bytes);  // [H hi][H lo][X hi][X lo]
+  constexpr int S = TN_RING_BYTES / stage_bytes;          // 2, 4 or 8 slots
+  constexpr int NSUB = SLICE_BYTES / SB;                  // ring slots per schedule slice
+  constexpr int ESZ = MODE_ == MODE_TF32 ? 4 : 2;
+  static_assert((S & (S - 1)) == 0, "ring depth must be a power of two");
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
   int32_t* sched_sh0 = reinterpret_cast<int32_t*>(bars + 2 * S + 4);
   int32_t* sched_sh1 = sched_sh0 + p.maxent * (1 + G);
@@ -573,24 +590,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (lane == 0 && ok) {
         for (int e = 0; e < ne && ok; ++e) {
           const int32_t* ent = sched_sh0 + e * (1 + G);
-          const int st = c & (S - 1);
-          const uint32_t ph = (uint32_t)(c / S) & 1u;
-          if (!mbar_wait(empty0 + 8 * st, ph ^ 1u)) {
-            ok = false;
-            break;
-          }
-          const uint32_t fb = full0 + 8 * st;
-          mbar_expect_tx(fb, (uint32_t)stage_bytes);
-          uint8_t* sst = smem + st * stage_bytes;
 #pragma unroll
-          for (int v = 0; v < NA; ++v) {
+          for (int sub = 0; sub < NSUB; ++sub) {
+            const int st = c & (S - 1);
+            const uint32_t ph = (uint32_t)(c / S) & 1u;
+            if (!mbar_wait(empty0 + 8 * st, ph ^ 1u)) {
+              ok = false;
+              break;
+            }
+            const uint32_t fb = full0 + 8 * st;
+            mbar_expect_tx(fb, (uint32_t)stage_bytes);
+            uint8_t* sst = smem + st * stage_bytes;
+            const int xo = sub * (SB / ESZ);  // element offset of this K part (16-byte multiple)
 #pragma unroll
-            for (int g = 0; g < G; ++g)  // H tiles (zero tiles for non-coupling elements)
-              tma_load_2d(smem_u32(sst + v * a_bytes + g * h_bytes), &tmB, 0,
-                          (int)(ent[1 + g] + (v == 1 ? p.lo_rows : 0)), fb);
-            tma_load_2d(smem_u32(sst + NA * a_bytes + v * x_bytes), v == 1 ? &tmA1 : &tmA0, ent[0], s0, fb);
+            for (int v = 0; v < NA; ++v) {
+#pragma unroll
+              for (int g = 0; g < G; ++g)  // H tiles (zero tiles for non-coupling elements)
+                tma_load_2d(smem_u32(sst + v * a_bytes + g * h_bytes), &tmB, xo,
+                            (int)(ent[1 + g] + (v == 1 ? p.lo_rows : 0)), fb);
+              tma_load_2d(smem_u32(sst + NA * a_bytes + v * x_bytes), v == 1 ? &tmA1 : &tmA0, ent[0] + xo, s0, fb);
+            }
+            ++c;
           }
-          ++c;
         }
       }
       ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -609,7 +630,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     constexpr uint32_t fmt = MODE_ == MODE_TF32 ? 2u : 1u;
     constexpr uint32_t ID = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(NS >> 3) << 17) |
                             ((uint32_t)(128 >> 4) << 24);
-    const uint64_t desc0 = sdesc(smem_u32(smem));
+    const uint64_t desc0 = sdesc_sb<SB>(smem_u32(smem));
     int c = 0, i = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++i) {
@@ -622,7 +643,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(buf * NS);
         uint32_t first = 0;
-        for (int e = 0; e < ne && ok; ++e) {
+        for (int e = 0; e < ne * NSUB && ok; ++e) {  // one iteration per ring slot
           const int st = c & (S - 1);
           const uint32_t ph = (uint32_t)(c / S) & 1u;
           if (!mbar_wait(full0 + 8 * st, ph)) {
@@ -633,7 +654,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const uint64_t dh = desc0 + (uint64_t)((st * stage_bytes) >> 4);  // H hi (A)
           const uint64_t dx = dh + (uint64_t)((NA * a_bytes) >> 4);         // X hi (B)
 #pragma unroll
-          for (int kk = 0; kk < SLICE_BYTES / 32; ++kk) {
+          for (int kk = 0; kk < SB / 32; ++kk) {
             const uint64_t ad = dh + (uint64_t)((32 * kk) >> 4);
             const uint64_t bd = dx + (uint64_t)((32 * kk) >> 4);
             const uint32_t acc = kk > 0 ? 1u : first;
@@ -732,12 +753,12 @@ using FilterKernel = void (*)(const CUtensorMap, const CUtensorMap, const CUtens
 // Unit shapes {G elements, T tiles of 128 states, ACC accumulator columns per
 // element, layout} that have kernels; layout 0 = states along the MMA's M
 // (k_filter_step_tc), 1 = element rows along M, 256 states along N
-// (k_filter_step_tn, G = 128/ACC, T = 2). The autotuner picks among those
-// matching ACC.
-constexpr int NSHAPES = 10;
+// (k_filter_step_tn, G = 128/ACC, T = 2), 2 = layout 1 with 64-byte ring
+// slots. The autotuner picks among those matching ACC.
+constexpr int NSHAPES = 13;
 constexpr int SHAPES[NSHAPES][4] = {{2, 2, 64, 0}, {1, 2, 64, 0}, {2, 1, 64, 0}, {4, 2, 32, 0}, {2, 2, 32, 0},
                                     {2, 1, 128, 0}, {1, 2, 128, 0}, {2, 2, 64, 1}, {4, 2, 32, 1},
-                                    {1, 2, 128, 1}};
+                                    {1, 2, 128, 1}, {2, 2, 64, 2}, {4, 2, 32, 2}, {1, 2, 128, 2}};
 
 template <int MODE_>
 FilterKernel pick_shape(int G, int T, int ACC, int layout) {
@@ -745,6 +766,12 @@ FilterKernel pick_shape(int G, int T, int ACC, int layout) {
     if (ACC == 64 && G == 2 && T == 2) return k_filter_step_tn<MODE_, 64>;
     if (ACC == 32 && G == 4 && T == 2) return k_filter_step_tn<MODE_, 32>;
     if (ACC == 128 && G == 1 && T == 2) return k_filter_step_tn<MODE_, 128>;
+    return nullptr;
+  }
+  if (layout == 2) {
+    if (ACC == 64 && G == 2 && T == 2) return k_filter_step_tn<MODE_, 64, 64>;
+    if (ACC == 32 && G == 4 && T == 2) return k_filter_step_tn<MODE_, 32, 64>;
+    if (ACC == 128 && G == 1 && T == 2) return k_filter_step_tn<MODE_, 128, 64>;
     return nullptr;
   }
   if (layout != 0) return nullptr;

@@ -242,3 +242,37 @@ def make_problem(cfg: ProblemConfig):
     H = make_blocks(cfg)
     Ns, Ne = resolve_sizes(cfg, H)
     return H, make_X(H.N, Ns, cfg.seed), make_start_vector(H.N, cfg.seed), Ns, Ne
+
+
+def _orthonormal_columns(rng, R: int, n: int) -> np.ndarray:
+    """R x n with orthonormal columns (QR of a Gaussian, signs fixed)."""
+    Q, Rf = np.linalg.qr(rng.standard_normal((R, n)))
+    return Q * np.where(np.diag(Rf) < 0, -1.0, 1.0)[None, :]
+
+
+def make_basis_pair(nb_old, nb_new, nr, delta: float = 0.05, seed: int = 0):
+    """Synthetic adaptive local bases of two consecutive SCF steps, sampled on
+    each element's grid points: per element K an R_K x J_K^{old} matrix with
+    orthonormal columns, and an R_K x J_K^{new} one spanning a perturbation of
+    it (the old columns plus delta-scaled Gaussian noise, extended by random
+    directions when the element gains basis functions), the kind of small basis
+    change between SCF steps that re-alignment is for. Returns
+    (V_old list, V_new list)."""
+    rng = np.random.default_rng(seed + 3)
+    V_old, V_new = [], []
+    for K in range(len(nb_old)):
+        R, n0, n1 = int(nr[K]), int(nb_old[K]), int(nb_new[K])
+        if not (1 <= n0 <= R and 1 <= n1 <= R):
+            raise ValueError("need 1 <= basis functions <= grid points on every element")
+        A = _orthonormal_columns(rng, R, n0)
+        B = np.hstack([A, rng.standard_normal((R, max(n1 - n0, 0)))])[:, :n1]
+        Q, Rf = np.linalg.qr(B + delta * rng.standard_normal((R, n1)))
+        V_old.append(A)
+        V_new.append(Q * np.where(np.diag(Rf) < 0, -1.0, 1.0)[None, :])
+    return V_old, V_new
+
+
+def pack_blocks(blocks) -> np.ndarray:
+    """Concatenate row-major blocks into one float64 array (the packed layout
+    of the re-alignment call)."""
+    return np.concatenate([np.ascontiguousarray(b, dtype=np.float64).ravel() for b in blocks])

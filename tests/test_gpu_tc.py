@@ -104,8 +104,8 @@ def test_mixed_cycles_converge(prec):
     assert err <= limit
 
 
-SHAPES = {32: [(4, 2, 0), (2, 2, 0), (4, 2, 1)], 64: [(2, 2, 0), (1, 2, 0), (2, 1, 0), (2, 2, 1)],
-          128: [(2, 1, 0), (1, 2, 0), (1, 2, 1)]}
+SHAPES = {32: [(4, 2, 0), (2, 2, 0), (4, 2, 1), (4, 2, 2)], 64: [(2, 2, 0), (1, 2, 0), (2, 1, 0), (2, 2, 1), (2, 2, 2)],
+          128: [(2, 1, 0), (1, 2, 0), (1, 2, 1), (1, 2, 2)]}
 
 
 @pytest.mark.parametrize("prec", ["bf16", "bf16x3", "tf32"])

@@ -113,11 +113,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def profiled_traffic(prec: str, Ns: int):
+def profiled_traffic(prec: str, Ns: int, layout: int = -1):
     """DRAM bytes per launch of the tensor-core filter step from the committed
     ncu summary, if that summary was taken on the current kernel source (its
-    recorded source hash matches) for this precision; scaled to N_s (traffic
-    grows in proportion). None otherwise."""
+    recorded source hash matches) for this precision and, when it records one,
+    this unit-shape layout; scaled to N_s (traffic grows in proportion). None
+    otherwise."""
     import glob
     import hashlib
     src = os.path.join(ROOT, "paper_1606_03416_gb300", "csrc", "tc_kernel.cuh")
@@ -125,6 +126,8 @@ def profiled_traffic(prec: str, Ns: int):
     for path in glob.glob(os.path.join(ROOT, "profiles", f"k_filter_step_t?_{prec}_bulk3d_*.md")):
         text = open(path).read()
         if f"source-sha1 (paper_1606_03416_gb300/csrc/tc_kernel.cuh, first 12): {sha}" not in text:
+            continue
+        if "unit-shape-layout:" in text and f"unit-shape-layout: {layout}" not in text:
             continue
         for line in text.splitlines():
             key = f"traffic-per-launch-bytes-{prec}-Ns"
@@ -376,6 +379,64 @@ def run_adjoint(args):
     return 0
 
 
+def measure_next_rows(ctx, H, X, Ns, m, prec, dev):
+    """Steps around the cycle on the same workload, FP64 on the CUDA cores:
+    re-alignment to a perturbed basis (R = 216 sample points per element),
+    density blocks on all of H's pattern, and Rayleigh-Ritz under each
+    orthonormalisation (one filtered block, the same for all three)."""
+    import torch
+    from paper_1606_03416_gb300 import inputs as G
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=2):
+        best, out = 1e30, None
+        for _ in range(reps):
+            s_, e_ = torch.cuda.Event(True), torch.cuda.Event(True)
+            torch.cuda.synchronize()
+            s_.record(stream)
+            out = fn()
+            e_.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, s_.elapsed_time(e_) / 1e3)
+        return best, out
+
+    res = {}
+    nb = np.asarray(H.nb)
+    R = np.full(nb.shape, 216, dtype=np.int32)
+    Vo, Vn = G.make_basis_pair(nb, nb, R, delta=0.05, seed=0)
+    Vod, Vnd = torch.from_numpy(G.pack_blocks(Vo)).to(dev), torch.from_numpy(G.pack_blocks(Vn)).to(dev)
+    Xn = torch.empty_like(X)
+    t, _ = timed(lambda: ctx.realign(X, nb, R, Vod, Vnd, X_new=Xn))
+    fl = 2.0 * (float((R.astype(np.int64) * nb * nb).sum()) + Ns * float((nb.astype(np.int64) ** 2).sum()))
+    res["realign"] = {"ms": t * 1e3, "gflop": fl / 1e9, "tflops": fl / t / 1e12,
+                      "frac_of_fp64_peak": fl / t / 1e12 / F64_PEAK_TFLOPS, "sample_points_per_element": 216}
+    Vod = Vnd = Xn = None
+    f = torch.full((Ns,), 0.5, dtype=torch.float64, device=dev)
+    t, _ = timed(lambda: ctx.density_pattern(X, f), reps=1)
+    fl = 2.0 * float(nnz_of(H)) * Ns
+    res["density_pattern"] = {"ms": t * 1e3, "gflop": fl / 1e9, "tflops": fl / t / 1e12,
+                              "frac_of_fp64_peak": fl / t / 1e12 / F64_PEAK_TFLOPS}
+    b, tmin = ctx.bounds(torch.ones(H.N, dtype=torch.float64, device=dev), 10)
+    Yf = torch.empty_like(X)
+    ctx.filter(X, m, tmin + (b - tmin) * Ns / H.N, b, tmin, prec=prec, Y=Yf)
+    Yw = torch.empty_like(X)
+    rr = {}
+    for mode in ("cholqr", "cholqr2", "shifted_cholqr3"):
+        ctx.set_orthonormalisation(mode)
+        Yw.copy_(Yf)
+        t, _ = timed(lambda: ctx.rayleigh_ritz(Yw), reps=1)
+        rr[mode] = t
+    ctx.set_orthonormalisation("cholqr")
+    res["rayleigh_ritz_s_by_orthonormalisation"] = rr
+    return res
+
+
+def nnz_of(H) -> int:
+    nb = np.asarray(H.nb, dtype=np.int64)
+    rp, col = np.asarray(H.row_ptr), np.asarray(H.col)
+    return int(sum(nb[K] * nb[col[e]] for K in range(len(nb)) for e in range(rp[K], rp[K + 1])))
+
+
 def run_converge(args):
     """Cycles to the 1e-8 target: from the same random start, CheFSI cycles in the
     mixed form (--prec) and in FP64 until the Ritz values of the occupied states
@@ -457,6 +518,8 @@ def main():
     ap.add_argument("--ref-states", type=int, default=64, help="states in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-n_b 2D sheet measurement")
+    ap.add_argument("--no-next-rows", action="store_true",
+                    help="skip re-alignment, pattern density and orthonormalisation timings")
     ap.add_argument("--adjoint", action="store_true", help="differentiation workload instead of the cycle")
     ap.add_argument("--adjoint-full", action="store_true", help="with --adjoint: also time the full 12^3 size")
     ap.add_argument("--adjoint-f64", action="store_true", help="with --adjoint-full: time the FP64 gradient too")
@@ -588,7 +651,7 @@ def main():
             rf = {"bound": "tensor", "achieved": mult * step_fl / (ms_launch * 1e-3) / 1e12, "peak": tpeak,
                   "unit": "TFLOP/s"}
     rf["frac"] = rf["achieved"] / rf["peak"]
-    rf["traffic"] = profiled_traffic(args.prec, Ns) if args.prec != "f64" else None
+    rf["traffic"] = profiled_traffic(args.prec, Ns, ctx.tile_shape(args.prec)[3]) if args.prec != "f64" else None
     rf["algorithmic_bytes"] = byts
     if args.prec == "f64":
         rf["kernel"] = "k_filter_step_f64"
@@ -711,6 +774,8 @@ def main():
         "roofline": roof, "roofline_filter": rf, "filter_tflops_other_precisions": other,
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }
+    if not args.no_next_rows and args.prec != "f64":
+        line["next_rows"] = measure_next_rows(ctx, H, X, Ns, m, args.prec, dev)
     ctx.close()
     X = Y = Xd = Yd = Xs = Xh = Yh = S = None  # free the 8x8x8 buffers before the next workload
     torch.cuda.empty_cache()

@@ -181,8 +181,29 @@ dgchefsi_status dgchefsi_gram(dgchefsi_ctx* ctx, const double* Y, int64_t Ns, in
  * Returns DGCHEFSI_ERR_NOT_SPD if S is not numerically positive definite
  * (Cholesky-QR has no fallback), DGCHEFSI_ERR_NO_CONVERGENCE if the dense
  * eigensolver fails, DGCHEFSI_ERR_NONFINITE on NaN/Inf Ritz values.
- * Synchronises (checks the factorisation status). Needs Ns <= N. */
+ * Synchronises (checks the factorisation status). Needs Ns <= N.
+ * The orthonormalisation is the context's (dgchefsi_set_orthonormalisation). */
 dgchefsi_status dgchefsi_rayleigh_ritz(dgchefsi_ctx* ctx, double* Y, int64_t Ns, int64_t ld, double* ritz);
+
+/* Orthonormalisation of Alg. 1 step 3 used by dgchefsi_rayleigh_ritz and
+ * dgchefsi_cycle. The paper uses Cholesky-QR and notes it can be less stable
+ * than QR (Sec. III.B.2); the two alternatives are published remedies that
+ * give the same Y_hat in exact arithmetic (the thin-QR factor, positive R
+ * diagonal):
+ *   DGCHEFSI_ORTH_CHOLQR            one Cholesky-QR pass (default, the paper's)
+ *   DGCHEFSI_ORTH_CHOLQR2           CholeskyQR2 (Fukaya et al. 2014): the pass
+ *                                   repeated on Y_hat; orthonormal to rounding
+ *                                   while cond(Y) < ~u^{-1/2}; 2x the Gram and
+ *                                   triangular products
+ *   DGCHEFSI_ORTH_SHIFTED_CHOLQR3   shifted CholeskyQR3 (Fukaya et al. 2020):
+ *                                   first pass on Y^T Y + s I with
+ *                                   s = 11 (N N_s + N_s (N_s + 1)) 2^-53 ||Y||_F^2,
+ *                                   then CholeskyQR2; for cond(Y) up to ~u^{-1}
+ * ERR_ARG for another value. The band-energy gradient always uses one pass. */
+#define DGCHEFSI_ORTH_CHOLQR 0
+#define DGCHEFSI_ORTH_CHOLQR2 1
+#define DGCHEFSI_ORTH_SHIFTED_CHOLQR3 2
+dgchefsi_status dgchefsi_set_orthonormalisation(dgchefsi_ctx* ctx, int mode);
 
 /* Fermi-Dirac occupations f_i = 1/(1 + exp((lambda_i - mu)/kT)) with mu set by
  * 2 sum_i f_i = Ne (spin factor 2; occupations of Eq. KS_DG_Energy, Sec. III.B.2).
@@ -201,6 +222,39 @@ dgchefsi_status dgchefsi_occupations(dgchefsi_ctx* ctx, const double* ritz, int6
  *      sum_{L<K} nb[L]^2. */
 dgchefsi_status dgchefsi_density_blocks(dgchefsi_ctx* ctx, const double* X, int64_t Ns, int64_t ld,
                                         const double* f, double* P);
+
+/* Density-matrix blocks on all of H's pattern (Eq. densitymatrix for
+ * neighbouring elements K, K'; the paper forms the diagonal ones, Sec. II.C,
+ * and needs the off-diagonal ones for forces): P_KK' = sum_i f_i x_{i;K}
+ * x_{i;K'}^T for every stored block (K, K'), FP64.
+ *   X  device (Ns x ld) state-major;  f  device [Ns]
+ *   P  device [n_values] out, laid out like H's values (block e at blk_off[e],
+ *      row-major n_K x n_K'); the diagonal blocks equal dgchefsi_density_blocks'.
+ * Asynchronous on the context's stream. */
+dgchefsi_status dgchefsi_density_pattern(dgchefsi_ctx* ctx, const double* X, int64_t Ns, int64_t ld,
+                                         const double* f, double* P);
+
+/* Re-alignment of a coefficient block to the next SCF step's basis
+ * (Sec. III.B.3, Eq. basis_rotation_3): per element K,
+ *   X_new_K = (V_K^{new})^T V_K^{old} X_old_K,
+ * the l2 projection of the old states onto the new basis (the bases of
+ * different elements have disjoint supports, so the global product of
+ * Eq. basis_rotation_1 splits by element). FP64: T_K = (V_K^{new})^T V_K^{old}
+ * first (J_K^{new} x J_K^{old}), then X_new_K = T_K X_old_K.
+ *   ctx     context of the NEW Hamiltonian: its element sizes J_K^{new} give
+ *           X_new's layout (element K at columns off_K .. off_K + J_K^{new})
+ *   nb_old  host [M]: old element sizes J_K^{old}, 1..256
+ *   nr      host [M]: grid points R_K sampling element K's basis functions, >= 1
+ *   V_old   device: element K's R_K x J_K^{old} samples, row-major, blocks
+ *           concatenated in element order
+ *   V_new   device: R_K x J_K^{new} blocks, same packing
+ *   X_old   device (Ns x ld_old) state-major, old layout (element K at the
+ *           prefix sum of J^{old}); ld_old >= sum J^{old}
+ *   X_new   device (Ns x ld) out, ld >= N; must not overlap X_old (ERR_ARG)
+ * Synchronises (the per-element tables are copied from the host). */
+dgchefsi_status dgchefsi_realign(dgchefsi_ctx* ctx, const int32_t* nb_old, const int32_t* nr, const double* V_old,
+                                 const double* V_new, const double* X_old, int64_t Ns, int64_t ld_old,
+                                 double* X_new, int64_t ld);
 
 /* One full CheFSI cycle (Alg. 1) plus occupations and density blocks:
  * bounds -> filter -> Cholesky-QR -> Rayleigh-Ritz -> rotation -> f, mu -> P_KK.

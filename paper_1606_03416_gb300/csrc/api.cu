@@ -235,20 +235,39 @@ static dgchefsi_status rr_impl(dgchefsi_ctx* ctx, double* Y, int64_t Ns, int64_t
   double* work = static_cast<double*>(ctx->ws_solver.p);
   const int lwork = (int)(ctx->ws_solver.bytes / sizeof(double));
   DG_CUDA(cudaMemsetAsync(ctx->info_d, 0, 4 * sizeof(int), s));
-  // Step 3: S = Y^T Y (lower tiles, mirrored), S = U^T U.
-  DG_CUDA(gemm_nt_f64(Y, ld, Y, ld, S, Ns, Ns, Ns, N, true, false, s));
-  DG_SOLVER(cusolverDnDpotrf(ctx->solver, CUBLAS_FILL_MODE_UPPER, n, S, n, work, lwork, ctx->info_d));
   int info[4] = {0, 0, 0, 0};
-  DG_CUDA(cudaMemcpyAsync(info, ctx->info_d, sizeof(int), cudaMemcpyDeviceToHost, s));
-  DG_CUDA(cudaStreamSynchronize(s));
-  if (info[0] != 0)
-    return set_error(DGCHEFSI_ERR_NOT_SPD, "Cholesky of S = Y^T Y failed at column %d (S not positive definite)", info[0]);
-  // U^{-1} in place. Column-major U^{-1} read row-major is U^{-T} (lower).
-  DG_SOLVER(cusolverDnXtrtri(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, Ns, CUDA_R_64F, S, Ns, work,
-                             ctx->ws_solver.bytes, ctx->solver_host.empty() ? nullptr : ctx->solver_host.data(),
-                             lw_trtri_h, ctx->info_d + 1));
-  // Y_hat^T = U^{-T} Y^T  (W holds Y_hat, state-major, ld N)
-  DG_CUDA(gemm_nn_f64(S, Ns, Y, ld, W, N, Ns, N, Ns, true, s));
+  // Step 3: S = Y^T Y (lower tiles, mirrored), S = U^T U, Y_hat = Y U^{-1}.
+  // CholeskyQR2 repeats the pass on Y_hat; shifted CholeskyQR3 factors
+  // Y^T Y + s I first, s = 11 (N N_s + N_s (N_s + 1)) u ||Y||_F^2, then repeats
+  // twice. Pass 1 reads Y and writes W; later passes read W, write Y and copy
+  // back, so Y_hat always ends in W (state-major, ld N).
+  const int passes = ctx->orth_mode == DGCHEFSI_ORTH_CHOLQR2 ? 2 : (ctx->orth_mode == DGCHEFSI_ORTH_SHIFTED_CHOLQR3 ? 3 : 1);
+  for (int pass = 0; pass < passes; ++pass) {
+    const double* in = pass == 0 ? Y : W;
+    const int64_t ldi = pass == 0 ? ld : N;
+    double* outp = pass == 0 ? W : Y;
+    const int64_t ldo = pass == 0 ? N : ld;
+    DG_CUDA(gemm_nt_f64(in, ldi, in, ldi, S, Ns, Ns, Ns, N, true, false, s));
+    if (pass == 0 && ctx->orth_mode == DGCHEFSI_ORTH_SHIFTED_CHOLQR3)
+      DG_CUDA(shift_diagonal_by_trace_f64(S, Ns, 11.0 * ((double)N * (double)Ns + (double)Ns * (double)(Ns + 1)) *
+                                                     0x1p-53, s));
+    DG_SOLVER(cusolverDnDpotrf(ctx->solver, CUBLAS_FILL_MODE_UPPER, n, S, n, work, lwork, ctx->info_d));
+    DG_CUDA(cudaMemcpyAsync(info, ctx->info_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaStreamSynchronize(s));
+    if (info[0] != 0)
+      return set_error(DGCHEFSI_ERR_NOT_SPD,
+                       "Cholesky of S = Y^T Y failed at column %d (S not positive definite; orthonormalisation pass %d)",
+                       info[0], pass + 1);
+    // U^{-1} in place. Column-major U^{-1} read row-major is U^{-T} (lower).
+    DG_SOLVER(cusolverDnXtrtri(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, Ns, CUDA_R_64F, S, Ns, work,
+                               ctx->ws_solver.bytes, ctx->solver_host.empty() ? nullptr : ctx->solver_host.data(),
+                               lw_trtri_h, ctx->info_d + 1));
+    // Y_hat^T = U^{-T} Y^T
+    DG_CUDA(gemm_nn_f64(S, Ns, in, ldi, outp, ldo, Ns, N, Ns, true, s));
+    if (pass > 0)
+      DG_CUDA(cudaMemcpy2DAsync(W, sizeof(double) * N, Y, sizeof(double) * ld, sizeof(double) * N, Ns,
+                                cudaMemcpyDeviceToDevice, s));
+  }
   // Step 4: H Y_hat into Y (Y is free now), H_hat = Y_hat^T (H Y_hat). H_hat is
   // symmetric up to rounding and the eigensolver reads one triangle (row-major
   // lower = column-major upper), so only the tiles on and below the diagonal
@@ -415,6 +434,7 @@ void dgchefsi_destroy(dgchefsi_ctx* ctx) {
   free_buf(ctx->ws_cycle);
   free_buf(ctx->ws_lanczos);
   free_buf(ctx->ws_adjoint);
+  free_buf(ctx->ws_realign);
   delete ctx;
 }
 
@@ -481,6 +501,15 @@ dgchefsi_status dgchefsi_filter_graph(dgchefsi_ctx* ctx, int prec, const double*
   if (prec == DGCHEFSI_F64) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "the graph form runs the tensor-core filter");
   if (Ns == 0) return DGCHEFSI_OK;
   return filter_tc_graph(ctx, prec, X, Y, Ns, ld, m, a, b, a0);
+}
+
+dgchefsi_status dgchefsi_set_orthonormalisation(dgchefsi_ctx* ctx, int mode) {
+  clear_error();
+  if (!ctx) return set_error(DGCHEFSI_ERR_ARG, "null context");
+  if (mode != DGCHEFSI_ORTH_CHOLQR && mode != DGCHEFSI_ORTH_CHOLQR2 && mode != DGCHEFSI_ORTH_SHIFTED_CHOLQR3)
+    return set_error(DGCHEFSI_ERR_ARG, "unknown orthonormalisation %d", mode);
+  ctx->orth_mode = mode;
+  return DGCHEFSI_OK;
 }
 
 dgchefsi_status dgchefsi_set_tile_shape(dgchefsi_ctx* ctx, int prec, int G, int T, int layout) {

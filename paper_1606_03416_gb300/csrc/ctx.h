@@ -50,6 +50,8 @@ struct dgchefsi_ctx {
   dg::DevBuf ws_cycle;    // filtered block inside dgchefsi_cycle
   dg::DevBuf ws_lanczos;  // Lanczos basis and scalars
   dg::DevBuf ws_adjoint;  // checkpoints and blocks of the band-energy gradient
+  dg::DevBuf ws_realign;  // per-element tables and overlaps of the re-alignment
+  int orth_mode = 0;      // DGCHEFSI_ORTH_*: orthonormalisation of step 3
   std::vector<char> solver_host;
   int* info_d = nullptr;  // [4] cuSOLVER infos + finite flag
   cusolverDnHandle_t solver = nullptr;

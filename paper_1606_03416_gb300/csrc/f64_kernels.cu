@@ -367,6 +367,20 @@ __global__ void __launch_bounds__(256) k_occupations_f64(const double* __restric
   if (threadIdx.x == 0) *mu_out = mu;
 }
 
+__global__ void k_shift_diag_f64(double* A, int64_t n, double coef) {
+  __shared__ double red[256];
+  double t = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) t += A[i * n + i];
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double sft = coef * red[0];
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) A[i * n + i] += sft;
+}
+
 __global__ void k_zero_strict_upper_f64(double* A, int64_t n, int64_t lda) {
   const int64_t i = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -567,6 +581,12 @@ cudaError_t density_f64(const HView& h, const int64_t* poff, const double* X, in
 cudaError_t occupations_f64(const double* ritz, int64_t Ns, double Ne, double kT, double* f, double* mu,
                             cudaStream_t s) {
   k_occupations_f64<<<1, 256, 0, s>>>(ritz, Ns, Ne, kT, f, mu);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t shift_diagonal_by_trace_f64(double* A, int64_t n, double coef, cudaStream_t s) {
+  k_shift_diag_f64<<<1, 256, 0, s>>>(A, n, coef);
   count_launch();
   return cudaGetLastError();
 }

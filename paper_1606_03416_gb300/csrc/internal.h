@@ -67,6 +67,9 @@ cudaError_t gemm_tn_f64(const double* A, int64_t lda, const double* B, int64_t l
 cudaError_t scaled_residual_f64(const double* HX, const double* X, int64_t ld, const double* lam, const double* g,
                                 double scale, int64_t Ns, int64_t n, double* out, int64_t ldo, cudaStream_t s);
 
+// A[i,i] += coef * trace(A) for a row-major n x n matrix (one CTA, fixed
+// summation order).
+cudaError_t shift_diagonal_by_trace_f64(double* A, int64_t n, double coef, cudaStream_t s);
 // Zero the strict upper triangle of a row-major n x n matrix.
 cudaError_t zero_strict_upper_f64(double* A, int64_t n, int64_t lda, cudaStream_t s);
 // flag[0] |= 1 if any of x[0..n) is not finite.

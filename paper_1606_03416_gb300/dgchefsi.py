@@ -29,7 +29,11 @@ EXPORTS = ["dgchefsi_create", "dgchefsi_destroy", "dgchefsi_set_stream", "dgchef
            "dgchefsi_density_blocks", "dgchefsi_cycle", "dgchefsi_last_error", "dgchefsi_launch_count",
            "dgchefsi_bounds_static", "dgchefsi_gram", "dgchefsi_set_values", "dgchefsi_energy_grad",
            "dgchefsi_filter_graph", "dgchefsi_set_tile_shape", "dgchefsi_get_tile_shape",
-           "dgchefsi_selftest_wait"]
+           "dgchefsi_selftest_wait", "dgchefsi_set_orthonormalisation", "dgchefsi_density_pattern",
+           "dgchefsi_realign"]
+
+# Orthonormalisations of Alg. 1 step 3 (dgchefsi_set_orthonormalisation).
+ORTHONORMALISATIONS = {"cholqr": 0, "cholqr2": 1, "shifted_cholqr3": 2}
 
 # Capacity (doubles) of the library's fixed scratch array for bounds_static.
 BOUNDS_STATIC_DOUBLES = 1 << 20
@@ -62,6 +66,9 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_set_tile_shape": (st, [P, C.c_int, C.c_int, C.c_int, C.c_int]),
         "dgchefsi_get_tile_shape": (st, [P, C.c_int, P, P, P, P]),
         "dgchefsi_selftest_wait": (st, [P, I64]),
+        "dgchefsi_set_orthonormalisation": (st, [P, C.c_int]),
+        "dgchefsi_density_pattern": (st, [P, P, I64, I64, P, P]),
+        "dgchefsi_realign": (st, [P, P, P, P, P, P, I64, I64, P, I64]),
         "dgchefsi_set_values": (st, [P, P]),
         "dgchefsi_energy_grad": (st, [P, C.c_int, P, I64, I64, C.c_int, D, D, D, D, D, C.c_int, P, P, P, P]),
         "dgchefsi_occupations": (st, [P, P, I64, D, D, P, P]),
@@ -257,6 +264,45 @@ class Context:
         self._sync_stream()
         _check(_lib.dgchefsi_density_blocks(self._h, _ptr(X), Ns, ld, _ptr(f), _ptr(P)))
         return P
+
+    def density_pattern(self, X: torch.Tensor, f: torch.Tensor, P: torch.Tensor | None = None) -> torch.Tensor:
+        """P_KK' = sum_i f_i x_{i;K} x_{i;K'}^T on every stored block of H, laid
+        out like H's values."""
+        Ns, ld = _block(X, self.N, "X")
+        if P is None:
+            P = torch.empty(self.n_values, dtype=torch.float64, device=X.device)
+        self._sync_stream()
+        _check(_lib.dgchefsi_density_pattern(self._h, _ptr(X), Ns, ld, _ptr(f), _ptr(P)))
+        return P
+
+    def set_orthonormalisation(self, mode: str):
+        """"cholqr" (Alg. 1 step 3 as in the paper), "cholqr2" or "shifted_cholqr3"."""
+        _check(_lib.dgchefsi_set_orthonormalisation(self._h, ORTHONORMALISATIONS[mode]))
+
+    # -- Sec. III.B.3: coefficients carried to the next SCF step's basis
+    def realign(self, X_old: torch.Tensor, nb_old, nr, V_old: torch.Tensor, V_new: torch.Tensor,
+                X_new: torch.Tensor | None = None) -> torch.Tensor:
+        """X_new_K = (V_K^new)^T V_K^old X_old_K for every element. X_old is
+        (N_s, sum nb_old) state-major; V_old / V_new are the packed per-element
+        R_K x J_K sample blocks (float64 CUDA); this context's H is the new one."""
+        nb_old = np.ascontiguousarray(nb_old, dtype=np.int32)
+        nr = np.ascontiguousarray(nr, dtype=np.int32)
+        if nb_old.shape != (self.M,) or nr.shape != (self.M,):
+            raise ValueError("nb_old and nr need one entry per element")
+        Ns, ld_old = _block(X_old, int(nb_old.astype(np.int64).sum()), "X_old")
+        for name, V in (("V_old", V_old), ("V_new", V_new)):
+            if not (V.is_cuda and V.dtype == torch.float64 and V.is_contiguous()):
+                raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+        if V_old.numel() != int((nr.astype(np.int64) * nb_old).sum()) or \
+                V_new.numel() != int((nr.astype(np.int64) * self.nb).sum()):
+            raise ValueError("V_old / V_new sizes do not match nr x element sizes")
+        if X_new is None:
+            X_new = torch.empty((Ns, self.N), dtype=torch.float64, device=X_old.device)
+        _, ld = _block(X_new, self.N, "X_new")
+        self._sync_stream()
+        _check(_lib.dgchefsi_realign(self._h, nb_old.ctypes.data, nr.ctypes.data, _ptr(V_old), _ptr(V_new),
+                                     _ptr(X_old), Ns, ld_old, _ptr(X_new), ld))
+        return X_new
 
     # -- differentiation of one cycle (band energy)
     def set_values(self, values: torch.Tensor):

@@ -137,6 +137,24 @@ def profiled_traffic(prec: str, Ns: int, layout: int = -1):
     return None
 
 
+def profiled_gram_traffic(Ns: int):
+    """DRAM bytes of one k_gemm_nt_f64 Gram launch from the committed ncu
+    summary taken at this N_s on the current FP64 kernel source; else None."""
+    import glob
+    import hashlib
+    src = os.path.join(ROOT, "paper_1606_03416_gb300", "csrc", "f64_kernels.cu")
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    for path in glob.glob(os.path.join(ROOT, "profiles", "k_gemm_nt_f64_*.md")):
+        text = open(path).read()
+        if f"source-sha1 (paper_1606_03416_gb300/csrc/f64_kernels.cu, first 12): {sha}" not in text:
+            continue
+        key = f"traffic-per-launch-bytes-gram-Ns{Ns}:"
+        for line in text.splitlines():
+            if line.startswith(key):
+                return float(line[len(key):])
+    return None
+
+
 def dist_env():
     from paper_1606_03416_gb300.replicas import rank_info
     return rank_info()
@@ -260,6 +278,21 @@ def measure_uneven(dev, precs=("bf16x3", "tf32"), reps=3):
             g_, t_, acc, lay = ctx.tile_shape(pr)
             out[pr] = {"ms_per_filter": min(ts), "tflops": fl / (min(ts) * 1e-3) / 1e12,
                        "unit_shape": {"G": g_, "T": t_, "ACC": acc, "layout": lay}, "graph": True}
+        # FP64 variant: the same grouped steps on the DFMA pipe, also from a graph;
+        # two steps timed (the whole m = 16 filter takes ~16 s at the FP64 rate)
+        m64 = 2
+        fl64 = filter_flops(H, Ns, m64)
+        ctx.filter_graph(X, m64, 10.0, 45.0, -2.0, prec="f64", Y=Y)
+        s_, e_ = torch.cuda.Event(True), torch.cuda.Event(True)
+        torch.cuda.synchronize()
+        s_.record()
+        ctx.filter_graph(X, m64, 10.0, 45.0, -2.0, prec="f64", Y=Y)
+        e_.record()
+        torch.cuda.synchronize()
+        t64 = s_.elapsed_time(e_)
+        out["f64"] = {"ms_per_step": t64 / m64, "tflops": fl64 / (t64 * 1e-3) / 1e12,
+                      "frac_of_fp64_peak": fl64 / (t64 * 1e-3) / 1e12 / F64_PEAK_TFLOPS,
+                      "steps_timed": m64, "graph": True}
     del X, Y
     torch.cuda.empty_cache()
     return out
@@ -376,6 +409,36 @@ def run_adjoint(args):
                 torch.cuda.empty_cache()
         out["full_12x12x12"] = full
     print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_gram_only(args):
+    """One FP64 Gram S = Y^T Y (k_gemm_nt_f64, lower tiles) of the workload's
+    block after one warm-up: the profiling case of the cycle's dominant kernel
+    (~2 GB on the device at the bench size)."""
+    import torch
+    from paper_1606_03416_gb300 import dgchefsi as D
+    from paper_1606_03416_gb300 import inputs as G
+    dev = torch.device("cuda:0")
+    cfg = G.CONFIGS[args.workload]
+    H = G.make_blocks(cfg)
+    Ns, _ = G.resolve_sizes(cfg, H)
+    Ns = args.ns or Ns
+    Y = torch.from_numpy(G.make_X(H.N, Ns, cfg.seed)).to(dev)
+    S = torch.empty((Ns, Ns), dtype=torch.float64, device=dev)
+    with D.Context(H) as ctx:
+        ctx.gram(Y, S)
+        s_, e_ = torch.cuda.Event(True), torch.cuda.Event(True)
+        torch.cuda.synchronize()
+        s_.record()
+        ctx.gram(Y, S)
+        e_.record()
+        torch.cuda.synchronize()
+    ms = s_.elapsed_time(e_)
+    nt = (Ns + 63) // 64
+    fl = 2.0 * (nt * (nt + 1) // 2) * 64 * 64 * H.N  # the 64 x 64 tiles on and below the diagonal
+    print(json.dumps({"mode": "gram-only", "workload": cfg.name, "Ns": Ns, "N": H.N, "ms": ms,
+                      "tflops": fl / (ms * 1e-3) / 1e12}), flush=True)
     return 0
 
 
@@ -526,6 +589,7 @@ def main():
     ap.add_argument("--converge", action="store_true",
                     help="cycles to Ritz error <= 1e-8 against a dense eigensolve, mixed and FP64")
     ap.add_argument("--max-cycles", type=int, default=40)
+    ap.add_argument("--gram-only", action="store_true", help="time one FP64 Gram (profiling case)")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--filter-only", action="store_true",
                     help="time only the filter (profiling case); --ns and --m override the workload")
@@ -541,6 +605,8 @@ def main():
         return run_adjoint(args)
     if args.converge:
         return run_converge(args)
+    if args.gram_only:
+        return run_gram_only(args)
 
     import torch
     rank, world, local = dist_env()
@@ -678,7 +744,7 @@ def main():
     gram_fl = 2.0 * (nt * (nt + 1) // 2) * 64 * 64 * N
     g_ach = gram_fl / (statistics.median(gms) * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": g_ach, "peak": F64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": g_ach / F64_PEAK_TFLOPS, "traffic": None, "kernel": "k_gemm_nt_f64",
+            "frac": g_ach / F64_PEAK_TFLOPS, "traffic": profiled_gram_traffic(Ns), "kernel": "k_gemm_nt_f64",
             "ms_per_launch": statistics.median(gms),
             "peak_source": "FP64 DFMA peak derived in DESIGN.md (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz); "
                            "cuBLAS DGEMM measured 1.10 TFLOP/s on this GB300"}

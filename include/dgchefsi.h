@@ -143,13 +143,16 @@ dgchefsi_status dgchefsi_bounds_static(dgchefsi_ctx* ctx, const double* v0, int 
 dgchefsi_status dgchefsi_filter(dgchefsi_ctx* ctx, int prec, const double* X, double* Y,
                                 int64_t Ns, int64_t ld, int m, double a, double b, double a0);
 
-/* The tensor-core filter of dgchefsi_filter (same arguments, results and
- * synchronisation), replayed from a CUDA graph: the first call for a given
- * (prec, X, Y, Ns, ld, m) tunes the unit shape if needed, captures the whole
- * launch sequence (operand copy of H, packing, the m steps, unpacking) and
- * later calls only update the recurrence coefficients and relaunch the graph.
- * Every element size runs in the same persistent grouped launch per step.
- * prec must be a tensor-core precision (DGCHEFSI_ERR_UNSUPPORTED for F64). */
+/* The filter of dgchefsi_filter (same arguments and results, bit for bit),
+ * replayed from a CUDA graph: the first call for a given (prec, X, Y, Ns, ld,
+ * m) tunes the unit shape if needed, captures the whole launch sequence and
+ * later calls only update the recurrence coefficients (copied from a pinned
+ * host mirror by the graph's first node) and relaunch it. A graph is captured
+ * again when X, Y, Ns, ld, m or any library buffer it refers to changed.
+ *   tensor-core precisions: operand copy of H, packing, the m persistent
+ *     grouped steps (every element size in the same launch), unpacking;
+ *     synchronises (checks the pipeline's bounded-wait status)
+ *   DGCHEFSI_F64: the m grouped DFMA steps; asynchronous on the stream. */
 dgchefsi_status dgchefsi_filter_graph(dgchefsi_ctx* ctx, int prec, const double* X, double* Y, int64_t Ns,
                                       int64_t ld, int m, double a, double b, double a0);
 

@@ -157,6 +157,95 @@ static dgchefsi_status filter_f64(dgchefsi_ctx* ctx, const double* X, double* Y,
   return DGCHEFSI_OK;
 }
 
+// The FP64 filter captured once as a graph (coefficient copy + m steps, the
+// same ping-pong as filter_f64) and replayed.
+static dgchefsi_status filter_f64_graph(dgchefsi_ctx* ctx, const double* X, double* Y, int64_t Ns, int64_t ld, int m,
+                                        double a, double b, double a0) {
+  cudaStream_t s = ctx->stream;
+  // the previous replay may still read the pinned mirror or the coefficients
+  DG_CUDA(cudaStreamSynchronize(s));
+  if (ctx->f64_coef_cap < 1 + 2 * m) {
+    if (ctx->f64_gexec) {
+      cudaGraphExecDestroy(ctx->f64_gexec);
+      ctx->f64_gexec = nullptr;
+    }
+    cudaFree(ctx->f64_coef_d);
+    cudaFreeHost(ctx->f64_coef_h);
+    ctx->f64_coef_d = nullptr;
+    ctx->f64_coef_h = nullptr;
+    ctx->f64_coef_cap = 0;
+    DG_CUDA(cudaMalloc(&ctx->f64_coef_d, sizeof(double) * (1 + 2 * m)));
+    DG_CUDA(cudaMallocHost(&ctx->f64_coef_h, sizeof(double) * (1 + 2 * m)));
+    ctx->f64_coef_cap = 1 + 2 * m;
+  }
+  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+  const double s1 = e / (a0 - c);
+  double* ch = ctx->f64_coef_h;
+  ch[0] = c;
+  ch[1] = s1 / e;
+  ch[2] = 0.0;
+  double sig = s1;
+  for (int k = 1; k < m; ++k) {
+    const double sn = 1.0 / (2.0 / s1 - sig);
+    ch[1 + 2 * k] = 2.0 * sn / e;
+    ch[2 + 2 * k] = sig * sn;
+    sig = sn;
+  }
+  double* T = nullptr;
+  if (m >= 2) {  // a regrow moves the workspace; the graph key below then differs
+    DG_TRY(ensure(ctx, ctx->ws_filter, sizeof(double) * (size_t)Ns * (size_t)ld, "filter iterate"));
+    T = static_cast<double*>(ctx->ws_filter.p);
+  }
+  const bool same = ctx->f64_gexec && ctx->f64_m == m && ctx->f64_X == X && ctx->f64_Y == Y && ctx->f64_Ns == Ns &&
+                    ctx->f64_ld == ld && ctx->f64_T == (void*)T;
+  if (!same) {
+    if (ctx->f64_gexec) {
+      cudaGraphExecDestroy(ctx->f64_gexec);
+      ctx->f64_gexec = nullptr;
+    }
+    if (!ctx->f64_cap) DG_CUDA(cudaStreamCreateWithFlags(&ctx->f64_cap, cudaStreamNonBlocking));
+    cudaStream_t cs = ctx->f64_cap;
+    const HView h = ctx->view();
+    double* A = (m % 2 == 1) ? Y : T;
+    double* B = (m % 2 == 1) ? T : Y;
+    cudaGraph_t graph = nullptr;
+    DG_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaMemcpyAsync(ctx->f64_coef_d, ctx->f64_coef_h, sizeof(double) * (1 + 2 * m),
+                                      cudaMemcpyHostToDevice, cs);
+    if (err == cudaSuccess) err = filter_step_f64_dev(h, X, ld, nullptr, A, ld, Ns, ctx->f64_coef_d, 0, cs);
+    const double* prev = X;
+    double* cur = A;
+    for (int k = 1; k < m && err == cudaSuccess; ++k) {
+      double* out = (k % 2 == 1) ? B : A;
+      err = filter_step_f64_dev(h, cur, ld, prev, out, ld, Ns, ctx->f64_coef_d, k, cs);
+      prev = cur;
+      cur = out;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (err != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return set_error(DGCHEFSI_ERR_CUDA, "capture of the FP64 filter graph failed: %s",
+                       cudaGetErrorString(err != cudaSuccess ? err : e2));
+    }
+    cudaError_t e3 = cudaGraphInstantiate(&ctx->f64_gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e3 != cudaSuccess) {
+      ctx->f64_gexec = nullptr;
+      return set_error(DGCHEFSI_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e3));
+    }
+    ctx->f64_m = m;
+    ctx->f64_T = T;
+    ctx->f64_X = X;
+    ctx->f64_Y = Y;
+    ctx->f64_Ns = Ns;
+    ctx->f64_ld = ld;
+  }
+  DG_CUDA(cudaGraphLaunch(ctx->f64_gexec, s));
+  count_launch(m);
+  return DGCHEFSI_OK;
+}
+
 static dgchefsi_status bounds_impl(dgchefsi_ctx* ctx, const double* v0, int k, double* b_upper, double* theta_min) {
   const int64_t N = ctx->N;
   if (k > N) k = (int)N;
@@ -435,6 +524,10 @@ void dgchefsi_destroy(dgchefsi_ctx* ctx) {
   free_buf(ctx->ws_lanczos);
   free_buf(ctx->ws_adjoint);
   free_buf(ctx->ws_realign);
+  if (ctx->f64_gexec) cudaGraphExecDestroy(ctx->f64_gexec);
+  if (ctx->f64_cap) cudaStreamDestroy(ctx->f64_cap);
+  cudaFree(ctx->f64_coef_d);
+  cudaFreeHost(ctx->f64_coef_h);
   delete ctx;
 }
 
@@ -498,8 +591,8 @@ dgchefsi_status dgchefsi_filter_graph(dgchefsi_ctx* ctx, int prec, const double*
                                       int64_t ld, int m, double a, double b, double a0) {
   clear_error();
   DG_TRY(check_filter_args(ctx, prec, X, Y, Ns, ld, m, a, b, a0));
-  if (prec == DGCHEFSI_F64) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "the graph form runs the tensor-core filter");
   if (Ns == 0) return DGCHEFSI_OK;
+  if (prec == DGCHEFSI_F64) return filter_f64_graph(ctx, X, Y, Ns, ld, m, a, b, a0);
   return filter_tc_graph(ctx, prec, X, Y, Ns, ld, m, a, b, a0);
 }
 

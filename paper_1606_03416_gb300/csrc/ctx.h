@@ -52,6 +52,18 @@ struct dgchefsi_ctx {
   dg::DevBuf ws_adjoint;  // checkpoints and blocks of the band-energy gradient
   dg::DevBuf ws_realign;  // per-element tables and overlaps of the re-alignment
   int orth_mode = 0;      // DGCHEFSI_ORTH_*: orthonormalisation of step 3
+  // FP64 filter as a CUDA graph: coefficients copied from a pinned mirror at
+  // every replay; the graph is captured again when X, Y, N_s, ld, m or the
+  // workspace it refers to change
+  cudaGraphExec_t f64_gexec = nullptr;
+  cudaStream_t f64_cap = nullptr;
+  double* f64_coef_d = nullptr;
+  double* f64_coef_h = nullptr;
+  int f64_coef_cap = 0, f64_m = 0;
+  const void* f64_X = nullptr;
+  void* f64_Y = nullptr;
+  void* f64_T = nullptr;
+  int64_t f64_Ns = 0, f64_ld = 0;
   std::vector<char> solver_host;
   int* info_d = nullptr;  // [4] cuSOLVER infos + finite flag
   cusolverDnHandle_t solver = nullptr;

@@ -46,7 +46,13 @@ __device__ __forceinline__ void fma_tile(const double (&As)[BK][TP], const doubl
 // out = alpha * (sum_{K'} H_KK' in_K' - c in_K) - beta * prev_K.
 __global__ void __launch_bounds__(NT) k_filter_step_f64(HView h, const double* __restrict__ in, int64_t ld,
                                                         const double* prev, double* out, int64_t ldo,
-                                                        int64_t Ns, double alpha, double c, double beta) {
+                                                        int64_t Ns, double alpha, double c, double beta,
+                                                        const double* __restrict__ coef, int step) {
+  if (coef) {  // coefficients in device memory ([c, alpha_0, beta_0, alpha_1, ...]; graph replays)
+    c = coef[0];
+    alpha = coef[1 + 2 * step];
+    beta = coef[2 + 2 * step];
+  }
   const int K = blockIdx.y;
   const int nK = h.nb[K];
   const int j0 = blockIdx.z * T;
@@ -513,7 +519,16 @@ cudaError_t filter_step_f64(const HView& h, const double* in, int64_t ld_in, con
                             int64_t ld_out, int64_t Ns, double alpha, double c, double beta, cudaStream_t s) {
   if (Ns == 0) return cudaSuccess;
   dim3 grid(cdiv(Ns, T), (unsigned)h.M, cdiv(h.max_nb, T));
-  k_filter_step_f64<<<grid, NT, 0, s>>>(h, in, ld_in, prev, out, ld_out, Ns, alpha, c, beta);
+  k_filter_step_f64<<<grid, NT, 0, s>>>(h, in, ld_in, prev, out, ld_out, Ns, alpha, c, beta, nullptr, 0);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t filter_step_f64_dev(const HView& h, const double* in, int64_t ld_in, const double* prev, double* out,
+                                int64_t ld_out, int64_t Ns, const double* coef, int step, cudaStream_t s) {
+  if (Ns <= 0) return cudaSuccess;
+  dim3 grid(cdiv(Ns, T), (unsigned)h.M, cdiv(h.max_nb, T));
+  k_filter_step_f64<<<grid, NT, 0, s>>>(h, in, ld_in, prev, out, ld_out, Ns, 0.0, 0.0, 0.0, coef, step);
   count_launch();
   return cudaGetLastError();
 }

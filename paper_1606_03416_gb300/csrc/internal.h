@@ -26,6 +26,12 @@ void count_launch(int n = 1);
 cudaError_t filter_step_f64(const HView& h, const double* in, int64_t ld_in, const double* prev, double* out,
                             int64_t ld_out, int64_t Ns, double alpha, double c, double beta, cudaStream_t s);
 
+// The same step with c, alpha_k = coef[1 + 2 step], beta_k = coef[2 + 2 step]
+// read from device memory (coef[0] = c), so a captured graph can be replayed
+// with new filter bounds.
+cudaError_t filter_step_f64_dev(const HView& h, const double* in, int64_t ld_in, const double* prev, double* out,
+                                int64_t ld_out, int64_t Ns, const double* coef, int step, cudaStream_t s);
+
 // y = H x for one vector (Lanczos).
 cudaError_t spmv_f64(const HView& h, const double* x, double* y, cudaStream_t s);
 

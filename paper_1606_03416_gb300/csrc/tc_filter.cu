@@ -233,6 +233,9 @@ struct TcState {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int g_mode = -1, g_m = 0, g_G = 0, g_T = 0, g_L = 0;
+  // bumped whenever a buffer or plan a captured graph may refer to is
+  // (re)allocated or freed; a graph is replayed only under the same generation
+  uint64_t gen = 1, g_gen = 0;
   const void* g_X = nullptr;
   void* g_Y = nullptr;
   int64_t g_Ns = 0, g_ld = 0;
@@ -297,6 +300,7 @@ static dgchefsi_status ensure_layout(dgchefsi_ctx* ctx, TcState& t) {
 static dgchefsi_status ensure_mode(dgchefsi_ctx* ctx, TcState& t, int mode) {
   if (t.mode == mode) return DGCHEFSI_OK;
   const int W = mode == MODE_TF32 ? 32 : 64;
+  ++t.gen;
   for (auto& kv : t.plans) free_plan(kv.second);
   t.plans.clear();
   t.brow_h.resize(ctx->nnzb);
@@ -381,7 +385,18 @@ static dgchefsi_status get_plan(dgchefsi_ctx* ctx, TcState& t, int G, Plan** out
   return DGCHEFSI_OK;
 }
 
+static dgchefsi_status grow_iterates(dgchefsi_ctx* ctx, TcState& t, int mode, int64_t Ns);
+
 static dgchefsi_status ensure_iterates(dgchefsi_ctx* ctx, TcState& t, int mode, int64_t Ns) {
+  const void* before[6] = {t.F[0].p, t.F[1].p, t.Sh[0].p, t.Sh[1].p, t.Sl[0].p, t.Sl[1].p};
+  DG_TRY(grow_iterates(ctx, t, mode, Ns));
+  const void* after[6] = {t.F[0].p, t.F[1].p, t.Sh[0].p, t.Sh[1].p, t.Sl[0].p, t.Sl[1].p};
+  for (int i = 0; i < 6; ++i)
+    if (before[i] != after[i]) ++t.gen;
+  return DGCHEFSI_OK;
+}
+
+static dgchefsi_status grow_iterates(dgchefsi_ctx* ctx, TcState& t, int mode, int64_t Ns) {
   if (t.Ns < Ns || t.F[0].p == nullptr) {
     const size_t n = (size_t)Ns * (size_t)t.ldp;
     for (int i = 0; i < 2; ++i) {
@@ -746,7 +761,7 @@ dgchefsi_status filter_tc_graph(dgchefsi_ctx* ctx, int prec, const double* X, do
   int G = 0, T = 0, layout = 0;
   DG_TRY(choose_shape(ctx, t, mode, Ns, &G, &T, &layout));
   const bool same = t.gexec && t.g_mode == mode && t.g_m == m && t.g_G == G && t.g_T == T && t.g_L == layout &&
-                    t.g_X == X && t.g_Y == Y && t.g_Ns == Ns && t.g_ld == ld;
+                    t.g_X == X && t.g_Y == Y && t.g_Ns == Ns && t.g_ld == ld && t.g_gen == t.gen;
   if (!same) {
     if (t.gexec) {
       DG_CUDA(cudaStreamSynchronize(s));
@@ -778,6 +793,7 @@ dgchefsi_status filter_tc_graph(dgchefsi_ctx* ctx, int prec, const double* X, do
       return set_error(DGCHEFSI_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e4));
     }
     t.g_mode = mode;
+    t.g_gen = t.gen;
     t.g_m = m;
     t.g_G = G;
     t.g_T = T;

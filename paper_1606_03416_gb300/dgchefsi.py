@@ -217,7 +217,7 @@ class Context:
 
     def filter_graph(self, X: torch.Tensor, m: int, a: float, b: float, a0: float, prec: str = "bf16x3",
                      Y: torch.Tensor | None = None) -> torch.Tensor:
-        """The tensor-core filter replayed from a CUDA graph (captured on first use)."""
+        """The filter replayed from a CUDA graph (captured on first use); any precision."""
         Ns, ld = _block(X, self.N, "X")
         if Y is None:
             Y = torch.empty_like(X)

@@ -147,10 +147,33 @@ def test_graph_filter_equals_direct_filter(prec):
             assert torch.equal(Yd, Yg), shift
         ref = O.chebyshev_filter(Ho, X0.T, 7, lam[Ns], lam[-1] + 0.5, lam[0] - 0.5).T
         assert np.linalg.norm(Yg.cpu().numpy() - ref) <= 14 * U_OP[prec] * np.linalg.norm(ref)
+    with D.Context(H) as ctx:  # the FP64 graph replays the FP64 steps bit for bit
+        Yg = torch.empty_like(X)
+        for shift in (0.5, 1.5):
+            a0, b, a = lam[0] - shift, lam[-1] + shift, lam[Ns]
+            Yd = ctx.filter(X, 6, a, b, a0, prec="f64")
+            ctx.filter_graph(X, 6, a, b, a0, prec="f64", Y=Yg)
+            torch.cuda.synchronize()
+            assert torch.equal(Yd, Yg), shift
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "f64"])
+def test_graph_recaptured_after_buffers_move(prec):
+    """A direct call with more states regrows the library's iterate buffers
+    between two graph calls of the same shape; the second graph call must
+    capture again (not replay a graph that refers to freed memory) and still
+    give the direct result."""
+    H, Ho, X0, _, Ns, _, lam = problem(problems()[1])
+    a0, b, a = lam[0] - 0.5, lam[-1] + 0.5, lam[Ns]
+    X = torch.from_numpy(X0[:100]).to(torch.device("cuda:0"))
+    Xbig = torch.from_numpy(X0).to(torch.device("cuda:0"))
     with D.Context(H) as ctx:
-        with pytest.raises(D.DGChefsiError) as e:
-            ctx.filter_graph(X, 3, 1.0, 2.0, 0.0, prec="f64")
-        assert e.value.status == "ERR_UNSUPPORTED"
+        Yg = torch.empty_like(X)
+        ctx.filter_graph(X, 5, a, b, a0, prec=prec, Y=Yg)
+        ctx.filter(Xbig, 5, a, b, a0, prec=prec)          # regrows the workspace / iterates
+        ctx.filter_graph(X, 5, a, b, a0, prec=prec, Y=Yg)
+        torch.cuda.synchronize()
+        assert torch.equal(Yg, ctx.filter(X, 5, a, b, a0, prec=prec))
 
 
 def edge_problems():

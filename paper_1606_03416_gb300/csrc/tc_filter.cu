@@ -209,6 +209,8 @@ struct Plan {
   int32_t* grp_elem_d = nullptr;
   int32_t* sched_d = nullptr;
   int32_t* sched_ptr_d = nullptr;
+  uint8_t* nsub_d = nullptr;    // 64-byte ring slots per slice entry (1 or 2)
+  int32_t* gslots_d = nullptr;  // 64-byte ring slots per element group
 };
 
 struct TcState {
@@ -261,6 +263,8 @@ static void free_plan(Plan& pl) {
   cudaFree(pl.grp_elem_d);
   cudaFree(pl.sched_d);
   cudaFree(pl.sched_ptr_d);
+  cudaFree(pl.nsub_d);
+  cudaFree(pl.gslots_d);
   pl = Plan();
 }
 
@@ -337,7 +341,8 @@ static dgchefsi_status get_plan(dgchefsi_ctx* ctx, TcState& t, int G, Plan** out
   pl.ngroups = (M + G - 1) / G;
   std::vector<int32_t> grp((size_t)pl.ngroups * G, -1);
   for (int K = 0; K < M; ++K) grp[K] = K;  // group eg holds elements eg*G .. eg*G+G-1
-  std::vector<int32_t> sched, sptr(pl.ngroups + 1, 0);
+  std::vector<int32_t> sched, sptr(pl.ngroups + 1, 0), gslots(pl.ngroups, 0);
+  std::vector<uint8_t> nsub;
   for (int eg = 0; eg < pl.ngroups; ++eg) {
     std::vector<int> nbrs;
     for (int g = 0; g < G; ++g) {
@@ -351,6 +356,11 @@ static dgchefsi_status get_plan(dgchefsi_ctx* ctx, TcState& t, int G, Plan** out
       const int nsl = (t.pnb_h[Kp] + W - 1) / W;
       for (int sl = 0; sl < nsl; ++sl) {
         sched.push_back(t.poff_h[Kp] + sl * W);
+        // with 64-byte slots a slice is two halves of W/2 columns; the second
+        // is skipped when it lies past K''s padded size (H is zero there)
+        const uint8_t ns = (t.pnb_h[Kp] - sl * W) <= W / 2 ? 1 : 2;
+        nsub.push_back(ns);
+        gslots[eg] += ns;
         for (int g = 0; g < G; ++g) {
           const int K = grp[(size_t)eg * G + g];
           // a zero tile (one of ZERO_TILES, spread over L2) when K does not couple to K'
@@ -380,6 +390,10 @@ static dgchefsi_status get_plan(dgchefsi_ctx* ctx, TcState& t, int G, Plan** out
   DG_CUDA(cudaMemcpy(pl.grp_elem_d, grp.data(), sizeof(int32_t) * grp.size(), cudaMemcpyHostToDevice));
   DG_CUDA(cudaMemcpy(pl.sched_d, sched.data(), sizeof(int32_t) * sched.size(), cudaMemcpyHostToDevice));
   DG_CUDA(cudaMemcpy(pl.sched_ptr_d, sptr.data(), sizeof(int32_t) * sptr.size(), cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMalloc(&pl.nsub_d, std::max<size_t>(nsub.size(), 1)));
+  DG_CUDA(cudaMalloc(&pl.gslots_d, sizeof(int32_t) * std::max<size_t>(gslots.size(), 1)));
+  if (!nsub.empty()) DG_CUDA(cudaMemcpy(pl.nsub_d, nsub.data(), nsub.size(), cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMemcpy(pl.gslots_d, gslots.data(), sizeof(int32_t) * gslots.size(), cudaMemcpyHostToDevice));
   t.plans[G] = pl;
   *out = &t.plans[G];
   return DGCHEFSI_OK;
@@ -500,6 +514,8 @@ static dgchefsi_status prepare_launch(dgchefsi_ctx* ctx, TcState& t, int mode, i
   p = Params{};
   p.sched = pl->sched_d;
   p.sched_ptr = pl->sched_ptr_d;
+  p.nsub = pl->nsub_d;
+  p.gslots = pl->gslots_d;
   p.grp_elem = pl->grp_elem_d;
   p.nb = ctx->nb_d;
   p.pnb = t.pnb_d;

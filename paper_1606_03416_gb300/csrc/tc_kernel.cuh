@@ -84,6 +84,11 @@ struct Params {
   int ngroups, ntg;
   int maxent;  // most slice entries of any element group (shared-memory copy size)
   int* err;
+  // 64-byte ring slots only: ring slots of each slice entry (1 when the slice's
+  // second half lies past its element's padded size, so its H columns are all
+  // zero) and of each element group
+  const uint8_t* nsub;
+  const int32_t* gslots;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -590,8 +595,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (lane == 0 && ok) {
         for (int e = 0; e < ne && ok; ++e) {
           const int32_t* ent = sched_sh0 + e * (1 + G);
-#pragma unroll
-          for (int sub = 0; sub < NSUB; ++sub) {
+          const int nsub = NSUB == 1 ? 1 : (int)p.nsub[e0 + e];
+          for (int sub = 0; sub < nsub; ++sub) {
             const int st = c & (S - 1);
             const uint32_t ph = (uint32_t)(c / S) & 1u;
             if (!mbar_wait(empty0 + 8 * st, ph ^ 1u)) {
@@ -643,7 +648,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(buf * NS);
         uint32_t first = 0;
-        for (int e = 0; e < ne * NSUB && ok; ++e) {  // one iteration per ring slot
+        const int nslots = NSUB == 1 ? ne : p.gslots[eg];
+        for (int e = 0; e < nslots && ok; ++e) {  // one iteration per ring slot
           const int st = c & (S - 1);
           const uint32_t ph = (uint32_t)(c / S) & 1u;
           if (!mbar_wait(full0 + 8 * st, ph)) {

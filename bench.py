@@ -220,8 +220,8 @@ def run_filter_only(args):
     from paper_1606_03416_gb300 import dgchefsi as D
     from paper_1606_03416_gb300 import inputs as G
     base = G.CONFIGS[args.workload]
-    cfg = G.scaled_copy(base, Ns=args.ns or base.Ns, m=args.m or base.m, name=base.name)
-    H = G.make_blocks(cfg)
+    H = G.make_blocks(base)
+    cfg = G.scaled_copy(base, Ns=args.ns or G.resolve_sizes(base, H)[0], m=args.m or base.m, name=base.name)
     dev = torch.device("cuda:0")
     X = torch.from_numpy(G.make_X(H.N, cfg.Ns, cfg.seed)).to(dev)
     Y = torch.empty_like(X)

@@ -591,11 +591,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int e0 = p.sched_ptr[eg], ne = p.sched_ptr[eg + 1] - e0;
       __syncwarp();
       for (int z = lane; z < ne * (1 + G); z += 32) sched_sh0[z] = p.sched[(int64_t)e0 * (1 + G) + z];
+      if constexpr (NSUB > 1)  // ring slots per entry, staged beside the schedule
+        for (int z = lane; z < ne; z += 32) sched_sh1[z] = p.nsub[e0 + z];
       __syncwarp();
       if (lane == 0 && ok) {
         for (int e = 0; e < ne && ok; ++e) {
           const int32_t* ent = sched_sh0 + e * (1 + G);
-          const int nsub = NSUB == 1 ? 1 : (int)p.nsub[e0 + e];
+          const int nsub = NSUB == 1 ? 1 : sched_sh1[e];
           for (int sub = 0; sub < nsub; ++sub) {
             const int st = c & (S - 1);
             const uint32_t ph = (uint32_t)(c / S) & 1u;

@@ -160,9 +160,10 @@ def dist_env():
     return rank_info()
 
 
-def oracle_sample(Ns_sample: int, m: int, reps: int = 1):
+def oracle_sample(Ns_sample: int, m: int, reps: int = 1, threads: int = 1):
     """Time the FP64 oracle's filter on the first Ns_sample states (run in a
-    child process pinned to one BLAS thread so the core count is exact)."""
+    child process with the BLAS thread count fixed, so the core count is
+    exact)."""
     code = (
         "import os,sys,time,json\n"
         f"sys.path.insert(0,{ROOT!r})\n"
@@ -180,7 +181,8 @@ def oracle_sample(Ns_sample: int, m: int, reps: int = 1):
         f"    O.chebyshev_filter(Ho,X,{m},a,lam_hi,lam_lo)\n"
         "    ts.append(time.perf_counter()-t)\n"
         "print(json.dumps({'t':ts,'nnz':int(H.values.shape[0])}))\n")
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    nt = str(int(threads))
+    env = dict(os.environ, OMP_NUM_THREADS=nt, OPENBLAS_NUM_THREADS=nt, MKL_NUM_THREADS=nt)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
@@ -853,6 +855,13 @@ def main():
         line["cpu_baseline"] = {"value": cv, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
                                 "sample": f"FP64 NumPy oracle filter (m={m}) on {args.ref_states} of {Ns} states, "
                                           f"one BLAS thread, {ts[0]:.1f} s"}
+        ncpu = os.cpu_count() or 1
+        ns_all = 4 * args.ref_states
+        ts_all, _ = oracle_sample(ns_all, m, reps=1, threads=ncpu)
+        line["cpu_baseline_all_cores"] = {
+            "value": 2.0 * nnz * ns_all * m / ts_all[0] / 1e12, "unit": "TFLOP/s", "cores": ncpu, "kind": "oracle",
+            "sample": f"FP64 NumPy oracle filter (m={m}) on {ns_all} of {Ns} states, {ncpu} BLAS threads, "
+                      f"{ts_all[0]:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

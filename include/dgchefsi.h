@@ -143,6 +143,19 @@ dgchefsi_status dgchefsi_bounds_static(dgchefsi_ctx* ctx, const double* v0, int 
 dgchefsi_status dgchefsi_filter(dgchefsi_ctx* ctx, int prec, const double* X, double* Y,
                                 int64_t Ns, int64_t ld, int m, double a, double b, double a0);
 
+/* The filter of dgchefsi_filter on HOST buffers: X and Y are host (Ns x ld)
+ * row-major arrays (page-locked memory, e.g. cudaHostAlloc or torch's
+ * pin_memory, lets the copies overlap; pageable memory works, serialised).
+ * The states are filtered in chunks of `chunk` rows (0 = about Ns/4, a
+ * multiple of 256): while chunk k is filtered on the context's stream, chunk
+ * k+1 is copied in and chunk k-1 copied out on two library streams, through
+ * two pairs of device buffers the context owns (2 x 2 x chunk x N doubles).
+ * Each state is filtered independently of the others, so the result equals
+ * dgchefsi_filter's bit for bit. Synchronises; on error every copy in flight
+ * has finished before the call returns. */
+dgchefsi_status dgchefsi_filter_host(dgchefsi_ctx* ctx, int prec, const double* X, double* Y, int64_t Ns,
+                                     int64_t ld, int m, double a, double b, double a0, int64_t chunk);
+
 /* The filter of dgchefsi_filter (same arguments and results, bit for bit),
  * replayed from a CUDA graph: the first call for a given (prec, X, Y, Ns, ld,
  * m) tunes the unit shape if needed, captures the whole launch sequence and

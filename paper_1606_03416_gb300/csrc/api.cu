@@ -524,6 +524,15 @@ void dgchefsi_destroy(dgchefsi_ctx* ctx) {
   free_buf(ctx->ws_lanczos);
   free_buf(ctx->ws_adjoint);
   free_buf(ctx->ws_realign);
+  for (int i = 0; i < 2; ++i) {
+    free_buf(ctx->ws_hin[i]);
+    free_buf(ctx->ws_hout[i]);
+    if (ctx->ev_in[i]) cudaEventDestroy(ctx->ev_in[i]);
+    if (ctx->ev_f[i]) cudaEventDestroy(ctx->ev_f[i]);
+    if (ctx->ev_out[i]) cudaEventDestroy(ctx->ev_out[i]);
+  }
+  if (ctx->h_in) cudaStreamDestroy(ctx->h_in);
+  if (ctx->h_out) cudaStreamDestroy(ctx->h_out);
   if (ctx->f64_gexec) cudaGraphExecDestroy(ctx->f64_gexec);
   if (ctx->f64_cap) cudaStreamDestroy(ctx->f64_cap);
   cudaFree(ctx->f64_coef_d);
@@ -594,6 +603,83 @@ dgchefsi_status dgchefsi_filter_graph(dgchefsi_ctx* ctx, int prec, const double*
   if (Ns == 0) return DGCHEFSI_OK;
   if (prec == DGCHEFSI_F64) return filter_f64_graph(ctx, X, Y, Ns, ld, m, a, b, a0);
   return filter_tc_graph(ctx, prec, X, Y, Ns, ld, m, a, b, a0);
+}
+
+// Host-buffer filter: chunks of states pipelined over three streams (upload
+// of chunk k+1 and download of chunk k-1 overlap the filter of chunk k).
+static dgchefsi_status filter_host_impl(dgchefsi_ctx* ctx, int prec, const double* X, double* Y, int64_t Ns,
+                                        int64_t ld, int m, double a, double b, double a0, int64_t chunk) {
+  const int64_t N = ctx->N;
+  cudaStream_t s = ctx->stream;
+  if (!ctx->h_in) DG_CUDA(cudaStreamCreateWithFlags(&ctx->h_in, cudaStreamNonBlocking));
+  if (!ctx->h_out) DG_CUDA(cudaStreamCreateWithFlags(&ctx->h_out, cudaStreamNonBlocking));
+  for (int i = 0; i < 2; ++i) {
+    if (!ctx->ev_in[i]) DG_CUDA(cudaEventCreateWithFlags(&ctx->ev_in[i], cudaEventDisableTiming));
+    if (!ctx->ev_f[i]) DG_CUDA(cudaEventCreateWithFlags(&ctx->ev_f[i], cudaEventDisableTiming));
+    if (!ctx->ev_out[i]) DG_CUDA(cudaEventCreateWithFlags(&ctx->ev_out[i], cudaEventDisableTiming));
+  }
+  // nothing of an earlier call may still use the chunk buffers or events
+  DG_CUDA(cudaStreamSynchronize(ctx->h_in));
+  DG_CUDA(cudaStreamSynchronize(ctx->h_out));
+  const size_t cb = sizeof(double) * (size_t)chunk * (size_t)N;
+  for (int i = 0; i < 2; ++i) {
+    DG_TRY(ensure(ctx, ctx->ws_hin[i], cb, "host-filter input chunk"));
+    DG_TRY(ensure(ctx, ctx->ws_hout[i], cb, "host-filter output chunk"));
+  }
+  const int64_t nch = (Ns + chunk - 1) / chunk;
+  auto rows = [&](int64_t k) { return std::min(chunk, Ns - k * chunk); };
+  auto upload = [&](int64_t k) -> dgchefsi_status {
+    const int i = (int)(k & 1);
+    if (k >= 2) DG_CUDA(cudaStreamWaitEvent(ctx->h_in, ctx->ev_f[i], 0));  // filter k-2 done with it
+    DG_CUDA(cudaMemcpy2DAsync(ctx->ws_hin[i].p, sizeof(double) * N, X + k * chunk * ld, sizeof(double) * ld,
+                              sizeof(double) * N, rows(k), cudaMemcpyHostToDevice, ctx->h_in));
+    DG_CUDA(cudaEventRecord(ctx->ev_in[i], ctx->h_in));
+    return DGCHEFSI_OK;
+  };
+  dgchefsi_status st = upload(0);
+  for (int64_t k = 0; k < nch && st == DGCHEFSI_OK; ++k) {
+    const int i = (int)(k & 1);
+    if (k + 1 < nch) st = upload(k + 1);
+    if (st != DGCHEFSI_OK) break;
+    cudaError_t e = cudaStreamWaitEvent(s, ctx->ev_in[i], 0);
+    if (e == cudaSuccess && k >= 2) e = cudaStreamWaitEvent(s, ctx->ev_out[i], 0);  // download k-2 done
+    if (e != cudaSuccess) {
+      st = set_error(DGCHEFSI_ERR_CUDA, "stream wait failed: %s", cudaGetErrorString(e));
+      break;
+    }
+    const double* xi = static_cast<const double*>(ctx->ws_hin[i].p);
+    double* yo = static_cast<double*>(ctx->ws_hout[i].p);
+    st = prec == DGCHEFSI_F64 ? filter_f64(ctx, xi, yo, rows(k), N, m, a, b, a0)
+                              : filter_tc(ctx, prec, xi, yo, rows(k), N, m, a, b, a0);
+    if (st != DGCHEFSI_OK) break;
+    e = cudaEventRecord(ctx->ev_f[i], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->h_out, ctx->ev_f[i], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(Y + k * chunk * ld, sizeof(double) * ld, yo, sizeof(double) * N, sizeof(double) * N,
+                            rows(k), cudaMemcpyDeviceToHost, ctx->h_out);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_out[i], ctx->h_out);
+    if (e != cudaSuccess) st = set_error(DGCHEFSI_ERR_CUDA, "chunk download failed: %s", cudaGetErrorString(e));
+  }
+  // drain all three streams whatever happened, so no copy is left in flight
+  cudaError_t e1 = cudaStreamSynchronize(ctx->h_in);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  cudaError_t e3 = cudaStreamSynchronize(ctx->h_out);
+  if (st != DGCHEFSI_OK) return st;
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+    return set_error(DGCHEFSI_ERR_CUDA, "host-filter pipeline failed: %s",
+                     cudaGetErrorString(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3)));
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status dgchefsi_filter_host(dgchefsi_ctx* ctx, int prec, const double* X, double* Y, int64_t Ns,
+                                     int64_t ld, int m, double a, double b, double a0, int64_t chunk) {
+  clear_error();
+  DG_TRY(check_filter_args(ctx, prec, X, Y, Ns, ld, m, a, b, a0));
+  if (chunk < 0) return set_error(DGCHEFSI_ERR_ARG, "chunk < 0");
+  if (Ns == 0) return DGCHEFSI_OK;
+  if (chunk == 0) chunk = std::max<int64_t>(256, (Ns / 4 + 255) / 256 * 256);
+  if (chunk > Ns) chunk = Ns;
+  return filter_host_impl(ctx, prec, X, Y, Ns, ld, m, a, b, a0, chunk);
 }
 
 dgchefsi_status dgchefsi_set_orthonormalisation(dgchefsi_ctx* ctx, int mode) {

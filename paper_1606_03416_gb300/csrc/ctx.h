@@ -64,6 +64,10 @@ struct dgchefsi_ctx {
   void* f64_Y = nullptr;
   void* f64_T = nullptr;
   int64_t f64_Ns = 0, f64_ld = 0;
+  // host-buffer filter: double-buffered device chunks, copy streams, events
+  dg::DevBuf ws_hin[2], ws_hout[2];
+  cudaStream_t h_in = nullptr, h_out = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_f[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
   std::vector<char> solver_host;
   int* info_d = nullptr;  // [4] cuSOLVER infos + finite flag
   cusolverDnHandle_t solver = nullptr;

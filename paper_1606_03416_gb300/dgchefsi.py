@@ -30,7 +30,7 @@ EXPORTS = ["dgchefsi_create", "dgchefsi_destroy", "dgchefsi_set_stream", "dgchef
            "dgchefsi_bounds_static", "dgchefsi_gram", "dgchefsi_set_values", "dgchefsi_energy_grad",
            "dgchefsi_filter_graph", "dgchefsi_set_tile_shape", "dgchefsi_get_tile_shape",
            "dgchefsi_selftest_wait", "dgchefsi_set_orthonormalisation", "dgchefsi_density_pattern",
-           "dgchefsi_realign"]
+           "dgchefsi_realign", "dgchefsi_filter_host"]
 
 # Orthonormalisations of Alg. 1 step 3 (dgchefsi_set_orthonormalisation).
 ORTHONORMALISATIONS = {"cholqr": 0, "cholqr2": 1, "shifted_cholqr3": 2}
@@ -69,6 +69,7 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_set_orthonormalisation": (st, [P, C.c_int]),
         "dgchefsi_density_pattern": (st, [P, P, I64, I64, P, P]),
         "dgchefsi_realign": (st, [P, P, P, P, P, P, I64, I64, P, I64]),
+        "dgchefsi_filter_host": (st, [P, C.c_int, P, P, I64, I64, C.c_int, D, D, D, I64]),
         "dgchefsi_set_values": (st, [P, P]),
         "dgchefsi_energy_grad": (st, [P, C.c_int, P, I64, I64, C.c_int, D, D, D, D, D, C.c_int, P, P, P, P]),
         "dgchefsi_occupations": (st, [P, P, I64, D, D, P, P]),
@@ -214,6 +215,26 @@ class Context:
         self._sync_stream()
         _check(_lib.dgchefsi_gram(self._h, _ptr(Y), Ns, ld, _ptr(S)))
         return S
+
+    def filter_host(self, X: torch.Tensor, m: int, a: float, b: float, a0: float, prec: str = "bf16x3",
+                    Y: torch.Tensor | None = None, chunk: int = 0) -> torch.Tensor:
+        """The filter on host (CPU) float64 blocks, (N_s, N) with unit column
+        stride; copies in, filters and copies out in overlapping chunks. Pinned
+        tensors (``pin_memory()``) let the copies overlap the filter."""
+        if not (isinstance(X, torch.Tensor) and X.device.type == "cpu" and X.dtype == torch.float64 and X.dim() == 2):
+            raise TypeError("X must be a 2-D float64 CPU tensor (N_s, N)")
+        if X.shape[1] != self.N or (X.shape[0] > 0 and X.stride(1) != 1):
+            raise ValueError(f"X must have shape (N_s, {self.N}) with unit column stride")
+        ld = max(X.stride(0) if X.shape[0] > 1 else self.N, self.N)
+        if Y is None:
+            Y = torch.empty(X.shape, dtype=torch.float64, pin_memory=X.is_pinned())
+        if Y.device.type != "cpu" or Y.dtype != torch.float64 or Y.shape != X.shape or \
+                (Y.shape[0] > 1 and Y.stride(0) != ld) or (Y.shape[0] > 0 and Y.stride(1) != 1):
+            raise ValueError("Y must be a CPU float64 tensor laid out like X")
+        self._sync_stream()
+        _check(_lib.dgchefsi_filter_host(self._h, PRECISIONS[prec], _ptr(X), _ptr(Y), X.shape[0], ld, int(m),
+                                         float(a), float(b), float(a0), int(chunk)))
+        return Y
 
     def filter_graph(self, X: torch.Tensor, m: int, a: float, b: float, a0: float, prec: str = "bf16x3",
                      Y: torch.Tensor | None = None) -> torch.Tensor:

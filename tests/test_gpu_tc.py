@@ -208,3 +208,27 @@ def test_edge_shapes_filter_and_rayleigh_ritz(cfg):
     Yh, _, _ = O.cholesky_qr(ref.T)
     _, Do, _ = O.rayleigh_ritz(Ho, Yh)
     assert np.max(np.abs(ritz - Do)) <= 1e-10 * max(abs(a0), abs(b))
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32", "f64"])
+def test_filter_host_equals_device_filter(prec):
+    """dgchefsi_filter_host pipelines chunks of states between host and device;
+    each state is filtered independently, so every chunking gives the device
+    filter's result bit for bit, for pinned, strided and pageable host blocks."""
+    H, Ho, X0, _, Ns, _, lam = problem(problems()[1])   # N_s = 300: ragged last chunk
+    a0, b, a = lam[0] - 0.5, lam[-1] + 0.5, lam[Ns]
+    dev = torch.device("cuda:0")
+    with D.Context(H) as ctx:
+        ref = ctx.filter(torch.from_numpy(X0).to(dev), 6, a, b, a0, prec=prec).cpu()
+        Xh = torch.from_numpy(X0).pin_memory()
+        for chunk in (0, 100, 1000):
+            Yh = ctx.filter_host(Xh, 6, a, b, a0, prec=prec, chunk=chunk)
+            assert torch.equal(Yh, ref), chunk
+        big = torch.full((Ns, Ho.N + 9), 2.0, dtype=torch.float64).pin_memory()
+        big[:, :Ho.N] = torch.from_numpy(X0)
+        out = torch.full((Ns, Ho.N + 9), -1.0, dtype=torch.float64).pin_memory()
+        ctx.filter_host(big[:, :Ho.N], 6, a, b, a0, prec=prec, Y=out[:, :Ho.N], chunk=128)
+        assert torch.equal(out[:, :Ho.N], ref)
+        assert torch.all(out[:, Ho.N:] == -1.0)
+        Yp = ctx.filter_host(torch.from_numpy(X0.copy()), 6, a, b, a0, prec=prec)   # pageable
+        assert torch.equal(Yp, ref)

@@ -138,9 +138,14 @@ extern "C" dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, con
                               cudaMemcpyDeviceToDevice, s));
     return DGCHEFSI_OK;
   };
-  if (tc) {
+  if (tc && want_grad) {
     // tensor-core filter; FP32 checkpoints are kept inside the filter state
     DG_TRY(tc_grad_forward(ctx, prec, X, ld, Ns, m, a, b, a0, stride, Yt));
+  } else if (tc) {
+    // energy only: the ordinary tensor-core filter (same kernel, no checkpoints)
+    // on a compact copy of X
+    DG_TRY(copy_blk(T0, N, X, ld));
+    DG_TRY(filter_tc(ctx, prec, T0, Yt, Ns, N, m, a, b, a0));
   } else {
     // Y_0 = X (caller layout ld); iterates in T0/T1/T2 rotation (ld = N)
     double* rot[3] = {T0, T1, T2};

@@ -156,6 +156,8 @@ def test_tensor_core_grad_independent_of_checkpoint_stride(prec):
     X = torch.from_numpy(X0).to(dev)
     with D.Context(H) as ctx:
         ref = ctx.energy_grad(X, cfg.m, a, b, a0, Ne, cfg.kT, stride=1, prec=prec)
+        # the energy-only call (no checkpoints) runs the same filter kernel
+        assert ctx.energy_grad(X, cfg.m, a, b, a0, Ne, cfg.kT, grad=False, prec=prec)[0] == ref[0]
         for s in (2, 3, 0, cfg.m):
             out = ctx.energy_grad(X, cfg.m, a, b, a0, Ne, cfg.kT, stride=s, prec=prec)
             assert out[0] == ref[0]

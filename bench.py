@@ -793,8 +793,8 @@ def main():
     e2e = {"value": world * fl / min(host_s) / 1e12, "unit": "TFLOP/s",
            "h2d_bytes_per_step": int(Xh.numel() * 8), "d2h_bytes_per_step": int(Yh.numel() * 8),
            "ms": 1e3 * min(host_s), "serial_copies_tflops": serial,
-           "what": "dgchefsi_filter_host on pinned host blocks (copies overlapped with the filter in chunks of "
-                   "~N_s/4 states), host wall clock around the synchronous call; serial_copies_tflops: copy in, "
+           "what": "dgchefsi_filter_host on pinned host blocks (copies overlapped with the filter in five "
+                   "chunks, small first and last), host wall clock around the synchronous call; serial_copies_tflops: copy in, "
                    "filter, copy out one after the other"}
 
     # ---- FP64 cycle for the per-cycle comparison, and precision of the mixed cycle

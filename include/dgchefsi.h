@@ -146,8 +146,11 @@ dgchefsi_status dgchefsi_filter(dgchefsi_ctx* ctx, int prec, const double* X, do
 /* The filter of dgchefsi_filter on HOST buffers: X and Y are host (Ns x ld)
  * row-major arrays (page-locked memory, e.g. cudaHostAlloc or torch's
  * pin_memory, lets the copies overlap; pageable memory works, serialised).
- * The states are filtered in chunks of `chunk` rows (0 = about Ns/4, a
- * multiple of 256): while chunk k is filtered on the context's stream, chunk
+ * The states are filtered in chunks of `chunk` rows (0 = the library's split:
+ * for Ns >= 2048 a first and a last chunk of ~Ns/16 and three chunks of
+ * 256-state multiples between them, else chunks of ~Ns/4; the first upload
+ * and the last download are the only copies not overlapped, so they are kept
+ * small): while chunk k is filtered on the context's stream, chunk
  * k+1 is copied in and chunk k-1 copied out on two library streams, through
  * two pairs of device buffers the context owns (2 x 2 x chunk x N doubles).
  * Each state is filtered independently of the others, so the result equals

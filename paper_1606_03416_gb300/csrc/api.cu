@@ -608,7 +608,11 @@ dgchefsi_status dgchefsi_filter_graph(dgchefsi_ctx* ctx, int prec, const double*
 // Host-buffer filter: chunks of states pipelined over three streams (upload
 // of chunk k+1 and download of chunk k-1 overlap the filter of chunk k).
 static dgchefsi_status filter_host_impl(dgchefsi_ctx* ctx, int prec, const double* X, double* Y, int64_t Ns,
-                                        int64_t ld, int m, double a, double b, double a0, int64_t chunk) {
+                                        int64_t ld, int m, double a, double b, double a0,
+                                        const std::vector<int64_t>& start) {
+  // chunk k holds states start[k] .. start[k+1]-1
+  int64_t chunk = 0;
+  for (size_t k = 0; k + 1 < start.size(); ++k) chunk = std::max(chunk, start[k + 1] - start[k]);
   const int64_t N = ctx->N;
   cudaStream_t s = ctx->stream;
   if (!ctx->h_in) DG_CUDA(cudaStreamCreateWithFlags(&ctx->h_in, cudaStreamNonBlocking));
@@ -626,12 +630,12 @@ static dgchefsi_status filter_host_impl(dgchefsi_ctx* ctx, int prec, const doubl
     DG_TRY(ensure(ctx, ctx->ws_hin[i], cb, "host-filter input chunk"));
     DG_TRY(ensure(ctx, ctx->ws_hout[i], cb, "host-filter output chunk"));
   }
-  const int64_t nch = (Ns + chunk - 1) / chunk;
-  auto rows = [&](int64_t k) { return std::min(chunk, Ns - k * chunk); };
+  const int64_t nch = (int64_t)start.size() - 1;
+  auto rows = [&](int64_t k) { return start[k + 1] - start[k]; };
   auto upload = [&](int64_t k) -> dgchefsi_status {
     const int i = (int)(k & 1);
     if (k >= 2) DG_CUDA(cudaStreamWaitEvent(ctx->h_in, ctx->ev_f[i], 0));  // filter k-2 done with it
-    DG_CUDA(cudaMemcpy2DAsync(ctx->ws_hin[i].p, sizeof(double) * N, X + k * chunk * ld, sizeof(double) * ld,
+    DG_CUDA(cudaMemcpy2DAsync(ctx->ws_hin[i].p, sizeof(double) * N, X + start[k] * ld, sizeof(double) * ld,
                               sizeof(double) * N, rows(k), cudaMemcpyHostToDevice, ctx->h_in));
     DG_CUDA(cudaEventRecord(ctx->ev_in[i], ctx->h_in));
     return DGCHEFSI_OK;
@@ -655,7 +659,7 @@ static dgchefsi_status filter_host_impl(dgchefsi_ctx* ctx, int prec, const doubl
     e = cudaEventRecord(ctx->ev_f[i], s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->h_out, ctx->ev_f[i], 0);
     if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(Y + k * chunk * ld, sizeof(double) * ld, yo, sizeof(double) * N, sizeof(double) * N,
+      e = cudaMemcpy2DAsync(Y + start[k] * ld, sizeof(double) * ld, yo, sizeof(double) * N, sizeof(double) * N,
                             rows(k), cudaMemcpyDeviceToHost, ctx->h_out);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_out[i], ctx->h_out);
     if (e != cudaSuccess) st = set_error(DGCHEFSI_ERR_CUDA, "chunk download failed: %s", cudaGetErrorString(e));
@@ -677,9 +681,26 @@ dgchefsi_status dgchefsi_filter_host(dgchefsi_ctx* ctx, int prec, const double* 
   DG_TRY(check_filter_args(ctx, prec, X, Y, Ns, ld, m, a, b, a0));
   if (chunk < 0) return set_error(DGCHEFSI_ERR_ARG, "chunk < 0");
   if (Ns == 0) return DGCHEFSI_OK;
-  if (chunk == 0) chunk = std::max<int64_t>(256, (Ns / 4 + 255) / 256 * 256);
-  if (chunk > Ns) chunk = Ns;
-  return filter_host_impl(ctx, prec, X, Y, Ns, ld, m, a, b, a0, chunk);
+  std::vector<int64_t> start{0};
+  if (chunk > 0) {
+    for (int64_t s0 = chunk; s0 < Ns; s0 += chunk) start.push_back(s0);
+  } else if (Ns >= 2048) {
+    // small first and last chunks (their copies are the only ones not
+    // overlapped), three equal chunks of 256-state multiples between
+    const int64_t edge = std::max<int64_t>(256, Ns / 16 / 256 * 256);
+    const int64_t span = Ns - 2 * edge;
+    start.push_back(edge);
+    for (int q = 1; q < 3; ++q) {
+      const int64_t b = edge + (q * span / 3 + 255) / 256 * 256;
+      if (b > start.back() && b < Ns - edge) start.push_back(b);
+    }
+    start.push_back(Ns - edge);
+  } else {
+    const int64_t c = std::max<int64_t>(256, (Ns / 4 + 255) / 256 * 256);
+    for (int64_t s0 = c; s0 < Ns; s0 += c) start.push_back(s0);
+  }
+  start.push_back(Ns);
+  return filter_host_impl(ctx, prec, X, Y, Ns, ld, m, a, b, a0, start);
 }
 
 dgchefsi_status dgchefsi_set_orthonormalisation(dgchefsi_ctx* ctx, int mode) {

@@ -715,23 +715,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const bool row_ok = go && K >= 0 && j < (K >= 0 ? p.nb[K] : 0);
       const int64_t col = (K >= 0 ? (int64_t)p.poff[K] : 0) + j;
       const uint32_t ta = tmem + (uint32_t)(buf * NS) + ((uint32_t)(32 * q) << 16);
+      const int64_t ldp = p.ldp;
+      const bool need_prev = row_ok && beta != 0.f;
 #pragma unroll 1
       for (int cc = 0; cc < NS / 32; ++cc) {
         const int c0 = 16 * (h + 2 * cc);
+        const int64_t sb = s0 + c0;
+        const int nz = (int)(p.Ns - sb < 16 ? p.Ns - sb : 16);  // states of this chunk inside N_s
+        const int64_t base = sb * ldp + col;                      // dereferenced only for z < nz
         float pr[16];
+        if (need_prev && nz == 16) {
 #pragma unroll
-        for (int z = 0; z < 16; ++z) {
-          const int64_t s = s0 + c0 + z;
-          pr[z] = (row_ok && beta != 0.f && s < p.Ns) ? p.Fprev[s * p.ldp + col] : 0.f;
+          for (int z = 0; z < 16; ++z) pr[z] = p.Fprev[base + z * ldp];
+        } else {
+#pragma unroll
+          for (int z = 0; z < 16; ++z) pr[z] = (need_prev && z < nz) ? p.Fprev[base + z * ldp] : 0.f;
         }
         float v[16];
         tmem_ld16(ta + (uint32_t)c0, v);
         if (row_ok) {
 #pragma unroll
           for (int z = 0; z < 16; ++z) {
-            const int64_t s = s0 + c0 + z;
-            if (s < p.Ns) {
-              const int64_t idx = s * p.ldp + col;
+            if (z < nz) {
+              const int64_t idx = base + z * ldp;
               const float y = alpha * v[z] - beta * pr[z];
               p.Fout[idx] = y;
               if constexpr (MODE_ != MODE_TF32) {

@@ -414,6 +414,9 @@ dgchefsi_status dgchefsi_create(int32_t M, const int32_t* nb, const int64_t* row
       ctx->max_nb = std::max(ctx->max_nb, nb[K]);
     }
     ctx->N = ctx->off_h[M];
+    ctx->f64_tj = 64;
+    for (int K = 0; K < M; ++K)
+      if (nb[K] % 64 != 0) ctx->f64_tj = 32;
     if (row_ptr[0] != 0) return bail(set_error(DGCHEFSI_ERR_ARG, "row_ptr[0] != 0"));
     for (int K = 0; K < M; ++K)
       if (row_ptr[K + 1] < row_ptr[K]) return bail(set_error(DGCHEFSI_ERR_ARG, "row_ptr decreases at %d", K));

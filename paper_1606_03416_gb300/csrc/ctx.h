@@ -52,6 +52,7 @@ struct dgchefsi_ctx {
   dg::DevBuf ws_adjoint;  // checkpoints and blocks of the band-energy gradient
   dg::DevBuf ws_realign;  // per-element tables and overlaps of the re-alignment
   int orth_mode = 0;      // DGCHEFSI_ORTH_*: orthonormalisation of step 3
+  int32_t f64_tj = 64;    // column tile of the FP64 filter (set at create)
   // FP64 filter as a CUDA graph: coefficients copied from a pinned mirror at
   // every replay; the graph is captured again when X, Y, N_s, ld, m or the
   // workspace it refers to change
@@ -84,6 +85,7 @@ struct dgchefsi_ctx {
     h.blk_off = blk_off_d;
     h.vals = vals_d;
     h.max_nb = max_nb;
+    h.tj = f64_tj;
     return h;
   }
 };

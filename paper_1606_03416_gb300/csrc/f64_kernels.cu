@@ -42,12 +42,16 @@ __device__ __forceinline__ void fma_tile(const double (&As)[BK][TP], const doubl
   }
 }
 
-// One Chebyshev step on a (64 states) x (64 rows of element K) tile:
+// One Chebyshev step on a (64 states) x (TJ rows of element K) tile:
 // out = alpha * (sum_{K'} H_KK' in_K' - c in_K) - beta * prev_K.
+// TJ = 64 when every element size is a multiple of 64, else 32, so uneven
+// elements leave fewer idle columns in their last tile.
+template <int TJ>
 __global__ void __launch_bounds__(NT) k_filter_step_f64(HView h, const double* __restrict__ in, int64_t ld,
                                                         const double* prev, double* out, int64_t ldo,
                                                         int64_t Ns, double alpha, double c, double beta,
                                                         const double* __restrict__ coef, int step) {
+  constexpr int JR = TJ / 16;  // output columns per thread
   if (coef) {  // coefficients in device memory ([c, alpha_0, beta_0, alpha_1, ...]; graph replays)
     c = coef[0];
     alpha = coef[1 + 2 * step];
@@ -55,17 +59,17 @@ __global__ void __launch_bounds__(NT) k_filter_step_f64(HView h, const double* _
   }
   const int K = blockIdx.y;
   const int nK = h.nb[K];
-  const int j0 = blockIdx.z * T;
+  const int j0 = blockIdx.z * TJ;
   if (j0 >= nK) return;
   const int64_t s0 = (int64_t)blockIdx.x * T;
   __shared__ double As[BK][TP];
-  __shared__ double Bs[BK][TP];
+  __shared__ double Bs[BK][TJ + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
+  double acc[4][JR];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < JR; ++j) acc[i][j] = 0.0;
   const int64_t offK = h.off[K];
   const int64_t e_end = h.row_ptr[K + 1];
   for (int64_t e = h.row_ptr[K]; e < e_end; ++e) {
@@ -79,14 +83,26 @@ __global__ void __launch_bounds__(NT) k_filter_step_f64(HView h, const double* _
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int r = (tid >> 4) + 16 * i;
-        double v = 0.0, w = 0.0;
-        if (kin && s0 + r < Ns) v = in[(s0 + r) * ld + offKp + k0 + kk];
-        if (kin && j0 + r < nK) w = blk[(int64_t)(j0 + r) * nKp + k0 + kk];
-        As[kk][r] = v;
-        Bs[kk][r] = w;
+        As[kk][r] = (kin && s0 + r < Ns) ? in[(s0 + r) * ld + offKp + k0 + kk] : 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < JR; ++i) {
+        const int r = (tid >> 4) + 16 * i;
+        Bs[kk][r] = (kin && j0 + r < nK) ? blk[(int64_t)(j0 + r) * nKp + k0 + kk] : 0.0;
       }
       __syncthreads();
-      fma_tile(As, Bs, acc, tx, ty);
+#pragma unroll
+      for (int q = 0; q < BK; ++q) {
+        double a[4], b[JR];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[q][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < JR; ++j) b[j] = Bs[q][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < JR; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
       __syncthreads();
     }
   }
@@ -95,7 +111,7 @@ __global__ void __launch_bounds__(NT) k_filter_step_f64(HView h, const double* _
     const int64_t s = s0 + ty + 16 * i;
     if (s >= Ns) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < JR; ++j) {
       const int jj = j0 + tx + 16 * j;
       if (jj >= nK) continue;
       const int64_t idx = s * ldo + offK + jj;
@@ -518,8 +534,12 @@ inline unsigned stream_grid(int64_t n) {
 cudaError_t filter_step_f64(const HView& h, const double* in, int64_t ld_in, const double* prev, double* out,
                             int64_t ld_out, int64_t Ns, double alpha, double c, double beta, cudaStream_t s) {
   if (Ns == 0) return cudaSuccess;
-  dim3 grid(cdiv(Ns, T), (unsigned)h.M, cdiv(h.max_nb, T));
-  k_filter_step_f64<<<grid, NT, 0, s>>>(h, in, ld_in, prev, out, ld_out, Ns, alpha, c, beta, nullptr, 0);
+  if (h.tj == 64)
+    k_filter_step_f64<64><<<dim3(cdiv(Ns, T), (unsigned)h.M, cdiv(h.max_nb, 64)), NT, 0, s>>>(
+        h, in, ld_in, prev, out, ld_out, Ns, alpha, c, beta, nullptr, 0);
+  else
+    k_filter_step_f64<32><<<dim3(cdiv(Ns, T), (unsigned)h.M, cdiv(h.max_nb, 32)), NT, 0, s>>>(
+        h, in, ld_in, prev, out, ld_out, Ns, alpha, c, beta, nullptr, 0);
   count_launch();
   return cudaGetLastError();
 }
@@ -527,8 +547,12 @@ cudaError_t filter_step_f64(const HView& h, const double* in, int64_t ld_in, con
 cudaError_t filter_step_f64_dev(const HView& h, const double* in, int64_t ld_in, const double* prev, double* out,
                                 int64_t ld_out, int64_t Ns, const double* coef, int step, cudaStream_t s) {
   if (Ns <= 0) return cudaSuccess;
-  dim3 grid(cdiv(Ns, T), (unsigned)h.M, cdiv(h.max_nb, T));
-  k_filter_step_f64<<<grid, NT, 0, s>>>(h, in, ld_in, prev, out, ld_out, Ns, 0.0, 0.0, 0.0, coef, step);
+  if (h.tj == 64)
+    k_filter_step_f64<64><<<dim3(cdiv(Ns, T), (unsigned)h.M, cdiv(h.max_nb, 64)), NT, 0, s>>>(
+        h, in, ld_in, prev, out, ld_out, Ns, 0.0, 0.0, 0.0, coef, step);
+  else
+    k_filter_step_f64<32><<<dim3(cdiv(Ns, T), (unsigned)h.M, cdiv(h.max_nb, 32)), NT, 0, s>>>(
+        h, in, ld_in, prev, out, ld_out, Ns, 0.0, 0.0, 0.0, coef, step);
   count_launch();
   return cudaGetLastError();
 }

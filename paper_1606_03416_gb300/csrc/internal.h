@@ -16,6 +16,7 @@ struct HView {
   const int64_t* blk_off;  // [nnzb] offsets into vals (doubles)
   const double* vals;
   int32_t max_nb;
+  int32_t tj = 64;  // FP64 filter: output columns per tile (64 if every n_K is a multiple of 64, else 32)
 };
 
 void count_launch(int n = 1);

@@ -657,7 +657,7 @@ static dgchefsi_status filter_host_impl(dgchefsi_ctx* ctx, int prec, const doubl
     const double* xi = static_cast<const double*>(ctx->ws_hin[i].p);
     double* yo = static_cast<double*>(ctx->ws_hout[i].p);
     st = prec == DGCHEFSI_F64 ? filter_f64(ctx, xi, yo, rows(k), N, m, a, b, a0)
-                              : filter_tc(ctx, prec, xi, yo, rows(k), N, m, a, b, a0);
+                              : filter_tc(ctx, prec, xi, yo, rows(k), N, m, a, b, a0, /*reuse_hop=*/k > 0);
     if (st != DGCHEFSI_OK) break;
     e = cudaEventRecord(ctx->ev_f[i], s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->h_out, ctx->ev_f[i], 0);

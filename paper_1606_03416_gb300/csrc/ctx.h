@@ -99,8 +99,11 @@ void clear_error();
 dgchefsi_status ensure(dgchefsi_ctx* ctx, DevBuf& b, size_t bytes, const char* what);
 
 // Tensor-core filter (tc_filter.cu). X, Y FP64 (Ns x ld) state-major.
+// reuse_hop: the operand copy of H - cI built by the previous call of this
+// precision with the same (a, b) is still valid (consecutive chunks of one
+// host-buffer call), so it is not rebuilt.
 dgchefsi_status filter_tc(dgchefsi_ctx* ctx, int prec, const double* X, double* Y, int64_t Ns, int64_t ld, int m,
-                          double a, double b, double a0);
+                          double a, double b, double a0, bool reuse_hop = false);
 // The same filter replayed from a CUDA graph captured for (prec, X, Y, Ns, ld, m).
 dgchefsi_status filter_tc_graph(dgchefsi_ctx* ctx, int prec, const double* X, double* Y, int64_t Ns, int64_t ld,
                                 int m, double a, double b, double a0);

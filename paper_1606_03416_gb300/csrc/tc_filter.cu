@@ -625,14 +625,17 @@ static dgchefsi_status upload_coefficients(dgchefsi_ctx* ctx, TcState& t, int m,
 
 // build_hop -> pack -> steps -> unpack, all on stream s (the coefficients must be on the device).
 static dgchefsi_status enqueue_filter(dgchefsi_ctx* ctx, TcState& t, int mode, Launch& L, const double* X,
-                                      double* Y, int64_t Ns, int64_t ld, int m, cudaStream_t s) {
+                                      double* Y, int64_t Ns, int64_t ld, int m, cudaStream_t s,
+                                      bool reuse_hop = false) {
   const bool f32 = mode == MODE_TF32;
   const int W = f32 ? 32 : 64;
-  k_build_hop<<<(unsigned)ctx->nnzb, 256, 0, s>>>(
-      t.blk_row_d, ctx->col_d, ctx->blk_off_d, ctx->vals_d, ctx->nb_d, t.pnb_d, t.brow_d, W, t.coef_d, mode, t.b_rows,
-      f32 ? static_cast<float*>(t.Hop.p) : nullptr, f32 ? nullptr : static_cast<__nv_bfloat16*>(t.Hop.p));
-  count_launch();
-  DG_CUDA(cudaGetLastError());
+  if (!reuse_hop) {
+    k_build_hop<<<(unsigned)ctx->nnzb, 256, 0, s>>>(
+        t.blk_row_d, ctx->col_d, ctx->blk_off_d, ctx->vals_d, ctx->nb_d, t.pnb_d, t.brow_d, W, t.coef_d, mode,
+        t.b_rows, f32 ? static_cast<float*>(t.Hop.p) : nullptr, f32 ? nullptr : static_cast<__nv_bfloat16*>(t.Hop.p));
+    count_launch();
+    DG_CUDA(cudaGetLastError());
+  }
   dim3 g((unsigned)std::min<int64_t>(Ns, 1024), (unsigned)ctx->M);
   k_pack<<<g, 128, 0, s>>>(X, ld, Ns, ctx->off_d, ctx->nb_d, t.poff_d, t.ldp, static_cast<float*>(t.F[0].p),
                            f32 ? nullptr : static_cast<__nv_bfloat16*>(t.Sh[0].p),
@@ -748,7 +751,7 @@ static dgchefsi_status tc_prepare(dgchefsi_ctx* ctx, int prec, int64_t Ns, int m
 }
 
 dgchefsi_status filter_tc(dgchefsi_ctx* ctx, int prec, const double* X, double* Y, int64_t Ns, int64_t ld, int m,
-                          double a, double b, double a0) {
+                          double a, double b, double a0, bool reuse_hop) {
   int mode = 0;
   DG_TRY(tc_prepare(ctx, prec, Ns, m, a, b, a0, &mode));
   TcState& t = *ctx->tc;
@@ -759,7 +762,7 @@ dgchefsi_status filter_tc(dgchefsi_ctx* ctx, int prec, const double* X, double* 
   DG_TRY(select_shape(ctx, t, mode, X, ld, Ns, &G, &T, &layout));
   Launch L;
   DG_TRY(prepare_launch(ctx, t, mode, G, T, layout, Ns, L));
-  DG_TRY(enqueue_filter(ctx, t, mode, L, X, Y, Ns, ld, m, s));
+  DG_TRY(enqueue_filter(ctx, t, mode, L, X, Y, Ns, ld, m, s, reuse_hop && t.shapeG[mode] + t.forceG[mode] > 0));
   return check_err(t, s);
 }
 

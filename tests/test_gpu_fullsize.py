@@ -96,3 +96,18 @@ def test_full_sheet_graph_filter_sampled_states():
         del X, Y
     check_rows(Ys, Ho, X0, rows, cfg.m, a, b, a0, 2 * cfg.m * U_OP["bf16x3"])
     _full.pop("sheet2d_24x20", None)
+
+
+def test_full_12cubed_filter_sampled_states():
+    """The differentiation workload (12^3 elements, n_b = 48: every slice only
+    partly filled) through the BF16x3 filter at full size."""
+    cfg, H, Ho, X0, v0, Ns, Ne = full("bulk3d_12x12x12")
+    rows = [0, 256, Ns // 2, Ns - 1]
+    with D.Context(H) as ctx:
+        a, b, a0 = first_cycle_bounds(ctx, v0, Ns, H.N)
+        X = torch.from_numpy(X0).cuda()
+        Y = ctx.filter(X, cfg.m, a, b, a0, prec="bf16x3")
+        Ys = Y[rows].cpu().numpy()
+        del X, Y
+    check_rows(Ys, Ho, X0, rows, cfg.m, a, b, a0, 2 * cfg.m * U_OP["bf16x3"])
+    _full.pop("bulk3d_12x12x12", None)

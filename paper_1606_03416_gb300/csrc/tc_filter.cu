@@ -11,7 +11,9 @@
 namespace dg {
 namespace {
 
-// X (FP64, natural layout, ld) -> FP32 master + BF16 hi / lo copies in the padded layout.
+// X (FP64, natural layout, ld) -> FP32 master + BF16 hi / lo copies in the
+// padded layout. Block (x, K) strides over the flattened (state, column)
+// pairs of element K, so every thread has work whatever n_K is.
 __global__ void k_pack(const double* __restrict__ X, int64_t ld, int64_t Ns, const int64_t* __restrict__ off,
                        const int32_t* __restrict__ nb, const int32_t* __restrict__ poff, int64_t ldp,
                        float* __restrict__ F, __nv_bfloat16* __restrict__ Hh, __nv_bfloat16* __restrict__ Hl) {
@@ -19,21 +21,22 @@ __global__ void k_pack(const double* __restrict__ X, int64_t ld, int64_t Ns, con
   const int n = nb[K];
   const int64_t o = off[K];
   const int po = poff[K];
-  for (int64_t s = blockIdx.x; s < Ns; s += gridDim.x) {
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const float v = (float)X[s * ld + o + j];
-      const int64_t q = s * ldp + po + j;
-      F[q] = v;
-      if (Hh) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        Hh[q] = h;
-        if (Hl) Hl[q] = __float2bfloat16_rn(v - __bfloat162float(h));
-      }
+  const int64_t total = Ns * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = t / n;
+    const int j = (int)(t - s * n);
+    const float v = (float)X[s * ld + o + j];
+    const int64_t q = s * ldp + po + j;
+    F[q] = v;
+    if (Hh) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      Hh[q] = h;
+      if (Hl) Hl[q] = __float2bfloat16_rn(v - __bfloat162float(h));
     }
   }
 }
 
-// FP32 padded layout -> FP64 natural layout.
+// FP32 padded layout -> FP64 natural layout (same flattened mapping).
 __global__ void k_unpack(const float* __restrict__ F, int64_t ldp, int64_t Ns, const int64_t* __restrict__ off,
                          const int32_t* __restrict__ nb, const int32_t* __restrict__ poff, double* __restrict__ Y,
                          int64_t ld) {
@@ -41,8 +44,19 @@ __global__ void k_unpack(const float* __restrict__ F, int64_t ldp, int64_t Ns, c
   const int n = nb[K];
   const int64_t o = off[K];
   const int po = poff[K];
-  for (int64_t s = blockIdx.x; s < Ns; s += gridDim.x)
-    for (int j = threadIdx.x; j < n; j += blockDim.x) Y[s * ld + o + j] = (double)F[s * ldp + po + j];
+  const int64_t total = Ns * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = t / n;
+    const int j = (int)(t - s * n);
+    Y[s * ld + o + j] = (double)F[s * ldp + po + j];
+  }
+}
+
+// Grid of k_pack / k_unpack: blocks of 256 threads per element, about four
+// (state, column) pairs per thread.
+static dim3 pack_grid(int64_t Ns, int max_nb, int M) {
+  const int64_t per = (Ns * (int64_t)max_nb + 1023) / 1024;
+  return dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(per, 65535)), (unsigned)M);
 }
 
 // Operand copy of (H - cI): for block e = (K, K') and slice sl of K', rows
@@ -636,14 +650,14 @@ static dgchefsi_status enqueue_filter(dgchefsi_ctx* ctx, TcState& t, int mode, L
     count_launch();
     DG_CUDA(cudaGetLastError());
   }
-  dim3 g((unsigned)std::min<int64_t>(Ns, 1024), (unsigned)ctx->M);
-  k_pack<<<g, 128, 0, s>>>(X, ld, Ns, ctx->off_d, ctx->nb_d, t.poff_d, t.ldp, static_cast<float*>(t.F[0].p),
+  const dim3 g = pack_grid(Ns, ctx->max_nb, ctx->M);
+  k_pack<<<g, 256, 0, s>>>(X, ld, Ns, ctx->off_d, ctx->nb_d, t.poff_d, t.ldp, static_cast<float*>(t.F[0].p),
                            f32 ? nullptr : static_cast<__nv_bfloat16*>(t.Sh[0].p),
                            mode == MODE_BF16X3 ? static_cast<__nv_bfloat16*>(t.Sl[0].p) : nullptr);
   count_launch();
   DG_CUDA(cudaGetLastError());
   for (int k = 0; k < m; ++k) DG_TRY(launch_step(ctx, t, mode, L, k, s));
-  k_unpack<<<g, 128, 0, s>>>(static_cast<float*>(t.F[m & 1].p), t.ldp, Ns, ctx->off_d, ctx->nb_d, t.poff_d, Y, ld);
+  k_unpack<<<g, 256, 0, s>>>(static_cast<float*>(t.F[m & 1].p), t.ldp, Ns, ctx->off_d, ctx->nb_d, t.poff_d, Y, ld);
   count_launch();
   DG_CUDA(cudaGetLastError());
   return DGCHEFSI_OK;
@@ -723,8 +737,8 @@ static dgchefsi_status select_shape(dgchefsi_ctx* ctx, TcState& t, int mode, con
         mode, t.b_rows, f32 ? static_cast<float*>(t.Hop.p) : nullptr,
         f32 ? nullptr : static_cast<__nv_bfloat16*>(t.Hop.p));
     count_launch();
-    dim3 g((unsigned)std::min<int64_t>(Ns, 1024), (unsigned)ctx->M);
-    k_pack<<<g, 128, 0, s>>>(X, ld, Ns, ctx->off_d, ctx->nb_d, t.poff_d, t.ldp, static_cast<float*>(t.F[0].p),
+    const dim3 g = pack_grid(Ns, ctx->max_nb, ctx->M);
+    k_pack<<<g, 256, 0, s>>>(X, ld, Ns, ctx->off_d, ctx->nb_d, t.poff_d, t.ldp, static_cast<float*>(t.F[0].p),
                              f32 ? nullptr : static_cast<__nv_bfloat16*>(t.Sh[0].p),
                              mode == MODE_BF16X3 ? static_cast<__nv_bfloat16*>(t.Sl[0].p) : nullptr);
     count_launch();
@@ -890,8 +904,8 @@ dgchefsi_status tc_grad_forward(dgchefsi_ctx* ctx, int prec, const double* X, in
       t.blk_row_d, ctx->col_d, ctx->blk_off_d, ctx->vals_d, ctx->nb_d, t.pnb_d, t.brow_d, W, t.coef_d, mode, t.b_rows,
       f32 ? static_cast<float*>(t.Hop.p) : nullptr, f32 ? nullptr : bf_ptr(t.Hop));
   count_launch();
-  dim3 g((unsigned)std::min<int64_t>(Ns, 1024), (unsigned)ctx->M);
-  k_pack<<<g, 128, 0, s>>>(X, ld, Ns, ctx->off_d, ctx->nb_d, t.poff_d, t.ldp, t.cp0[0], f32 ? nullptr : bf_ptr(t.Sh[0]),
+  const dim3 g = pack_grid(Ns, ctx->max_nb, ctx->M);
+  k_pack<<<g, 256, 0, s>>>(X, ld, Ns, ctx->off_d, ctx->nb_d, t.poff_d, t.ldp, t.cp0[0], f32 ? nullptr : bf_ptr(t.Sh[0]),
                            mode == MODE_BF16X3 ? bf_ptr(t.Sl[0]) : nullptr);
   count_launch();
   DG_CUDA(cudaGetLastError());
@@ -915,7 +929,7 @@ dgchefsi_status tc_grad_forward(dgchefsi_ctx* ctx, int prec, const double* X, in
     DG_TRY(launch_io(t, mode, L, k, t.coef_d, io, s));
     pos[kk] = out;
   }
-  k_unpack<<<g, 128, 0, s>>>(pos[m], t.ldp, Ns, ctx->off_d, ctx->nb_d, t.poff_d, Ym, ctx->N);
+  k_unpack<<<g, 256, 0, s>>>(pos[m], t.ldp, Ns, ctx->off_d, ctx->nb_d, t.poff_d, Ym, ctx->N);
   count_launch();
   DG_CUDA(cudaGetLastError());
   return check_err(t, s);
@@ -951,8 +965,8 @@ dgchefsi_status tc_grad_backward(dgchefsi_ctx* ctx, int prec, const double* Wm, 
   DG_CUDA(cudaMemsetAsync(t.err_d, 0, sizeof(int), s));
   Launch L;
   DG_TRY(prepare_launch(ctx, t, mode, t.g_mG, t.g_mT, t.g_mL, Ns, L));
-  dim3 g((unsigned)std::min<int64_t>(Ns, 1024), (unsigned)ctx->M);
-  k_pack<<<g, 128, 0, s>>>(Wm, ctx->N, Ns, ctx->off_d, ctx->nb_d, t.poff_d, t.ldp, t.WF[0], t.WSh[0], t.WSl[0]);
+  const dim3 g = pack_grid(Ns, ctx->max_nb, ctx->M);
+  k_pack<<<g, 256, 0, s>>>(Wm, ctx->N, Ns, ctx->off_d, ctx->nb_d, t.poff_d, t.ldp, t.WF[0], t.WSh[0], t.WSl[0]);
   count_launch();
   DG_CUDA(cudaGetLastError());
   const int tiles = (ctx->max_nb + 63) / 64;
@@ -1007,7 +1021,7 @@ dgchefsi_status tc_grad_backward(dgchefsi_ctx* ctx, int prec, const double* Wm, 
     }
   }
   if (X_bar) {
-    k_unpack<<<g, 128, 0, s>>>(t.WF[m & 1], t.ldp, Ns, ctx->off_d, ctx->nb_d, t.poff_d, X_bar, ld_xbar);
+    k_unpack<<<g, 256, 0, s>>>(t.WF[m & 1], t.ldp, Ns, ctx->off_d, ctx->nb_d, t.poff_d, X_bar, ld_xbar);
     count_launch();
     DG_CUDA(cudaGetLastError());
   }

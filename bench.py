@@ -676,6 +676,7 @@ def main():
         t1.record(stream)
         barrier()
     launches = D.launch_count() - n0
+    X_warm = X.clone()  # the block the timed cycles left (later measurements reuse X and Y)
     ms_step = t0.elapsed_time(t1) / args.steps
     ms_filter = statistics.mean(a.elapsed_time(b) for a, b in fl_t)
     from paper_1606_03416_gb300.replicas import max_over_ranks
@@ -797,45 +798,51 @@ def main():
                    "chunks, small first and last), host wall clock around the synchronous call; serial_copies_tflops: copy in, "
                    "filter, copy out one after the other"}
 
-    # ---- FP64 cycle for the per-cycle comparison, and precision of the mixed cycle
+    # ---- FP64 cycle for the per-cycle comparison, and precision of one mixed
+    # cycle against one FP64 cycle from the same block with the same bounds:
+    # cold = the random start block (first-cycle bounds), warm = the block left
+    # by the warm-up and timed cycles (bounds from their last Ritz values)
     f64 = {}
     if args.f64_steps > 0 and args.prec != "f64":
-        state["prev"] = None
-        Xa, Ya = Xd.clone(), torch.empty_like(Xd)
-        Xb, Yb = Xd.clone(), torch.empty_like(Xd)
+        warm_prev = state["prev"]
         b, tmin = ctx.bounds(vd, 10)
-        a0 = tmin
-        a = a0 + (b - a0) * Ns / N
-        s, e = ev(), ev()
-        torch.cuda.synchronize()
-        s.record(stream)
-        ctx.filter(Xa, m, a, b, a0, prec="f64", Y=Ya)
-        r64 = ctx.rayleigh_ritz(Ya)
-        fo, _ = ctx.occupations(r64, Ne, kT)
-        ctx.density_blocks(Ya, fo)
-        e.record(stream)
-        torch.cuda.synchronize()
-        f64["s_per_cycle"] = s.elapsed_time(e) / 1e3
-        ctx.filter(Xb, m, a, b, a0, prec=args.prec, Y=Yb)
-        rmx = ctx.rayleigh_ritz(Yb)
-        scale = max(abs(a0), abs(b))
-        f64["ritz_err_first_cycle"] = float((rmx - r64).abs().max().item() / scale)
-        # largest principal angle between the occupied subspaces (sin, by power
-        # iteration on R = Xm - X64 (X64^T Xm)) and the density-block error
-        n_occ = int(round(Ne / 2))
-        X64o, Xmo = Ya[:n_occ], Yb[:n_occ]          # state-major rows
-        R = Xmo - (Xmo @ X64o.T) @ X64o
-        v = torch.ones(n_occ, dtype=torch.float64, device=dev)
-        for _ in range(30):
-            v = R @ (R.T @ v)
-            v = v / v.norm()
-        f64["max_subspace_angle_sin"] = float((R.T @ v).norm().item())  # top singular value of R
-        fm, _ = ctx.occupations(rmx, Ne, kT)
-        P64 = ctx.density_blocks(Ya, fo)
-        Pmx = ctx.density_blocks(Yb, fm)
-        f64["density_rel_err"] = float((Pmx - P64).norm().item() / P64.norm().item())
-        R = X64o = Xmo = P64 = Pmx = None
-        Xa = Ya = Xb = Yb = None
+
+        def compare(Xstart, a, a0, timed):
+            Xa, Ya = Xstart.clone(), torch.empty_like(Xstart)
+            Xb, Yb = Xstart.clone(), torch.empty_like(Xstart)
+            s, e = ev(), ev()
+            torch.cuda.synchronize()
+            s.record(stream)
+            ctx.filter(Xa, m, a, b, a0, prec="f64", Y=Ya)
+            r64 = ctx.rayleigh_ritz(Ya)
+            fo, _ = ctx.occupations(r64, Ne, kT)
+            P64 = ctx.density_blocks(Ya, fo)
+            e.record(stream)
+            torch.cuda.synchronize()
+            if timed:
+                f64["s_per_cycle"] = s.elapsed_time(e) / 1e3
+            ctx.filter(Xb, m, a, b, a0, prec=args.prec, Y=Yb)
+            rmx = ctx.rayleigh_ritz(Yb)
+            scale = max(abs(a0), abs(b))
+            out = {"ritz_err": float((rmx - r64).abs().max().item() / scale)}
+            # largest principal angle between the occupied subspaces (sine, by
+            # power iteration on R = Xm - X64 (X64^T Xm)) and the density error
+            n_occ = int(round(Ne / 2))
+            X64o, Xmo = Ya[:n_occ], Yb[:n_occ]          # state-major rows
+            R = Xmo - (Xmo @ X64o.T) @ X64o
+            v = torch.ones(n_occ, dtype=torch.float64, device=dev)
+            for _ in range(30):
+                v = R @ (R.T @ v)
+                v = v / v.norm()
+            out["subspace_sin_max"] = float((R.T @ v).norm().item())  # top singular value of R
+            fm, _ = ctx.occupations(rmx, Ne, kT)
+            Pmx = ctx.density_blocks(Yb, fm)
+            out["density_rel_err"] = float((Pmx - P64).norm().item() / P64.norm().item())
+            return out
+
+        f64["cold_first_cycle"] = compare(torch.from_numpy(X0).to(dev), tmin + (b - tmin) * Ns / N, tmin, True)
+        f64["warm"] = compare(X_warm, float(warm_prev.max()), float(warm_prev.min()), False)
+        f64["warm"]["after_cycles"] = args.warmup + args.steps
 
     clocks = clk.summary()
     line = {
@@ -848,16 +855,14 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "s_per_cycle": {"mixed": ms_step / 1e3, "f64": f64.get("s_per_cycle")},
         "filter_ms": ms_filter,
-        "ritz_err_mixed_vs_f64_first_cycle": f64.get("ritz_err_first_cycle"),
-        "subspace_sin_max_mixed_vs_f64": f64.get("max_subspace_angle_sin"),
-        "density_rel_err_mixed_vs_f64": f64.get("density_rel_err"),
+        "mixed_vs_f64_one_cycle": {k: f64[k] for k in ("cold_first_cycle", "warm") if k in f64},
         "roofline": roof, "roofline_filter": rf, "filter_tflops_other_precisions": other,
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }
     if not args.no_next_rows and args.prec != "f64":
         line["next_rows"] = measure_next_rows(ctx, H, X, Ns, m, args.prec, dev)
     ctx.close()
-    X = Y = Xd = Yd = Xs = Xh = Yh = S = None  # free the 8x8x8 buffers before the next workload
+    X = Y = Xd = Yd = Xs = Xh = Yh = S = X_warm = None  # free the 8x8x8 buffers before the next workload
     torch.cuda.empty_cache()
     if not args.no_uneven and args.prec != "f64":
         line["batched_uneven"] = measure_uneven(dev)

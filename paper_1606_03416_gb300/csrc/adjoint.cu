@@ -150,7 +150,6 @@ extern "C" dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, con
     // Y_0 = X (caller layout ld); iterates in T0/T1/T2 rotation (ld = N)
     double* rot[3] = {T0, T1, T2};
     const double* prev = nullptr;
-    int64_t ldp = N;
     const double* cur = X;
     int64_t ldc = ld;
     if (want_grad) DG_TRY(copy_blk(cp0[0], N, X, ld));
@@ -163,9 +162,7 @@ extern "C" dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, con
         if (kk % stride == 0) DG_TRY(copy_blk(cp0[kk / stride], N, out, N));
         if (kk % stride == 1) DG_TRY(copy_blk(cp1[kk / stride], N, out, N));
       }
-      (void)ldp;
       prev = cur;
-      ldp = ldc;
       cur = out;
       ldc = N;
     }

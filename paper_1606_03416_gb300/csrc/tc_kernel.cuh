@@ -293,7 +293,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
   // per-role copies of the current group's slice entries (producer, MMA issuer)
   int32_t* sched_sh0 = reinterpret_cast<int32_t*>(bars + 2 * S + 4);
-  int32_t* sched_sh1 = sched_sh0 + p.maxent * (1 + G);
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
 
@@ -393,10 +392,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     bool ok = true;
     for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++i) {
       const int eg = u / p.ntg;
-      const int e0 = p.sched_ptr[eg], ne = p.sched_ptr[eg + 1] - e0;
-      __syncwarp();
-      for (int z = lane; z < ne * (1 + G); z += 32) sched_sh1[z] = p.sched[(int64_t)e0 * (1 + G) + z];
-      __syncwarp();
+      const int ne = p.sched_ptr[eg + 1] - p.sched_ptr[eg];
       if (lane == 0 && ok) {
         const int buf = p.NBUF == 2 ? (i & 1) : 0;
         const int use = p.NBUF == 2 ? (i >> 1) : i;
@@ -688,7 +684,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       atomicOr(p.err, 1);
       atomicExch(&abort_sh, 1);
     }
-    (void)sched_sh1;
   } else {
     // ---------------- epilogue: warps 2..9; lane quarter q = element rows 32q..32q+31,
     // the two warps of a quarter take alternate 16-state chunks

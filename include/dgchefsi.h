@@ -22,7 +22,13 @@
  *        enqueued, except where it says it synchronises (it returns host
  *        scalars or checks a device status).
  * Ownership: the context owns its copy of H and all workspace; callers own
- *        every buffer they pass. No call keeps a caller pointer after return.
+ *        every buffer they pass. No call dereferences a caller pointer after it
+ *        returns (the graph form remembers the addresses of its last capture
+ *        only to recognise a call that passes the same buffers again).
+ * Threads: a context is not thread-safe; calls on one context must not run
+ *        concurrently. Different contexts may be used from different threads
+ *        (each has its own workspace and streams), except that every caller of
+ *        dgchefsi_bounds_static on a GPU shares that entry point's one array.
  * Errors: every call returns a dgchefsi_status. On error the outputs are
  *        unspecified, nothing leaks, and dgchefsi_last_error() returns a
  *        message for the calling thread. No C++ exception crosses the ABI.

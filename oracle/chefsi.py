@@ -32,6 +32,11 @@ Readings where the paper is silent (each is also listed in the design notes):
     [lambda_1 - 50 kT, lambda_Ns + 50 kT] until |2 sum f - N_e| <= 1e-13 N_e
     or 200 halvings.
 
+Parity unpinned: ``first_cycle_bounds`` (a heuristic the paper does not state;
+the bounds change only the convergence rate, not the fixed point, and parity
+tests pass the same bounds to both sides) and the accuracy floor of the
+mixed-precision filter (measured, not a property of this module).
+
 Parity pins (tests/test_oracle_pins.py) check every function here against
 results the mathematics fixes independently of this code: brute-force dense
 products, the closed form V C_m(Lambda) V^T X of the filter, dense eigh of H,
@@ -167,7 +172,8 @@ def lanczos_bounds(H: DGHamiltonian, v0: np.ndarray, k: int = 10):
 
 
 def first_cycle_bounds(b_upper: float, theta_min: float, Ns: int, N: int):
-    """(a, a0) for the first cycle, before any Ritz values exist."""
+    """(a, a0) for the first cycle, before any Ritz values exist (parity
+    unpinned: a reading of the paper's silence, see the module header)."""
     a0 = theta_min
     a = a0 + (b_upper - a0) * Ns / N
     return a, a0

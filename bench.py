@@ -749,7 +749,7 @@ def main():
     roof = {"bound": "alu", "achieved": g_ach, "peak": F64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": g_ach / F64_PEAK_TFLOPS, "traffic": profiled_gram_traffic(Ns), "kernel": "k_gemm_nt_f64",
             "ms_per_launch": statistics.median(gms),
-            "peak_source": "FP64 DFMA peak derived in DESIGN.md (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz); "
+            "peak_source": "FP64 DFMA peak from the unit counts and clock (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz); "
                            "cuBLAS DGEMM measured 1.10 TFLOP/s on this GB300"}
 
     # ---- filter throughput of the other tensor-core precisions (filter alone)

@@ -146,3 +146,25 @@ def test_shifted_cholesky_qr3_where_cholesky_fails():
     # moderate conditioning: the same Q as one Cholesky-QR pass, whose own error is ~kappa^2 u
     Yw = ill_conditioned(200, 12, 1e3, seed=4)
     assert np.max(np.abs(O.shifted_cholesky_qr3(Yw)[0] - O.cholesky_qr(Yw)[0])) <= 10 * 1e3 ** 2 * 2.0 ** -53
+
+
+def test_basis_pair_generator_properties():
+    """Synthetic bases: orthonormal columns of the stated sizes, the new basis a
+    small perturbation of the old one where sizes agree, seeded, and packed
+    row-major in element order."""
+    nb_old, nb_new, nr = [4, 7, 5], [5, 7, 3], [20, 30, 9]
+    Vo, Vn = G.make_basis_pair(nb_old, nb_new, nr, delta=0.05, seed=1)
+    for K, (a, b) in enumerate(zip(Vo, Vn)):
+        assert a.shape == (nr[K], nb_old[K]) and b.shape == (nr[K], nb_new[K])
+        assert np.max(np.abs(a.T @ a - np.eye(nb_old[K]))) <= 1e-13
+        assert np.max(np.abs(b.T @ b - np.eye(nb_new[K]))) <= 1e-13
+    # same size: the new basis spans nearly the old span (principal angles ~ delta)
+    s = np.linalg.svd(Vo[1].T @ Vn[1], compute_uv=False)
+    assert s.min() > 0.9
+    Vo2, Vn2 = G.make_basis_pair(nb_old, nb_new, nr, delta=0.05, seed=1)
+    assert all(np.array_equal(x, y) for x, y in zip(Vo + Vn, Vo2 + Vn2))
+    packed = G.pack_blocks(Vo)
+    assert packed.shape == (sum(r * n for r, n in zip(nr, nb_old)),)
+    assert np.array_equal(packed[:nr[0] * nb_old[0]].reshape(nr[0], nb_old[0]), Vo[0])
+    with pytest.raises(ValueError):
+        G.make_basis_pair([40], [4], [20])   # more basis functions than grid points

@@ -207,3 +207,24 @@ def test_tensor_core_converged_gradient_is_dense_eigen_formula():
     xb = float(Xb.norm()) / float(X.norm())
     print(f"TC_CONVERGED cond={kappa:.2e} H={err:.2e} Xbar={xb:.2e} tol={tol:.2e}")
     assert err <= tol and xb <= tol
+
+
+@pytest.mark.parametrize("prec", ["f64", "bf16x3"])
+@pytest.mark.parametrize("m", [1, 2])
+def test_energy_grad_lowest_degrees(m, prec):
+    """Degrees 1 and 2: one segment, no recomputed iterates (m = 1: a single
+    checkpoint; m = 2: the pair), for both the FP64 and the tensor-core
+    gradient, against the oracle adjoint."""
+    cfg, H, Ho, X0, Ns, Ne, (a, b, a0) = case("small")
+    E_o, G_o, Xb_o = O.band_energy_grad(Ho, X0.T, m, a, b, a0, Ne, cfg.kT)
+    dev = torch.device("cuda:0")
+    with D.Context(H) as ctx:
+        E, _, Hb, Xb = ctx.energy_grad(torch.from_numpy(X0).to(dev), m, a, b, a0, Ne, cfg.kT, prec=prec)
+    Gflat = np.concatenate([g.ravel() for g in G_o])
+    if prec == "f64":
+        tol = 1e-8
+    else:
+        tol = 2 * m * U_OP[prec] * np.linalg.cond(O.chebyshev_filter(Ho, X0.T, m, a, b, a0))
+    assert abs(E - E_o) <= max(tol, 1e-11) * abs(E_o)
+    assert rel(Hb.cpu().numpy(), Gflat) <= tol
+    assert rel(Xb.cpu().numpy(), Xb_o.T) <= tol

@@ -502,11 +502,95 @@ def nnz_of(H) -> int:
     return int(sum(nb[K] * nb[col[e]] for K in range(len(nb)) for e in range(rp[K], rp[K + 1])))
 
 
+def measure_sliced(ctx, X_warm, state, cycle, vd, Ns, N, m, Ne, kT, args, dev, bf16_peak):
+    """Mixed cycles with the Rayleigh-Ritz products rebuilt from exact BF16
+    slices, started from the warm block the timed cycles left; one filtered warm
+    block through Rayleigh-Ritz with FP64 and with sliced products (accuracy and
+    time); the Gram- and rotation-shaped sliced products against the BF16
+    tensor peak (tensor work = slice pairs x 2 M N K)."""
+    import torch
+    from paper_1606_03416_gb300 import dgchefsi as D
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    s = args.slices
+    pairs = s * (s + 1) // 2
+    warm_prev = state["prev"]
+    out = {"slices": s, "slice_pairs": pairs}
+    b, _ = ctx.bounds(vd, 10)
+    a, a0 = float(warm_prev.max()), float(warm_prev.min())
+    Y1 = torch.empty_like(X_warm)
+    ctx.filter(X_warm, m, a, b, a0, prec=args.prec, Y=Y1)
+    Y2, Y3 = Y1.clone(), Y1.clone()
+    ctx.set_subspace_products("sliced_bf16", s)
+    ctx.rayleigh_ritz(Y3)                      # first use: workspace and cuBLAS set-up
+    del Y3
+    res = {}
+    for mode, Yb in (("f64", Y1), ("sliced_bf16", Y2)):
+        ctx.set_subspace_products(mode, s)
+        s_, e_ = ev(), ev()
+        torch.cuda.synchronize()
+        s_.record(stream)
+        r = ctx.rayleigh_ritz(Yb)
+        e_.record(stream)
+        torch.cuda.synchronize()
+        f, _ = ctx.occupations(r, Ne, kT)
+        res[mode] = (r, ctx.density_blocks(Yb, f), s_.elapsed_time(e_) / 1e3)
+    scale = max(abs(a0), abs(b))
+    out["warm_block_vs_f64_products"] = {
+        "ritz_err": float((res["f64"][0] - res["sliced_bf16"][0]).abs().max().item() / scale),
+        "density_rel_err": float((res["f64"][1] - res["sliced_bf16"][1]).norm().item() / res["f64"][1].norm().item()),
+        "orthonormality": float((Y2 @ Y2.T - torch.eye(Ns, dtype=torch.float64, device=dev)).abs().max().item())}
+    out["s_rayleigh_ritz"] = {"f64_products": res["f64"][2], "sliced_products": res["sliced_bf16"][2]}
+    del Y1, Y2, res
+    # whole mixed cycles with sliced products
+    ctx.set_subspace_products("sliced_bf16", s)
+    state["prev"] = warm_prev
+    X, Y = X_warm.clone(), torch.empty_like(X_warm)
+    _, X, Y = cycle(args.prec, X, Y)
+    n0 = D.launch_count()
+    t0, t1 = ev(), ev()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    reps = 3
+    for _ in range(reps):
+        _, X, Y = cycle(args.prec, X, Y)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    out["s_per_cycle"] = t0.elapsed_time(t1) / 1e3 / reps
+    out["gpu_launches_per_cycle"] = (D.launch_count() - n0) / reps
+    del X, Y
+    # the products alone: Gram shape (N_s x N_s, K = N) and rotation shape (N_s x N, K = N_s)
+    S = torch.empty((Ns, Ns), dtype=torch.float64, device=dev)
+    W = torch.empty_like(X_warm)
+    prods = {}
+    for name, fn, mnk in (("gram", lambda: ctx.sliced_gemm(X_warm, X_warm, slices=s, out=S), Ns * Ns * N),
+                          ("rotation", lambda: ctx.sliced_gemm(S, X_warm, b_rows=False, slices=s, out=W),
+                           Ns * N * Ns)):
+        ts = []
+        for _ in range(3):
+            s_, e_ = ev(), ev()
+            torch.cuda.synchronize()
+            s_.record(stream)
+            fn()
+            e_.record(stream)
+            torch.cuda.synchronize()
+            ts.append(s_.elapsed_time(e_))
+        t = statistics.median(ts[1:]) * 1e-3
+        tens = pairs * 2.0 * mnk / t / 1e12
+        prods[name] = {"ms": t * 1e3, "fp64_equivalent_tflops": 2.0 * mnk / t / 1e12, "tensor_tflops": tens,
+                       "bound": "tensor", "peak": bf16_peak, "frac": tens / bf16_peak}
+    out["products"] = prods
+    ctx.set_subspace_products("f64", s)
+    state["prev"] = warm_prev
+    return out
+
+
 def run_converge(args):
     """Cycles to the 1e-8 target: from the same random start, CheFSI cycles in the
     mixed form (--prec) and in FP64 until the Ritz values of the occupied states
     (i < N_e/2) agree with the exact eigenvalues of the dense H to 1e-8 of
-    max(|a0|, |b|), or --max-cycles. The exact eigenvalues come from a dense FP64
+    max(|a0|, |b|), or --max-cycles. --forms lists filter precisions, each
+    optionally "/sliced" for Rayleigh-Ritz products from BF16 slices. The exact eigenvalues come from a dense FP64
     eigensolve of H on the GPU (an error metric only, outside the timed cycles);
     each cycle (Lanczos bound, filter, Rayleigh-Ritz, occupations, density
     blocks) is timed with CUDA events."""
@@ -537,7 +621,10 @@ def run_converge(args):
     stream = torch.cuda.current_stream()
     with D.Context(H) as ctx:
         vd = torch.from_numpy(v0).to(dev)
-        for prec in (args.prec, "f64"):
+        forms = [f for f in args.forms.split(",") if f] if args.forms else [args.prec, "f64"]
+        for form in forms:
+            prec, _, products = form.partition("/")
+            ctx.set_subspace_products("sliced_bf16" if products == "sliced" else "f64", max(args.slices, 2))
             X = torch.from_numpy(X0).to(dev)
             Y = torch.empty_like(X)
             prev, errs, times, reached = None, [], [], None
@@ -562,12 +649,13 @@ def run_converge(args):
                 if err <= 1e-8 and reached is None:
                     reached = c + 1
                     break
-            out["forms"][prec] = {"cycles_to_target": reached, "ritz_err_by_cycle": errs,
+            out["forms"][form] = {"cycles_to_target": reached, "ritz_err_by_cycle": errs,
                                   "s_per_cycle_median": float(np.median(times)),
                                   "s_to_target": float(np.sum(times)) if reached else None}
-    f, g = out["forms"].get(args.prec), out["forms"].get("f64")
-    if f and g and f["s_to_target"] and g["s_to_target"]:
-        out["speedup_to_target"] = g["s_to_target"] / f["s_to_target"]
+    g = out["forms"].get("f64")
+    for form, f in out["forms"].items():
+        if form != "f64" and g and f["s_to_target"] and g["s_to_target"]:
+            out.setdefault("speedup_to_target", {})[form] = g["s_to_target"] / f["s_to_target"]
     print(json.dumps(out), flush=True)
     return 0
 
@@ -592,6 +680,10 @@ def main():
                     help="cycles to Ritz error <= 1e-8 against a dense eigensolve, mixed and FP64")
     ap.add_argument("--max-cycles", type=int, default=40)
     ap.add_argument("--gram-only", action="store_true", help="time one FP64 Gram (profiling case)")
+    ap.add_argument("--slices", type=int, default=10,
+                    help="BF16 slices of the sliced Rayleigh-Ritz products measured beside the FP64 ones (0: skip)")
+    ap.add_argument("--forms", default="",
+                    help="converge: comma list of filter[/sliced] forms (default: --prec and f64)")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--filter-only", action="store_true",
                     help="time only the filter (profiling case); --ns and --m override the workload")
@@ -844,6 +936,12 @@ def main():
         f64["warm"] = compare(X_warm, float(warm_prev.max()), float(warm_prev.min()), False)
         f64["warm"]["after_cycles"] = args.warmup + args.steps
 
+    # ---- the same mixed cycle with the four dense Rayleigh-Ritz products rebuilt
+    # from exact BF16 slices on the tensor cores (dgchefsi_set_subspace_products)
+    sliced = None
+    if args.slices > 0 and args.prec != "f64":
+        sliced = measure_sliced(ctx, X_warm, state, cycle, vd, Ns, N, m, Ne, kT, args, dev, bf16_peak)
+
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -853,12 +951,15 @@ def main():
                    "Ns": Ns, "m": m, "Ne": Ne, "kT": kT, "filter": args.prec, "subspace": "f64",
                    "l2": "inputs larger than L2 (X 1.07 GB FP64), no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "s_per_cycle": {"mixed": ms_step / 1e3, "f64": f64.get("s_per_cycle")},
+        "s_per_cycle": {"mixed": ms_step / 1e3, "f64": f64.get("s_per_cycle"),
+                        "mixed_sliced_products": sliced["s_per_cycle"] if sliced else None},
         "filter_ms": ms_filter,
         "mixed_vs_f64_one_cycle": {k: f64[k] for k in ("cold_first_cycle", "warm") if k in f64},
         "roofline": roof, "roofline_filter": rf, "filter_tflops_other_precisions": other,
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }
+    if sliced:
+        line["sliced_products"] = sliced
     if not args.no_next_rows and args.prec != "f64":
         line["next_rows"] = measure_next_rows(ctx, H, X, Ns, m, args.prec, dev)
     ctx.close()

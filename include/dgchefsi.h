@@ -56,7 +56,8 @@ typedef enum {
   DGCHEFSI_ERR_UNSUPPORTED = 8     /* shape or precision this build does not run */
 } dgchefsi_status;
 
-/* Arithmetic of the filter (Alg. 1 step 2). The subspace steps are FP64 always. */
+/* Arithmetic of the filter (Alg. 1 step 2). The subspace steps are FP64, their dense
+ * products optionally FP64 rebuilt from BF16 slices (dgchefsi_set_subspace_products). */
 typedef enum {
   DGCHEFSI_F64 = 0,    /* FP64 operands, FP64 accumulation (CUDA-core DFMA) */
   DGCHEFSI_TF32 = 1,   /* tcgen05 kind::tf32: TF32 operands, FP32 accumulation, FP32 iterates */
@@ -229,6 +230,53 @@ dgchefsi_status dgchefsi_rayleigh_ritz(dgchefsi_ctx* ctx, double* Y, int64_t Ns,
 #define DGCHEFSI_ORTH_CHOLQR2 1
 #define DGCHEFSI_ORTH_SHIFTED_CHOLQR3 2
 dgchefsi_status dgchefsi_set_orthonormalisation(dgchefsi_ctx* ctx, int mode);
+
+/* Arithmetic of the four dense products of the Rayleigh-Ritz step (Alg. 1
+ * steps 3-5: S = Y^T Y, Y_hat = Y U^{-1}, H_hat = Y_hat^T (H Y_hat), X_new =
+ * Y_hat Q) in dgchefsi_rayleigh_ritz and dgchefsi_cycle. The paper finds the
+ * subspace problem the largest share of its largest runs and proposes moving
+ * it onto dense matrix products (Table scf_walltime; Conclusion).
+ *   DGCHEFSI_PRODUCTS_F64          FP64 operands, FP64 accumulation on the
+ *                                  CUDA cores (default)
+ *   DGCHEFSI_PRODUCTS_SLICED_BF16  each FP64 operand split exactly into
+ *                                  `slices` BF16 integer slices of 6 bits per
+ *                                  row (column) and 4096-long K chunk, the
+ *                                  slice pairs multiplied on the BF16 tensor
+ *                                  cores with exact FP32 accumulation, summed
+ *                                  and rescaled in FP64 (the Ozaki scheme; see
+ *                                  dgchefsi_sliced_gemm)
+ *   slices  2..16 for the sliced form (ignored for FP64); 10 gives an error
+ *           below the FP64 worst-case bound for rows of similar magnitude
+ * ERR_ARG for another mode or slice count. H Y_hat stays on the FP64 cores; the
+ * band-energy gradient and dgchefsi_gram always use FP64 products. */
+#define DGCHEFSI_PRODUCTS_F64 0
+#define DGCHEFSI_PRODUCTS_SLICED_BF16 1
+dgchefsi_status dgchefsi_set_subspace_products(dgchefsi_ctx* ctx, int mode, int slices);
+
+/* FP64 matrix product from exact BF16 slices on the tensor cores (the form
+ * DGCHEFSI_PRODUCTS_SLICED_BF16 uses; error-free splitting of Ozaki, Ogita,
+ * Oishi and Rump 2012, on BF16 tensor cores as Mukunoki et al. 2020 do on
+ * FP16 ones):
+ *   b_rows = 1:  C = A B^T,  B device row-major Nc x K (ldb >= K)
+ *   b_rows = 0:  C = A B,    B device row-major K x Nc (ldb >= Nc)
+ *   A  device row-major M x K (lda >= K); a_lower = 1: entries k > r of row r
+ *      are taken as zero and not read
+ *   C  device out, row-major M x Nc (ldc >= Nc); must not overlap A or B
+ *   slices  2..16
+ * For b_rows = 0 every K index k is first balanced exactly: row k of B times
+ * 2^{-s_k}, column k of A times 2^{s_k}, s_k the exponent of max_c |B[k, c]|
+ * (rows of B with very different norms would otherwise share one column
+ * scale); the bound below is then for the balanced operands.
+ * With row maxima m_r of A and column maxima n_c of the product's right
+ * operand over each 4096-long chunk of K (length L), the error of C[r, c] is at
+ * most the sum over chunks of L m_r n_c (2^{-6 slices} (slices + 4) + (5 + chunks) 2^{-53}).
+ * Uses up to ~4 GB of FP32 workspace for the slice
+ * products plus the slices (2 bytes x slices per operand entry). Synchronises;
+ * ERR_NONFINITE if A or B holds NaN/Inf (C is then unspecified), ERR_ARG on bad
+ * sizes, ERR_UNSUPPORTED when K / 4096 > 65535 or M, Nc > 2^31 - 1. */
+dgchefsi_status dgchefsi_sliced_gemm(dgchefsi_ctx* ctx, int b_rows, int a_lower, int64_t M, int64_t Nc, int64_t K,
+                                     const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
+                                     int64_t ldc, int slices);
 
 /* Fermi-Dirac occupations f_i = 1/(1 + exp((lambda_i - mu)/kT)) with mu set by
  * 2 sum_i f_i = Ne (spin factor 2; occupations of Eq. KS_DG_Energy, Sec. III.B.2).

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgchefsi.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "f64_kernels.cu", "tc_filter.cu", "tc_tf32.cu", "tc_bf16.cu", "tc_bf16x3.cu", "noalloc.cu",
-           "adjoint.cu", "realign.cu"]
+           "adjoint.cu", "realign.cu", "sliced.cu"]
 
 
 def nvcc() -> str:
@@ -68,7 +68,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         list(ex.map(run, jobs))
     if jobs or not os.path.exists(LIB):
         libdir = os.path.join(cuda_home(), "lib64")
-        run([nvcc(), "-shared", "-o", LIB] + objs + ARCH + ["-L", libdir, "-lcusolver", "-lcudart",
+        run([nvcc(), "-shared", "-o", LIB] + objs + ARCH + ["-L", libdir, "-lcusolver", "-lcublas", "-lcudart",
             "-Xlinker", "-rpath," + libdir])
     return LIB
 

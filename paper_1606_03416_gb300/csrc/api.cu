@@ -325,6 +325,10 @@ static dgchefsi_status rr_impl(dgchefsi_ctx* ctx, double* Y, int64_t Ns, int64_t
   const int lwork = (int)(ctx->ws_solver.bytes / sizeof(double));
   DG_CUDA(cudaMemsetAsync(ctx->info_d, 0, 4 * sizeof(int), s));
   int info[4] = {0, 0, 0, 0};
+  // Products on the FP64 cores, or from exact BF16 slices on the tensor cores
+  // (non-finite operands there raise info[3], like a non-finite Ritz value).
+  const bool sl = ctx->products_mode == DGCHEFSI_PRODUCTS_SLICED_BF16;
+  int* bad = ctx->info_d + 3;
   // Step 3: S = Y^T Y (lower tiles, mirrored), S = U^T U, Y_hat = Y U^{-1}.
   // CholeskyQR2 repeats the pass on Y_hat; shifted CholeskyQR3 factors
   // Y^T Y + s I first, s = 11 (N N_s + N_s (N_s + 1)) u ||Y||_F^2, then repeats
@@ -336,7 +340,10 @@ static dgchefsi_status rr_impl(dgchefsi_ctx* ctx, double* Y, int64_t Ns, int64_t
     const int64_t ldi = pass == 0 ? ld : N;
     double* outp = pass == 0 ? W : Y;
     const int64_t ldo = pass == 0 ? N : ld;
-    DG_CUDA(gemm_nt_f64(in, ldi, in, ldi, S, Ns, Ns, Ns, N, true, false, s));
+    if (sl)
+      DG_TRY(sliced_gemm(ctx, true, false, Ns, Ns, N, in, ldi, in, ldi, S, Ns, ctx->products_slices, bad));
+    else
+      DG_CUDA(gemm_nt_f64(in, ldi, in, ldi, S, Ns, Ns, Ns, N, true, false, s));
     if (pass == 0 && ctx->orth_mode == DGCHEFSI_ORTH_SHIFTED_CHOLQR3)
       DG_CUDA(shift_diagonal_by_trace_f64(S, Ns, 11.0 * ((double)N * (double)Ns + (double)Ns * (double)(Ns + 1)) *
                                                      0x1p-53, s));
@@ -352,7 +359,10 @@ static dgchefsi_status rr_impl(dgchefsi_ctx* ctx, double* Y, int64_t Ns, int64_t
                                ctx->ws_solver.bytes, ctx->solver_host.empty() ? nullptr : ctx->solver_host.data(),
                                lw_trtri_h, ctx->info_d + 1));
     // Y_hat^T = U^{-T} Y^T
-    DG_CUDA(gemm_nn_f64(S, Ns, in, ldi, outp, ldo, Ns, N, Ns, true, s));
+    if (sl)
+      DG_TRY(sliced_gemm(ctx, false, true, Ns, N, Ns, S, Ns, in, ldi, outp, ldo, ctx->products_slices, bad));
+    else
+      DG_CUDA(gemm_nn_f64(S, Ns, in, ldi, outp, ldo, Ns, N, Ns, true, s));
     if (pass > 0)
       DG_CUDA(cudaMemcpy2DAsync(W, sizeof(double) * N, Y, sizeof(double) * ld, sizeof(double) * N, Ns,
                                 cudaMemcpyDeviceToDevice, s));
@@ -362,17 +372,24 @@ static dgchefsi_status rr_impl(dgchefsi_ctx* ctx, double* Y, int64_t Ns, int64_t
   // lower = column-major upper), so only the tiles on and below the diagonal
   // are computed.
   DG_CUDA(filter_step_f64(ctx->view(), W, N, nullptr, Y, ld, Ns, 1.0, 0.0, 0.0, s));
-  DG_CUDA(gemm_nt_f64(W, N, Y, ld, S, Ns, Ns, Ns, N, true, false, s));
+  if (sl)
+    DG_TRY(sliced_gemm(ctx, true, false, Ns, Ns, N, W, N, Y, ld, S, Ns, ctx->products_slices, bad));
+  else
+    DG_CUDA(gemm_nt_f64(W, N, Y, ld, S, Ns, Ns, Ns, N, true, false, s));
   DG_SOLVER(cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n, S, n, ritz, work, lwork,
                              ctx->info_d + 2));
   // Step 5: X_new^T = Q^T Y_hat^T (column-major Q read row-major is Q^T).
-  DG_CUDA(gemm_nn_f64(S, Ns, W, N, Y, ld, Ns, N, Ns, false, s));
+  if (sl)
+    DG_TRY(sliced_gemm(ctx, false, false, Ns, N, Ns, S, Ns, W, N, Y, ld, ctx->products_slices, bad));
+  else
+    DG_CUDA(gemm_nn_f64(S, Ns, W, N, Y, ld, Ns, N, Ns, false, s));
   DG_CUDA(check_finite_f64(ritz, Ns, ctx->info_d + 3, s));
   DG_CUDA(cudaMemcpyAsync(info, ctx->info_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   DG_CUDA(cudaStreamSynchronize(s));
   if (info[1] != 0) return set_error(DGCHEFSI_ERR_NOT_SPD, "triangular inverse failed (info %d)", info[1]);
   if (info[2] != 0) return set_error(DGCHEFSI_ERR_NO_CONVERGENCE, "dense eigensolver failed (info %d)", info[2]);
-  if (info[3] != 0) return set_error(DGCHEFSI_ERR_NONFINITE, "non-finite Ritz value");
+  if (info[3] != 0)
+    return set_error(DGCHEFSI_ERR_NONFINITE, sl ? "non-finite Ritz value or Rayleigh-Ritz operand" : "non-finite Ritz value");
   return DGCHEFSI_OK;
 }
 
@@ -509,6 +526,7 @@ void dgchefsi_destroy(dgchefsi_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream || ctx->vals_d) cudaStreamSynchronize(ctx->stream);
   tc_destroy(ctx);
+  sliced_destroy(ctx);
   if (ctx->solver) cusolverDnDestroy(ctx->solver);
   cudaFree(ctx->nb_d);
   cudaFree(ctx->off_d);
@@ -527,6 +545,7 @@ void dgchefsi_destroy(dgchefsi_ctx* ctx) {
   free_buf(ctx->ws_lanczos);
   free_buf(ctx->ws_adjoint);
   free_buf(ctx->ws_realign);
+  free_buf(ctx->ws_sliced);
   for (int i = 0; i < 2; ++i) {
     free_buf(ctx->ws_hin[i]);
     free_buf(ctx->ws_hout[i]);
@@ -712,6 +731,40 @@ dgchefsi_status dgchefsi_set_orthonormalisation(dgchefsi_ctx* ctx, int mode) {
   if (mode != DGCHEFSI_ORTH_CHOLQR && mode != DGCHEFSI_ORTH_CHOLQR2 && mode != DGCHEFSI_ORTH_SHIFTED_CHOLQR3)
     return set_error(DGCHEFSI_ERR_ARG, "unknown orthonormalisation %d", mode);
   ctx->orth_mode = mode;
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status dgchefsi_set_subspace_products(dgchefsi_ctx* ctx, int mode, int slices) {
+  clear_error();
+  if (!ctx) return set_error(DGCHEFSI_ERR_ARG, "null context");
+  if (mode != DGCHEFSI_PRODUCTS_F64 && mode != DGCHEFSI_PRODUCTS_SLICED_BF16)
+    return set_error(DGCHEFSI_ERR_ARG, "unknown product arithmetic %d", mode);
+  if (mode == DGCHEFSI_PRODUCTS_SLICED_BF16 && (slices < 2 || slices > 16))
+    return set_error(DGCHEFSI_ERR_ARG, "slices = %d outside 2..16", slices);
+  ctx->products_mode = mode;
+  if (mode == DGCHEFSI_PRODUCTS_SLICED_BF16) ctx->products_slices = slices;
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status dgchefsi_sliced_gemm(dgchefsi_ctx* ctx, int b_rows, int a_lower, int64_t M, int64_t Nc, int64_t K,
+                                     const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
+                                     int64_t ldc, int slices) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  if (M < 0 || Nc < 0 || K < 0) return set_error(DGCHEFSI_ERR_ARG, "negative size");
+  if (slices < 2 || slices > 16) return set_error(DGCHEFSI_ERR_ARG, "slices = %d outside 2..16", slices);
+  if (M == 0 || Nc == 0) return DGCHEFSI_OK;
+  if (!C || (K > 0 && (!A || !B))) return set_error(DGCHEFSI_ERR_ARG, "null matrix pointer");
+  if (ldc < Nc || (K > 0 && (lda < K || ldb < (b_rows ? K : Nc))))
+    return set_error(DGCHEFSI_ERR_ARG, "leading dimension smaller than the row length");
+  if ((K + 4095) / 4096 > 65535 || M > 0x7fffffff || Nc > 0x7fffffff)
+    return set_error(DGCHEFSI_ERR_UNSUPPORTED, "sizes beyond this build's grid limits");
+  DG_CUDA(cudaMemsetAsync(ctx->info_d + 3, 0, sizeof(int), ctx->stream));
+  DG_TRY(sliced_gemm(ctx, b_rows != 0, a_lower != 0, M, Nc, K, A, lda, B, ldb, C, ldc, slices, ctx->info_d + 3));
+  int bad = 0;
+  DG_CUDA(cudaMemcpyAsync(&bad, ctx->info_d + 3, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  DG_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (bad) return set_error(DGCHEFSI_ERR_NONFINITE, "non-finite entry in A or B");
   return DGCHEFSI_OK;
 }
 

@@ -52,6 +52,12 @@ struct dgchefsi_ctx {
   dg::DevBuf ws_adjoint;  // checkpoints and blocks of the band-energy gradient
   dg::DevBuf ws_realign;  // per-element tables and overlaps of the re-alignment
   int orth_mode = 0;      // DGCHEFSI_ORTH_*: orthonormalisation of step 3
+  // Rayleigh-Ritz products: DGCHEFSI_PRODUCTS_*, slice count of the sliced
+  // BF16 form, its cuBLAS handle (created on first use) and workspace
+  int products_mode = 0;
+  int products_slices = 10;
+  void* blas = nullptr;
+  dg::DevBuf ws_sliced;
   int32_t f64_tj = 64;    // column tile of the FP64 filter (set at create)
   // FP64 filter as a CUDA graph: coefficients copied from a pinned mirror at
   // every replay; the graph is captured again when X, Y, N_s, ld, m or the
@@ -120,6 +126,15 @@ dgchefsi_status tc_grad_forward(dgchefsi_ctx* ctx, int prec, const double* X, in
 dgchefsi_status tc_grad_backward(dgchefsi_ctx* ctx, int prec, const double* Wm, int64_t Ns, int m, int stride,
                                  double* H_bar, double* X_bar, int64_t ld_xbar);
 void tc_destroy(dgchefsi_ctx* ctx);
+
+// C (M x Nc, row-major, ldc) = A B^T (b_rows: B is Nc x K) or A B (B is K x Nc),
+// A (M x K, lda) row-major, all FP64, computed from s exact BF16 slices per
+// operand on the tensor cores (sliced.cu). a_lower: entries k > r of A are
+// zero and not read. flag (device int) gets 1 if an operand is not finite.
+dgchefsi_status sliced_gemm(dgchefsi_ctx* ctx, bool b_rows, bool a_lower, int64_t M, int64_t Nc, int64_t K,
+                            const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int s,
+                            int* flag);
+void sliced_destroy(dgchefsi_ctx* ctx);
 
 }  // namespace dg
 

@@ -1,0 +1,330 @@
+// FP64 products of the Rayleigh-Ritz step (Alg. 1 steps 3-5: Gram matrix,
+// Y U^{-1}, projected H, rotation) emulated on the BF16 tensor cores by exact
+// splitting (the Ozaki scheme: Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59,
+// 2012; BF16/FP16 tensor-core form after Mukunoki, Ozaki, Ogita, Imamura,
+// ISC 2020).
+//
+// Over one K chunk of length L <= 4096, row r of A is written as
+//   a[r,k] = 2^{e_r} sum_{i<s} q_i[r,k] 2^{-6(i+1)},  q_i integer, |q_0| <= 64, |q_i| <= 32,
+// with 2^{e_r} > max_k |a[r,k]| (and likewise each column of the product's
+// right operand with exponent f_c). Every q is exact in BF16, every product
+// q_i q_j is at most 2^12, so a slice-pair product summed over L <= 4096 terms
+// is an integer of magnitude <= 2^24: the tensor core's FP32 accumulation
+// returns it exactly, whatever its summation order. The pairs with
+// i + j <= s - 1 are kept; their FP32 results are summed per t = i + j in FP64
+// (exact: integers below 2^53), combined by Horner in 2^{-6}, scaled by
+// 2^{e_r + f_c - 12} and added over the chunks. The slice-pair products are
+// plain BF16 GEMMs (cuBLAS, FP32 output); splitting and the FP64 reduction are
+// the kernels below.
+//
+// Error per chunk (row and column maxima m_r, n_c over the chunk): the
+// remainders after s slices and the dropped pairs contribute at most
+// L 2^{e_r + f_c} 2^{-6s} (s + 4)/4 <= L m_r n_c 2^{-6s} (s + 4); the FP64
+// Horner sum and the sum over chunks add at most (5 + chunks) u L m_r n_c,
+// u = 2^{-53}. For s = 10 the splitting term is below u L m_r n_c, the size of
+// FP64's own worst-case bound. The bound is normwise per row and column:
+// entries far below their row's maximum keep fewer significant bits than FP64.
+#include <cuda_bf16.h>
+#include <cublas_v2.h>
+
+#include <algorithm>
+
+#include "ctx.h"
+
+namespace dg {
+
+static constexpr int kBeta = 6;      // bits per slice
+static constexpr int64_t kL = 4096;  // K chunk: 4096 * 2^12 = 2^24
+static constexpr int kCols = 64;     // columns per CTA of the column split
+
+__device__ __forceinline__ void atomic_flag(int* flag) {
+  if (flag) atomicOr(flag, 1);
+}
+
+// One CTA per (row, chunk), 256 threads, 16 entries each. Q: s slices of
+// rows x ldq BF16 (slice i at Q + i * sstride); E[row * nch + chunk] = e_r.
+// lower: entries k > row are zero (a lower-triangular operand). bal (may be
+// null): entry k is split as X[row, k] 2^{bal[k]}.
+__global__ void __launch_bounds__(256) k_split_rows(const double* __restrict__ X, int64_t ldx, int64_t K, int s,
+                                                    int lower, const int32_t* __restrict__ bal,
+                                                    __nv_bfloat16* __restrict__ Q, int64_t ldq, int64_t sstride,
+                                                    int32_t* __restrict__ E, int nch, int* __restrict__ flag) {
+  const int64_t row = blockIdx.x;
+  const int chunk = blockIdx.y;
+  const int64_t k0 = (int64_t)chunk * kL;
+  double v[16];
+  double mx = 0.0;
+  bool bad = false;
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const int64_t k = k0 + threadIdx.x + 256 * u;
+    double x = 0.0;
+    if (k < K && !(lower && k > row)) {
+      x = X[row * ldx + k];
+      if (bal) x = ldexp(x, bal[k]);
+    }
+    if (!isfinite(x)) bad = true;
+    v[u] = x;
+    mx = fmax(mx, fabs(x));
+  }
+  __shared__ double red[8];
+  __shared__ int sbad;
+  if (threadIdx.x == 0) sbad = 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  if (bad) sbad = 1;
+  __syncthreads();
+  mx = red[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) mx = fmax(mx, red[w]);
+  int e = 0;
+  if (sbad) {
+    mx = 0.0;
+    if (threadIdx.x == 0) atomic_flag(flag);
+  }
+  if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)
+  if (threadIdx.x == 0) E[row * nch + chunk] = e;
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const int64_t k = k0 + threadIdx.x + 256 * u;
+    if (k >= K) break;
+    double r = sbad ? 0.0 : ldexp(v[u], -e);
+    for (int i = 0; i < s; ++i) {
+      r *= (double)(1 << kBeta);
+      const double q = rint(r);
+      r -= q;
+      Q[i * sstride + row * ldq + k] = __float2bfloat16_rn((float)q);
+    }
+  }
+}
+
+// One CTA per (64 columns, chunk) of a row-major K x C operand, 256 threads:
+// lane group of 64 columns x 4 row phases. Column maxima first, then the
+// slices (the second read of the chunk comes from L2). Q: s slices of
+// K x ldq BF16; E[col * nch + chunk] = f_c. Row k is split as X[k, :] 2^{-bal[k]}.
+__global__ void __launch_bounds__(256) k_split_cols(const double* __restrict__ X, int64_t ldx, int64_t K, int64_t C,
+                                                    int s, const int32_t* __restrict__ bal,
+                                                    __nv_bfloat16* __restrict__ Q, int64_t ldq, int64_t sstride,
+                                                    int32_t* __restrict__ E, int nch, int* __restrict__ flag) {
+  const int cl = threadIdx.x % kCols;
+  const int ph = threadIdx.x / kCols;
+  const int64_t col = (int64_t)blockIdx.x * kCols + cl;
+  const int chunk = blockIdx.y;
+  const int64_t k0 = (int64_t)chunk * kL;
+  const int64_t k1 = std::min<int64_t>(K, k0 + kL);
+  double mx = 0.0;
+  bool bad = false;
+  if (col < C)
+    for (int64_t k = k0 + ph; k < k1; k += 4) {
+      const double x = ldexp(X[k * ldx + col], -bal[k]);
+      if (!isfinite(x)) bad = true;
+      mx = fmax(mx, fabs(x));
+    }
+  __shared__ double red[4][kCols];
+  __shared__ int sbad[kCols];
+  if (ph == 0) sbad[cl] = 0;
+  red[ph][cl] = mx;
+  __syncthreads();
+  if (bad) sbad[cl] = 1;
+  __syncthreads();
+  mx = fmax(fmax(red[0][cl], red[1][cl]), fmax(red[2][cl], red[3][cl]));
+  const bool cbad = sbad[cl] != 0;
+  if (cbad) mx = 0.0;
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);
+  if (col >= C) return;
+  if (ph == 0) {
+    E[col * nch + chunk] = e;
+    if (cbad) atomic_flag(flag);
+  }
+  for (int64_t k = k0 + ph; k < k1; k += 4) {
+    double r = cbad ? 0.0 : ldexp(X[k * ldx + col], -bal[k] - e);
+    for (int i = 0; i < s; ++i) {
+      r *= (double)(1 << kBeta);
+      const double q = rint(r);
+      r -= q;
+      Q[i * sstride + k * ldq + col] = __float2bfloat16_rn((float)q);
+    }
+  }
+}
+
+// bal[k] = exponent of max_c |X[k, c]| (X row-major K x C), 0 for a zero or
+// non-finite row (the split then flags the latter). One CTA per row.
+__global__ void __launch_bounds__(256) k_row_exponents(const double* __restrict__ X, int64_t ldx, int64_t C,
+                                                       int32_t* __restrict__ bal) {
+  const int64_t k = blockIdx.x;
+  double mx = 0.0;
+  for (int64_t c = threadIdx.x; c < C; c += 256) mx = fmax(mx, fabs(X[k * ldx + c]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mx = red[0];
+    for (int w = 1; w < 8; ++w) mx = fmax(mx, red[w]);
+    int e = 0;
+    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
+    bal[k] = e;
+  }
+}
+
+// C[r, n0 + c] (+)= 2^{e_r + f_{n0+c} - 12} sum_t 2^{-6t} sum_{i+j=t} P_{ij}[r, c]
+// for r < M, c < P. Pair (i, j) is slab i*s - i(i-1)/2 + j of P (M x P FP32).
+__global__ void k_sliced_reduce(const float* __restrict__ Pw, int64_t M, int64_t P, int s,
+                                const int32_t* __restrict__ Ea, const int32_t* __restrict__ Eb, int nch, int chunk,
+                                int64_t n0, double* __restrict__ C, int64_t ldc, int accumulate) {
+  const int64_t total = M * P;
+  const int64_t slab = M * P;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / P;
+    const int64_t c = idx - r * P;
+    double acc = 0.0;
+    for (int t = s - 1; t >= 0; --t) {
+      double g = 0.0;
+      for (int i = 0; i <= t; ++i) {
+        const int j = t - i;
+        const int64_t p = (int64_t)i * s - (int64_t)i * (i - 1) / 2 + j;
+        g += (double)Pw[p * slab + idx];
+      }
+      acc = acc * (1.0 / (double)(1 << kBeta)) + g;
+    }
+    const double v = ldexp(acc, Ea[r * nch + chunk] + Eb[(n0 + c) * nch + chunk] - 2 * kBeta);
+    double* out = C + r * ldc + n0 + c;
+    *out = accumulate ? *out + v : v;
+  }
+}
+
+static const char* blas_str(cublasStatus_t s) {
+  switch (s) {
+    case CUBLAS_STATUS_SUCCESS: return "success";
+    case CUBLAS_STATUS_NOT_INITIALIZED: return "not initialised";
+    case CUBLAS_STATUS_ALLOC_FAILED: return "allocation failed";
+    case CUBLAS_STATUS_INVALID_VALUE: return "invalid value";
+    case CUBLAS_STATUS_ARCH_MISMATCH: return "architecture mismatch";
+    case CUBLAS_STATUS_EXECUTION_FAILED: return "execution failed";
+    case CUBLAS_STATUS_NOT_SUPPORTED: return "not supported";
+    default: return "cuBLAS error";
+  }
+}
+
+#define DG_BLAS(call)                                                                                         \
+  do {                                                                                                        \
+    cublasStatus_t b_ = (call);                                                                               \
+    if (b_ != CUBLAS_STATUS_SUCCESS)                                                                          \
+      return set_error(DGCHEFSI_ERR_CUDA, "%s failed: %s (%s:%d)", #call, blas_str(b_), __FILE__, __LINE__); \
+  } while (0)
+
+static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Workspace cap of the FP32 slice-pair products; wider outputs run in column panels.
+static constexpr size_t kPairBytes = size_t(4) << 30;
+
+dgchefsi_status sliced_gemm(dgchefsi_ctx* ctx, bool b_rows, bool a_lower, int64_t M, int64_t Nc, int64_t K,
+                            const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int s,
+                            int* flag) {
+  if (M <= 0 || Nc <= 0) return DGCHEFSI_OK;
+  cudaStream_t st = ctx->stream;
+  if (K <= 0) {
+    DG_CUDA(cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * Nc, M, st));
+    return DGCHEFSI_OK;
+  }
+  if (!ctx->blas) {
+    cublasHandle_t h = nullptr;
+    DG_BLAS(cublasCreate(&h));
+    ctx->blas = h;
+  }
+  cublasHandle_t h = static_cast<cublasHandle_t>(ctx->blas);
+  DG_BLAS(cublasSetStream(h, st));
+  DG_BLAS(cublasSetPointerMode(h, CUBLAS_POINTER_MODE_HOST));
+  const int nch = (int)((K + kL - 1) / kL);
+  const int64_t pairs = (int64_t)s * (s + 1) / 2;
+  // Slices of A: s x M x lqa (K contiguous). Slices of B: b_rows ? s x Nc x lqb
+  // (K contiguous) : s x K x lqb (Nc contiguous).
+  const int64_t lqa = round_up(K, 8);
+  const int64_t lqb = b_rows ? round_up(K, 8) : round_up(Nc, 8);
+  const int64_t sa = M * lqa;
+  const int64_t sb = b_rows ? Nc * lqb : K * lqb;
+  const bool same = b_rows && A == B && lda == ldb && M == Nc && !a_lower;
+  const size_t qa_bytes = sizeof(__nv_bfloat16) * (size_t)(s * sa);
+  const size_t qb_bytes = same ? 0 : sizeof(__nv_bfloat16) * (size_t)(s * sb);
+  const size_t ea_bytes = sizeof(int32_t) * (size_t)(M * nch);
+  const size_t eb_bytes = sizeof(int32_t) * (size_t)(Nc * nch);
+  const size_t bal_bytes = b_rows ? 0 : sizeof(int32_t) * (size_t)K;
+  const size_t a256 = 256;
+  auto up = [&](size_t x) { return (x + a256 - 1) / a256 * a256; };
+  // Column panel of the product so that the FP32 pair slabs stay under the cap.
+  int64_t P = (int64_t)(kPairBytes / (sizeof(float) * (size_t)pairs * (size_t)M));
+  P = std::max<int64_t>(8, P / 8 * 8);
+  if (P >= Nc) P = Nc;
+  const size_t pw_bytes = sizeof(float) * (size_t)pairs * (size_t)M * (size_t)P;
+  DG_TRY(ensure(ctx, ctx->ws_sliced,
+                up(qa_bytes) + up(qb_bytes) + up(ea_bytes) + up(eb_bytes) + up(bal_bytes) + up(pw_bytes),
+                "sliced-product workspace"));
+  char* base = static_cast<char*>(ctx->ws_sliced.p);
+  __nv_bfloat16* Qa = reinterpret_cast<__nv_bfloat16*>(base);
+  __nv_bfloat16* Qb = same ? Qa : reinterpret_cast<__nv_bfloat16*>(base + up(qa_bytes));
+  int32_t* Ea = reinterpret_cast<int32_t*>(base + up(qa_bytes) + up(qb_bytes));
+  int32_t* Eb = same ? Ea : reinterpret_cast<int32_t*>(base + up(qa_bytes) + up(qb_bytes) + up(ea_bytes));
+  int32_t* bal = b_rows ? nullptr
+                        : reinterpret_cast<int32_t*>(base + up(qa_bytes) + up(qb_bytes) + up(ea_bytes) + up(eb_bytes));
+  float* Pw =
+      reinterpret_cast<float*>(base + up(qa_bytes) + up(qb_bytes) + up(ea_bytes) + up(eb_bytes) + up(bal_bytes));
+
+  // C = A B with B (K x Nc): every K index k is balanced first, row k of B by
+  // 2^{-s_k} and column k of A by 2^{s_k} (exact), s_k the exponent of B's row
+  // maximum, so that rows of B with very different norms (the filtered states
+  // of Y_hat^T = U^{-T} Y^T) do not share one column scale.
+  if (!b_rows) {
+    k_row_exponents<<<(unsigned)K, 256, 0, st>>>(B, ldb, Nc, bal);
+    count_launch();
+    DG_CUDA(cudaGetLastError());
+  }
+  k_split_rows<<<dim3((unsigned)M, (unsigned)nch), 256, 0, st>>>(A, lda, K, s, a_lower ? 1 : 0, bal, Qa, lqa, sa,
+                                                                  Ea, nch, flag);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  if (!same) {
+    if (b_rows)
+      k_split_rows<<<dim3((unsigned)Nc, (unsigned)nch), 256, 0, st>>>(B, ldb, K, s, 0, nullptr, Qb, lqb, sb, Eb, nch,
+                                                                       flag);
+    else
+      k_split_cols<<<dim3((unsigned)((Nc + kCols - 1) / kCols), (unsigned)nch), 256, 0, st>>>(
+          B, ldb, K, Nc, s, bal, Qb, lqb, sb, Eb, nch, flag);
+    count_launch();
+    DG_CUDA(cudaGetLastError());
+  }
+  const float one = 1.0f, zero = 0.0f;
+  for (int64_t n0 = 0; n0 < Nc; n0 += P) {
+    const int64_t pn = std::min<int64_t>(P, Nc - n0);
+    for (int chunk = 0; chunk < nch; ++chunk) {
+      const int64_t k0 = (int64_t)chunk * kL;
+      const int kc = (int)std::min<int64_t>(kL, K - k0);
+      // Column-major view: (pn x M) slab of pair (i, j) = op(Qb_j) (pn x kc) * Qa_i (kc x M).
+      for (int i = 0; i < s; ++i) {
+        const int64_t p0 = (int64_t)i * s - (int64_t)i * (i - 1) / 2;
+        const __nv_bfloat16* bq = b_rows ? Qb + n0 * lqb + k0 : Qb + k0 * lqb + n0;
+        DG_BLAS(cublasGemmStridedBatchedEx(h, b_rows ? CUBLAS_OP_T : CUBLAS_OP_N, CUBLAS_OP_N, (int)pn, (int)M, kc,
+                                           &one, bq, CUDA_R_16BF, (int)lqb, sb, Qa + i * sa + k0, CUDA_R_16BF,
+                                           (int)lqa, 0, &zero, Pw + p0 * M * pn, CUDA_R_32F, (int)pn, M * pn, s - i,
+                                           CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT));
+      }
+      const int64_t total = M * pn;
+      const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+      k_sliced_reduce<<<grid, 256, 0, st>>>(Pw, M, pn, s, Ea, Eb, nch, chunk, n0, C, ldc, chunk > 0 ? 1 : 0);
+      count_launch();
+      DG_CUDA(cudaGetLastError());
+    }
+  }
+  return DGCHEFSI_OK;
+}
+
+void sliced_destroy(dgchefsi_ctx* ctx) {
+  if (ctx->blas) cublasDestroy(static_cast<cublasHandle_t>(ctx->blas));
+  ctx->blas = nullptr;
+}
+
+}  // namespace dg

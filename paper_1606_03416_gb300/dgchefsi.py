@@ -30,10 +30,14 @@ EXPORTS = ["dgchefsi_create", "dgchefsi_destroy", "dgchefsi_set_stream", "dgchef
            "dgchefsi_bounds_static", "dgchefsi_gram", "dgchefsi_set_values", "dgchefsi_energy_grad",
            "dgchefsi_filter_graph", "dgchefsi_set_tile_shape", "dgchefsi_get_tile_shape",
            "dgchefsi_selftest_wait", "dgchefsi_set_orthonormalisation", "dgchefsi_density_pattern",
-           "dgchefsi_realign", "dgchefsi_filter_host"]
+           "dgchefsi_realign", "dgchefsi_filter_host", "dgchefsi_set_subspace_products",
+           "dgchefsi_sliced_gemm"]
 
 # Orthonormalisations of Alg. 1 step 3 (dgchefsi_set_orthonormalisation).
 ORTHONORMALISATIONS = {"cholqr": 0, "cholqr2": 1, "shifted_cholqr3": 2}
+
+# Arithmetic of the Rayleigh-Ritz products (dgchefsi_set_subspace_products).
+SUBSPACE_PRODUCTS = {"f64": 0, "sliced_bf16": 1}
 
 # Capacity (doubles) of the library's fixed scratch array for bounds_static.
 BOUNDS_STATIC_DOUBLES = 1 << 20
@@ -67,6 +71,8 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_get_tile_shape": (st, [P, C.c_int, P, P, P, P]),
         "dgchefsi_selftest_wait": (st, [P, I64]),
         "dgchefsi_set_orthonormalisation": (st, [P, C.c_int]),
+        "dgchefsi_set_subspace_products": (st, [P, C.c_int, C.c_int]),
+        "dgchefsi_sliced_gemm": (st, [P, C.c_int, C.c_int, I64, I64, I64, P, I64, P, I64, P, I64, C.c_int]),
         "dgchefsi_density_pattern": (st, [P, P, I64, I64, P, P]),
         "dgchefsi_realign": (st, [P, P, P, P, P, P, I64, I64, P, I64]),
         "dgchefsi_filter_host": (st, [P, C.c_int, P, P, I64, I64, C.c_int, D, D, D, I64]),
@@ -299,6 +305,32 @@ class Context:
     def set_orthonormalisation(self, mode: str):
         """"cholqr" (Alg. 1 step 3 as in the paper), "cholqr2" or "shifted_cholqr3"."""
         _check(_lib.dgchefsi_set_orthonormalisation(self._h, ORTHONORMALISATIONS[mode]))
+
+    def set_subspace_products(self, mode: str, slices: int = 10):
+        """"f64" (FP64 cores) or "sliced_bf16" (FP64 products rebuilt from
+        `slices` exact BF16 slices per operand on the tensor cores) for the
+        Gram, Y U^-1, projected-H and rotation products of Rayleigh-Ritz."""
+        _check(_lib.dgchefsi_set_subspace_products(self._h, SUBSPACE_PRODUCTS[mode], int(slices)))
+
+    def sliced_gemm(self, A: torch.Tensor, B: torch.Tensor, b_rows: bool = True, a_lower: bool = False,
+                    slices: int = 10, out: torch.Tensor | None = None) -> torch.Tensor:
+        """A @ B.T (b_rows) or A @ B in FP64 from exact BF16 slices. A, B: 2-D
+        float64 CUDA tensors, rows contiguous; a_lower treats A as lower triangular."""
+        for name, T in (("A", A), ("B", B)):
+            if not (T.is_cuda and T.dtype == torch.float64 and T.dim() == 2 and T.stride(1) == 1):
+                raise TypeError(f"{name} must be a 2-D float64 CUDA tensor with contiguous rows")
+        M, K = A.shape
+        Nc = B.shape[0] if b_rows else B.shape[1]
+        if (B.shape[1] if b_rows else B.shape[0]) != K:
+            raise ValueError("inner dimensions differ")
+        if out is None:
+            out = torch.empty((M, Nc), dtype=torch.float64, device=A.device)
+        if not (out.is_cuda and out.dtype == torch.float64 and out.shape == (M, Nc) and out.stride(1) == 1):
+            raise TypeError("out must be a float64 CUDA tensor of shape (M, Nc) with contiguous rows")
+        self._sync_stream()
+        _check(_lib.dgchefsi_sliced_gemm(self._h, int(b_rows), int(a_lower), M, Nc, K, _ptr(A), A.stride(0),
+                                         _ptr(B), B.stride(0), _ptr(out), out.stride(0), int(slices)))
+        return out
 
     # -- Sec. III.B.3: coefficients carried to the next SCF step's basis
     def realign(self, X_old: torch.Tensor, nb_old, nr, V_old: torch.Tensor, V_new: torch.Tensor,

@@ -1,0 +1,212 @@
+"""FP64 products rebuilt from exact BF16 slices on the tensor cores (the Ozaki
+scheme) and the Rayleigh-Ritz step / cycle that uses them, through the C ABI.
+
+* Integer operands of at most 12 bits: every slice is exact after two slices,
+  every slice-pair product is an exactly accumulated integer, and the FP64
+  sums are exact, so the result equals the exact integer product bit for bit
+  (ragged K chunks, strided operands, both operand layouts, triangular A).
+* Gaussian operands with rows scaled over e^{+-3}: |C - A B| within the
+  splitting bound sum over chunks of L m_r n_c (2^{-6s}(s + 4) + (5 + chunks) u)
+  plus FP64's own bound on the reference product; fewer slices are less
+  accurate.
+* Cycles with the sliced products match the FP64 oracle at the FP64 path's
+  tolerances (Ritz values 1e-10 of max(|a0|, |b|), density blocks 1e-9), on
+  blocks with one and with several K chunks, and the tiny problem converges
+  to the dense spectrum.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import chefsi as O
+from paper_1606_03416_gb300 import inputs as G
+
+pytestmark = pytest.mark.gpu
+
+D = pytest.importorskip("paper_1606_03416_gb300.dgchefsi") if torch.cuda.is_available() else None
+dev = torch.device("cuda:0")
+U = 2.0 ** -53
+L_CHUNK = 4096
+
+
+def tiny_ctx():
+    H, _, _, _, _ = G.make_problem(G.CONFIGS["tiny_2x2x2"])
+    return D.Context(H)
+
+
+def strided(a, pad=3, fill=7.0):
+    """a as a CUDA tensor whose rows are `pad` entries longer than its width."""
+    big = torch.full((a.shape[0], a.shape[1] + pad), fill, dtype=torch.float64, device=dev)
+    big[:, :a.shape[1]] = torch.from_numpy(np.ascontiguousarray(a))
+    return big[:, :a.shape[1]]
+
+
+@pytest.mark.parametrize("b_rows,a_lower", [(True, False), (False, False), (False, True), (True, True)])
+@pytest.mark.parametrize("slices", [3, 10])
+def test_integer_operands_bit_exact(b_rows, a_lower, slices):
+    rng = np.random.default_rng(11)
+    M, Nc, K = 190, 333, 2 * L_CHUNK + 1000
+    A = rng.integers(-2047, 2048, size=(M, K)).astype(np.int64)
+    A[5] = rng.integers(-5, 6, size=K)           # a row of small integers (one slice)
+    Bm = rng.integers(-2047, 2048, size=(Nc, K) if b_rows else (K, Nc)).astype(np.int64)
+    Aeff = np.tril(A) if a_lower else A
+    ref = (Aeff @ (Bm.T if b_rows else Bm)).astype(np.float64)   # exact: |entries| < 2^36
+    with tiny_ctx() as ctx:
+        out = torch.full((M, Nc + 5), -1.0, dtype=torch.float64, device=dev)
+        ctx.sliced_gemm(strided(A.astype(np.float64)), strided(Bm.astype(np.float64), pad=8), b_rows=b_rows,
+                        a_lower=a_lower, slices=slices, out=out[:, :Nc])
+        got = out.cpu().numpy()
+    assert np.array_equal(got[:, :Nc], ref)
+    assert np.all(got[:, Nc:] == -1.0)
+
+
+def splitting_bound(A, B, s, balance=False):
+    """Sum over K chunks of L m_r n_c (2^{-6s}(s + 4) + (5 + chunks) u), B given
+    as the rows of the right operand's transpose. balance: the operands as the
+    A B form splits them, column k of A times 2^{s_k} and row k of the right
+    operand times 2^{-s_k}, s_k the exponent of that row's maximum."""
+    if balance:
+        sk = np.frexp(np.abs(B).max(axis=0))[1]
+        A, B = np.ldexp(A, sk[None, :]), np.ldexp(B, -sk[None, :])
+    K = A.shape[1]
+    nch = -(-K // L_CHUNK)
+    bound = np.zeros((A.shape[0], B.shape[0]))
+    for c in range(nch):
+        a = A[:, c * L_CHUNK:(c + 1) * L_CHUNK]
+        b = B[:, c * L_CHUNK:(c + 1) * L_CHUNK]
+        L = a.shape[1]
+        bound += L * np.outer(np.abs(a).max(1), np.abs(b).max(1)) * (2.0 ** (-6 * s) * (s + 4) + (5 + nch) * U)
+    return bound
+
+
+@pytest.mark.parametrize("b_rows", [True, False])
+def test_gaussian_operands_within_bound(b_rows):
+    rng = np.random.default_rng(3)
+    M, Nc, K = 256, 320, 2 * L_CHUNK + 808
+    A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-3, 3, (M, 1)))
+    B = rng.standard_normal((Nc, K)) * np.exp(rng.uniform(-3, 3, (Nc, 1)))   # B as rows of B^T
+    ref = A @ B.T
+    absab = np.abs(A) @ np.abs(B).T
+    gamma = K * U / (1 - K * U)
+    errs = {}
+    with tiny_ctx() as ctx:
+        Bd = torch.from_numpy(B if b_rows else np.ascontiguousarray(B.T)).to(dev)
+        for s in (7, 10):
+            got = ctx.sliced_gemm(torch.from_numpy(A).to(dev), Bd, b_rows=b_rows, slices=s).cpu().numpy()
+            err = np.abs(got - ref)
+            assert np.all(err <= splitting_bound(A, B, s, balance=not b_rows) + gamma * absab), s
+            errs[s] = float(np.max(err / absab))
+    print(f"SLICED b_rows={b_rows} max |C - A B| / (|A||B|): s=7 {errs[7]:.2e}, s=10 {errs[10]:.2e}")
+    assert errs[10] <= 1e-15 < errs[7]
+
+
+def test_edge_sizes_and_errors():
+    rng = np.random.default_rng(5)
+    with tiny_ctx() as ctx:
+        A = torch.empty((7, 0), dtype=torch.float64, device=dev)
+        B = torch.empty((9, 0), dtype=torch.float64, device=dev)
+        out = torch.full((7, 9), 3.0, dtype=torch.float64, device=dev)
+        ctx.sliced_gemm(A, B, out=out)                      # K = 0: C = 0
+        assert torch.all(out == 0.0)
+        A1 = rng.standard_normal((1, 5))
+        B1 = rng.standard_normal((1, 5))
+        got = ctx.sliced_gemm(torch.from_numpy(A1).to(dev), torch.from_numpy(B1).to(dev)).item()
+        assert abs(got - (A1 @ B1.T).item()) <= 1e-15 * (np.abs(A1) @ np.abs(B1).T).item()
+        Abad = torch.from_numpy(rng.standard_normal((20, 50))).to(dev)
+        Abad[3, 7] = float("nan")
+        with pytest.raises(D.DGChefsiError) as e:
+            ctx.sliced_gemm(Abad, torch.from_numpy(rng.standard_normal((4, 50))).to(dev))
+        assert e.value.status == "ERR_NONFINITE"
+        for s in (1, 17):
+            with pytest.raises(D.DGChefsiError) as e:
+                ctx.sliced_gemm(Abad, Abad, slices=s)
+            assert e.value.status == "ERR_ARG"
+            with pytest.raises(D.DGChefsiError) as e:
+                ctx.set_subspace_products("sliced_bf16", s)
+            assert e.value.status == "ERR_ARG"
+        with pytest.raises(D.DGChefsiError) as e:
+            D._check(D._lib.dgchefsi_set_subspace_products(ctx._h, 5, 10))
+        assert e.value.status == "ERR_ARG"
+
+
+def cycle_configs():
+    tiny = G.CONFIGS["tiny_2x2x2"]
+    uneven = G.ProblemConfig(name="uneven", grid=(3, 2, 2), periodic=(True, False, True), stencil="27",
+                             nb=(40, 120), Ns=100, m=7, Ne=150.0, seed=5)
+    bulk = G.scaled_copy(G.CONFIGS["bulk3d_8x8x8"], grid=(5, 4, 4), nb=64, Ns=200, m=10, name="bulk5x4x4")
+    return [tiny, uneven, bulk]   # N = 256, ~1000, 5120 (two K chunks, the second ragged)
+
+
+@pytest.mark.parametrize("cfg", cycle_configs(), ids=lambda c: c.name)
+def test_cycles_with_sliced_products_match_oracle(cfg):
+    H, X0, v0, Ns, Ne = G.make_problem(cfg)
+    Ho = O.DGHamiltonian.from_blocksparse(H)
+    with D.Context(H) as ctx:
+        ctx.set_subspace_products("sliced_bf16", 10)
+        X = torch.from_numpy(X0).to(dev)
+        v = torch.from_numpy(v0).to(dev)
+        prev = None
+        for cyc in range(3):
+            Xin = X.cpu().numpy().T.copy()
+            out = ctx.cycle(X, cfg.m, Ne, cfg.kT, v0=v, prev_ritz=prev)
+            a, b, a0 = out["bounds"]
+            ref = O.chefsi_cycle(Ho, Xin, cfg.m, Ne, cfg.kT, v0, bounds=(a, b, a0))
+            scale = max(abs(a0), abs(b))
+            ritz = out["ritz"].cpu().numpy()
+            er = np.max(np.abs(ritz - ref["ritz"])) / scale
+            Pr = O.packed_density(Ho, ref["P"])
+            ep = np.linalg.norm(out["P"].cpu().numpy() - Pr) / np.linalg.norm(Pr)
+            print(f"SLICED cycle {cfg.name} {cyc}: ritz {er:.2e}, density {ep:.2e}")
+            assert er <= 1e-10 and ep <= 1e-9, cyc
+            prev = ritz
+
+
+def test_tiny_converges_with_sliced_products():
+    cfg = G.CONFIGS["tiny_2x2x2"]
+    H, X0, v0, Ns, Ne = G.make_problem(cfg)
+    lam = np.linalg.eigvalsh(O.DGHamiltonian.from_blocksparse(H).dense())
+    with D.Context(H) as ctx:
+        ctx.set_subspace_products("sliced_bf16")
+        X = torch.from_numpy(X0).to(dev)
+        v = torch.from_numpy(v0).to(dev)
+        prev = None
+        for _ in range(cfg.cycles):
+            prev = ctx.cycle(X, cfg.m, Ne, cfg.kT, v0=v, prev_ritz=prev)["ritz"].cpu().numpy()
+    g = 8
+    assert np.max(np.abs(prev[:Ns - g] - lam[:Ns - g])) <= 1e-10 * max(abs(lam[0]), abs(lam[-1]))
+
+
+def test_full_bulk_rayleigh_ritz_sliced_vs_f64_products():
+    """8x8x8 workload (N = 32768, N_s = 4096: eight K chunks for the Gram and
+    projected-H products, 4096 for the triangular and rotation products), in
+    the bench's configuration: a BF16x3-filtered block after one mixed cycle
+    (warm), Rayleigh-Ritz with FP64 products and with sliced products from the
+    same block. Ritz values agree to the FP64 tolerance, the rotated blocks are
+    orthonormal, and the density blocks of the occupied states agree."""
+    cfg = G.CONFIGS["bulk3d_8x8x8"]
+    H = G.make_blocks(cfg)
+    Ns, Ne = G.resolve_sizes(cfg, H)
+    X0 = G.make_X(H.N, Ns, cfg.seed)
+    v0 = G.make_start_vector(H.N, cfg.seed)
+    with D.Context(H) as ctx:
+        X = torch.from_numpy(X0).cuda()
+        out = ctx.cycle(X, cfg.m, Ne, cfg.kT, v0=torch.from_numpy(v0).cuda(), prec="bf16x3")
+        r = out["ritz"].cpu().numpy()
+        b = out["bounds"][1]
+        Y = ctx.filter(X, cfg.m, float(r[-1]), b, float(r[0]), prec="bf16x3")
+        Y2 = Y.clone()
+        ritz = {}
+        P = {}
+        for mode, Yb in (("f64", Y), ("sliced_bf16", Y2)):
+            ctx.set_subspace_products(mode)
+            ritz[mode] = ctx.rayleigh_ritz(Yb)
+            f, _ = ctx.occupations(ritz[mode], Ne, cfg.kT)
+            P[mode] = ctx.density_blocks(Yb, f)
+            G_ = Yb @ Yb.T
+            G_.diagonal().sub_(1.0)
+            assert float(G_.abs().max()) <= 1e-12, mode
+        scale = max(abs(float(r[0])), abs(b))
+        er = float((ritz["f64"] - ritz["sliced_bf16"]).abs().max()) / scale
+        ep = float(torch.linalg.norm(P["f64"] - P["sliced_bf16"]) / torch.linalg.norm(P["f64"]))
+    print(f"SLICED full 8x8x8 warm: ritz {er:.2e}, density {ep:.2e}")
+    assert er <= 1e-10 and ep <= 1e-9

@@ -585,6 +585,37 @@ def measure_sliced(ctx, X_warm, state, cycle, vd, Ns, N, m, Ne, kT, args, dev, b
     return out
 
 
+def run_rr_only(args):
+    """One Rayleigh-Ritz step (Alg. 1 steps 3-5) on the workload's BF16x3-filtered
+    first block, with --subspace products, bracketed by cudaProfilerStart/Stop
+    (profiling case: ncu --profile-from-start off sees only this call). A first
+    call on a copy of the block sets up the workspace outside the bracket."""
+    import torch
+    from paper_1606_03416_gb300 import dgchefsi as D
+    from paper_1606_03416_gb300 import inputs as G
+    dev = torch.device("cuda:0")
+    cfg = G.CONFIGS[args.workload]
+    H, X0, v0, Ns, Ne = G.make_problem(cfg)
+    stream = torch.cuda.current_stream()
+    with D.Context(H) as ctx:
+        ctx.set_subspace_products("sliced_bf16" if args.subspace == "sliced" else "f64", max(args.slices, 2))
+        b, tmin = ctx.bounds(torch.from_numpy(v0).to(dev), 10)
+        X = torch.from_numpy(X0).to(dev)
+        Y = ctx.filter(X, cfg.m, tmin + (b - tmin) * Ns / H.N, b, tmin, prec="bf16x3")
+        ctx.rayleigh_ritz(Y.clone())
+        s_, e_ = torch.cuda.Event(True), torch.cuda.Event(True)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        s_.record(stream)
+        ctx.rayleigh_ritz(Y)
+        e_.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+    print(json.dumps({"mode": "rr_only", "workload": cfg.name, "subspace": args.subspace, "slices": args.slices,
+                      "ms": s_.elapsed_time(e_)}), flush=True)
+    return 0
+
+
 def run_converge(args):
     """Cycles to the 1e-8 target: from the same random start, CheFSI cycles in the
     mixed form (--prec) and in FP64 until the Ritz values of the occupied states
@@ -680,6 +711,8 @@ def main():
                     help="cycles to Ritz error <= 1e-8 against a dense eigensolve, mixed and FP64")
     ap.add_argument("--max-cycles", type=int, default=40)
     ap.add_argument("--gram-only", action="store_true", help="time one FP64 Gram (profiling case)")
+    ap.add_argument("--rr-only", action="store_true", help="one Rayleigh-Ritz step (profiling case)")
+    ap.add_argument("--subspace", default="sliced", choices=["f64", "sliced"], help="with --rr-only")
     ap.add_argument("--slices", type=int, default=10,
                     help="BF16 slices of the sliced Rayleigh-Ritz products measured beside the FP64 ones (0: skip)")
     ap.add_argument("--forms", default="",
@@ -701,6 +734,8 @@ def main():
         return run_converge(args)
     if args.gram_only:
         return run_gram_only(args)
+    if args.rr_only:
+        return run_rr_only(args)
 
     import torch
     rank, world, local = dist_env()

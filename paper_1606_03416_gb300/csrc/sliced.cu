@@ -28,6 +28,7 @@
 #include <cublas_v2.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "ctx.h"
 
@@ -41,10 +42,74 @@ __device__ __forceinline__ void atomic_flag(int* flag) {
   if (flag) atomicOr(flag, 1);
 }
 
+// |x| = M 2^{E - 1075} with M normalised to [2^52, 2^53) (subnormals too).
+// Returns 0 for zero, 1 for a finite nonzero x, 2 for NaN/Inf. The frexp
+// exponent of x (|x| = f 2^e, f in [0.5, 1)) is E - 1022.
+__device__ __forceinline__ int decompose(double x, int64_t& M, int& E) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int Eb = (int)((u >> 52) & 0x7ff);
+  const long long m = (long long)(u & 0xfffffffffffffULL);
+  if (Eb == 0x7ff) return 2;
+  if (Eb == 0) {
+    if (m == 0) return 0;
+    const int sh = __clzll(m) - 11;  // bring the leading bit to position 52
+    M = m << sh;
+    E = 1 - sh;
+    return 1;
+  }
+  M = m | (1LL << 52);
+  E = Eb;
+  return 1;
+}
+
+// Slices of v = x 2^{-e'} (|v| < 1), where x = (-1)^neg M 2^{E - 1075} and
+// base = -1075 - e' + 6s, s <= 10: F = round(v 2^{6s}) as a 64-bit integer
+// (|F| <= 2^60, |v 2^{6s} - F| <= 1/2), then its balanced base-64 digits
+// q_{s-1}, ..., q_1 in [-32, 31] and the leading q_0 = the rest, |q_0| <= 64;
+// v = sum_i q_i 2^{-6(i+1)} up to 2^{-6s}/2. Integer arithmetic only.
+__device__ __forceinline__ void slice_fixed(int64_t M, int E, bool neg, int base, int s,
+                                            __nv_bfloat16* __restrict__ q, int64_t stride) {
+  const int sh = E + base;
+  int64_t F = 0;
+  if (M != 0) {
+    if (sh >= 0)
+      F = M << sh;
+    else if (sh > -54)
+      F = (M + (1LL << (-sh - 1))) >> (-sh);
+  }
+  if (neg) F = -F;
+  for (int i = s - 1; i >= 1; --i) {
+    const int64_t d = ((F + 32) & 63) - 32;
+    q[i * stride] = __float2bfloat16_rn((float)(int)d);
+    F = (F - d) >> 6;
+  }
+  q[0] = __float2bfloat16_rn((float)(int)F);
+}
+
+// The same digits for s > 10 (F would not fit 64 bits): v is scaled in FP64,
+// each digit rounded to nearest and subtracted (every step exact).
+__device__ __forceinline__ void slice_fp64(double v, int s, __nv_bfloat16* __restrict__ q, int64_t stride) {
+  double r = v;
+  for (int i = 0; i < s; ++i) {
+    r *= 64.0;
+    const double d = rint(r);
+    r -= d;
+    q[i * stride] = __float2bfloat16_rn((float)d);
+  }
+}
+
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 // One CTA per (row, chunk), 256 threads, 16 entries each. Q: s slices of
-// rows x ldq BF16 (slice i at Q + i * sstride); E[row * nch + chunk] = e_r.
+// rows x ldq BF16 (slice i at Q + i * sstride); E[row * nch + chunk] = e_r, the
+// frexp exponent of the row's largest |entry| in the chunk (0 if all are zero).
 // lower: entries k > row are zero (a lower-triangular operand). bal (may be
-// null): entry k is split as X[row, k] 2^{bal[k]}.
+// null): entry k is split as X[row, k] 2^{bal[k]}. A row chunk holding NaN/Inf
+// gets zero slices and raises flag.
 __global__ void __launch_bounds__(256) k_split_rows(const double* __restrict__ X, int64_t ldx, int64_t K, int s,
                                                     int lower, const int32_t* __restrict__ bal,
                                                     __nv_bfloat16* __restrict__ Q, int64_t ldq, int64_t sstride,
@@ -53,55 +118,56 @@ __global__ void __launch_bounds__(256) k_split_rows(const double* __restrict__ X
   const int chunk = blockIdx.y;
   const int64_t k0 = (int64_t)chunk * kL;
   double v[16];
-  double mx = 0.0;
+  int emax = INT_MIN;
   bool bad = false;
 #pragma unroll
   for (int u = 0; u < 16; ++u) {
     const int64_t k = k0 + threadIdx.x + 256 * u;
     double x = 0.0;
-    if (k < K && !(lower && k > row)) {
-      x = X[row * ldx + k];
-      if (bal) x = ldexp(x, bal[k]);
-    }
-    if (!isfinite(x)) bad = true;
+    if (k < K && !(lower && k > row)) x = X[row * ldx + k];
     v[u] = x;
-    mx = fmax(mx, fabs(x));
+    int64_t M;
+    int Ex;
+    const int c = decompose(x, M, Ex);
+    if (c == 2) bad = true;
+    if (c == 1) emax = max(emax, Ex + (bal ? bal[k] : 0));
   }
-  __shared__ double red[8];
+  __shared__ int red[8];
   __shared__ int sbad;
   if (threadIdx.x == 0) sbad = 0;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  emax = warp_max(emax);
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
   if (bad) sbad = 1;
   __syncthreads();
-  mx = red[0];
+  emax = red[0];
 #pragma unroll
-  for (int w = 1; w < 8; ++w) mx = fmax(mx, red[w]);
-  int e = 0;
-  if (sbad) {
-    mx = 0.0;
-    if (threadIdx.x == 0) atomic_flag(flag);
+  for (int w = 1; w < 8; ++w) emax = max(emax, red[w]);
+  const bool zero = sbad != 0;
+  const int e = (emax == INT_MIN || zero) ? 0 : emax - 1022;
+  if (threadIdx.x == 0) {
+    E[row * nch + chunk] = e;
+    if (zero) atomic_flag(flag);
   }
-  if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)
-  if (threadIdx.x == 0) E[row * nch + chunk] = e;
 #pragma unroll
   for (int u = 0; u < 16; ++u) {
     const int64_t k = k0 + threadIdx.x + 256 * u;
     if (k >= K) break;
-    double r = sbad ? 0.0 : ldexp(v[u], -e);
-    for (int i = 0; i < s; ++i) {
-      r *= (double)(1 << kBeta);
-      const double q = rint(r);
-      r -= q;
-      Q[i * sstride + row * ldq + k] = __float2bfloat16_rn((float)q);
+    __nv_bfloat16* q = Q + row * ldq + k;
+    const int b = bal ? bal[k] : 0;
+    if (s <= 10) {
+      int64_t M = 0;
+      int Ex = 0;
+      if (zero || decompose(v[u], M, Ex) != 1) M = 0;
+      slice_fixed(M, Ex + b, v[u] < 0.0, -1075 - e + 6 * s, s, q, sstride);
+    } else {
+      slice_fp64(zero ? 0.0 : ldexp(v[u], b - e), s, q, sstride);
     }
   }
 }
 
 // One CTA per (64 columns, chunk) of a row-major K x C operand, 256 threads:
-// lane group of 64 columns x 4 row phases. Column maxima first, then the
+// lane group of 64 columns x 4 row phases. Column exponents first, then the
 // slices (the second read of the chunk comes from L2). Q: s slices of
 // K x ldq BF16; E[col * nch + chunk] = f_c. Row k is split as X[k, :] 2^{-bal[k]}.
 __global__ void __launch_bounds__(256) k_split_cols(const double* __restrict__ X, int64_t ldx, int64_t K, int64_t C,
@@ -114,87 +180,121 @@ __global__ void __launch_bounds__(256) k_split_cols(const double* __restrict__ X
   const int chunk = blockIdx.y;
   const int64_t k0 = (int64_t)chunk * kL;
   const int64_t k1 = std::min<int64_t>(K, k0 + kL);
-  double mx = 0.0;
+  int emax = INT_MIN;
   bool bad = false;
   if (col < C)
     for (int64_t k = k0 + ph; k < k1; k += 4) {
-      const double x = ldexp(X[k * ldx + col], -bal[k]);
-      if (!isfinite(x)) bad = true;
-      mx = fmax(mx, fabs(x));
+      int64_t M;
+      int Ex;
+      const int c = decompose(X[k * ldx + col], M, Ex);
+      if (c == 2) bad = true;
+      if (c == 1) emax = max(emax, Ex - bal[k]);
     }
-  __shared__ double red[4][kCols];
+  __shared__ int red[4][kCols];
   __shared__ int sbad[kCols];
   if (ph == 0) sbad[cl] = 0;
-  red[ph][cl] = mx;
+  red[ph][cl] = emax;
   __syncthreads();
   if (bad) sbad[cl] = 1;
   __syncthreads();
-  mx = fmax(fmax(red[0][cl], red[1][cl]), fmax(red[2][cl], red[3][cl]));
-  const bool cbad = sbad[cl] != 0;
-  if (cbad) mx = 0.0;
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);
+  emax = max(max(red[0][cl], red[1][cl]), max(red[2][cl], red[3][cl]));
+  const bool zero = sbad[cl] != 0;
+  const int e = (emax == INT_MIN || zero) ? 0 : emax - 1022;
   if (col >= C) return;
   if (ph == 0) {
     E[col * nch + chunk] = e;
-    if (cbad) atomic_flag(flag);
+    if (zero) atomic_flag(flag);
   }
   for (int64_t k = k0 + ph; k < k1; k += 4) {
-    double r = cbad ? 0.0 : ldexp(X[k * ldx + col], -bal[k] - e);
-    for (int i = 0; i < s; ++i) {
-      r *= (double)(1 << kBeta);
-      const double q = rint(r);
-      r -= q;
-      Q[i * sstride + k * ldq + col] = __float2bfloat16_rn((float)q);
+    const double x = X[k * ldx + col];
+    __nv_bfloat16* q = Q + k * ldq + col;
+    if (s <= 10) {
+      int64_t M = 0;
+      int Ex = 0;
+      if (zero || decompose(x, M, Ex) != 1) M = 0;
+      slice_fixed(M, Ex - bal[k], x < 0.0, -1075 - e + 6 * s, s, q, sstride);
+    } else {
+      slice_fp64(zero ? 0.0 : ldexp(x, -bal[k] - e), s, q, sstride);
     }
   }
 }
 
-// bal[k] = exponent of max_c |X[k, c]| (X row-major K x C), 0 for a zero or
-// non-finite row (the split then flags the latter). One CTA per row.
+// bal[k] = frexp exponent of max_c |X[k, c]| (X row-major K x C), 0 for a row
+// with no finite nonzero entry. One CTA per row.
 __global__ void __launch_bounds__(256) k_row_exponents(const double* __restrict__ X, int64_t ldx, int64_t C,
                                                        int32_t* __restrict__ bal) {
   const int64_t k = blockIdx.x;
-  double mx = 0.0;
-  for (int64_t c = threadIdx.x; c < C; c += 256) mx = fmax(mx, fabs(X[k * ldx + c]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  __shared__ double red[8];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  int emax = INT_MIN;
+  for (int64_t c = threadIdx.x; c < C; c += 256) {
+    int64_t M;
+    int Ex;
+    if (decompose(X[k * ldx + c], M, Ex) == 1) emax = max(emax, Ex);
+  }
+  emax = warp_max(emax);
+  __shared__ int red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
   __syncthreads();
   if (threadIdx.x == 0) {
-    mx = red[0];
-    for (int w = 1; w < 8; ++w) mx = fmax(mx, red[w]);
-    int e = 0;
-    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
-    bal[k] = e;
+    for (int w = 1; w < 8; ++w) emax = max(emax, red[w]);
+    emax = max(emax, red[0]);
+    bal[k] = emax == INT_MIN ? 0 : emax - 1022;
   }
 }
 
-// C[r, n0 + c] (+)= 2^{e_r + f_{n0+c} - 12} sum_t 2^{-6t} sum_{i+j=t} P_{ij}[r, c]
-// for r < M, c < P. Pair (i, j) is slab i*s - i(i-1)/2 + j of P (M x P FP32).
-__global__ void k_sliced_reduce(const float* __restrict__ Pw, int64_t M, int64_t P, int s,
-                                const int32_t* __restrict__ Ea, const int32_t* __restrict__ Eb, int nch, int chunk,
-                                int64_t n0, double* __restrict__ C, int64_t ldc, int accumulate) {
+// C[r, n0 + c] (+)= 2^{e_r + f_{n0+c} - 12} sum_t 2^{-6t} g_t,  g_t = sum_{i+j=t} P_{ij}[r, c],
+// for r < M, c < P. Pair (i, j) is slab i*S - i(i-1)/2 + j of Pw (M x P FP32).
+// Each P_ij is an exact integer of magnitude <= 2^24, so g_t is summed in
+// int32 (|g_t| <= 16 * 2^24), five consecutive t are combined exactly in int64
+// (< 2^53, exact in FP64), and the blocks meet in FP64: one rounding per 30
+// bits of weight. Every slab value is loaded once, all loads of an output
+// before any use, so the kernel streams Pw at memory speed.
+template <int S>
+__global__ void __launch_bounds__(256) k_sliced_reduce(const float* __restrict__ Pw, int64_t M, int64_t P,
+                                                       const int32_t* __restrict__ Ea, const int32_t* __restrict__ Eb,
+                                                       int nch, int chunk, int64_t n0, double* __restrict__ C,
+                                                       int64_t ldc, int accumulate) {
+  constexpr int NB = (S + 4) / 5;  // blocks of five t
   const int64_t total = M * P;
   const int64_t slab = M * P;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
+    int g[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) g[t] = 0;
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+      for (int j = 0; j < S - i; ++j)
+        g[i + j] += __float2int_rn(__ldcs(Pw + (int64_t)(i * S - i * (i - 1) / 2 + j) * slab + idx));
+    // h = sum_b B_b 2^{-30 b}, B_b = sum_{t = 5b}^{5b+4} g_t 2^{6(5b + 4 - t)}; sum_t g_t 2^{-6t} = h 2^{-24}
+    double h = 0.0;
+#pragma unroll
+    for (int b = NB - 1; b >= 0; --b) {
+      int64_t B = 0;
+#pragma unroll
+      for (int t = 5 * b; t < 5 * b + 5; ++t) B = B * 64 + (t < S ? (int64_t)g[t] : 0);
+      h = h * 0x1p-30 + (double)B;
+    }
     const int64_t r = idx / P;
     const int64_t c = idx - r * P;
-    double acc = 0.0;
-    for (int t = s - 1; t >= 0; --t) {
-      double g = 0.0;
-      for (int i = 0; i <= t; ++i) {
-        const int j = t - i;
-        const int64_t p = (int64_t)i * s - (int64_t)i * (i - 1) / 2 + j;
-        g += (double)Pw[p * slab + idx];
-      }
-      acc = acc * (1.0 / (double)(1 << kBeta)) + g;
-    }
-    const double v = ldexp(acc, Ea[r * nch + chunk] + Eb[(n0 + c) * nch + chunk] - 2 * kBeta);
+    const double v = ldexp(h, Ea[r * nch + chunk] + Eb[(n0 + c) * nch + chunk] - 12 - 24);
     double* out = C + r * ldc + n0 + c;
     *out = accumulate ? *out + v : v;
+  }
+}
+
+typedef void (*ReduceKernel)(const float*, int64_t, int64_t, const int32_t*, const int32_t*, int, int, int64_t,
+                             double*, int64_t, int);
+
+static ReduceKernel reduce_kernel(int s) {
+  switch (s) {
+#define DG_REDUCE_CASE(n) \
+  case n: return k_sliced_reduce<n>;
+    DG_REDUCE_CASE(2) DG_REDUCE_CASE(3) DG_REDUCE_CASE(4) DG_REDUCE_CASE(5) DG_REDUCE_CASE(6)
+    DG_REDUCE_CASE(7) DG_REDUCE_CASE(8) DG_REDUCE_CASE(9) DG_REDUCE_CASE(10) DG_REDUCE_CASE(11)
+    DG_REDUCE_CASE(12) DG_REDUCE_CASE(13) DG_REDUCE_CASE(14) DG_REDUCE_CASE(15) DG_REDUCE_CASE(16)
+#undef DG_REDUCE_CASE
+    default: return nullptr;
   }
 }
 
@@ -227,6 +327,7 @@ dgchefsi_status sliced_gemm(dgchefsi_ctx* ctx, bool b_rows, bool a_lower, int64_
                             const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int s,
                             int* flag) {
   if (M <= 0 || Nc <= 0) return DGCHEFSI_OK;
+  if (!reduce_kernel(s)) return set_error(DGCHEFSI_ERR_ARG, "slices = %d outside 2..16", s);
   cudaStream_t st = ctx->stream;
   if (K <= 0) {
     DG_CUDA(cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * Nc, M, st));
@@ -314,7 +415,7 @@ dgchefsi_status sliced_gemm(dgchefsi_ctx* ctx, bool b_rows, bool a_lower, int64_
       }
       const int64_t total = M * pn;
       const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
-      k_sliced_reduce<<<grid, 256, 0, st>>>(Pw, M, pn, s, Ea, Eb, nch, chunk, n0, C, ldc, chunk > 0 ? 1 : 0);
+      reduce_kernel(s)<<<grid, 256, 0, st>>>(Pw, M, pn, Ea, Eb, nch, chunk, n0, C, ldc, chunk > 0 ? 1 : 0);
       count_launch();
       DG_CUDA(cudaGetLastError());
     }

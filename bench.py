@@ -364,13 +364,15 @@ def run_adjoint(args):
             ctx.set_values(vals)
             return np.array(fds)
 
+        if args.no_fd:
+            picks = []
         fd = fd_values(1e-4, picks)
-        err64 = np.abs(fd - tied[picks]) / gmax
-        errtc = np.abs(fd - tied_tc[picks]) / gmax
+        err64 = np.abs(fd - tied[picks]) / gmax if picks else np.zeros(1)
+        errtc = np.abs(fd - tied_tc[picks]) / gmax if picks else np.zeros(1)
         # the same 8 entries at four step sizes: truncation error falls as h^2,
         # rounding noise of the energy grows as 1/h
         sweep = {}
-        for h in (1e-3, 1e-4, 1e-5, 1e-6):
+        for h in (() if args.no_fd else (1e-3, 1e-4, 1e-5, 1e-6)):
             f8 = fd_values(h, picks[:8])
             sweep[f"{h:g}"] = {"f64": float(np.max(np.abs(f8 - tied[picks[:8]])) / gmax),
                                tc: float(np.max(np.abs(f8 - tied_tc[picks[:8]])) / gmax)}
@@ -379,13 +381,23 @@ def run_adjoint(args):
         d = torch.from_numpy(0.5 * (r + r[mirror])).to(dev)
         dd64, ddtc = float((Hb * d).sum()), float((Hbt * d).sum())
         direc = {}
-        for h in (1e-3, 1e-4, 1e-5):
+        for h in (() if args.no_fd else (1e-3, 1e-4, 1e-5)):
             fdd = (energy_at(vals + h * d) - energy_at(vals - h * d)) / (2 * h)
             direc[f"{h:g}"] = {"fd": fdd, "rel_err_f64": abs(fdd - dd64) / abs(dd64),
                                f"rel_err_{tc}": abs(fdd - ddtc) / abs(dd64)}
         ctx.set_values(vals)
+        sliced_small = None
+        if args.slices > 0:
+            ctx.set_subspace_products("sliced_bf16", args.slices)
+            (Es, _, Hbs, Xbs), t_sl = timed(lambda: ctx.energy_grad(X, small.m, a, b, a0, Ne, small.kT, prec=tc))
+            ctx.set_subspace_products("f64", args.slices)
+            sliced_small = {"energy_rel": abs(Es - Et) / abs(Et),
+                            "grad_H_rel_max": float(np.max(np.abs(A.tie_symmetric(Hbs, mirror).cpu().numpy()
+                                                                  - tied_tc)) / gmax),
+                            "grad_X_rel_max": float((Xbs - Xbt).abs().max() / Xbt.abs().max()),
+                            "s_forward_backward": t_sl}
     out["fd_check_6x6x6"] = {
-        "N": H.N, "Ns": Ns, "m": small.m, "entries": 32, "h": 1e-4,
+        "N": H.N, "Ns": Ns, "m": small.m, "entries": len(picks), "h": 1e-4,
         "max_rel_err_vs_max_grad": {"f64": float(err64.max()), tc: float(errtc.max())},
         "max_rel_err_by_h_8_entries": sweep,
         "directional_derivative": {"analytic_f64": dd64, f"analytic_{tc}": ddtc, "by_h": direc},
@@ -393,6 +405,8 @@ def run_adjoint(args):
                          "grad_H_rel_max": float(np.max(np.abs(tied_tc - tied)) / gmax),
                          "grad_X_rel_max": float((Xbt - Xb).abs().max() / Xb.abs().max())},
         "s_forward_backward": {"f64": t_grad, tc: t_grad_tc}}
+    if sliced_small:
+        out["fd_check_6x6x6"][f"{tc}_sliced_vs_{tc}_f64_products"] = sliced_small
     if args.adjoint_full:
         H, X0, v0, Ns, Ne = G.make_problem(base)
         full = {"N": H.N, "Ns": Ns, "m": base.m, "checkpoint_stride": int(np.ceil(np.sqrt(base.m)))}
@@ -400,15 +414,29 @@ def run_adjoint(args):
             X = torch.from_numpy(X0).to(dev)
             v = torch.from_numpy(v0).to(dev)
             a, b, a0 = bounds_for(ctx, X, v, Ns, H.N)
-            precs = [tc] + (["f64"] if args.adjoint_f64 else [])
-            for p in precs:
+            forms = [(tc, "f64")] + ([(tc, "sliced")] if args.slices > 0 else []) + \
+                ([("f64", "f64")] if args.adjoint_f64 else [])
+            ref = None
+            for p, prod in forms:
+                ctx.set_subspace_products("sliced_bf16" if prod == "sliced" else "f64", max(args.slices, 2))
                 (E, _, _, _), t_fwd = timed(lambda: ctx.energy_grad(X, base.m, a, b, a0, Ne, base.kT, grad=False,
                                                                     prec=p))
                 (E2, _, Hb, Xb), t_all = timed(lambda: ctx.energy_grad(X, base.m, a, b, a0, Ne, base.kT, prec=p))
-                full[p] = {"s_forward": t_fwd, "s_forward_and_backward": t_all, "energy": E,
-                           "grad_norm_H": float(Hb.norm()), "grad_norm_X": float(Xb.norm())}
-                del Hb, Xb
+                key = p if prod == "f64" else f"{p}/sliced"
+                full[key] = {"s_forward": t_fwd, "s_forward_and_backward": t_all, "energy": E,
+                             "grad_norm_H": float(Hb.norm()), "grad_norm_X": float(Xb.norm())}
+                if p == tc and prod == "f64":
+                    ref = (E2, Hb, Xb)
+                else:
+                    if p == tc and ref is not None:
+                        full[key]["vs_f64_products"] = {
+                            "energy_rel": abs(E2 - ref[0]) / abs(ref[0]),
+                            "grad_H_rel_max": float((Hb - ref[1]).abs().max() / ref[1].abs().max()),
+                            "grad_X_rel_max": float((Xb - ref[2]).abs().max() / ref[2].abs().max())}
+                        ref = None
+                    del Hb, Xb
                 torch.cuda.empty_cache()
+            ctx.set_subspace_products("f64", max(args.slices, 2))
         out["full_12x12x12"] = full
     print(json.dumps(out), flush=True)
     return 0
@@ -707,6 +735,7 @@ def main():
     ap.add_argument("--adjoint", action="store_true", help="differentiation workload instead of the cycle")
     ap.add_argument("--adjoint-full", action="store_true", help="with --adjoint: also time the full 12^3 size")
     ap.add_argument("--adjoint-f64", action="store_true", help="with --adjoint-full: time the FP64 gradient too")
+    ap.add_argument("--no-fd", action="store_true", help="with --adjoint: skip the finite-difference checks")
     ap.add_argument("--converge", action="store_true",
                     help="cycles to Ritz error <= 1e-8 against a dense eigensolve, mixed and FP64")
     ap.add_argument("--max-cycles", type=int, default=40)

@@ -247,8 +247,10 @@ dgchefsi_status dgchefsi_set_orthonormalisation(dgchefsi_ctx* ctx, int mode);
  *                                  dgchefsi_sliced_gemm)
  *   slices  2..16 for the sliced form (ignored for FP64); 10 gives an error
  *           below the FP64 worst-case bound for rows of similar magnitude
- * ERR_ARG for another mode or slice count. H Y_hat stays on the FP64 cores; the
- * band-energy gradient and dgchefsi_gram always use FP64 products. */
+ * ERR_ARG for another mode or slice count. H Y_hat stays on the FP64 cores.
+ * dgchefsi_energy_grad follows the same setting for its forward products and
+ * the dense products of its adjoint (Z = U^{-1} Q, W_m = Z (2 G R^T));
+ * dgchefsi_gram always uses FP64 products. */
 #define DGCHEFSI_PRODUCTS_F64 0
 #define DGCHEFSI_PRODUCTS_SLICED_BF16 1
 dgchefsi_status dgchefsi_set_subspace_products(dgchefsi_ctx* ctx, int mode, int slices);

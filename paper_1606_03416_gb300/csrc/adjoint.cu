@@ -167,9 +167,26 @@ extern "C" dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, con
       ldc = N;
     }
   }
-  // ---- Cholesky-QR and Rayleigh-Ritz, keeping U^{-T} (L) and Q^T (row-major views)
+  // ---- Cholesky-QR and Rayleigh-Ritz, keeping U^{-T} (L) and Q^T (row-major views).
+  // The dense products run on the FP64 cores or from exact BF16 slices on the
+  // tensor cores, as the context's product setting says (non-finite operands
+  // of the sliced form raise info[3]).
+  const bool sl = ctx->products_mode == DGCHEFSI_PRODUCTS_SLICED_BF16;
+  const int nsl = ctx->products_slices;
+  int* bad = ctx->info_d + 3;
+  auto prod_nt = [&](const double* A_, const double* B_, double* C_) -> dgchefsi_status {  // C = A B^T, K = N
+    if (sl) return sliced_gemm(ctx, true, false, Ns, Ns, N, A_, N, B_, N, C_, Ns, nsl, bad);
+    DG_CUDA(gemm_nt_f64(A_, N, B_, N, C_, Ns, Ns, Ns, N, true, false, s));
+    return DGCHEFSI_OK;
+  };
+  auto prod_nn = [&](const double* A_, const double* B_, int64_t ldb_, int64_t cols, double* C_, int64_t ldc_,
+                     bool lower) -> dgchefsi_status {  // C = A B, A N_s x N_s, K = N_s
+    if (sl) return sliced_gemm(ctx, false, lower, Ns, cols, Ns, A_, Ns, B_, ldb_, C_, ldc_, nsl, bad);
+    DG_CUDA(gemm_nn_f64(A_, Ns, B_, ldb_, C_, ldc_, Ns, cols, Ns, lower, s));
+    return DGCHEFSI_OK;
+  };
   DG_CUDA(cudaMemsetAsync(ctx->info_d, 0, 4 * sizeof(int), s));
-  DG_CUDA(gemm_nt_f64(Yt, N, Yt, N, S, Ns, Ns, Ns, N, true, false, s));
+  DG_TRY(prod_nt(Yt, Yt, S));
   ADJ_SOLVER(cusolverDnSetStream(ctx->solver, s));
   int lw_potrf = 0, lw_syevd = 0;
   size_t lw_tr_d = 0, lw_tr_h = 0;
@@ -194,13 +211,13 @@ extern "C" dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, con
                               lw_tr_h, ctx->info_d + 1));
   DG_CUDA(zero_strict_upper_f64(S, Ns, Ns, s));  // S now holds L = U^{-T} exactly (lower)
   DG_CUDA(cudaMemcpyAsync(L, S, sizeof(double) * small, cudaMemcpyDeviceToDevice, s));
-  DG_CUDA(gemm_nn_f64(L, Ns, Yt, N, Yh, N, Ns, N, Ns, true, s));
+  DG_TRY(prod_nn(L, Yt, N, N, Yh, N, true));
   DG_CUDA(filter_step_f64(h, Yh, N, nullptr, HY, N, Ns, 1.0, 0.0, 0.0, s));
-  DG_CUDA(gemm_nt_f64(Yh, N, HY, N, S, Ns, Ns, Ns, N, true, false, s));
+  DG_TRY(prod_nt(Yh, HY, S));
   ADJ_SOLVER(cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n, S, n, lam, work, lwork,
                               ctx->info_d + 2));
-  DG_CUDA(gemm_nn_f64(S, Ns, Yh, N, XN, N, Ns, N, Ns, false, s));   // X_new^T = Q^T Y_hat^T
-  DG_CUDA(gemm_nn_f64(S, Ns, HY, N, HXN, N, Ns, N, Ns, false, s));  // (H X_new)^T
+  DG_TRY(prod_nn(S, Yh, N, N, XN, N, false));   // X_new^T = Q^T Y_hat^T
+  DG_TRY(prod_nn(S, HY, N, N, HXN, N, false));  // (H X_new)^T
   DG_CUDA(occupations_f64(lam, Ns, Ne, kT, f, mu, s));
   std::vector<double> lam_h(Ns), f_h(Ns);
   DG_CUDA(cudaMemcpyAsync(lam_h.data(), lam, sizeof(double) * Ns, cudaMemcpyDeviceToHost, s));
@@ -209,6 +226,7 @@ extern "C" dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, con
   DG_CUDA(cudaStreamSynchronize(s));
   if (info[1] != 0) return set_error(DGCHEFSI_ERR_NOT_SPD, "triangular inverse failed (info %d)", info[1]);
   if (info[2] != 0) return set_error(DGCHEFSI_ERR_NO_CONVERGENCE, "dense eigensolver failed (info %d)", info[2]);
+  if (sl && info[3] != 0) return set_error(DGCHEFSI_ERR_NONFINITE, "non-finite Rayleigh-Ritz operand");
   double E = 0.0;
   for (int64_t i = 0; i < Ns; ++i) E += f_h[i] * lam_h[i];
   if (!std::isfinite(E)) return set_error(DGCHEFSI_ERR_NONFINITE, "non-finite band energy");
@@ -240,8 +258,11 @@ extern "C" dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, con
   }
   // Y~bar = 2 R G Z^T, in state-major form Y~bar^T = Z (2 G R^T), Z^T = Q^T L
   DG_CUDA(scaled_residual_f64(HXN, XN, N, lam, g, 2.0, Ns, N, T0, N, s));
-  DG_CUDA(gemm_nn_f64(S, Ns, L, Ns, Z, Ns, Ns, Ns, Ns, false, s));  // Z^T = Q^T L
-  DG_CUDA(gemm_tn_f64(Z, Ns, T0, N, WA, N, Ns, N, Ns, s));         // W_m = Z (2 G R^T)
+  DG_TRY(prod_nn(S, L, Ns, Ns, Z, Ns, false));  // Z^T = Q^T L
+  if (sl)                                        // W_m = Z (2 G R^T)
+    DG_TRY(sliced_gemm_tn(ctx, Ns, N, Ns, Z, Ns, T0, N, WA, N, nsl, bad));
+  else
+    DG_CUDA(gemm_tn_f64(Z, Ns, T0, N, WA, N, Ns, N, Ns, s));
   if (tc) {
     DG_TRY(tc_grad_backward(ctx, prec, WA, Ns, m, stride, Hb, X_bar, ld));
     DG_CUDA(cudaStreamSynchronize(s));

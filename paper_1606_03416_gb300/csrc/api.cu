@@ -546,6 +546,7 @@ void dgchefsi_destroy(dgchefsi_ctx* ctx) {
   free_buf(ctx->ws_adjoint);
   free_buf(ctx->ws_realign);
   free_buf(ctx->ws_sliced);
+  free_buf(ctx->ws_sliced_t);
   for (int i = 0; i < 2; ++i) {
     free_buf(ctx->ws_hin[i]);
     free_buf(ctx->ws_hout[i]);

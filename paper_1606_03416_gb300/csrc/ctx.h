@@ -58,6 +58,7 @@ struct dgchefsi_ctx {
   int products_slices = 10;
   void* blas = nullptr;
   dg::DevBuf ws_sliced;
+  dg::DevBuf ws_sliced_t;  // transposed left operand of the A^T B form
   int32_t f64_tj = 64;    // column tile of the FP64 filter (set at create)
   // FP64 filter as a CUDA graph: coefficients copied from a pinned mirror at
   // every replay; the graph is captured again when X, Y, N_s, ld, m or the
@@ -134,6 +135,10 @@ void tc_destroy(dgchefsi_ctx* ctx);
 dgchefsi_status sliced_gemm(dgchefsi_ctx* ctx, bool b_rows, bool a_lower, int64_t M, int64_t Nc, int64_t K,
                             const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int s,
                             int* flag);
+// C (M x Nc) = A^T B with A (K x M, lda) and B (K x Nc, ldb) row-major: A is
+// transposed into a library buffer, then the A B form above.
+dgchefsi_status sliced_gemm_tn(dgchefsi_ctx* ctx, int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda,
+                               const double* B, int64_t ldb, double* C, int64_t ldc, int s, int* flag);
 void sliced_destroy(dgchefsi_ctx* ctx);
 
 }  // namespace dg

@@ -423,6 +423,39 @@ dgchefsi_status sliced_gemm(dgchefsi_ctx* ctx, bool b_rows, bool a_lower, int64_
   return DGCHEFSI_OK;
 }
 
+// T (cols x rows, row-major, ldt) = X^T for X (rows x cols, row-major, ldx);
+// 32 x 32 tiles through shared memory, 32 x 8 threads.
+__global__ void __launch_bounds__(256) k_transpose_f64(const double* __restrict__ X, int64_t ldx, int64_t rows,
+                                                       int64_t cols, double* __restrict__ T, int64_t ldt) {
+  __shared__ double tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int64_t r = r0 + j, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[j][threadIdx.x] = X[r * ldx + c];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int64_t c = c0 + j, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) T[c * ldt + r] = tile[threadIdx.x][j];
+  }
+}
+
+dgchefsi_status sliced_gemm_tn(dgchefsi_ctx* ctx, int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda,
+                               const double* B, int64_t ldb, double* C, int64_t ldc, int s, int* flag) {
+  if (M <= 0 || Nc <= 0) return DGCHEFSI_OK;
+  if (K > 0) {
+    if ((K + 31) / 32 > 65535) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "transpose of %lld rows", (long long)K);
+    DG_TRY(ensure(ctx, ctx->ws_sliced_t, sizeof(double) * (size_t)M * (size_t)K, "transposed operand"));
+    double* At = static_cast<double*>(ctx->ws_sliced_t.p);
+    k_transpose_f64<<<dim3((unsigned)((M + 31) / 32), (unsigned)((K + 31) / 32)), dim3(32, 8), 0, ctx->stream>>>(
+        A, lda, K, M, At, K);
+    count_launch();
+    DG_CUDA(cudaGetLastError());
+    return sliced_gemm(ctx, false, false, M, Nc, K, At, K, B, ldb, C, ldc, s, flag);
+  }
+  return sliced_gemm(ctx, false, false, M, Nc, K, A, lda, B, ldb, C, ldc, s, flag);
+}
+
 void sliced_destroy(dgchefsi_ctx* ctx) {
   if (ctx->blas) cublasDestroy(static_cast<cublasHandle_t>(ctx->blas));
   ctx->blas = nullptr;

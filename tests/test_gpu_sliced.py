@@ -210,3 +210,55 @@ def test_full_bulk_rayleigh_ritz_sliced_vs_f64_products():
         ep = float(torch.linalg.norm(P["f64"] - P["sliced_bf16"]) / torch.linalg.norm(P["f64"]))
     print(f"SLICED full 8x8x8 warm: ritz {er:.2e}, density {ep:.2e}")
     assert er <= 1e-10 and ep <= 1e-9
+
+
+def adjoint_case(kind):
+    if kind == "small":
+        cfg = G.ProblemConfig(name="adj", grid=(3, 2, 2), periodic=(True, False, True), stencil="27",
+                              nb=(4, 7), Ns=10, m=6, Ne=10.0, seed=11, kT=0.3)
+    elif kind == "tiny":
+        cfg = G.scaled_copy(G.CONFIGS["tiny_2x2x2"], Ns=48, m=7, Ne=64.0)
+        cfg = G.ProblemConfig(**{**cfg.__dict__, "kT": 0.05})
+    else:
+        cfg = G.scaled_copy(G.CONFIGS["bulk3d_8x8x8"], grid=(3, 3, 3), nb=16, Ns=64, m=9, Ne=96.0)
+    H, X0, _, Ns, Ne = G.make_problem(cfg)
+    Ho = O.DGHamiltonian.from_blocksparse(H)
+    lam = np.linalg.eigvalsh(Ho.dense())
+    return cfg, H, Ho, X0, Ns, Ne, (lam[min(Ns + 3, len(lam) - 1)], lam[-1] + 0.3, lam[0] - 0.3)
+
+
+@pytest.mark.parametrize("kind", ["small", "tiny", "bulk3"])
+def test_band_energy_gradient_with_sliced_products_matches_oracle(kind):
+    """The band-energy adjoint with the sliced products against the oracle's
+    adjoint, at the FP64 path's tolerances (E 1e-11, dE/dH and dE/dX 1e-8 of
+    their largest entry)."""
+    cfg, H, Ho, X0, Ns, Ne, (a, b, a0) = adjoint_case(kind)
+    E_o, G_o, Xb_o = O.band_energy_grad(Ho, X0.T, cfg.m, a, b, a0, Ne, cfg.kT)
+    with D.Context(H) as ctx:
+        ctx.set_subspace_products("sliced_bf16")
+        E, _, Hb, Xb = ctx.energy_grad(torch.from_numpy(X0).to(dev), cfg.m, a, b, a0, Ne, cfg.kT)
+    Gflat = np.concatenate([g.ravel() for g in G_o])
+    eH = float(np.max(np.abs(Hb.cpu().numpy() - Gflat)) / np.max(np.abs(Gflat)))
+    eX = float(np.max(np.abs(Xb.cpu().numpy() - Xb_o.T)) / np.max(np.abs(Xb_o)))
+    print(f"SLICED adjoint {kind}: E {abs(E - E_o) / abs(E_o):.2e}, dE/dH {eH:.2e}, dE/dX {eX:.2e}")
+    assert abs(E - E_o) <= 1e-11 * abs(E_o) and eH <= 1e-8 and eX <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["f64", "bf16x3"])
+def test_band_energy_gradient_sliced_vs_f64_products_two_chunks(prec):
+    """N = 5120 (two K chunks): with either filter form, the gradient with
+    sliced products equals the one with FP64-core products to the FP64
+    tolerances."""
+    cfg = G.scaled_copy(G.CONFIGS["bulk3d_8x8x8"], grid=(5, 4, 4), nb=64, Ns=200, m=10, Ne=300.0, name="adj5x4x4")
+    H, X0, v0, Ns, Ne = G.make_problem(cfg)
+    with D.Context(H) as ctx:
+        X = torch.from_numpy(X0).to(dev)
+        b, tmin = ctx.bounds(torch.from_numpy(v0).to(dev), 10)
+        a0, a = tmin, tmin + (b - tmin) * Ns / H.N
+        E0, _, H0, X0b = ctx.energy_grad(X, cfg.m, a, b, a0, Ne, cfg.kT, prec=prec)
+        ctx.set_subspace_products("sliced_bf16")
+        E1, _, H1, X1b = ctx.energy_grad(X, cfg.m, a, b, a0, Ne, cfg.kT, prec=prec)
+    eH = float((H1 - H0).abs().max() / H0.abs().max())
+    eX = float((X1b - X0b).abs().max() / X0b.abs().max())
+    print(f"SLICED adjoint 5x4x4 {prec}: E {abs(E1 - E0) / abs(E0):.2e}, dE/dH {eH:.2e}, dE/dX {eX:.2e}")
+    assert abs(E1 - E0) <= 1e-11 * abs(E0) and eH <= 1e-8 and eX <= 1e-8

@@ -31,10 +31,12 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 WORKLOAD = "bulk3d_8x8x8"
-# FP64 peak of the GB300 CUDA cores: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
-# (the FP64 rate NVIDIA states for this part is 1.25 TFLOP/s; cuBLAS DGEMM
-# measured 1.10 TFLOP/s here).
+# FP64 peak of the GB300 CUDA cores from the unit counts: 152 SMs x 2 DFMA/clk
+# x 2 flop x 2.07 GHz. Only a fallback: the bench measures the rate with the
+# library's DFMA probe (dgchefsi_selftest_fp64_rate) and uses that.
 F64_PEAK_TFLOPS = 1.259
+F64_PEAK = {"tflops": F64_PEAK_TFLOPS, "source": "derived from unit counts and clock (probe not run)"}
+SPECTRUM = os.path.join(ROOT, "tests", "golden", "bulk3d_8x8x8_spectrum.txt")
 METRIC = "CheFSI filter TFLOP/s + s per CheFSI cycle, mixed vs FP64 at Ritz err<=1e-8"
 
 
@@ -293,7 +295,7 @@ def measure_uneven(dev, precs=("bf16x3", "tf32"), reps=3):
         torch.cuda.synchronize()
         t64 = s_.elapsed_time(e_)
         out["f64"] = {"ms_per_step": t64 / m64, "tflops": fl64 / (t64 * 1e-3) / 1e12,
-                      "frac_of_fp64_peak": fl64 / (t64 * 1e-3) / 1e12 / F64_PEAK_TFLOPS,
+                      "frac_of_fp64_peak": fl64 / (t64 * 1e-3) / 1e12 / F64_PEAK["tflops"],
                       "steps_timed": m64, "graph": True}
     del X, Y
     torch.cuda.empty_cache()
@@ -502,13 +504,13 @@ def measure_next_rows(ctx, H, X, Ns, m, prec, dev):
     t, _ = timed(lambda: ctx.realign(X, nb, R, Vod, Vnd, X_new=Xn))
     fl = 2.0 * (float((R.astype(np.int64) * nb * nb).sum()) + Ns * float((nb.astype(np.int64) ** 2).sum()))
     res["realign"] = {"ms": t * 1e3, "gflop": fl / 1e9, "tflops": fl / t / 1e12,
-                      "frac_of_fp64_peak": fl / t / 1e12 / F64_PEAK_TFLOPS, "sample_points_per_element": 216}
+                      "frac_of_fp64_peak": fl / t / 1e12 / F64_PEAK["tflops"], "sample_points_per_element": 216}
     Vod = Vnd = Xn = None
     f = torch.full((Ns,), 0.5, dtype=torch.float64, device=dev)
     t, _ = timed(lambda: ctx.density_pattern(X, f), reps=1)
     fl = 2.0 * float(nnz_of(H)) * Ns
     res["density_pattern"] = {"ms": t * 1e3, "gflop": fl / 1e9, "tflops": fl / t / 1e12,
-                              "frac_of_fp64_peak": fl / t / 1e12 / F64_PEAK_TFLOPS}
+                              "frac_of_fp64_peak": fl / t / 1e12 / F64_PEAK["tflops"]}
     b, tmin = ctx.bounds(torch.ones(H.N, dtype=torch.float64, device=dev), 10)
     Yf = torch.empty_like(X)
     ctx.filter(X, m, tmin + (b - tmin) * Ns / H.N, b, tmin, prec=prec, Y=Yf)
@@ -570,23 +572,24 @@ def measure_sliced(ctx, X_warm, state, cycle, vd, Ns, N, m, Ne, kT, args, dev, b
         "orthonormality": float((Y2 @ Y2.T - torch.eye(Ns, dtype=torch.float64, device=dev)).abs().max().item())}
     out["s_rayleigh_ritz"] = {"f64_products": res["f64"][2], "sliced_products": res["sliced_bf16"][2]}
     del Y1, Y2, res
-    # whole mixed cycles with sliced products
-    ctx.set_subspace_products("sliced_bf16", s)
-    state["prev"] = warm_prev
-    X, Y = X_warm.clone(), torch.empty_like(X_warm)
-    _, X, Y = cycle(args.prec, X, Y)
-    n0 = D.launch_count()
-    t0, t1 = ev(), ev()
-    torch.cuda.synchronize()
-    t0.record(stream)
-    reps = 3
-    for _ in range(reps):
+    # whole mixed cycles with sliced products (when the timed cycles used FP64 products)
+    if args.subspace != "sliced":
+        ctx.set_subspace_products("sliced_bf16", s)
+        state["prev"] = warm_prev
+        X, Y = X_warm.clone(), torch.empty_like(X_warm)
         _, X, Y = cycle(args.prec, X, Y)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    out["s_per_cycle"] = t0.elapsed_time(t1) / 1e3 / reps
-    out["gpu_launches_per_cycle"] = (D.launch_count() - n0) / reps
-    del X, Y
+        n0 = D.launch_count()
+        t0, t1 = ev(), ev()
+        torch.cuda.synchronize()
+        t0.record(stream)
+        reps = 3
+        for _ in range(reps):
+            _, X, Y = cycle(args.prec, X, Y)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        out["s_per_cycle"] = t0.elapsed_time(t1) / 1e3 / reps
+        out["gpu_launches_per_cycle"] = (D.launch_count() - n0) / reps
+        del X, Y
     # the products alone: Gram shape (N_s x N_s, K = N) and rotation shape (N_s x N, K = N_s)
     S = torch.empty((Ns, Ns), dtype=torch.float64, device=dev)
     W = torch.empty_like(X_warm)
@@ -644,23 +647,26 @@ def run_rr_only(args):
     return 0
 
 
-def run_converge(args):
-    """Cycles to the 1e-8 target: from the same random start, CheFSI cycles in the
-    mixed form (--prec) and in FP64 until the Ritz values of the occupied states
-    (i < N_e/2) agree with the exact eigenvalues of the dense H to 1e-8 of
-    max(|a0|, |b|), or --max-cycles. --forms lists filter precisions, each
-    optionally "/sliced" for Rayleigh-Ritz products from BF16 slices. The exact eigenvalues come from a dense FP64
-    eigensolve of H on the GPU (an error metric only, outside the timed cycles);
-    each cycle (Lanczos bound, filter, Rayleigh-Ritz, occupations, density
-    blocks) is timed with CUDA events."""
+def read_spectrum(path):
+    """The stored exact eigenvalues (tests/golden format: 'eigenvalues: v v ...')."""
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("eigenvalues:"):
+                return np.array([float(x) for x in line.split(":", 1)[1].split()])
+    raise ValueError(f"no eigenvalues in {path}")
+
+
+def reference_spectrum(cfg, H, nocc, dev):
+    """Exact lowest nocc eigenvalues of H, an error metric only (outside every
+    timed region): the values the oracle's dense eigensolve wrote to
+    tests/golden for the 8x8x8 workload, else a dense FP64 eigensolve of H on
+    the GPU (torch.linalg.eigvalsh) for other workloads."""
     import torch
-    from paper_1606_03416_gb300 import dgchefsi as D
-    from paper_1606_03416_gb300 import inputs as G
-    dev = torch.device("cuda:0")
-    cfg = G.CONFIGS[args.workload]
-    H, X0, v0, Ns, Ne = G.make_problem(cfg)
-    N, m, kT = H.N, cfg.m, cfg.kT
-    t0 = time.time()
+    if cfg.name == "bulk3d_8x8x8" and os.path.exists(SPECTRUM):
+        lam = read_spectrum(SPECTRUM)
+        if lam.size >= nocc:
+            return lam[:nocc], "stored oracle eigenvalues (tests/golden/bulk3d_8x8x8_spectrum.txt)"
+    N = H.N
     Hd = torch.zeros((N, N), dtype=torch.float64, device=dev)
     vals = torch.from_numpy(np.asarray(H.values)).to(dev)
     nb, off = np.asarray(H.nb), np.concatenate([[0], np.cumsum(np.asarray(H.nb))])
@@ -673,44 +679,78 @@ def run_converge(args):
     lam = torch.linalg.eigvalsh(Hd).cpu().numpy()
     del Hd
     torch.cuda.empty_cache()
-    t_eig = time.time() - t0
-    nocc = int(np.ceil(Ne / 2))
-    out = {"mode": "converge", "workload": cfg.name, "N": N, "Ns": Ns, "m": m, "Ne": Ne,
-           "states_compared": nocc, "target": 1e-8, "s_dense_eigensolve": t_eig, "forms": {}}
+    return lam[:nocc], "dense FP64 eigensolve of H on the GPU (torch.linalg.eigvalsh)"
+
+
+def converge_forms(ctx, X0, vd, Ns, N, m, Ne, kT, forms, max_cycles, lam, slices, dev):
+    """From the same random start block, CheFSI cycles of each form until the
+    Ritz values of the occupied states (i < N_e/2) agree with the exact
+    eigenvalues lam to 1e-8 of max(|a0|, |b|) (the normwise reading of the
+    target), or max_cycles. A form is a filter precision, optionally
+    "/sliced" for Rayleigh-Ritz products from BF16 slices. Each cycle (Lanczos
+    bound, filter, Rayleigh-Ritz, occupations, density blocks) is timed with
+    CUDA events. Also reported per cycle: the per-value error
+    max_i |dlambda_i| / max(|lambda_i|, 1) (1 = a floor in the units of H)."""
+    import torch
     stream = torch.cuda.current_stream()
+    nocc = lam.size
+    out = {}
+    for form in forms:
+        prec, _, products = form.partition("/")
+        ctx.set_subspace_products("sliced_bf16" if products == "sliced" else "f64", max(slices, 2))
+        X = torch.from_numpy(X0).to(dev)
+        Y = torch.empty_like(X)
+        prev, errs, errs_v, times, reached = None, [], [], [], None
+        for c in range(max_cycles):
+            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+            e0.record(stream)
+            b, tmin = ctx.bounds(vd, 10)
+            if prev is None:
+                a0, a = tmin, tmin + (b - tmin) * Ns / N
+            else:
+                a, a0 = float(prev.max()), float(prev.min())
+            ctx.filter(X, m, a, b, a0, prec=prec, Y=Y)
+            ritz = ctx.rayleigh_ritz(Y)
+            f, mu = ctx.occupations(ritz, Ne, kT)
+            ctx.density_blocks(Y, f)
+            e1.record(stream)
+            prev = ritz.cpu().numpy()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            X, Y = Y, X
+            d = np.abs(prev[:nocc] - lam[:nocc])
+            errs.append(float(np.max(d) / max(abs(a0), abs(b))))
+            errs_v.append(float(np.max(d / np.maximum(np.abs(lam[:nocc]), 1.0))))
+            if errs[-1] <= 1e-8:
+                reached = c + 1
+                break
+        out[form] = {"cycles_to_target": reached, "ritz_err_by_cycle": errs,
+                     "ritz_err_per_value_by_cycle": errs_v,
+                     "s_per_cycle_median": float(np.median(times)),
+                     "s_to_target": float(np.sum(times)) if reached else None}
+        del X, Y
+    ctx.set_subspace_products("f64", max(slices, 2))
+    return out
+
+
+def run_converge(args):
+    """Cycles to the 1e-8 target for --forms (default: --prec and f64), printed as one JSON line."""
+    import torch
+    from paper_1606_03416_gb300 import dgchefsi as D
+    from paper_1606_03416_gb300 import inputs as G
+    dev = torch.device("cuda:0")
+    cfg = G.CONFIGS[args.workload]
+    H, X0, v0, Ns, Ne = G.make_problem(cfg)
+    N, m, kT = H.N, cfg.m, cfg.kT
+    nocc = int(np.ceil(Ne / 2))
+    t0 = time.time()
+    lam, lam_src = reference_spectrum(cfg, H, nocc, dev)
+    out = {"mode": "converge", "workload": cfg.name, "N": N, "Ns": Ns, "m": m, "Ne": Ne,
+           "states_compared": nocc, "target": 1e-8, "exact_eigenvalues": lam_src,
+           "s_exact_eigenvalues": time.time() - t0}
     with D.Context(H) as ctx:
         vd = torch.from_numpy(v0).to(dev)
         forms = [f for f in args.forms.split(",") if f] if args.forms else [args.prec, "f64"]
-        for form in forms:
-            prec, _, products = form.partition("/")
-            ctx.set_subspace_products("sliced_bf16" if products == "sliced" else "f64", max(args.slices, 2))
-            X = torch.from_numpy(X0).to(dev)
-            Y = torch.empty_like(X)
-            prev, errs, times, reached = None, [], [], None
-            for c in range(args.max_cycles):
-                e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
-                e0.record(stream)
-                b, tmin = ctx.bounds(vd, 10)
-                if prev is None:
-                    a0, a = tmin, tmin + (b - tmin) * Ns / N
-                else:
-                    a, a0 = float(prev.max()), float(prev.min())
-                ctx.filter(X, m, a, b, a0, prec=prec, Y=Y)
-                ritz = ctx.rayleigh_ritz(Y)
-                f, mu = ctx.occupations(ritz, Ne, kT)
-                ctx.density_blocks(Y, f)
-                e1.record(stream)
-                prev = ritz.cpu().numpy()
-                times.append(e0.elapsed_time(e1) / 1e3)
-                X, Y = Y, X
-                err = float(np.max(np.abs(prev[:nocc] - lam[:nocc])) / max(abs(a0), abs(b)))
-                errs.append(err)
-                if err <= 1e-8 and reached is None:
-                    reached = c + 1
-                    break
-            out["forms"][form] = {"cycles_to_target": reached, "ritz_err_by_cycle": errs,
-                                  "s_per_cycle_median": float(np.median(times)),
-                                  "s_to_target": float(np.sum(times)) if reached else None}
+        out["forms"] = converge_forms(ctx, X0, vd, Ns, N, m, Ne, kT, forms, args.max_cycles, lam, args.slices, dev)
     g = out["forms"].get("f64")
     for form, f in out["forms"].items():
         if form != "f64" and g and f["s_to_target"] and g["s_to_target"]:
@@ -739,9 +779,13 @@ def main():
     ap.add_argument("--converge", action="store_true",
                     help="cycles to Ritz error <= 1e-8 against a dense eigensolve, mixed and FP64")
     ap.add_argument("--max-cycles", type=int, default=40)
+    ap.add_argument("--no-converge", action="store_true",
+                    help="skip the cycles-to-1e-8 runs (sliced, mixed and FP64 forms) of the default line")
+    ap.add_argument("--converge-cycles", type=int, default=8, help="cycle limit of those runs")
     ap.add_argument("--gram-only", action="store_true", help="time one FP64 Gram (profiling case)")
     ap.add_argument("--rr-only", action="store_true", help="one Rayleigh-Ritz step (profiling case)")
-    ap.add_argument("--subspace", default="sliced", choices=["f64", "sliced"], help="with --rr-only")
+    ap.add_argument("--subspace", default="sliced", choices=["f64", "sliced"],
+                    help="Rayleigh-Ritz products of the timed cycles (and of --rr-only)")
     ap.add_argument("--slices", type=int, default=10,
                     help="BF16 slices of the sliced Rayleigh-Ritz products measured beside the FP64 ones (0: skip)")
     ap.add_argument("--forms", default="",
@@ -788,6 +832,9 @@ def main():
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     state = {"prev": None}
+    sliced_timed = args.subspace == "sliced" and args.prec != "f64" and args.slices > 0
+    products = "sliced_bf16" if sliced_timed else "f64"
+    ctx.set_subspace_products(products, max(args.slices, 2))
 
     def cycle(prec, X, Y, timers=None):
         """One CheFSI cycle via the public API; returns (ritz, new X buffer, spare buffer)."""
@@ -818,7 +865,7 @@ def main():
     X, Y = Xd, Yd
     for _ in range(args.warmup):
         _, X, Y = cycle(args.prec, X, Y)
-    # ---- timed mixed-precision cycles
+    # ---- timed cycles: mixed filter, Rayleigh-Ritz products as configured (default: BF16 slices)
     n0 = D.launch_count()
     fl_t = [(ev(), ev()) for _ in range(args.steps)]
     t0, t1 = ev(), ev()
@@ -839,6 +886,16 @@ def main():
     ms_step, ms_filter = max_over_ranks([ms_step, ms_filter], device=dev)
     fl = filter_flops(H, Ns, m)
     value = world * fl / (ms_filter * 1e-3) / 1e12
+    ctx.set_subspace_products("f64", max(args.slices, 2))
+
+    # ---- FP64 peak of the CUDA cores, measured by the library's DFMA probe (best of 10)
+    with ClockSampler(gid) as clk64:
+        f64_rate = ctx.fp64_rate(10) / 1e12
+    F64_PEAK.update({"tflops": f64_rate, "clocks": clk64.summary(),
+                     "source": "measured: dgchefsi_selftest_fp64_rate (8 independent DFMA chains per thread, "
+                               "8 CTAs x 256 threads per SM, best of 10, CUDA events)",
+                     "derived_from_unit_counts": F64_PEAK_TFLOPS})
+    f64_peak = F64_PEAK["tflops"]
 
     # ---- per-launch time of the filter step kernel: T(m) - T(1) over m-1 launches
     Xs = Xd.clone()
@@ -863,7 +920,7 @@ def main():
     src = "measured (MEASURED_PEAKS.json)" if peaks else "fallback"
     byts = filter_bytes_per_step(H, Ns, args.prec)
     if args.prec == "f64":
-        rf = {"bound": "alu", "achieved": step_fl / (ms_launch * 1e-3) / 1e12, "peak": F64_PEAK_TFLOPS,
+        rf = {"bound": "alu", "achieved": step_fl / (ms_launch * 1e-3) / 1e12, "peak": f64_peak,
               "unit": "TFLOP/s"}
     else:
         mult = 3.0 if args.prec == "bf16x3" else 1.0
@@ -885,10 +942,13 @@ def main():
         rf["kernel"] = (("k_filter_step_tn" if lay_ >= 1 else "k_filter_step_tc") + f"<{args.prec}, G={g_}, T={t_}"
                         + (", 64-byte slots>" if lay_ == 2 else ">"))
     rf["ms_per_launch"] = ms_launch
-    rf["peak_source"] = src + (" x 1.1/2.25 (nominal TF32/BF16 ratio)" if args.prec == "tf32" else "")
+    rf["peak_source"] = (F64_PEAK["source"] if args.prec == "f64" else
+                         src + (" x 1.1/2.25 (nominal TF32/BF16 ratio)" if args.prec == "tf32" else ""))
+    if args.prec == "bf16x3":
+        rf["work"] = "three BF16 products per step (hi*hi + lo*hi + hi*lo) counted as tensor work"
 
-    # ---- the cycle's dominant kernel: the FP64 N_s x N_s products of Rayleigh-Ritz
-    # (k_gemm_nt_f64 / k_gemm_nn_f64); timed through dgchefsi_gram, one launch of k_gemm_nt_f64.
+    # ---- FP64 Gram kernel of the Rayleigh-Ritz step with FP64 products (k_gemm_nt_f64),
+    # timed through dgchefsi_gram, one launch
     S = torch.empty((Ns, Ns), dtype=torch.float64, device=dev)
     gms = []
     for _ in range(3):
@@ -902,11 +962,10 @@ def main():
     nt = (Ns + 63) // 64
     gram_fl = 2.0 * (nt * (nt + 1) // 2) * 64 * 64 * N
     g_ach = gram_fl / (statistics.median(gms) * 1e-3) / 1e12
-    roof = {"bound": "alu", "achieved": g_ach, "peak": F64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": g_ach / F64_PEAK_TFLOPS, "traffic": profiled_gram_traffic(Ns), "kernel": "k_gemm_nt_f64",
-            "ms_per_launch": statistics.median(gms),
-            "peak_source": "FP64 DFMA peak from the unit counts and clock (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz); "
-                           "cuBLAS DGEMM measured 1.10 TFLOP/s on this GB300"}
+    roof_gram = {"bound": "alu", "achieved": g_ach, "peak": f64_peak, "unit": "TFLOP/s",
+                 "frac": g_ach / f64_peak, "traffic": profiled_gram_traffic(Ns), "kernel": "k_gemm_nt_f64",
+                 "ms_per_launch": statistics.median(gms), "peak_source": F64_PEAK["source"],
+                 "role": "FP64 Gram of the Rayleigh-Ritz step with FP64 products (not run by the sliced cycle)"}
 
     # ---- filter throughput of the other tensor-core precisions (filter alone)
     other = {}
@@ -953,11 +1012,35 @@ def main():
            "what": "dgchefsi_filter_host on pinned host blocks (copies overlapped with the filter in five "
                    "chunks, small first and last), host wall clock around the synchronous call; serial_copies_tflops: copy in, "
                    "filter, copy out one after the other"}
+    # a whole cycle end to end: the block from pinned host memory, one cycle as timed above,
+    # the new block and the Ritz values back to pinned host memory
+    ctx.set_subspace_products(products, max(args.slices, 2))
+    Rh = torch.empty(Ns, dtype=torch.float64).pin_memory()
+    cyc_ms = []
+    warm_prev = state["prev"]
+    for i in range(2):
+        state["prev"] = warm_prev
+        s, e = ev(), ev()
+        torch.cuda.synchronize()
+        s.record(stream)
+        Xs.copy_(Xh, non_blocking=True)
+        r_, Xn_, _ = cycle(args.prec, Xs, Yd)
+        Yh.copy_(Xn_, non_blocking=True)
+        Rh.copy_(r_, non_blocking=True)
+        e.record(stream)
+        torch.cuda.synchronize()
+        cyc_ms.append(s.elapsed_time(e))
+    state["prev"] = warm_prev
+    ctx.set_subspace_products("f64", max(args.slices, 2))
+    e2e_cycle = {"value": 1e-3 * min(cyc_ms), "unit": "s per CheFSI cycle", "higher_is_better": False,
+                 "h2d_bytes_per_step": int(Xh.numel() * 8), "d2h_bytes_per_step": int(Yh.numel() * 8 + Rh.numel() * 8),
+                 "what": "pinned host block -> device, one cycle through the public API (as the timed steps), "
+                         "new block and Ritz values -> pinned host; CUDA events"}
 
-    # ---- FP64 cycle for the per-cycle comparison, and precision of one mixed
-    # cycle against one FP64 cycle from the same block with the same bounds:
-    # cold = the random start block (first-cycle bounds), warm = the block left
-    # by the warm-up and timed cycles (bounds from their last Ritz values)
+    # ---- precision of one mixed cycle against one FP64 cycle (FP64 filter and FP64
+    # products) from the same block with the same bounds: cold = the random start
+    # block (first-cycle bounds), warm = the block left by the warm-up and timed
+    # cycles (bounds from their last Ritz values)
     f64 = {}
     if args.f64_steps > 0 and args.prec != "f64":
         warm_prev = state["prev"]
@@ -1000,32 +1083,65 @@ def main():
         f64["warm"] = compare(X_warm, float(warm_prev.max()), float(warm_prev.min()), False)
         f64["warm"]["after_cycles"] = args.warmup + args.steps
 
-    # ---- the same mixed cycle with the four dense Rayleigh-Ritz products rebuilt
-    # from exact BF16 slices on the tensor cores (dgchefsi_set_subspace_products)
+    # ---- the Rayleigh-Ritz products from exact BF16 slices on the tensor cores:
+    # accuracy against FP64 products on a warm block, products alone against the BF16 peak
     sliced = None
     if args.slices > 0 and args.prec != "f64":
         sliced = measure_sliced(ctx, X_warm, state, cycle, vd, Ns, N, m, Ne, kT, args, dev, bf16_peak)
+        if sliced_timed:
+            sliced["s_per_cycle"] = ms_step / 1e3
+
+    # ---- cycles to Ritz error <= 1e-8 from the random start block, three forms
+    conv = None
+    if not args.no_converge and args.prec != "f64":
+        nocc = int(np.ceil(Ne / 2))
+        lam, lam_src = reference_spectrum(cfg, H, nocc, dev)
+        forms = [f"{args.prec}/sliced", args.prec, "f64"]
+        conv = {"target": 1e-8, "states_compared": nocc, "exact_eigenvalues": lam_src,
+                "ritz_err": "max over occupied states i of |lambda_i - lambda_i^exact| / max(|a0|, |b|)",
+                "ritz_err_per_value": "max over occupied states i of |lambda_i - lambda_i^exact| / "
+                                      "max(|lambda_i^exact|, 1)",
+                "forms": converge_forms(ctx, X0, vd, Ns, N, m, Ne, kT, forms, args.converge_cycles, lam,
+                                        args.slices, dev)}
+        g = conv["forms"].get("f64")
+        for form, fr in conv["forms"].items():
+            if form != "f64" and g and fr["s_to_target"] and g["s_to_target"]:
+                conv.setdefault("speedup_to_target_vs_f64", {})[form] = g["s_to_target"] / fr["s_to_target"]
 
     clocks = clk.summary()
+    conv_f = conv["forms"] if conv else {}
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.prec, "data": "synthetic (seeded generator, random-init blocks)",
         "config": {"workload": args.workload, "grid": list(cfg.grid), "stencil": cfg.stencil, "nb": cfg.nb, "N": N,
-                   "Ns": Ns, "m": m, "Ne": Ne, "kT": kT, "filter": args.prec, "subspace": "f64",
+                   "Ns": Ns, "m": m, "Ne": Ne, "kT": kT, "filter": args.prec,
+                   "subspace": f"sliced_bf16 ({args.slices} slices)" if sliced_timed else "f64",
                    "l2": "inputs larger than L2 (X 1.07 GB FP64), no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "s_per_cycle": {"mixed": ms_step / 1e3, "f64": f64.get("s_per_cycle"),
-                        "mixed_sliced_products": sliced["s_per_cycle"] if sliced else None},
+        "s_per_cycle": {"mixed_sliced_products": (ms_step / 1e3 if sliced_timed else
+                                                  (sliced["s_per_cycle"] if sliced else None)),
+                        "mixed": (conv_f.get(args.prec, {}).get("s_per_cycle_median") if conv_f else
+                                  (None if sliced_timed else ms_step / 1e3)),
+                        "f64": (conv_f.get("f64", {}).get("s_per_cycle_median") if conv_f else f64.get("s_per_cycle")),
+                        "what": "timed steps: " + ("mixed_sliced_products" if sliced_timed else "mixed")
+                                + "; the other forms: median cycle of the convergence runs"},
+        "cycles_to_1e-8": {k: v["cycles_to_target"] for k, v in conv_f.items()},
+        "s_to_1e-8": {k: v["s_to_target"] for k, v in conv_f.items()},
         "filter_ms": ms_filter,
         "mixed_vs_f64_one_cycle": {k: f64[k] for k in ("cold_first_cycle", "warm") if k in f64},
-        "roofline": roof, "roofline_filter": rf, "filter_tflops_other_precisions": other,
-        "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "roofline": rf, "roofline_gram_f64": roof_gram, "fp64_peak": F64_PEAK,
+        "filter_tflops_other_precisions": other,
+        "e2e": e2e, "e2e_cycle": e2e_cycle, "gpu_launches": launches, "clocks": clocks,
     }
+    if conv:
+        line["converge"] = conv
     if sliced:
         line["sliced_products"] = sliced
     if not args.no_next_rows and args.prec != "f64":
-        line["next_rows"] = measure_next_rows(ctx, H, X, Ns, m, args.prec, dev)
+        Xn_rows = torch.from_numpy(X0).to(dev)
+        line["next_rows"] = measure_next_rows(ctx, H, Xn_rows, Ns, m, args.prec, dev)
+        Xn_rows = None
     ctx.close()
     X = Y = Xd = Yd = Xs = Xh = Yh = S = X_warm = None  # free the 8x8x8 buffers before the next workload
     torch.cuda.empty_cache()

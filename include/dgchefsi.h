@@ -111,7 +111,8 @@ dgchefsi_status dgchefsi_bounds(dgchefsi_ctx* ctx, const double* v0, int k,
                                 double* b_upper, double* theta_min);
 
 /* Capacity, in doubles, of the fixed device array used by dgchefsi_bounds_static
- * (8 MiB per GPU that loads this library, held until the process exits). */
+ * (8 MiB on every GPU where a context has been created, resident from the
+ * first dgchefsi_create on that GPU until the process exits). */
 #define DGCHEFSI_BOUNDS_STATIC_DOUBLES (1 << 20)
 
 /* The same k-step Lanczos bound as dgchefsi_bounds, for callers that must not
@@ -124,13 +125,17 @@ dgchefsi_status dgchefsi_bounds(dgchefsi_ctx* ctx, const double* v0, int k,
  * DGCHEFSI_BOUNDS_STATIC_DOUBLES doubles, and the call needs
  * (k + 2) * N + 72 of them (k clipped to N); larger requests return
  * DGCHEFSI_ERR_ARG with a message and touch nothing. The context itself must
- * have been created beforehand (dgchefsi_create does allocate).
- * The first call on a device looks up that array's device address once
- * (cudaGetSymbolAddress, with the context's device made current); make that
- * first call before any stream capture. Every call on a device shares the one
- * array and nothing in it needs to start at zero (each call writes every entry
- * it reads), but calls whose work overlaps on the GPU (other threads or
- * streams) race on it and must be serialised by the caller.
+ * have been created beforehand: dgchefsi_create allocates, and it is also
+ * where this entry point is set up, with the context's device current (the
+ * array's device address is looked up with cudaGetSymbolAddress, which makes
+ * the array resident, and the Lanczos kernels are loaded), so that no call of
+ * this entry point loads a module or allocates. Every dgchefsi_create refreshes
+ * the looked-up address; a cudaDeviceReset frees the array together with every
+ * context's memory, so contexts created before a reset must not be used after
+ * it. Every call on a device shares the one array and nothing in it needs to
+ * start at zero (each call writes every entry it reads), but calls whose work
+ * overlaps on the GPU (other threads or streams) race on it and must be
+ * serialised by the caller.
  * Arguments, results and synchronisation are those of dgchefsi_bounds. */
 dgchefsi_status dgchefsi_bounds_static(dgchefsi_ctx* ctx, const double* v0, int k,
                                        double* b_upper, double* theta_min);
@@ -384,6 +389,14 @@ dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, const double* 
  * (1 ns .. 10 s) and the call returns DGCHEFSI_ERR_TIMEOUT; the context stays
  * usable. Any other status means the timeout path is broken. Synchronises. */
 dgchefsi_status dgchefsi_selftest_wait(dgchefsi_ctx* ctx, int64_t limit_ns);
+
+/* Measurement aid (no counterpart in the paper): the FP64 rate of the GPU's
+ * CUDA cores, the roofline of this library's FP64 kernels. Launches 8 CTAs
+ * per SM of 256 threads, each thread running 8 independent chains of 2^15
+ * DFMAs with no memory traffic, `reps` times (1..100) on the context's
+ * stream, and returns in *flops_per_s (host) the best rate (2 flops per DFMA)
+ * by CUDA events. Synchronises. */
+dgchefsi_status dgchefsi_selftest_fp64_rate(dgchefsi_ctx* ctx, int reps, double* flops_per_s);
 
 /* Message describing the last error on the calling thread ("" if none). */
 const char* dgchefsi_last_error(void);

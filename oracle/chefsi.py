@@ -136,6 +136,96 @@ def chebyshev_filter(H: DGHamiltonian, X: np.ndarray, m: int, a: float, b: float
     return Y
 
 
+# --------------------------------------------------------------------------
+# Precision forms of the filter: the same recurrence with the operand
+# roundings of the tensor-core forms (filter products in TF32 or BF16 with
+# FP32 accumulation, FP32 iterates). Used to compare those forms with the
+# rounding they are meant to have, which is far tighter than comparing them
+# with the FP64 filter. Each product is evaluated exactly (FP64 here); only
+# the order of the FP32 accumulation is not emulated.
+# --------------------------------------------------------------------------
+
+
+def round_fp32(x) -> np.ndarray:
+    """Round to the nearest FP32 value (returned as float64)."""
+    return np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def round_bf16(x) -> np.ndarray:
+    """Round FP32 values to BF16 (8 significant bits), nearest, ties to even:
+    add half of the dropped 16 bits (minus one unless the kept last bit is
+    odd) and clear them. Finite inputs only."""
+    b = np.asarray(x, dtype=np.float64).astype(np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def truncate_tf32(x) -> np.ndarray:
+    """FP32 values cut to TF32 (11 significant bits) by dropping the low 13
+    mantissa bits, the way the TF32 tensor-core product reads FP32 operands."""
+    b = np.asarray(x, dtype=np.float64).astype(np.float32).view(np.uint32) & np.uint32(0xFFFFE000)
+    return b.view(np.float32).astype(np.float64)
+
+
+def _with_values(H: DGHamiltonian, values) -> DGHamiltonian:
+    return DGHamiltonian(H.nb, H.row_ptr, H.col, H.blk_off, values)
+
+
+def shifted_values(H: DGHamiltonian, c: float) -> np.ndarray:
+    """Values of H - cI, block by block (the shift on the diagonal blocks' diagonals)."""
+    v = H.values.copy()
+    for K in range(H.M):
+        for e in range(H.row_ptr[K], H.row_ptr[K + 1]):
+            if int(H.col[e]) == K:
+                n = int(H.nb[K])
+                idx = int(H.blk_off[e]) + np.arange(n) * (n + 1)
+                v[idx] -= c
+    return v
+
+
+def chebyshev_filter_rounded(H: DGHamiltonian, X: np.ndarray, m: int, a: float, b: float, a0: float,
+                             fmt: str) -> np.ndarray:
+    """Alg. 1 step 2 with the operand roundings of a tensor-core form.
+
+    The operator is H - cI rounded to FP32, the iterates are FP32, the
+    recurrence scalars FP32, and each product (H - cI) Y_k uses operands
+    rounded to the form's type:
+      "bf16"    bf16(H - cI) bf16(Y_k)
+      "bf16x3"  hi = bf16(v), lo = bf16(v - hi) for both operands;
+                hi*hi + lo(H)*hi(Y) + hi(H)*lo(Y)
+      "tf32"    tf32(H - cI) tf32(Y_k), TF32 cut from FP32 as above
+    then Y_{k+1} = fp32(alpha_k fp32(P) - fp32(beta_k Y_{k-1})) with the
+    scalars of the scaled recurrence (alpha_0 = s_1/e, beta_0 = 0)."""
+    c, alpha, beta = _recurrence_coefficients(m, a, b, a0)
+    Hs = round_fp32(shifted_values(H, c))
+    if fmt == "tf32":
+        ops = [(truncate_tf32(Hs), "t")]
+    elif fmt in ("bf16", "bf16x3"):
+        hi = round_bf16(Hs)
+        ops = [(hi, "hi")]
+        if fmt == "bf16x3":
+            ops += [(round_bf16(Hs - hi), "hi"), (hi, "lo")]
+    else:
+        raise ValueError(f"unknown format {fmt!r}")
+    ops = [(_with_values(H, v), which) for v, which in ops]
+
+    def parts(Y):
+        if fmt == "tf32":
+            return {"t": truncate_tf32(Y)}
+        hi = round_bf16(Y)
+        return {"hi": hi, "lo": round_bf16(Y - hi)}
+
+    Y_prev = None
+    Y = round_fp32(X)
+    for k in range(m):
+        p = parts(Y)
+        P = sum(matvec(Hop, p[which]) for Hop, which in ops)
+        al, be = float(np.float32(alpha[k])), float(np.float32(beta[k]))
+        prev = round_fp32(be * Y_prev) if Y_prev is not None else 0.0
+        Y_prev, Y = Y, round_fp32(al * round_fp32(P) - prev)
+    return Y
+
+
 def lanczos_bounds(H: DGHamiltonian, v0: np.ndarray, k: int = 10):
     """Upper spectral bound by k Lanczos steps (Alg. 1 step 1).
 
@@ -261,6 +351,16 @@ def chefsi_cycle(H: DGHamiltonian, X: np.ndarray, m: int, Ne: float, kT: float, 
     f, mu = fermi_occupations(D, Ne, kT)
     P = density_blocks(H, X_new, f)
     return dict(a=a, b=b, a0=a0, X=X_new, ritz=D, HX=HX, f=f, mu=mu, P=P)
+
+
+def lowest_eigenvalues(H: DGHamiltonian, n: int) -> np.ndarray:
+    """The n smallest eigenvalues of H, ascending, from a dense FP64 symmetric
+    eigensolve (LAPACK through SciPy) of the assembled matrix: the exact values
+    the Ritz values of Alg. 1 converge to (Sec. III.A). A reference for
+    convergence, not a step of the cycle."""
+    A = H.dense()
+    return sla.eigh(A, eigvals_only=True, subset_by_index=[0, n - 1], overwrite_a=True, check_finite=False,
+                    driver="evr")
 
 
 def chebyshev_value(m: int, t):

@@ -518,6 +518,9 @@ dgchefsi_status dgchefsi_create(int32_t M, const int32_t* nb, const int64_t* row
     return bail(set_error(DGCHEFSI_ERR_CUDA, "copy of H to the device failed"));
   if (cusolverDnCreate(&ctx->solver) != CUSOLVER_STATUS_SUCCESS)
     return bail(set_error(DGCHEFSI_ERR_CUDA, "cusolverDnCreate failed"));
+  // the fixed array of dgchefsi_bounds_static becomes resident here, while the
+  // caller can still allocate, not at that entry point's first call
+  if ((st = bounds_static_setup(ctx->device))) return bail(st);
   *out = ctx;
   return DGCHEFSI_OK;
 }
@@ -791,6 +794,39 @@ dgchefsi_status dgchefsi_selftest_wait(dgchefsi_ctx* ctx, int64_t limit_ns) {
   DG_TRY(check_ctx(ctx));
   if (limit_ns < 1 || limit_ns > 10000000000LL) return set_error(DGCHEFSI_ERR_ARG, "limit_ns outside 1 ns .. 10 s");
   return tc_wait_selftest(ctx, limit_ns);
+}
+
+dgchefsi_status dgchefsi_selftest_fp64_rate(dgchefsi_ctx* ctx, int reps, double* flops_per_s) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  if (reps < 1 || reps > 100 || !flops_per_s) return set_error(DGCHEFSI_ERR_ARG, "need 1 <= reps <= 100 and an output");
+  int nsm = 0;
+  DG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+  const int blocks = 8 * nsm;
+  const int64_t iters = 1 << 15;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  DG_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return set_error(DGCHEFSI_ERR_CUDA, "cudaEventCreate failed");
+  }
+  double* sink = reinterpret_cast<double*>(ctx->info_d);
+  float best = 0.f;
+  cudaError_t err = dfma_rate(iters / 8, blocks, sink, ctx->stream);  // warm-up
+  for (int r = 0; r < reps && err == cudaSuccess; ++r) {
+    cudaEventRecord(e0, ctx->stream);
+    err = dfma_rate(iters, blocks, sink, ctx->stream);
+    cudaEventRecord(e1, ctx->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err == cudaSuccess && (best == 0.f || ms < best)) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return set_error(DGCHEFSI_ERR_CUDA, "FP64 rate probe failed: %s", cudaGetErrorString(err));
+  *flops_per_s = 16.0 * (double)iters * (double)blocks * 256.0 / (1e-3 * (double)best);
+  return DGCHEFSI_OK;
 }
 
 dgchefsi_status dgchefsi_gram(dgchefsi_ctx* ctx, const double* Y, int64_t Ns, int64_t ld, double* S) {

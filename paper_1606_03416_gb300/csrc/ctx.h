@@ -141,6 +141,12 @@ dgchefsi_status sliced_gemm_tn(dgchefsi_ctx* ctx, int64_t M, int64_t Nc, int64_t
                                const double* B, int64_t ldb, double* C, int64_t ldc, int s, int* flag);
 void sliced_destroy(dgchefsi_ctx* ctx);
 
+// Set-up of dgchefsi_bounds_static for `device` (noalloc.cu), run by
+// dgchefsi_create with that device current: looks up the device address of
+// the fixed scratch array (which loads its module, so the array is resident
+// from then on) and loads the Lanczos kernels' modules.
+dgchefsi_status bounds_static_setup(int device);
+
 }  // namespace dg
 
 #define DG_CUDA(call)                                                                               \

@@ -557,6 +557,41 @@ cudaError_t filter_step_f64_dev(const HView& h, const double* in, int64_t ld_in,
   return cudaGetLastError();
 }
 
+// FP64 issue-rate probe: 8 independent DFMA chains per thread, nothing read
+// from memory; the store happens only if the result hits a value it cannot
+// take, which keeps the chains live without memory traffic.
+__global__ void __launch_bounds__(256) k_dfma_rate(int64_t iters, double x, double* __restrict__ sink) {
+  double a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = 1.0 + 1e-3 * (threadIdx.x + i);
+  const double y = -0.5 * x;
+  for (int64_t n = 0; n < iters; ++n) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = fma(a[i], x, y);
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) t += a[i];
+  if (t == 1234.5678) sink[0] = t;
+}
+
+cudaError_t dfma_rate(int64_t iters, int blocks, double* sink, cudaStream_t s) {
+  k_dfma_rate<<<blocks, 256, 0, s>>>(iters, 0.999999, sink);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t preload_lanczos_kernels() {
+  // cudaFuncGetAttributes loads a kernel's module on a lazily loading runtime,
+  // so a later launch of these kernels allocates no device memory for code.
+  cudaFuncAttributes a;
+  cudaError_t e;
+  if ((e = cudaFuncGetAttributes(&a, k_spmv_f64)) != cudaSuccess) return e;
+  if ((e = cudaFuncGetAttributes(&a, k_dots_f64)) != cudaSuccess) return e;
+  if ((e = cudaFuncGetAttributes(&a, k_sub_combination_f64)) != cudaSuccess) return e;
+  return cudaFuncGetAttributes(&a, k_axpby_f64);
+}
+
 cudaError_t spmv_f64(const HView& h, const double* x, double* y, cudaStream_t s) {
   const int64_t threads = h.N * 32;
   k_spmv_f64<<<cdiv(threads, 256), 256, 0, s>>>(h, x, y);

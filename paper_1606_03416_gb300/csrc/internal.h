@@ -33,6 +33,15 @@ cudaError_t filter_step_f64(const HView& h, const double* in, int64_t ld_in, con
 cudaError_t filter_step_f64_dev(const HView& h, const double* in, int64_t ld_in, const double* prev, double* out,
                                 int64_t ld_out, int64_t Ns, const double* coef, int step, cudaStream_t s);
 
+// Launches `blocks` x 256 threads, each running 8 independent chains of
+// `iters` DFMAs (16 iters flops per thread); `sink` (device, one double) is
+// written only in a case that does not occur.
+cudaError_t dfma_rate(int64_t iters, int blocks, double* sink, cudaStream_t s);
+
+// Loads the modules of the Lanczos kernels below (no launch), so that a later
+// first launch allocates nothing (used when a context is created).
+cudaError_t preload_lanczos_kernels();
+
 // y = H x for one vector (Lanczos).
 cudaError_t spmv_f64(const HView& h, const double* x, double* y, cudaStream_t s);
 

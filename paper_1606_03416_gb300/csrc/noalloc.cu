@@ -10,6 +10,7 @@
 #include <mutex>
 
 #include "ctx.h"
+#include "internal.h"
 
 namespace dg {
 namespace {
@@ -25,21 +26,28 @@ static __device__ __align__(256) double g_bounds_scratch[kStaticDoubles];
 std::mutex g_addr_mu;
 double* g_addr[kMaxDevices] = {};
 
-// Device address of g_bounds_scratch on `dev` (made current for the lookup).
+// Looks up the device address of g_bounds_scratch on `dev` (made current for
+// the lookup) and caches it. The lookup loads this file's module if it is not
+// loaded yet, which is when the array itself is allocated on the device.
+dgchefsi_status lookup_scratch(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "device index %d too large", dev);
+  int cur = 0;
+  DG_CUDA(cudaGetDevice(&cur));
+  if (cur != dev) DG_CUDA(cudaSetDevice(dev));
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_bounds_scratch);
+  if (cur != dev) cudaSetDevice(cur);
+  if (e != cudaSuccess)
+    return set_error(DGCHEFSI_ERR_CUDA, "cudaGetSymbolAddress of the bound scratch failed: %s", cudaGetErrorString(e));
+  g_addr[dev] = static_cast<double*>(p);
+  return DGCHEFSI_OK;
+}
+
+// Cached device address of g_bounds_scratch on `dev`.
 dgchefsi_status scratch_address(int dev, double** out) {
   if (dev < 0 || dev >= kMaxDevices) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "device index %d too large", dev);
   std::lock_guard<std::mutex> lock(g_addr_mu);
-  if (!g_addr[dev]) {
-    int cur = 0;
-    DG_CUDA(cudaGetDevice(&cur));
-    if (cur != dev) DG_CUDA(cudaSetDevice(dev));
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_bounds_scratch);
-    if (cur != dev) cudaSetDevice(cur);
-    if (e != cudaSuccess)
-      return set_error(DGCHEFSI_ERR_CUDA, "cudaGetSymbolAddress of the bound scratch failed: %s", cudaGetErrorString(e));
-    g_addr[dev] = static_cast<double*>(p);
-  }
+  if (!g_addr[dev]) DG_TRY(lookup_scratch(dev));
   *out = g_addr[dev];
   return DGCHEFSI_OK;
 }
@@ -79,6 +87,19 @@ double tridiag_eig_n(const double* a, const double* b, int n, int which) {
 }
 
 }  // namespace
+
+// Run by dgchefsi_create with `device` current. Every new context refreshes
+// the cached address, so a context created after a cudaDeviceReset (which
+// unloads modules and frees the array) gets the reloaded array's address.
+dgchefsi_status bounds_static_setup(int device) {
+  {
+    std::lock_guard<std::mutex> lock(g_addr_mu);
+    DG_TRY(lookup_scratch(device));
+  }
+  DG_CUDA(preload_lanczos_kernels());
+  return DGCHEFSI_OK;
+}
+
 }  // namespace dg
 
 using namespace dg;

@@ -29,7 +29,7 @@ EXPORTS = ["dgchefsi_create", "dgchefsi_destroy", "dgchefsi_set_stream", "dgchef
            "dgchefsi_density_blocks", "dgchefsi_cycle", "dgchefsi_last_error", "dgchefsi_launch_count",
            "dgchefsi_bounds_static", "dgchefsi_gram", "dgchefsi_set_values", "dgchefsi_energy_grad",
            "dgchefsi_filter_graph", "dgchefsi_set_tile_shape", "dgchefsi_get_tile_shape",
-           "dgchefsi_selftest_wait", "dgchefsi_set_orthonormalisation", "dgchefsi_density_pattern",
+           "dgchefsi_selftest_wait", "dgchefsi_selftest_fp64_rate", "dgchefsi_set_orthonormalisation", "dgchefsi_density_pattern",
            "dgchefsi_realign", "dgchefsi_filter_host", "dgchefsi_set_subspace_products",
            "dgchefsi_sliced_gemm"]
 
@@ -70,6 +70,7 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_set_tile_shape": (st, [P, C.c_int, C.c_int, C.c_int, C.c_int]),
         "dgchefsi_get_tile_shape": (st, [P, C.c_int, P, P, P, P]),
         "dgchefsi_selftest_wait": (st, [P, I64]),
+        "dgchefsi_selftest_fp64_rate": (st, [P, C.c_int, P]),
         "dgchefsi_set_orthonormalisation": (st, [P, C.c_int]),
         "dgchefsi_set_subspace_products": (st, [P, C.c_int, C.c_int]),
         "dgchefsi_sliced_gemm": (st, [P, C.c_int, C.c_int, I64, I64, I64, P, I64, P, I64, P, I64, C.c_int]),
@@ -257,6 +258,13 @@ class Context:
         """Run the bounded-wait self-test; returns the status name (ERR_TIMEOUT expected)."""
         st = _lib.dgchefsi_selftest_wait(self._h, int(limit_ns))
         return STATUS.get(st, str(st)), last_error()
+
+    def fp64_rate(self, reps: int = 10) -> float:
+        """Best FP64 DFMA rate of the GPU's CUDA cores over `reps` probe launches (flop/s)."""
+        r = C.c_double()
+        self._sync_stream()
+        _check(_lib.dgchefsi_selftest_fp64_rate(self._h, int(reps), C.byref(r)))
+        return r.value
 
     def set_tile_shape(self, prec: str, G: int, T: int, layout: int = 0):
         _check(_lib.dgchefsi_set_tile_shape(self._h, PRECISIONS[prec], int(G), int(T), int(layout)))

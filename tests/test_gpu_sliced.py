@@ -60,6 +60,31 @@ def test_integer_operands_bit_exact(b_rows, a_lower, slices):
     assert np.all(got[:, Nc:] == -1.0)
 
 
+@pytest.mark.parametrize("b_rows", [True, False])
+def test_pair_sums_at_the_fp32_limit_bit_exact(b_rows):
+    """One full K chunk (4096) of same-sign operands whose digits reach their
+    bounds: 4064 = 2^12 - 32 splits (row exponent 12) into q_0 = 64, q_1 = -32,
+    so the slice pairs sum to 64 * 64 * 4096 = 2^24, -2^23 and 2^22 exactly at
+    the edge of exact FP32 accumulation. The other rows and columns are
+    positive integers below 4064. The result must equal the exact integer
+    product bit for bit."""
+    rng = np.random.default_rng(5)
+    M, Nc, K = 70, 90, L_CHUNK
+    A = rng.integers(2000, 4065, size=(M, K)).astype(np.int64)
+    A[:3] = 4064
+    Bt = rng.integers(2000, 4065, size=(Nc, K)).astype(np.int64)
+    Bt[:4] = 4064
+    ref = (A @ Bt.T).astype(np.float64)                     # exact: entries < 2^37
+    assert ref[0, 0] == 4096 * 4064 ** 2
+    B = Bt if b_rows else np.ascontiguousarray(Bt.T)
+    with tiny_ctx() as ctx:
+        out = torch.empty((M, Nc), dtype=torch.float64, device=dev)
+        ctx.sliced_gemm(torch.from_numpy(A.astype(np.float64)).to(dev), torch.from_numpy(B.astype(np.float64)).to(dev),
+                        b_rows=b_rows, slices=10, out=out)
+        got = out.cpu().numpy()
+    assert np.array_equal(got, ref)
+
+
 def splitting_bound(A, B, s, balance=False):
     """Sum over K chunks of L m_r n_c (2^{-6s}(s + 4) + (5 + chunks) u), B given
     as the rows of the right operand's transpose. balance: the operands as the

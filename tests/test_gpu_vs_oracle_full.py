@@ -1,19 +1,22 @@
-"""The 8x8x8 workload at full size (N = 32768, N_s = 4096, m = 20) against
-the FP64 oracle on the host cores and a dense eigensolve. Minutes of host
-time, so these run only with DGCHEFSI_FULL_ORACLE=1 in the environment.
+"""The 8x8x8 workload (N = 32768, m = 20) against the FP64 oracle on the host
+cores and against the exact spectrum.
 
 * One cycle (same start block and bounds) in FP64 and in the mixed form
   (BF16x3 filter, FP64 subspace steps) against the oracle's cycle: Ritz
   values (relative to max(|a0|, |b|)), the largest principal angle between
-  the occupied subspaces, density blocks. From a random start block the
-  Cholesky factor of the filtered block is ill-conditioned (cond(U) ~ 3e4),
-  and both FP64 codes are exact only up to u cond(U)^2, which bounds their
-  difference; from a warm start (five FP64 cycles first) FP64 must meet the
-  1e-10 target. The mixed cycle's errors are reported: one mixed cycle moves
-  the subspace by about the filter's rounding, which the iteration does not
-  accumulate (next test).
-* Mixed cycles from the random start reach Ritz error <= 1e-8 against a
-  dense eigensolve of H on the occupied states within 8 cycles.
+  the occupied subspaces, density blocks. By default on the first N_s = 512
+  states of the workload's start block (the oracle cycle then takes about
+  half a minute of host time); with DGCHEFSI_FULL_ORACLE=1 on all 4096 (some
+  minutes). From a random start block the Cholesky factor of the filtered
+  block is ill-conditioned, and both FP64 codes are exact only up to
+  u cond(U)^2, which bounds their difference; from a warm start (five FP64
+  cycles first) FP64 must meet the 1e-10 target. The mixed cycle's errors
+  are reported: one mixed cycle moves the subspace by about the filter's
+  rounding, which the iteration does not accumulate (next test).
+* Mixed cycles at full size (N_s = 4096) from the random start reach Ritz
+  error <= 1e-8 on the occupied states within 8 cycles, against the exact
+  eigenvalues stored in tests/golden/bulk3d_8x8x8_spectrum.txt (written from
+  the oracle's dense eigensolve by tests/golden/make_golden.py --spectrum).
 """
 import os
 
@@ -24,9 +27,10 @@ import torch
 from oracle import chefsi as O
 from paper_1606_03416_gb300 import inputs as G
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("DGCHEFSI_FULL_ORACLE") != "1",
-                                 reason="set DGCHEFSI_FULL_ORACLE=1 (minutes of host time)")]
+pytestmark = pytest.mark.gpu
+
+NS_ORACLE = 4096 if os.environ.get("DGCHEFSI_FULL_ORACLE") == "1" else 512
+SPECTRUM = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "bulk3d_8x8x8_spectrum.txt")
 
 D = pytest.importorskip("paper_1606_03416_gb300.dgchefsi") if torch.cuda.is_available() else None
 
@@ -66,7 +70,11 @@ def _compare(ctx, Ho, H, X0, bounds, Ne, kT, m, nocc, scale, dev, label):
 
 def test_full_cycle_mixed_and_fp64_against_oracle():
     cfg = G.CONFIGS["bulk3d_8x8x8"]
-    H, X0, v0, Ns, Ne = G.make_problem(cfg)
+    H = G.make_blocks(cfg)
+    Ns = NS_ORACLE
+    Ne = G.default_ne(Ns)
+    X0 = G.make_X(H.N, Ns, cfg.seed)
+    v0 = G.make_start_vector(H.N, cfg.seed)
     N, m, kT = H.N, cfg.m, cfg.kT
     nocc = int(np.ceil(Ne / 2))
     dev = torch.device("cuda:0")
@@ -103,10 +111,13 @@ def test_full_mixed_cycles_reach_target():
     N, m, kT = H.N, cfg.m, cfg.kT
     nocc = int(np.ceil(Ne / 2))
     dev = torch.device("cuda:0")
-    Hd = torch.from_numpy(O.DGHamiltonian.from_blocksparse(H).dense()).to(dev)
-    lam = torch.linalg.eigvalsh(Hd).cpu().numpy()
-    del Hd
-    torch.cuda.empty_cache()
+    if not os.path.exists(SPECTRUM):
+        pytest.skip("exact spectrum not written (tests/golden/make_golden.py --spectrum)")
+    import sys
+    sys.path.insert(0, os.path.dirname(SPECTRUM))
+    import make_golden as MG
+    lam = MG.read(SPECTRUM)["eigenvalues"]
+    assert lam.size == nocc
     with D.Context(H) as ctx:
         X = torch.from_numpy(X0).to(dev)
         Y = torch.empty_like(X)

@@ -252,7 +252,9 @@ dgchefsi_status dgchefsi_set_orthonormalisation(dgchefsi_ctx* ctx, int mode);
  *                                  dgchefsi_sliced_gemm)
  *   slices  2..16 for the sliced form (ignored for FP64); 10 gives an error
  *           below the FP64 worst-case bound for rows of similar magnitude
- * ERR_ARG for another mode or slice count. H Y_hat stays on the FP64 cores.
+ * ERR_ARG for another mode or slice count. In the sliced form H Y_hat runs
+ * from slices too (dgchefsi_sliced_matvec) when H fits that form, else on the
+ * FP64 cores.
  * dgchefsi_energy_grad follows the same setting for its forward products and
  * the dense products of its adjoint (Z = U^{-1} Q, W_m = Z (2 G R^T));
  * dgchefsi_gram always uses FP64 products. */
@@ -284,6 +286,27 @@ dgchefsi_status dgchefsi_set_subspace_products(dgchefsi_ctx* ctx, int mode, int 
 dgchefsi_status dgchefsi_sliced_gemm(dgchefsi_ctx* ctx, int b_rows, int a_lower, int64_t M, int64_t Nc, int64_t K,
                                      const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
                                      int64_t ldc, int slices);
+
+/* Y = H X in FP64 from exact BF16 slices on the tensor cores: the block-sparse
+ * product of Eq. matvec_3 (y_K = sum over K' in N(K) of H_{K;K'} x_{K'}) that
+ * the Rayleigh-Ritz step (Alg. 1 step 4, H Y_hat) runs when the context's
+ * subspace products are DGCHEFSI_PRODUCTS_SLICED_BF16. Each row of H (element
+ * K, row n) is split into `slices` 6-bit digits with one exponent e_r for the
+ * whole row, which contracts over at most 4096 columns (the columns of K's
+ * neighbour blocks), so every slice-pair product is an exact FP32 integer;
+ * each state with one exponent f_s over all its N entries. The slice pairs
+ * (i + j <= slices - 1) run on the tensor-core filter's block-sparse step
+ * kernel, one pair per launch, into FP32 workspace (state panels under 8 GB),
+ * and are summed in FP64 as in dgchefsi_sliced_gemm. Error of Y[s, r]: at most
+ * L m_r n_s (2^{-6 slices} (slices + 4) + 6 u), L = the row's column count,
+ * m_r and n_s the row's and the state's largest |entry|.
+ *   X  device (Ns x ld) state-major, FP64;  Y  device (Ns x ld) out, must not overlap X
+ *   slices  2..16
+ * ERR_UNSUPPORTED when a block row of H spans more than 4096 columns or an
+ * element is larger than 128 (the FP64 dgchefsi_matvec serves those);
+ * ERR_NONFINITE on NaN/Inf in H or X. Synchronises. */
+dgchefsi_status dgchefsi_sliced_matvec(dgchefsi_ctx* ctx, const double* X, double* Y, int64_t Ns, int64_t ld,
+                                       int slices);
 
 /* Fermi-Dirac occupations f_i = 1/(1 + exp((lambda_i - mu)/kT)) with mu set by
  * 2 sum_i f_i = Ne (spin factor 2; occupations of Eq. KS_DG_Energy, Sec. III.B.2).

@@ -41,7 +41,12 @@ Parity pins (tests/test_oracle_pins.py) check every function here against
 results the mathematics fixes independently of this code: brute-force dense
 products, the closed form V C_m(Lambda) V^T X of the filter, dense eigh of H,
 QR uniqueness, exact spectra of diagonal matrices, and trace / symmetry
-identities.
+identities. The precision forms' rounded filter (``chebyshev_filter_rounded``)
+is pinned in tests/test_oracle_rounded.py: its BF16 rounding against
+PyTorch's conversion, its TF32 cut against the closed form, exactness on
+operands that need no rounding, and its distance from the FP64 filter.
+``lowest_eigenvalues`` is a library eigensolve of the assembled matrix (the
+definition of the exact spectrum).
 """
 from __future__ import annotations
 

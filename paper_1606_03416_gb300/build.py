@@ -68,7 +68,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         list(ex.map(run, jobs))
     if jobs or not os.path.exists(LIB):
         libdir = os.path.join(cuda_home(), "lib64")
-        run([nvcc(), "-shared", "-o", LIB] + objs + ARCH + ["-L", libdir, "-lcusolver", "-lcublas", "-lcudart",
+        run([nvcc(), "-shared", "-o", LIB] + objs + ARCH + ["-L", libdir, "-lcusolver", "-lcudart",
             "-Xlinker", "-rpath," + libdir])
     return LIB
 

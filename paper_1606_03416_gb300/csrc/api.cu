@@ -371,7 +371,11 @@ static dgchefsi_status rr_impl(dgchefsi_ctx* ctx, double* Y, int64_t Ns, int64_t
   // symmetric up to rounding and the eigensolver reads one triangle (row-major
   // lower = column-major upper), so only the tiles on and below the diagonal
   // are computed.
-  DG_CUDA(filter_step_f64(ctx->view(), W, N, nullptr, Y, ld, Ns, 1.0, 0.0, 0.0, s));
+  // With sliced products H Y_hat also runs from BF16 slices, on the
+  // tensor-core filter's block-sparse step kernel, when H fits that form.
+  bool hx_sliced = false;
+  if (sl) DG_TRY(tc_sliced_matvec(ctx, W, N, Y, ld, Ns, ctx->products_slices, bad, &hx_sliced));
+  if (!hx_sliced) DG_CUDA(filter_step_f64(ctx->view(), W, N, nullptr, Y, ld, Ns, 1.0, 0.0, 0.0, s));
   if (sl)
     DG_TRY(sliced_gemm(ctx, true, false, Ns, Ns, N, W, N, Y, ld, S, Ns, ctx->products_slices, bad));
   else
@@ -550,6 +554,7 @@ void dgchefsi_destroy(dgchefsi_ctx* ctx) {
   free_buf(ctx->ws_realign);
   free_buf(ctx->ws_sliced);
   free_buf(ctx->ws_sliced_t);
+  free_buf(ctx->ws_sliced_b);
   for (int i = 0; i < 2; ++i) {
     free_buf(ctx->ws_hin[i]);
     free_buf(ctx->ws_hout[i]);
@@ -769,6 +774,30 @@ dgchefsi_status dgchefsi_sliced_gemm(dgchefsi_ctx* ctx, int b_rows, int a_lower,
   DG_CUDA(cudaMemcpyAsync(&bad, ctx->info_d + 3, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   DG_CUDA(cudaStreamSynchronize(ctx->stream));
   if (bad) return set_error(DGCHEFSI_ERR_NONFINITE, "non-finite entry in A or B");
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status dgchefsi_sliced_matvec(dgchefsi_ctx* ctx, const double* X, double* Y, int64_t Ns, int64_t ld,
+                                       int slices) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  DG_TRY(check_block(ctx, X, Ns, ld, "X"));
+  DG_TRY(check_block(ctx, Y, Ns, ld, "Y"));
+  if (slices < 2 || slices > 16) return set_error(DGCHEFSI_ERR_ARG, "slices = %d outside 2..16", slices);
+  if (Ns == 0) return DGCHEFSI_OK;
+  if (overlaps(X, Y, sizeof(double) * (size_t)((Ns - 1) * ld + ctx->N)))
+    return set_error(DGCHEFSI_ERR_ARG, "Y overlaps X");
+  DG_CUDA(cudaMemsetAsync(ctx->info_d + 3, 0, sizeof(int), ctx->stream));
+  bool used = false;
+  DG_TRY(tc_sliced_matvec(ctx, X, ld, Y, ld, Ns, slices, ctx->info_d + 3, &used));
+  if (!used)
+    return set_error(DGCHEFSI_ERR_UNSUPPORTED,
+                     "H does not fit the sliced product (a block row longer than 4096 columns or an element "
+                     "larger than 128)");
+  int bad = 0;
+  DG_CUDA(cudaMemcpyAsync(&bad, ctx->info_d + 3, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  DG_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (bad) return set_error(DGCHEFSI_ERR_NONFINITE, "non-finite entry in H or X");
   return DGCHEFSI_OK;
 }
 

@@ -1,5 +1,6 @@
 // Library context and host-side helpers shared by the API translation units.
 #pragma once
+#include <cuda_bf16.h>
 #include <cusolverDn.h>
 
 #include <cstdarg>
@@ -53,12 +54,12 @@ struct dgchefsi_ctx {
   dg::DevBuf ws_realign;  // per-element tables and overlaps of the re-alignment
   int orth_mode = 0;      // DGCHEFSI_ORTH_*: orthonormalisation of step 3
   // Rayleigh-Ritz products: DGCHEFSI_PRODUCTS_*, slice count of the sliced
-  // BF16 form, its cuBLAS handle (created on first use) and workspace
+  // BF16 form and its workspace
   int products_mode = 0;
   int products_slices = 10;
-  void* blas = nullptr;
   dg::DevBuf ws_sliced;
   dg::DevBuf ws_sliced_t;  // transposed left operand of the A^T B form
+  dg::DevBuf ws_sliced_b;  // transposed right operand of the A B form
   int32_t f64_tj = 64;    // column tile of the FP64 filter (set at create)
   // FP64 filter as a CUDA graph: coefficients copied from a pinned mirror at
   // every replay; the graph is captured again when X, Y, N_s, ld, m or the
@@ -140,6 +141,38 @@ dgchefsi_status sliced_gemm(dgchefsi_ctx* ctx, bool b_rows, bool a_lower, int64_
 dgchefsi_status sliced_gemm_tn(dgchefsi_ctx* ctx, int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda,
                                const double* B, int64_t ldb, double* C, int64_t ldc, int s, int* flag);
 void sliced_destroy(dgchefsi_ctx* ctx);
+
+// Slices for the block-sparse product H X (sliced.cu). slices_of_h: the row
+// exponents E (element-padded rows) and s digit copies of H in the tensor-core
+// operand layout (brow: first row of each block, cstride: elements per copy).
+// slices_of_states: the state exponents E[Ns] and s digit copies of X in the
+// element-padded layout (cmap: padded column -> column, -1 for padding).
+// reduce_pair_slabs: C[r, cmap[c]] = the FP64 sum of the slice-pair slabs
+// (rows x cols FP32 each, pair order of the dense form) scaled by Erows[r] + Ecols[c].
+cudaError_t slices_of_h(const dgchefsi_ctx* ctx, const int32_t* blk_row, const int32_t* pnb, const int32_t* poff,
+                        const int64_t* brow, int s, __nv_bfloat16* Q, int64_t cstride, int32_t* E, int* flag,
+                        cudaStream_t st);
+cudaError_t slices_of_states(const double* X, int64_t ld, int64_t Ns, int64_t N, const int32_t* cmap, int64_t ldp,
+                             int s, __nv_bfloat16* Q, int64_t cstride, int32_t* E, int* flag, cudaStream_t st);
+dgchefsi_status reduce_pair_slabs(const float* Pw, int64_t rows, int64_t cols, const int32_t* Erows,
+                                  const int32_t* Ecols, const int32_t* cmap, double* C, int64_t ldc, int s,
+                                  cudaStream_t st);
+// The slice-pair products of the dense sliced GEMM on the tensor-core filter's
+// transposed step kernel (tc_filter.cu): for every pair i + j < s,
+// Pw[pair i*s - i(i-1)/2 + j] (M x pn, row-major FP32) = Qa_i[:, k0:k0+kc] times
+// Qb_j[n0:n0+pn, k0:k0+kc]^T, Qa_i = Qa + i*sa (M x K, row stride lqa),
+// Qb_j = Qb + j*sb (Nc x K, row stride lqb), entries k >= K read as zero.
+// Enqueued only; tc_slice_pairs_status synchronises and reports a pipeline timeout.
+dgchefsi_status tc_slice_pairs(dgchefsi_ctx* ctx, const __nv_bfloat16* Qa, int64_t lqa, int64_t sa, int64_t M,
+                               const __nv_bfloat16* Qb, int64_t lqb, int64_t sb, int64_t Nc, int64_t K, int64_t k0,
+                               int64_t kc, int64_t n0, int64_t pn, int s, float* Pw);
+dgchefsi_status tc_slice_pairs_status(dgchefsi_ctx* ctx);
+// Y = H X (X, Y: Ns x ld state-major FP64) from s BF16 slices of each operand on
+// the tensor-core filter's step kernel (tc_filter.cu). *used = false when this
+// H does not fit the form (a row longer than 4096 columns, or an element
+// larger than 128): the caller then runs the FP64 product.
+dgchefsi_status tc_sliced_matvec(dgchefsi_ctx* ctx, const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t Ns,
+                                 int s, int* flag, bool* used);
 
 // Set-up of dgchefsi_bounds_static for `device` (noalloc.cu), run by
 // dgchefsi_create with that device current: looks up the device address of

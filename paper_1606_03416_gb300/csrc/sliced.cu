@@ -13,9 +13,10 @@
 // returns it exactly, whatever its summation order. The pairs with
 // i + j <= s - 1 are kept; their FP32 results are summed per t = i + j in FP64
 // (exact: integers below 2^53), combined by Horner in 2^{-6}, scaled by
-// 2^{e_r + f_c - 12} and added over the chunks. The slice-pair products are
-// plain BF16 GEMMs (cuBLAS, FP32 output); splitting and the FP64 reduction are
-// the kernels below.
+// 2^{e_r + f_c - 12} and added over the chunks. The slice-pair products run
+// on this library's tcgen05 block-sparse step kernel (the filter's, with
+// 128-row blocks of the right operand as its elements, one pair per launch,
+// FP32 output); splitting and the FP64 reduction are the kernels below.
 //
 // Error per chunk (row and column maxima m_r, n_c over the chunk): the
 // remainders after s slices and the dropped pairs contribute at most
@@ -25,9 +26,9 @@
 // FP64's own worst-case bound. The bound is normwise per row and column:
 // entries far below their row's maximum keep fewer significant bits than FP64.
 #include <cuda_bf16.h>
-#include <cublas_v2.h>
 
 #include <algorithm>
+#include <cmath>
 #include <climits>
 
 #include "ctx.h"
@@ -36,7 +37,6 @@ namespace dg {
 
 static constexpr int kBeta = 6;      // bits per slice
 static constexpr int64_t kL = 4096;  // K chunk: 4096 * 2^12 = 2^24
-static constexpr int kCols = 64;     // columns per CTA of the column split
 
 __device__ __forceinline__ void atomic_flag(int* flag) {
   if (flag) atomicOr(flag, 1);
@@ -166,63 +166,10 @@ __global__ void __launch_bounds__(256) k_split_rows(const double* __restrict__ X
   }
 }
 
-// One CTA per (64 columns, chunk) of a row-major K x C operand, 256 threads:
-// lane group of 64 columns x 4 row phases. Column exponents first, then the
-// slices (the second read of the chunk comes from L2). Q: s slices of
-// K x ldq BF16; E[col * nch + chunk] = f_c. Row k is split as X[k, :] 2^{-bal[k]}.
-__global__ void __launch_bounds__(256) k_split_cols(const double* __restrict__ X, int64_t ldx, int64_t K, int64_t C,
-                                                    int s, const int32_t* __restrict__ bal,
-                                                    __nv_bfloat16* __restrict__ Q, int64_t ldq, int64_t sstride,
-                                                    int32_t* __restrict__ E, int nch, int* __restrict__ flag) {
-  const int cl = threadIdx.x % kCols;
-  const int ph = threadIdx.x / kCols;
-  const int64_t col = (int64_t)blockIdx.x * kCols + cl;
-  const int chunk = blockIdx.y;
-  const int64_t k0 = (int64_t)chunk * kL;
-  const int64_t k1 = std::min<int64_t>(K, k0 + kL);
-  int emax = INT_MIN;
-  bool bad = false;
-  if (col < C)
-    for (int64_t k = k0 + ph; k < k1; k += 4) {
-      int64_t M;
-      int Ex;
-      const int c = decompose(X[k * ldx + col], M, Ex);
-      if (c == 2) bad = true;
-      if (c == 1) emax = max(emax, Ex - bal[k]);
-    }
-  __shared__ int red[4][kCols];
-  __shared__ int sbad[kCols];
-  if (ph == 0) sbad[cl] = 0;
-  red[ph][cl] = emax;
-  __syncthreads();
-  if (bad) sbad[cl] = 1;
-  __syncthreads();
-  emax = max(max(red[0][cl], red[1][cl]), max(red[2][cl], red[3][cl]));
-  const bool zero = sbad[cl] != 0;
-  const int e = (emax == INT_MIN || zero) ? 0 : emax - 1022;
-  if (col >= C) return;
-  if (ph == 0) {
-    E[col * nch + chunk] = e;
-    if (zero) atomic_flag(flag);
-  }
-  for (int64_t k = k0 + ph; k < k1; k += 4) {
-    const double x = X[k * ldx + col];
-    __nv_bfloat16* q = Q + k * ldq + col;
-    if (s <= 10) {
-      int64_t M = 0;
-      int Ex = 0;
-      if (zero || decompose(x, M, Ex) != 1) M = 0;
-      slice_fixed(M, Ex - bal[k], x < 0.0, -1075 - e + 6 * s, s, q, sstride);
-    } else {
-      slice_fp64(zero ? 0.0 : ldexp(x, -bal[k] - e), s, q, sstride);
-    }
-  }
-}
-
 // bal[k] = frexp exponent of max_c |X[k, c]| (X row-major K x C), 0 for a row
-// with no finite nonzero entry. One CTA per row.
+// with no finite nonzero entry, and nbal[k] = -bal[k]. One CTA per row.
 __global__ void __launch_bounds__(256) k_row_exponents(const double* __restrict__ X, int64_t ldx, int64_t C,
-                                                       int32_t* __restrict__ bal) {
+                                                       int32_t* __restrict__ bal, int32_t* __restrict__ nbal) {
   const int64_t k = blockIdx.x;
   int emax = INT_MIN;
   for (int64_t c = threadIdx.x; c < C; c += 256) {
@@ -238,6 +185,7 @@ __global__ void __launch_bounds__(256) k_row_exponents(const double* __restrict_
     for (int w = 1; w < 8; ++w) emax = max(emax, red[w]);
     emax = max(emax, red[0]);
     bal[k] = emax == INT_MIN ? 0 : emax - 1022;
+    nbal[k] = -bal[k];
   }
 }
 
@@ -248,11 +196,13 @@ __global__ void __launch_bounds__(256) k_row_exponents(const double* __restrict_
 // (< 2^53, exact in FP64), and the blocks meet in FP64: one rounding per 30
 // bits of weight. Every slab value is loaded once, all loads of an output
 // before any use, so the kernel streams Pw at memory speed.
+// cmap (may be null): column c of the slabs goes to column cmap[c] of C, and
+// is skipped when cmap[c] < 0 (the padding columns of the element-padded layout).
 template <int S>
 __global__ void __launch_bounds__(256) k_sliced_reduce(const float* __restrict__ Pw, int64_t M, int64_t P,
                                                        const int32_t* __restrict__ Ea, const int32_t* __restrict__ Eb,
                                                        int nch, int chunk, int64_t n0, double* __restrict__ C,
-                                                       int64_t ldc, int accumulate) {
+                                                       int64_t ldc, int accumulate, const int32_t* __restrict__ cmap) {
   constexpr int NB = (S + 4) / 5;  // blocks of five t
   const int64_t total = M * P;
   const int64_t slab = M * P;
@@ -277,14 +227,16 @@ __global__ void __launch_bounds__(256) k_sliced_reduce(const float* __restrict__
     }
     const int64_t r = idx / P;
     const int64_t c = idx - r * P;
+    const int64_t oc = cmap ? (int64_t)cmap[c] : n0 + c;
+    if (oc < 0) continue;
     const double v = ldexp(h, Ea[r * nch + chunk] + Eb[(n0 + c) * nch + chunk] - 12 - 24);
-    double* out = C + r * ldc + n0 + c;
+    double* out = C + r * ldc + oc;
     *out = accumulate ? *out + v : v;
   }
 }
 
 typedef void (*ReduceKernel)(const float*, int64_t, int64_t, const int32_t*, const int32_t*, int, int, int64_t,
-                             double*, int64_t, int);
+                             double*, int64_t, int, const int32_t*);
 
 static ReduceKernel reduce_kernel(int s) {
   switch (s) {
@@ -298,130 +250,10 @@ static ReduceKernel reduce_kernel(int s) {
   }
 }
 
-static const char* blas_str(cublasStatus_t s) {
-  switch (s) {
-    case CUBLAS_STATUS_SUCCESS: return "success";
-    case CUBLAS_STATUS_NOT_INITIALIZED: return "not initialised";
-    case CUBLAS_STATUS_ALLOC_FAILED: return "allocation failed";
-    case CUBLAS_STATUS_INVALID_VALUE: return "invalid value";
-    case CUBLAS_STATUS_ARCH_MISMATCH: return "architecture mismatch";
-    case CUBLAS_STATUS_EXECUTION_FAILED: return "execution failed";
-    case CUBLAS_STATUS_NOT_SUPPORTED: return "not supported";
-    default: return "cuBLAS error";
-  }
-}
-
-#define DG_BLAS(call)                                                                                         \
-  do {                                                                                                        \
-    cublasStatus_t b_ = (call);                                                                               \
-    if (b_ != CUBLAS_STATUS_SUCCESS)                                                                          \
-      return set_error(DGCHEFSI_ERR_CUDA, "%s failed: %s (%s:%d)", #call, blas_str(b_), __FILE__, __LINE__); \
-  } while (0)
-
 static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // Workspace cap of the FP32 slice-pair products; wider outputs run in column panels.
-static constexpr size_t kPairBytes = size_t(4) << 30;
-
-dgchefsi_status sliced_gemm(dgchefsi_ctx* ctx, bool b_rows, bool a_lower, int64_t M, int64_t Nc, int64_t K,
-                            const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int s,
-                            int* flag) {
-  if (M <= 0 || Nc <= 0) return DGCHEFSI_OK;
-  if (!reduce_kernel(s)) return set_error(DGCHEFSI_ERR_ARG, "slices = %d outside 2..16", s);
-  cudaStream_t st = ctx->stream;
-  if (K <= 0) {
-    DG_CUDA(cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * Nc, M, st));
-    return DGCHEFSI_OK;
-  }
-  if (!ctx->blas) {
-    cublasHandle_t h = nullptr;
-    DG_BLAS(cublasCreate(&h));
-    ctx->blas = h;
-  }
-  cublasHandle_t h = static_cast<cublasHandle_t>(ctx->blas);
-  DG_BLAS(cublasSetStream(h, st));
-  DG_BLAS(cublasSetPointerMode(h, CUBLAS_POINTER_MODE_HOST));
-  const int nch = (int)((K + kL - 1) / kL);
-  const int64_t pairs = (int64_t)s * (s + 1) / 2;
-  // Slices of A: s x M x lqa (K contiguous). Slices of B: b_rows ? s x Nc x lqb
-  // (K contiguous) : s x K x lqb (Nc contiguous).
-  const int64_t lqa = round_up(K, 8);
-  const int64_t lqb = b_rows ? round_up(K, 8) : round_up(Nc, 8);
-  const int64_t sa = M * lqa;
-  const int64_t sb = b_rows ? Nc * lqb : K * lqb;
-  const bool same = b_rows && A == B && lda == ldb && M == Nc && !a_lower;
-  const size_t qa_bytes = sizeof(__nv_bfloat16) * (size_t)(s * sa);
-  const size_t qb_bytes = same ? 0 : sizeof(__nv_bfloat16) * (size_t)(s * sb);
-  const size_t ea_bytes = sizeof(int32_t) * (size_t)(M * nch);
-  const size_t eb_bytes = sizeof(int32_t) * (size_t)(Nc * nch);
-  const size_t bal_bytes = b_rows ? 0 : sizeof(int32_t) * (size_t)K;
-  const size_t a256 = 256;
-  auto up = [&](size_t x) { return (x + a256 - 1) / a256 * a256; };
-  // Column panel of the product so that the FP32 pair slabs stay under the cap.
-  int64_t P = (int64_t)(kPairBytes / (sizeof(float) * (size_t)pairs * (size_t)M));
-  P = std::max<int64_t>(8, P / 8 * 8);
-  if (P >= Nc) P = Nc;
-  const size_t pw_bytes = sizeof(float) * (size_t)pairs * (size_t)M * (size_t)P;
-  DG_TRY(ensure(ctx, ctx->ws_sliced,
-                up(qa_bytes) + up(qb_bytes) + up(ea_bytes) + up(eb_bytes) + up(bal_bytes) + up(pw_bytes),
-                "sliced-product workspace"));
-  char* base = static_cast<char*>(ctx->ws_sliced.p);
-  __nv_bfloat16* Qa = reinterpret_cast<__nv_bfloat16*>(base);
-  __nv_bfloat16* Qb = same ? Qa : reinterpret_cast<__nv_bfloat16*>(base + up(qa_bytes));
-  int32_t* Ea = reinterpret_cast<int32_t*>(base + up(qa_bytes) + up(qb_bytes));
-  int32_t* Eb = same ? Ea : reinterpret_cast<int32_t*>(base + up(qa_bytes) + up(qb_bytes) + up(ea_bytes));
-  int32_t* bal = b_rows ? nullptr
-                        : reinterpret_cast<int32_t*>(base + up(qa_bytes) + up(qb_bytes) + up(ea_bytes) + up(eb_bytes));
-  float* Pw =
-      reinterpret_cast<float*>(base + up(qa_bytes) + up(qb_bytes) + up(ea_bytes) + up(eb_bytes) + up(bal_bytes));
-
-  // C = A B with B (K x Nc): every K index k is balanced first, row k of B by
-  // 2^{-s_k} and column k of A by 2^{s_k} (exact), s_k the exponent of B's row
-  // maximum, so that rows of B with very different norms (the filtered states
-  // of Y_hat^T = U^{-T} Y^T) do not share one column scale.
-  if (!b_rows) {
-    k_row_exponents<<<(unsigned)K, 256, 0, st>>>(B, ldb, Nc, bal);
-    count_launch();
-    DG_CUDA(cudaGetLastError());
-  }
-  k_split_rows<<<dim3((unsigned)M, (unsigned)nch), 256, 0, st>>>(A, lda, K, s, a_lower ? 1 : 0, bal, Qa, lqa, sa,
-                                                                  Ea, nch, flag);
-  count_launch();
-  DG_CUDA(cudaGetLastError());
-  if (!same) {
-    if (b_rows)
-      k_split_rows<<<dim3((unsigned)Nc, (unsigned)nch), 256, 0, st>>>(B, ldb, K, s, 0, nullptr, Qb, lqb, sb, Eb, nch,
-                                                                       flag);
-    else
-      k_split_cols<<<dim3((unsigned)((Nc + kCols - 1) / kCols), (unsigned)nch), 256, 0, st>>>(
-          B, ldb, K, Nc, s, bal, Qb, lqb, sb, Eb, nch, flag);
-    count_launch();
-    DG_CUDA(cudaGetLastError());
-  }
-  const float one = 1.0f, zero = 0.0f;
-  for (int64_t n0 = 0; n0 < Nc; n0 += P) {
-    const int64_t pn = std::min<int64_t>(P, Nc - n0);
-    for (int chunk = 0; chunk < nch; ++chunk) {
-      const int64_t k0 = (int64_t)chunk * kL;
-      const int kc = (int)std::min<int64_t>(kL, K - k0);
-      // Column-major view: (pn x M) slab of pair (i, j) = op(Qb_j) (pn x kc) * Qa_i (kc x M).
-      for (int i = 0; i < s; ++i) {
-        const int64_t p0 = (int64_t)i * s - (int64_t)i * (i - 1) / 2;
-        const __nv_bfloat16* bq = b_rows ? Qb + n0 * lqb + k0 : Qb + k0 * lqb + n0;
-        DG_BLAS(cublasGemmStridedBatchedEx(h, b_rows ? CUBLAS_OP_T : CUBLAS_OP_N, CUBLAS_OP_N, (int)pn, (int)M, kc,
-                                           &one, bq, CUDA_R_16BF, (int)lqb, sb, Qa + i * sa + k0, CUDA_R_16BF,
-                                           (int)lqa, 0, &zero, Pw + p0 * M * pn, CUDA_R_32F, (int)pn, M * pn, s - i,
-                                           CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT));
-      }
-      const int64_t total = M * pn;
-      const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
-      reduce_kernel(s)<<<grid, 256, 0, st>>>(Pw, M, pn, Ea, Eb, nch, chunk, n0, C, ldc, chunk > 0 ? 1 : 0);
-      count_launch();
-      DG_CUDA(cudaGetLastError());
-    }
-  }
-  return DGCHEFSI_OK;
-}
+static constexpr size_t kPairBytes = size_t(8) << 30;
 
 // T (cols x rows, row-major, ldt) = X^T for X (rows x cols, row-major, ldx);
 // 32 x 32 tiles through shared memory, 32 x 8 threads.
@@ -440,25 +272,293 @@ __global__ void __launch_bounds__(256) k_transpose_f64(const double* __restrict_
   }
 }
 
+static dgchefsi_status transpose_f64(const double* X, int64_t ldx, int64_t rows, int64_t cols, double* T, int64_t ldt,
+                                     cudaStream_t st) {
+  if ((rows + 31) / 32 > 65535) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "transpose of %lld rows", (long long)rows);
+  k_transpose_f64<<<dim3((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32)), dim3(32, 8), 0, st>>>(
+      X, ldx, rows, cols, T, ldt);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status sliced_gemm(dgchefsi_ctx* ctx, bool b_rows, bool a_lower, int64_t M, int64_t Nc, int64_t K,
+                            const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int s,
+                            int* flag) {
+  if (M <= 0 || Nc <= 0) return DGCHEFSI_OK;
+  if (!reduce_kernel(s)) return set_error(DGCHEFSI_ERR_ARG, "slices = %d outside 2..16", s);
+  cudaStream_t st = ctx->stream;
+  if (K <= 0) {
+    DG_CUDA(cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * Nc, M, st));
+    return DGCHEFSI_OK;
+  }
+  const int nch = (int)((K + kL - 1) / kL);
+  const int64_t pairs = (int64_t)s * (s + 1) / 2;
+  // Slices of A: s x M x lqa, of the right operand as rows: s x Nc x lqb (K
+  // contiguous in both; the A B form transposes B first).
+  const int64_t lqa = round_up(K, 8);
+  const int64_t lqb = round_up(K, 8);
+  const int64_t sa = M * lqa;
+  const int64_t sb = Nc * lqb;
+  const bool same = b_rows && A == B && lda == ldb && M == Nc && !a_lower;
+  const size_t qa_bytes = sizeof(__nv_bfloat16) * (size_t)(s * sa);
+  const size_t qb_bytes = same ? 0 : sizeof(__nv_bfloat16) * (size_t)(s * sb);
+  const size_t ea_bytes = sizeof(int32_t) * (size_t)(M * nch);
+  const size_t eb_bytes = sizeof(int32_t) * (size_t)(Nc * nch);
+  const size_t bal_bytes = b_rows ? 0 : 2 * sizeof(int32_t) * (size_t)K;
+  const size_t a256 = 256;
+  auto up = [&](size_t x) { return (x + a256 - 1) / a256 * a256; };
+  // Column panel of the product (a multiple of the kernel's 128-column tiles)
+  // so that the FP32 pair slabs stay under the cap.
+  int64_t P = (int64_t)(kPairBytes / (sizeof(float) * (size_t)pairs * (size_t)M));
+  P = std::max<int64_t>(128, P / 128 * 128);
+  if (P >= Nc) P = Nc;
+  const size_t pw_bytes = sizeof(float) * (size_t)pairs * (size_t)M * (size_t)P;
+  DG_TRY(ensure(ctx, ctx->ws_sliced,
+                up(qa_bytes) + up(qb_bytes) + up(ea_bytes) + up(eb_bytes) + up(bal_bytes) + up(pw_bytes),
+                "sliced-product workspace"));
+  char* base = static_cast<char*>(ctx->ws_sliced.p);
+  __nv_bfloat16* Qa = reinterpret_cast<__nv_bfloat16*>(base);
+  __nv_bfloat16* Qb = same ? Qa : reinterpret_cast<__nv_bfloat16*>(base + up(qa_bytes));
+  int32_t* Ea = reinterpret_cast<int32_t*>(base + up(qa_bytes) + up(qb_bytes));
+  int32_t* Eb = same ? Ea : reinterpret_cast<int32_t*>(base + up(qa_bytes) + up(qb_bytes) + up(ea_bytes));
+  int32_t* bal = b_rows ? nullptr
+                        : reinterpret_cast<int32_t*>(base + up(qa_bytes) + up(qb_bytes) + up(ea_bytes) + up(eb_bytes));
+  int32_t* nbal = b_rows ? nullptr : bal + K;
+  float* Pw =
+      reinterpret_cast<float*>(base + up(qa_bytes) + up(qb_bytes) + up(ea_bytes) + up(eb_bytes) + up(bal_bytes));
+
+  // C = A B with B (K x Nc): every K index k is balanced first, row k of B by
+  // 2^{-s_k} and column k of A by 2^{s_k} (exact), s_k the exponent of B's row
+  // maximum, so that rows of B with very different norms (the filtered states
+  // of Y_hat^T = U^{-T} Y^T) do not share one column scale. B is then
+  // transposed (Nc x K) and split by rows like the A B^T form.
+  const double* Br = B;
+  int64_t ldbr = ldb;
+  if (!b_rows) {
+    k_row_exponents<<<(unsigned)K, 256, 0, st>>>(B, ldb, Nc, bal, nbal);
+    count_launch();
+    DG_CUDA(cudaGetLastError());
+    DG_TRY(ensure(ctx, ctx->ws_sliced_b, sizeof(double) * (size_t)Nc * (size_t)K, "transposed right operand"));
+    double* Bt = static_cast<double*>(ctx->ws_sliced_b.p);
+    DG_TRY(transpose_f64(B, ldb, K, Nc, Bt, K, st));
+    Br = Bt;
+    ldbr = K;
+  }
+  k_split_rows<<<dim3((unsigned)M, (unsigned)nch), 256, 0, st>>>(A, lda, K, s, a_lower ? 1 : 0, bal, Qa, lqa, sa,
+                                                                  Ea, nch, flag);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  if (!same) {
+    k_split_rows<<<dim3((unsigned)Nc, (unsigned)nch), 256, 0, st>>>(Br, ldbr, K, s, 0, nbal, Qb, lqb, sb, Eb, nch,
+                                                                     flag);
+    count_launch();
+    DG_CUDA(cudaGetLastError());
+  }
+  for (int64_t n0 = 0; n0 < Nc; n0 += P) {
+    const int64_t pn = std::min<int64_t>(P, Nc - n0);
+    for (int chunk = 0; chunk < nch; ++chunk) {
+      const int64_t k0 = (int64_t)chunk * kL;
+      const int64_t kc = std::min<int64_t>(kL, K - k0);
+      // slab of pair (i, j): M x pn, Qa_i times the panel's rows of Qb_j over this chunk
+      DG_TRY(tc_slice_pairs(ctx, Qa, lqa, sa, M, Qb, lqb, sb, Nc, K, k0, kc, n0, pn, s, Pw));
+      const int64_t total = M * pn;
+      const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+      reduce_kernel(s)<<<grid, 256, 0, st>>>(Pw, M, pn, Ea, Eb, nch, chunk, n0, C, ldc, chunk > 0 ? 1 : 0,
+                                             nullptr);
+      count_launch();
+      DG_CUDA(cudaGetLastError());
+    }
+  }
+  return tc_slice_pairs_status(ctx);
+}
+
+// ---------------------------------------------------------------------------
+// H X from slices (the block-sparse product of Rayleigh-Ritz, W = H Y_hat).
+// Row r of H (element K, row n) contracts over the columns of K's neighbour
+// blocks only, at most 4096 of them, so one K chunk covers every row: its
+// exponent e_r is over the whole row. Each state's exponent f_s is over all N
+// of its components (a valid bound for every row's column range). H's digits
+// are written in the block layout of the tensor-core filter's operand copy
+// of H (64-column slices of each block, element-padded rows), the states'
+// digits in its element-padded state-major layout, so the filter's step
+// kernel multiplies one slice pair per launch (alpha = 1, beta = 0) into an
+// FP32 slab, and k_sliced_reduce (with the padded-to-plain column map)
+// combines the slabs.
+
+// E[poff_K + n] = frexp exponent of max_j |H[(K, n), j]| over row n of element
+// K's blocks (0 for an all-zero row, and for the padding rows n >= nb[K]).
+// One CTA per element. A non-finite entry raises flag.
+__global__ void __launch_bounds__(256) k_h_row_exponents(const int64_t* __restrict__ row_ptr,
+                                                         const int32_t* __restrict__ col,
+                                                         const int64_t* __restrict__ blk_off,
+                                                         const double* __restrict__ vals,
+                                                         const int32_t* __restrict__ nb,
+                                                         const int32_t* __restrict__ pnb,
+                                                         const int32_t* __restrict__ poff, int32_t* __restrict__ E,
+                                                         int* __restrict__ flag) {
+  __shared__ int emax[256];
+  __shared__ int bad;
+  const int K = blockIdx.x;
+  const int nK = nb[K];
+  for (int n = threadIdx.x; n < 256; n += blockDim.x) emax[n] = INT_MIN;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int64_t e = row_ptr[K]; e < row_ptr[K + 1]; ++e) {
+    const int nKp = nb[col[e]];
+    const double* blk = vals + blk_off[e];
+    const int64_t total = (int64_t)nK * nKp;
+    for (int64_t t = threadIdx.x; t < total; t += blockDim.x) {
+      int64_t Mm;
+      int Ex;
+      const int c = decompose(blk[t], Mm, Ex);
+      if (c == 2) bad = 1;
+      if (c == 1) atomicMax(&emax[(int)(t / nKp)], Ex);
+    }
+  }
+  __syncthreads();
+  for (int n = threadIdx.x; n < pnb[K]; n += blockDim.x)
+    E[poff[K] + n] = (n < nK && emax[n] != INT_MIN && !bad) ? emax[n] - 1022 : 0;
+  if (threadIdx.x == 0 && bad) atomic_flag(flag);
+}
+
+// s digit copies of H in the filter's operand layout: block e, 64-column
+// slice sl, padded row n at row brow[e] + sl * pnb[K] + n of each copy (copy i
+// starts at Q + i * cstride); entries past the block (padding) are zero.
+__global__ void __launch_bounds__(256) k_build_h_slices(const int32_t* __restrict__ blk_row,
+                                                        const int32_t* __restrict__ col,
+                                                        const int64_t* __restrict__ blk_off,
+                                                        const double* __restrict__ vals,
+                                                        const int32_t* __restrict__ nb,
+                                                        const int32_t* __restrict__ pnb,
+                                                        const int32_t* __restrict__ poff,
+                                                        const int64_t* __restrict__ brow,
+                                                        const int32_t* __restrict__ E, int s,
+                                                        __nv_bfloat16* __restrict__ Q, int64_t cstride) {
+  constexpr int W = 64;
+  const int64_t e = blockIdx.x;
+  const int K = blk_row[e], Kp = col[e];
+  const int nK = nb[K], nKp = nb[Kp], pK = pnb[K];
+  const int nsl = (pnb[Kp] + W - 1) / W;
+  const double* blk = vals + blk_off[e];
+  const int64_t total = (int64_t)nsl * pK * W;
+  for (int64_t t = threadIdx.x; t < total; t += blockDim.x) {
+    const int w = (int)(t % W);
+    const int64_t rr = t / W;
+    const int n = (int)(rr % pK);
+    const int sl = (int)(rr / pK);
+    const int jp = sl * W + w;
+    const double v = (n < nK && jp < nKp) ? blk[(int64_t)n * nKp + jp] : 0.0;
+    const int er = E[poff[K] + n];
+    __nv_bfloat16* q = Q + (brow[e] + rr) * W + w;
+    if (s <= 10) {
+      int64_t Mm = 0;
+      int Ex = 0;
+      if (decompose(v, Mm, Ex) != 1) Mm = 0;
+      slice_fixed(Mm, Ex, v < 0.0, -1075 - er + 6 * s, s, q, cstride);
+    } else {
+      slice_fp64(std::isfinite(v) ? ldexp(v, -er) : 0.0, s, q, cstride);
+    }
+  }
+}
+
+// s digit copies of the states X (Ns x ld, state-major) in the element-padded
+// layout (Ns x ldp per copy, copy i at Q + i * cstride); cmap[c] is the
+// column of padded column c (-1 for padding, written as zero). E[s] = frexp
+// exponent of the state's largest |entry|. One CTA per state, two passes.
+__global__ void __launch_bounds__(256) k_pack_state_slices(const double* __restrict__ X, int64_t ld, int64_t N,
+                                                           const int32_t* __restrict__ cmap, int64_t ldp, int s,
+                                                           __nv_bfloat16* __restrict__ Q, int64_t cstride,
+                                                           int32_t* __restrict__ E, int* __restrict__ flag) {
+  const int64_t st = blockIdx.x;
+  const double* x = X + st * ld;
+  int emax = INT_MIN;
+  bool bad = false;
+  for (int64_t c = threadIdx.x; c < N; c += blockDim.x) {
+    int64_t Mm;
+    int Ex;
+    const int k = decompose(x[c], Mm, Ex);
+    if (k == 2) bad = true;
+    if (k == 1) emax = max(emax, Ex);
+  }
+  __shared__ int red[8];
+  __shared__ int sbad;
+  if (threadIdx.x == 0) sbad = 0;
+  emax = warp_max(emax);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
+  if (bad) sbad = 1;
+  __syncthreads();
+  emax = red[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) emax = max(emax, red[w]);
+  const bool zero = sbad != 0;
+  const int e = (emax == INT_MIN || zero) ? 0 : emax - 1022;
+  if (threadIdx.x == 0) {
+    E[st] = e;
+    if (zero) atomic_flag(flag);
+  }
+  for (int64_t c = threadIdx.x; c < ldp; c += blockDim.x) {
+    const int32_t oc = cmap[c];
+    const double v = (oc >= 0 && !zero) ? x[oc] : 0.0;
+    __nv_bfloat16* q = Q + st * ldp + c;
+    if (s <= 10) {
+      int64_t Mm = 0;
+      int Ex = 0;
+      if (decompose(v, Mm, Ex) != 1) Mm = 0;
+      slice_fixed(Mm, Ex, v < 0.0, -1075 - e + 6 * s, s, q, cstride);
+    } else {
+      slice_fp64(ldexp(v, -e), s, q, cstride);
+    }
+  }
+}
+
+cudaError_t slices_of_h(const dgchefsi_ctx* ctx, const int32_t* blk_row, const int32_t* pnb, const int32_t* poff,
+                        const int64_t* brow, int s, __nv_bfloat16* Q, int64_t cstride, int32_t* E, int* flag,
+                        cudaStream_t st) {
+  k_h_row_exponents<<<(unsigned)ctx->M, 256, 0, st>>>(ctx->row_ptr_d, ctx->col_d, ctx->blk_off_d, ctx->vals_d,
+                                                      ctx->nb_d, pnb, poff, E, flag);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_build_h_slices<<<(unsigned)ctx->nnzb, 256, 0, st>>>(blk_row, ctx->col_d, ctx->blk_off_d, ctx->vals_d, ctx->nb_d,
+                                                        pnb, poff, brow, E, s, Q, cstride);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t slices_of_states(const double* X, int64_t ld, int64_t Ns, int64_t N, const int32_t* cmap, int64_t ldp,
+                             int s, __nv_bfloat16* Q, int64_t cstride, int32_t* E, int* flag, cudaStream_t st) {
+  k_pack_state_slices<<<(unsigned)Ns, 256, 0, st>>>(X, ld, N, cmap, ldp, s, Q, cstride, E, flag);
+  count_launch();
+  return cudaGetLastError();
+}
+
+dgchefsi_status reduce_pair_slabs(const float* Pw, int64_t rows, int64_t cols, const int32_t* Erows,
+                                  const int32_t* Ecols, const int32_t* cmap, double* C, int64_t ldc, int s,
+                                  cudaStream_t st) {
+  const ReduceKernel k = reduce_kernel(s);
+  if (!k) return set_error(DGCHEFSI_ERR_ARG, "slices = %d outside 2..16", s);
+  const int64_t total = rows * cols;
+  const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  k<<<grid, 256, 0, st>>>(Pw, rows, cols, Erows, Ecols, 1, 0, 0, C, ldc, 0, cmap);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  return DGCHEFSI_OK;
+}
+
 dgchefsi_status sliced_gemm_tn(dgchefsi_ctx* ctx, int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda,
                                const double* B, int64_t ldb, double* C, int64_t ldc, int s, int* flag) {
   if (M <= 0 || Nc <= 0) return DGCHEFSI_OK;
   if (K > 0) {
-    if ((K + 31) / 32 > 65535) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "transpose of %lld rows", (long long)K);
     DG_TRY(ensure(ctx, ctx->ws_sliced_t, sizeof(double) * (size_t)M * (size_t)K, "transposed operand"));
     double* At = static_cast<double*>(ctx->ws_sliced_t.p);
-    k_transpose_f64<<<dim3((unsigned)((M + 31) / 32), (unsigned)((K + 31) / 32)), dim3(32, 8), 0, ctx->stream>>>(
-        A, lda, K, M, At, K);
-    count_launch();
-    DG_CUDA(cudaGetLastError());
+    DG_TRY(transpose_f64(A, lda, K, M, At, K, ctx->stream));
     return sliced_gemm(ctx, false, false, M, Nc, K, At, K, B, ldb, C, ldc, s, flag);
   }
   return sliced_gemm(ctx, false, false, M, Nc, K, A, lda, B, ldb, C, ldc, s, flag);
 }
 
-void sliced_destroy(dgchefsi_ctx* ctx) {
-  if (ctx->blas) cublasDestroy(static_cast<cublasHandle_t>(ctx->blas));
-  ctx->blas = nullptr;
-}
+void sliced_destroy(dgchefsi_ctx* ctx) { (void)ctx; }
 
 }  // namespace dg

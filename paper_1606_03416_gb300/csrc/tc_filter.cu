@@ -244,6 +244,7 @@ struct TcState {
   std::map<int, Plan> plans;  // keyed by G
   int shapeG[3] = {0, 0, 0}, shapeT[3] = {0, 0, 0}, shapeL[3] = {0, 0, 0};  // chosen per precision
   int forceG[3] = {0, 0, 0}, forceT[3] = {0, 0, 0}, forceL[3] = {0, 0, 0};  // dgchefsi_set_tile_shape
+  int tgb[3] = {-1, -1, -1};  // unit order (Params::tgb) chosen per precision; -1 = not tuned yet
   float tuned_ms[3][NSHAPES] = {};
   // graph form
   cudaStream_t cap_stream = nullptr;
@@ -261,6 +262,23 @@ struct TcState {
   int coefb_cap = 0;
   int g_stride = 0, g_nseg = 0, g_mG = 0, g_mT = 0, g_mL = 0, g_mm = 0;
   std::vector<float*> cp0, cp1, segb;
+  // H X from BF16 slices (tc_sliced_matvec): H's digits in the W = 64 operand
+  // layout (s copies), the states' digits (s copies, element-padded), the
+  // FP32 slice-pair slabs of one state panel, the exponents and the padded
+  // column map
+  struct {
+    bool layout = false, h_built = false;
+    int h_slices = 0;
+    std::vector<int64_t> brow_h;
+    int64_t b_rows = 0, zero_row = 0, max_row_len = 0;
+    int64_t* brow_d = nullptr;
+    int32_t* cmap_d = nullptr;
+    int32_t* eh_d = nullptr;   // [ldp] H row exponents
+    double* coef_d = nullptr;  // {c = 0, alpha = 1, beta = 0}
+    Plan plan;
+    DevBuf Hs, Xs, Pw, ex;
+    DevBuf dense;  // schedule and element tables of the dense slice-pair products
+  } sx;
   float* R[3] = {nullptr, nullptr, nullptr};
   float* WF[2] = {nullptr, nullptr};
   __nv_bfloat16* WSh[2] = {nullptr, nullptr};
@@ -341,14 +359,27 @@ static dgchefsi_status ensure_mode(dgchefsi_ctx* ctx, TcState& t, int mode) {
   return DGCHEFSI_OK;
 }
 
+static dgchefsi_status make_plan(dgchefsi_ctx* ctx, const TcState& t, int G, int W,
+                                 const std::vector<int64_t>& brow_h, int64_t zero_row, Plan& out);
+
 static dgchefsi_status get_plan(dgchefsi_ctx* ctx, TcState& t, int G, Plan** out) {
   auto it = t.plans.find(G);
   if (it != t.plans.end()) {
     *out = &it->second;
     return DGCHEFSI_OK;
   }
+  Plan pl;
+  DG_TRY(make_plan(ctx, t, G, t.mode == MODE_TF32 ? 32 : 64, t.brow_h, t.zero_row, pl));
+  t.plans[G] = pl;
+  *out = &t.plans[G];
+  return DGCHEFSI_OK;
+}
+
+// Element groups and their slice schedules for an operand copy of H laid out
+// with W-column slices, blocks starting at rows brow_h and zero tiles at zero_row.
+static dgchefsi_status make_plan(dgchefsi_ctx* ctx, const TcState& t, int G, int W,
+                                 const std::vector<int64_t>& brow_h, int64_t zero_row, Plan& out) {
   const int M = ctx->M;
-  const int W = t.mode == MODE_TF32 ? 32 : 64;
   Plan pl;
   pl.G = G;
   pl.W = W;
@@ -378,14 +409,14 @@ static dgchefsi_status get_plan(dgchefsi_ctx* ctx, TcState& t, int G, Plan** out
         for (int g = 0; g < G; ++g) {
           const int K = grp[(size_t)eg * G + g];
           // a zero tile (one of ZERO_TILES, spread over L2) when K does not couple to K'
-          int32_t row = (int32_t)(t.zero_row + (int64_t)(eg % ZERO_TILES) * t.boxn);
+          int32_t row = (int32_t)(zero_row + (int64_t)(eg % ZERO_TILES) * t.boxn);
           if (K >= 0) {
             int64_t lo = ctx->row_ptr_h[K], hi = ctx->row_ptr_h[K + 1] - 1;
             while (lo <= hi) {
               const int64_t mid = (lo + hi) / 2;
               const int cm = ctx->col_h[mid];
               if (cm == Kp) {
-                row = (int32_t)(t.brow_h[mid] + (int64_t)sl * t.pnb_h[K]);
+                row = (int32_t)(brow_h[mid] + (int64_t)sl * t.pnb_h[K]);
                 break;
               }
               if (cm < Kp) lo = mid + 1; else hi = mid - 1;
@@ -408,8 +439,7 @@ static dgchefsi_status get_plan(dgchefsi_ctx* ctx, TcState& t, int G, Plan** out
   DG_CUDA(cudaMalloc(&pl.gslots_d, sizeof(int32_t) * std::max<size_t>(gslots.size(), 1)));
   if (!nsub.empty()) DG_CUDA(cudaMemcpy(pl.nsub_d, nsub.data(), nsub.size(), cudaMemcpyHostToDevice));
   DG_CUDA(cudaMemcpy(pl.gslots_d, gslots.data(), sizeof(int32_t) * gslots.size(), cudaMemcpyHostToDevice));
-  t.plans[G] = pl;
-  *out = &t.plans[G];
+  out = pl;
   return DGCHEFSI_OK;
 }
 
@@ -449,13 +479,15 @@ static dgchefsi_status grow_iterates(dgchefsi_ctx* ctx, TcState& t, int mode, in
   return DGCHEFSI_OK;
 }
 
+// row_stride: elements between rows (0 = inner, a packed matrix).
 static dgchefsi_status make_map(CUtensorMap* map, void* base, bool f32, uint64_t inner, uint64_t rows,
-                                uint32_t box_inner, uint32_t box_rows, bool swizzle64 = false) {
+                                uint32_t box_inner, uint32_t box_rows, bool swizzle64 = false,
+                                uint64_t row_stride = 0) {
   auto enc = encode_fn();
   if (!enc) return set_error(DGCHEFSI_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   const size_t esz = f32 ? 4 : 2;
   cuuint64_t dims[2] = {inner, rows};
-  cuuint64_t strides[1] = {inner * esz};
+  cuuint64_t strides[1] = {(row_stride ? row_stride : inner) * esz};
   cuuint32_t box[2] = {box_inner, box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims,
@@ -550,6 +582,7 @@ static dgchefsi_status prepare_launch(dgchefsi_ctx* ctx, TcState& t, int mode, i
   p.ntg = (int)((Ns + (int64_t)BM * T - 1) / ((int64_t)BM * T));
   p.maxent = pl->maxent;
   p.err = t.err_d;
+  p.tgb = t.tgb[mode] > 0 ? t.tgb[mode] : 0;
   const int64_t nunits = (int64_t)p.ngroups * p.ntg;
   L.grid = dim3((unsigned)std::min<int64_t>(nunits, t.num_sms));
   return DGCHEFSI_OK;
@@ -706,9 +739,39 @@ static dgchefsi_status choose_shape(dgchefsi_ctx* ctx, TcState& t, int mode, int
       bL = SHAPES[i][3];
     }
   }
+  if (!bG) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return set_error(DGCHEFSI_ERR_UNSUPPORTED, "no tensor-core unit shape for accumulator width %d", t.ACC);
+  }
+  // unit order of the chosen shape: state tiles in blocks of 2, 4 or 8 per
+  // pass over the element groups (the Y_k slices a pass touches then stay in
+  // L2; H is read once per pass), or all state tiles of a group back to back
+  {
+    Launch L;
+    DG_TRY(prepare_launch(ctx, t, mode, bG, bT, bL, Ns, L));
+    float best_o = 1e30f;
+    int bo = 0;
+    for (int o : {0, 2, 4, 8}) {
+      if (o >= L.p.ntg) continue;
+      L.p.tgb = o;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        DG_CUDA(cudaEventRecord(e0, s));
+        DG_TRY(launch_step(ctx, t, mode, L, 0, s));
+        DG_CUDA(cudaEventRecord(e1, s));
+        DG_CUDA(cudaEventSynchronize(e1));
+        DG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      }
+      if (ms < best_o) {
+        best_o = ms;
+        bo = o;
+      }
+    }
+    t.tgb[mode] = bo;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (!bG) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "no tensor-core unit shape for accumulator width %d", t.ACC);
   t.shapeG[mode] = *G = bG;
   t.shapeT[mode] = *T = bT;
   t.shapeL[mode] = *layout = bL;
@@ -1028,6 +1091,250 @@ dgchefsi_status tc_grad_backward(dgchefsi_ctx* ctx, int prec, const double* Wm, 
   return check_err(t, s);
 }
 
+// Workspace cap of the FP32 slice-pair slabs of the sliced H X; the states run
+// in panels of 256-state multiples below it.
+static constexpr size_t kSlabBytes = size_t(8) << 30;
+
+dgchefsi_status tc_sliced_matvec(dgchefsi_ctx* ctx, const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t Ns,
+                                 int s, int* flag, bool* used) {
+  *used = false;
+  if (Ns <= 0) {
+    *used = true;
+    return DGCHEFSI_OK;
+  }
+  if (ctx->max_nb > 128 || s < 2 || s > 16) return DGCHEFSI_OK;
+  if (!ctx->tc) ctx->tc = new TcState();
+  TcState& t = *ctx->tc;
+  DG_TRY(ensure_layout(ctx, t));
+  auto& sx = t.sx;
+  constexpr int W = 64;
+  cudaStream_t st = ctx->stream;
+  if (!sx.layout) {
+    // W = 64 block layout of the slice copies (the BF16 filter's), the longest
+    // row (padded columns of its neighbour blocks) and the padded column map
+    sx.brow_h.resize(ctx->nnzb);
+    int64_t r = 0;
+    for (int64_t e = 0; e < ctx->nnzb; ++e) {
+      sx.brow_h[e] = r;
+      r += (int64_t)((t.pnb_h[ctx->col_h[e]] + W - 1) / W) * t.pnb_h[t.blk_row_h[e]];
+    }
+    sx.zero_row = r;
+    sx.b_rows = r + (int64_t)ZERO_TILES * t.boxn + t.boxn;
+    for (int K = 0; K < ctx->M; ++K) {
+      int64_t len = 0;
+      for (int64_t e = ctx->row_ptr_h[K]; e < ctx->row_ptr_h[K + 1]; ++e) len += ctx->nb_h[ctx->col_h[e]];
+      sx.max_row_len = std::max(sx.max_row_len, len);
+    }
+    std::vector<int32_t> cmap((size_t)t.ldp, -1);
+    for (int K = 0; K < ctx->M; ++K)
+      for (int j = 0; j < ctx->nb_h[K]; ++j) cmap[(size_t)t.poff_h[K] + j] = (int32_t)(ctx->off_h[K] + j);
+    DG_CUDA(cudaMalloc(&sx.brow_d, sizeof(int64_t) * std::max<int64_t>(ctx->nnzb, 1)));
+    DG_CUDA(cudaMalloc(&sx.cmap_d, sizeof(int32_t) * (size_t)t.ldp));
+    DG_CUDA(cudaMalloc(&sx.eh_d, sizeof(int32_t) * (size_t)t.ldp));
+    DG_CUDA(cudaMalloc(&sx.coef_d, sizeof(double) * 3));
+    const double coef[3] = {0.0, 1.0, 0.0};
+    DG_CUDA(cudaMemcpy(sx.brow_d, sx.brow_h.data(), sizeof(int64_t) * ctx->nnzb, cudaMemcpyHostToDevice));
+    DG_CUDA(cudaMemcpy(sx.cmap_d, cmap.data(), sizeof(int32_t) * (size_t)t.ldp, cudaMemcpyHostToDevice));
+    DG_CUDA(cudaMemcpy(sx.coef_d, coef, sizeof(coef), cudaMemcpyHostToDevice));
+    DG_TRY(make_plan(ctx, t, 128 / t.ACC, W, sx.brow_h, sx.zero_row, sx.plan));
+    sx.layout = true;
+  }
+  // every pair sum must stay an exact FP32 integer: at most 4096 terms per row
+  if (sx.max_row_len > 4096) return DGCHEFSI_OK;
+  if (sx.b_rows * (int64_t)W > ((int64_t)1 << 31) || Ns * t.ldp > ((int64_t)1 << 40)) return DGCHEFSI_OK;
+  const int G = 128 / t.ACC, T = 2;
+  FilterKernel kern = pick_kernel(MODE_BF16, G, T, t.ACC, 1);
+  if (!kern) return DGCHEFSI_OK;
+  // H's digits (once per H and slice count)
+  const int64_t hcopy = sx.b_rows * W;
+  if (!sx.h_built || sx.h_slices != s) {
+    if (sx.Hs.bytes < sizeof(__nv_bfloat16) * (size_t)(s * hcopy)) {
+      DG_TRY(ensure(ctx, sx.Hs, sizeof(__nv_bfloat16) * (size_t)(s * hcopy), "slices of H"));
+      DG_CUDA(cudaMemsetAsync(sx.Hs.p, 0, sx.Hs.bytes, st));  // zero tiles and slack rows
+    }
+    DG_CUDA(slices_of_h(ctx, t.blk_row_d, t.pnb_d, t.poff_d, sx.brow_d, s, static_cast<__nv_bfloat16*>(sx.Hs.p), hcopy,
+                        sx.eh_d, flag, st));
+    sx.h_built = true;
+    sx.h_slices = s;
+  }
+  // the states' digits and exponents
+  const int64_t xcopy = Ns * t.ldp;
+  DG_TRY(ensure(ctx, sx.Xs, sizeof(__nv_bfloat16) * (size_t)(s * xcopy), "slices of the states"));
+  DG_TRY(ensure(ctx, sx.ex, sizeof(int32_t) * (size_t)Ns, "state exponents"));
+  __nv_bfloat16* Xq = static_cast<__nv_bfloat16*>(sx.Xs.p);
+  int32_t* ex = static_cast<int32_t*>(sx.ex.p);
+  DG_CUDA(slices_of_states(X, ldx, Ns, ctx->N, sx.cmap_d, t.ldp, s, Xq, xcopy, ex, flag, st));
+  // state panels whose slabs fit the cap
+  const int pairs = s * (s + 1) / 2;
+  const int64_t per_state = (int64_t)pairs * t.ldp * (int64_t)sizeof(float);
+  int64_t P = (int64_t)(kSlabBytes / (size_t)per_state) / 256 * 256;
+  if (P < 256) P = 256;
+  if (P > Ns) P = Ns;
+  DG_TRY(ensure(ctx, sx.Pw, (size_t)per_state * (size_t)P, "slice-pair slabs"));
+  float* Pw = static_cast<float*>(sx.Pw.p);
+  // launch configuration of the transposed step kernel (layout 1, 128-byte slots)
+  const int stage_bytes = 128 * SLICE_BYTES + 256 * SLICE_BYTES;
+  const int stages = TN_RING_BYTES / stage_bytes;
+  const int smem = stages * stage_bytes + (2 * stages + 4) * 8 + 2 * sx.plan.maxent * (1 + G) * 4 + 1024;
+  if (smem > 227 * 1024) return DGCHEFSI_OK;
+  DG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  Params p{};
+  p.sched = sx.plan.sched_d;
+  p.sched_ptr = sx.plan.sched_ptr_d;
+  p.nsub = sx.plan.nsub_d;
+  p.gslots = sx.plan.gslots_d;
+  p.grp_elem = sx.plan.grp_elem_d;
+  p.nb = ctx->nb_d;
+  p.pnb = t.pnb_d;
+  p.poff = t.poff_d;
+  p.lo_rows = 0;
+  p.ldp = t.ldp;
+  p.coef = sx.coef_d;
+  p.step = 0;
+  p.W = W;
+  p.mode = MODE_BF16;
+  p.boxn = t.boxn;
+  p.G = G;
+  p.T = T;
+  p.ACC = t.ACC;
+  p.NBUF = 2;
+  p.stages = stages;
+  p.ngroups = sx.plan.ngroups;
+  p.maxent = sx.plan.maxent;
+  p.err = t.err_d;
+  p.Hout = nullptr;
+  p.Lout = nullptr;
+  DG_CUDA(cudaMemsetAsync(t.err_d, 0, sizeof(int), st));
+  std::vector<CUtensorMap> hmap(s);
+  for (int i = 0; i < s; ++i)
+    DG_TRY(make_map(&hmap[i], static_cast<__nv_bfloat16*>(sx.Hs.p) + (size_t)i * hcopy, false, (uint64_t)W,
+                    (uint64_t)sx.b_rows, (uint32_t)W, (uint32_t)t.boxn));
+  for (int64_t s0 = 0; s0 < Ns; s0 += P) {
+    const int64_t pn = std::min<int64_t>(P, Ns - s0);
+    p.Ns = pn;
+    p.ntg = (int)((pn + 255) / 256);
+    const unsigned grid = (unsigned)std::min<int64_t>((int64_t)p.ngroups * p.ntg, t.num_sms);
+    for (int j = 0; j < s; ++j) {
+      CUtensorMap xmap;
+      DG_TRY(make_map(&xmap, Xq + (size_t)j * xcopy + (size_t)s0 * t.ldp, false, (uint64_t)t.ldp, (uint64_t)pn,
+                      (uint32_t)W, 256u));
+      for (int i = 0; i + j < s; ++i) {
+        p.Fout = Pw + (size_t)(i * s - i * (i - 1) / 2 + j) * (size_t)(pn * t.ldp);
+        p.Fprev = p.Fout;
+        kern<<<grid, NTHREADS, smem, st>>>(xmap, xmap, hmap[i], p);
+        count_launch();
+        DG_CUDA(cudaGetLastError());
+      }
+    }
+    DG_TRY(reduce_pair_slabs(Pw, pn, t.ldp, ex + s0, sx.eh_d, sx.cmap_d, Y + s0 * ldy, ldy, s, st));
+  }
+  DG_TRY(check_err(t, st));
+  *used = true;
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status tc_slice_pairs(dgchefsi_ctx* ctx, const __nv_bfloat16* Qa, int64_t lqa, int64_t sa, int64_t M,
+                               const __nv_bfloat16* Qb, int64_t lqb, int64_t sb, int64_t Nc, int64_t K, int64_t k0,
+                               int64_t kc, int64_t n0, int64_t pn, int s, float* Pw) {
+  if (!ctx->tc) ctx->tc = new TcState();
+  TcState& t = *ctx->tc;
+  DG_TRY(ensure_layout(ctx, t));
+  cudaStream_t st = ctx->stream;
+  constexpr int ACC = 128, G = 1, T = 2, W = 64;
+  FilterKernel kern = pick_kernel(MODE_BF16, G, T, ACC, 1);
+  if (!kern) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "no step kernel for the slice-pair products");
+  if (M > 2147483647LL / 2 || pn > 2147483647LL || Nc > 2147483647LL || K > 2147483647LL)
+    return set_error(DGCHEFSI_ERR_UNSUPPORTED, "slice-pair product too large for 32-bit TMA coordinates");
+  // one element per 128 columns of the panel; its schedule walks the chunk's
+  // 64-wide K slices: [K coordinate (both operands), first row of the H-side tile]
+  const int nE = (int)((pn + ACC - 1) / ACC);
+  const int nS = (int)((kc + W - 1) / W);
+  std::vector<int32_t> tab((size_t)nE * 5 + 1 + (size_t)nE * nS * 2);
+  int32_t* grp = tab.data();
+  int32_t* nbv = grp + nE;
+  int32_t* poff = nbv + nE;
+  int32_t* pnb = poff + nE;
+  int32_t* sptr = pnb + nE;       // nE + 1
+  int32_t* sched = sptr + nE + 1;
+  for (int E = 0; E < nE; ++E) {
+    grp[E] = E;
+    nbv[E] = (int32_t)std::min<int64_t>(ACC, pn - (int64_t)E * ACC);
+    poff[E] = E * ACC;
+    pnb[E] = ACC;
+    sptr[E] = E * nS;
+    for (int S = 0; S < nS; ++S) {
+      sched[((size_t)E * nS + S) * 2] = (int32_t)(k0 + (int64_t)S * W);
+      sched[((size_t)E * nS + S) * 2 + 1] = (int32_t)(n0 + (int64_t)E * ACC);
+    }
+  }
+  sptr[nE] = nE * nS;
+  DG_TRY(ensure(ctx, t.sx.dense, sizeof(int32_t) * tab.size(), "slice-pair schedule"));
+  int32_t* d = static_cast<int32_t*>(t.sx.dense.p);
+  DG_CUDA(cudaMemcpyAsync(d, tab.data(), sizeof(int32_t) * tab.size(), cudaMemcpyHostToDevice, st));
+  const int stage_bytes = 128 * SLICE_BYTES + 256 * SLICE_BYTES;
+  const int stages = TN_RING_BYTES / stage_bytes;
+  const int smem = stages * stage_bytes + (2 * stages + 4) * 8 + 2 * nS * (1 + G) * 4 + 1024;
+  DG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  Params p{};
+  p.grp_elem = d;
+  p.nb = d + nE;
+  p.poff = d + 2 * nE;
+  p.pnb = d + 3 * nE;
+  p.sched_ptr = d + 4 * nE;
+  p.sched = d + 5 * nE + 1;
+  p.nsub = nullptr;
+  p.gslots = nullptr;
+  p.hx_sched = 1;
+  p.lo_rows = 0;
+  p.Ns = M;
+  p.ldp = pn;
+  p.W = W;
+  p.mode = MODE_BF16;
+  p.boxn = ACC;
+  p.G = G;
+  p.T = T;
+  p.ACC = ACC;
+  p.NBUF = 2;
+  p.stages = stages;
+  p.ngroups = nE;
+  p.ntg = (int)((M + 255) / 256);
+  p.maxent = nS;
+  p.err = t.err_d;
+  p.step = 0;
+  p.Hout = nullptr;
+  p.Lout = nullptr;
+  if (!t.sx.coef_d) {
+    DG_CUDA(cudaMalloc(&t.sx.coef_d, sizeof(double) * 3));
+    const double coef[3] = {0.0, 1.0, 0.0};
+    DG_CUDA(cudaMemcpy(t.sx.coef_d, coef, sizeof(coef), cudaMemcpyHostToDevice));
+  }
+  p.coef = t.sx.coef_d;
+  DG_CUDA(cudaMemsetAsync(t.err_d, 0, sizeof(int), st));
+  const unsigned grid = (unsigned)std::min<int64_t>((int64_t)nE * p.ntg, t.num_sms);
+  std::vector<CUtensorMap> bmap(s);
+  for (int j = 0; j < s; ++j)
+    DG_TRY(make_map(&bmap[j], const_cast<__nv_bfloat16*>(Qb) + (size_t)j * sb, false, (uint64_t)K, (uint64_t)Nc,
+                    (uint32_t)W, (uint32_t)ACC, false, (uint64_t)lqb));
+  for (int i = 0; i < s; ++i) {
+    CUtensorMap amap;
+    DG_TRY(make_map(&amap, const_cast<__nv_bfloat16*>(Qa) + (size_t)i * sa, false, (uint64_t)K, (uint64_t)M,
+                    (uint32_t)W, 256u, false, (uint64_t)lqa));
+    for (int j = 0; i + j < s; ++j) {
+      p.Fout = Pw + (size_t)(i * s - i * (i - 1) / 2 + j) * (size_t)(M * pn);
+      p.Fprev = p.Fout;
+      kern<<<grid, NTHREADS, smem, st>>>(amap, amap, bmap[j], p);
+      count_launch();
+      DG_CUDA(cudaGetLastError());
+    }
+  }
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status tc_slice_pairs_status(dgchefsi_ctx* ctx) {
+  if (!ctx->tc) return DGCHEFSI_OK;
+  return check_err(*ctx->tc, ctx->stream);
+}
+
 dgchefsi_status tc_set_shape(dgchefsi_ctx* ctx, int prec, int G, int T, int layout) {
   if (!ctx->tc) ctx->tc = new TcState();
   TcState& t = *ctx->tc;
@@ -1079,6 +1386,16 @@ void tc_destroy(dgchefsi_ctx* ctx) {
     cudaFree(t.Sl[i].p);
   }
   cudaFree(t.Hop.p);
+  free_plan(t.sx.plan);
+  cudaFree(t.sx.brow_d);
+  cudaFree(t.sx.cmap_d);
+  cudaFree(t.sx.eh_d);
+  cudaFree(t.sx.coef_d);
+  cudaFree(t.sx.Hs.p);
+  cudaFree(t.sx.Xs.p);
+  cudaFree(t.sx.Pw.p);
+  cudaFree(t.sx.ex.p);
+  cudaFree(t.sx.dense.p);
   cudaFree(t.gbuf.p);
   cudaFree(t.coefb_d);
   delete ctx->tc;

@@ -89,7 +89,25 @@ struct Params {
   // zero) and of each element group
   const uint8_t* nsub;
   const int32_t* gslots;
+  // 1: the K coordinate of the H-side tile is the schedule entry's (the dense
+  // slice-pair products, whose H side is a plain row-major matrix); 0: the
+  // operand copy of H, whose tiles start at column 0
+  int hx_sched;
+  // unit order: blocks of tgb state tiles, each walking every element group
+  // (tgb consecutive units per group) before the next block; 0 = all state
+  // tiles of a group back to back (one block)
+  int tgb;
 };
+
+// Element group and state tile of work unit u.
+__device__ __forceinline__ void unit_coords(const Params& p, int u, int& eg, int& tg) {
+  const int b = p.tgb > 0 && p.tgb < p.ntg ? p.tgb : p.ntg;
+  const int tb = u / (p.ngroups * b);
+  const int rem = u - tb * p.ngroups * b;
+  const int cnt = min(b, p.ntg - tb * b);
+  eg = rem / cnt;
+  tg = tb * b + (rem - eg * cnt);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -334,7 +352,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int c = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-      const int eg = u / p.ntg, tg = u % p.ntg;
+      int eg, tg;
+      unit_coords(p, u, eg, tg);
       const int s0 = tg * BM * T;
       const int e0 = p.sched_ptr[eg], ne = p.sched_ptr[eg + 1] - e0;
       __syncwarp();
@@ -391,7 +410,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int c = 0, i = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++i) {
-      const int eg = u / p.ntg;
+      int eg, tg_;
+      unit_coords(p, u, eg, tg_);
       const int ne = p.sched_ptr[eg + 1] - p.sched_ptr[eg];
       if (lane == 0 && ok) {
         const int buf = p.NBUF == 2 ? (i & 1) : 0;
@@ -454,7 +474,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++i) {
       const int buf = p.NBUF == 2 ? (i & 1) : 0;
       const int use = p.NBUF == 2 ? (i >> 1) : i;
-      const int eg = u / p.ntg, tg = u % p.ntg;
+      int eg, tg;
+      unit_coords(p, u, eg, tg);
       const int64_t s0 = (int64_t)tg * BM * T;
       bool ready = mbar_wait(accf0 + 8 * buf, (uint32_t)use & 1u);
       ready = __all_sync(0xffffffffu, ready);
@@ -582,7 +603,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int c = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-      const int eg = u / p.ntg, tg = u % p.ntg;
+      int eg, tg;
+      unit_coords(p, u, eg, tg);
       const int s0 = tg * NS;
       const int e0 = p.sched_ptr[eg], ne = p.sched_ptr[eg + 1] - e0;
       __syncwarp();
@@ -605,11 +627,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_expect_tx(fb, (uint32_t)stage_bytes);
             uint8_t* sst = smem + st * stage_bytes;
             const int xo = sub * (SB / ESZ);  // element offset of this K part (16-byte multiple)
+            const int hx = xo + (p.hx_sched ? ent[0] : 0);
 #pragma unroll
             for (int v = 0; v < NA; ++v) {
 #pragma unroll
               for (int g = 0; g < G; ++g)  // H tiles (zero tiles for non-coupling elements)
-                tma_load_2d(smem_u32(sst + v * a_bytes + g * h_bytes), &tmB, xo,
+                tma_load_2d(smem_u32(sst + v * a_bytes + g * h_bytes), &tmB, hx,
                             (int)(ent[1 + g] + (v == 1 ? p.lo_rows : 0)), fb);
               tma_load_2d(smem_u32(sst + NA * a_bytes + v * x_bytes), v == 1 ? &tmA1 : &tmA0, ent[0] + xo, s0, fb);
             }
@@ -637,7 +660,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int c = 0, i = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++i) {
-      const int eg = u / p.ntg;
+      int eg, tg_;
+      unit_coords(p, u, eg, tg_);
       const int ne = p.sched_ptr[eg + 1] - p.sched_ptr[eg];
       if (lane == 0) {
         const int buf = i & 1;
@@ -696,7 +720,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++i) {
       const int buf = i & 1;
       const int use = i >> 1;
-      const int eg = u / p.ntg, tg = u % p.ntg;
+      int eg, tg;
+      unit_coords(p, u, eg, tg);
       const int64_t s0 = (int64_t)tg * NS;
       bool ready = mbar_wait(accf0 + 8 * buf, (uint32_t)use & 1u);
       ready = __all_sync(0xffffffffu, ready);
@@ -712,6 +737,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const uint32_t ta = tmem + (uint32_t)(buf * NS) + ((uint32_t)(32 * q) << 16);
       const int64_t ldp = p.ldp;
       const bool need_prev = row_ok && beta != 0.f;
+      const bool write_ops = p.Hout != nullptr;
 #pragma unroll 1
       for (int cc = 0; cc < NS / 32; ++cc) {
         const int c0 = 16 * (h + 2 * cc);
@@ -736,9 +762,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               const float y = alpha * v[z] - beta * pr[z];
               p.Fout[idx] = y;
               if constexpr (MODE_ != MODE_TF32) {
-                const __nv_bfloat16 hb = __float2bfloat16_rn(y);
-                p.Hout[idx] = hb;
-                if constexpr (MODE_ == MODE_BF16X3) p.Lout[idx] = __float2bfloat16_rn(y - __bfloat162float(hb));
+                if (write_ops) {  // no operand copies for a plain product (slice pairs)
+                  const __nv_bfloat16 hb = __float2bfloat16_rn(y);
+                  p.Hout[idx] = hb;
+                  if constexpr (MODE_ == MODE_BF16X3) p.Lout[idx] = __float2bfloat16_rn(y - __bfloat162float(hb));
+                }
               }
             }
           }

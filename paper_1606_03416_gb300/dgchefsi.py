@@ -31,7 +31,7 @@ EXPORTS = ["dgchefsi_create", "dgchefsi_destroy", "dgchefsi_set_stream", "dgchef
            "dgchefsi_filter_graph", "dgchefsi_set_tile_shape", "dgchefsi_get_tile_shape",
            "dgchefsi_selftest_wait", "dgchefsi_selftest_fp64_rate", "dgchefsi_set_orthonormalisation", "dgchefsi_density_pattern",
            "dgchefsi_realign", "dgchefsi_filter_host", "dgchefsi_set_subspace_products",
-           "dgchefsi_sliced_gemm"]
+           "dgchefsi_sliced_gemm", "dgchefsi_sliced_matvec"]
 
 # Orthonormalisations of Alg. 1 step 3 (dgchefsi_set_orthonormalisation).
 ORTHONORMALISATIONS = {"cholqr": 0, "cholqr2": 1, "shifted_cholqr3": 2}
@@ -74,6 +74,7 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_set_orthonormalisation": (st, [P, C.c_int]),
         "dgchefsi_set_subspace_products": (st, [P, C.c_int, C.c_int]),
         "dgchefsi_sliced_gemm": (st, [P, C.c_int, C.c_int, I64, I64, I64, P, I64, P, I64, P, I64, C.c_int]),
+        "dgchefsi_sliced_matvec": (st, [P, P, P, I64, I64, C.c_int]),
         "dgchefsi_density_pattern": (st, [P, P, I64, I64, P, P]),
         "dgchefsi_realign": (st, [P, P, P, P, P, P, I64, I64, P, I64]),
         "dgchefsi_filter_host": (st, [P, C.c_int, P, P, I64, I64, C.c_int, D, D, D, I64]),
@@ -339,6 +340,18 @@ class Context:
         _check(_lib.dgchefsi_sliced_gemm(self._h, int(b_rows), int(a_lower), M, Nc, K, _ptr(A), A.stride(0),
                                          _ptr(B), B.stride(0), _ptr(out), out.stride(0), int(slices)))
         return out
+
+    def sliced_matvec(self, X: torch.Tensor, Y: torch.Tensor | None = None, slices: int = 10) -> torch.Tensor:
+        """Y = H X (Eq. matvec_3) in FP64 from exact BF16 slices on the tensor cores."""
+        Ns, ld = _block(X, self.N, "X")
+        if Y is None:
+            Y = torch.empty_like(X)
+        Ns2, ld2 = _block(Y, self.N, "Y")
+        if Ns2 != Ns or ld2 != ld:
+            raise ValueError("X and Y must have the same shape and row stride")
+        self._sync_stream()
+        _check(_lib.dgchefsi_sliced_matvec(self._h, _ptr(X), _ptr(Y), Ns, ld, int(slices)))
+        return Y
 
     # -- Sec. III.B.3: coefficients carried to the next SCF step's basis
     def realign(self, X_old: torch.Tensor, nb_old, nr, V_old: torch.Tensor, V_new: torch.Tensor,

@@ -4,7 +4,9 @@ scheme) and the Rayleigh-Ritz step / cycle that uses them, through the C ABI.
 * Integer operands of at most 12 bits: every slice is exact after two slices,
   every slice-pair product is an exactly accumulated integer, and the FP64
   sums are exact, so the result equals the exact integer product bit for bit
-  (ragged K chunks, strided operands, both operand layouts, triangular A).
+  (ragged K chunks, strided operands, both operand layouts, triangular A,
+  several column panels, pair sums at the 2^24 edge of exact FP32
+  accumulation). The slice pairs run on the library's tcgen05 step kernel.
 * Gaussian operands with rows scaled over e^{+-3}: |C - A B| within the
   splitting bound sum over chunks of L m_r n_c (2^{-6s}(s + 4) + (5 + chunks) u)
   plus FP64's own bound on the reference product; fewer slices are less
@@ -81,6 +83,26 @@ def test_pair_sums_at_the_fp32_limit_bit_exact(b_rows):
         out = torch.empty((M, Nc), dtype=torch.float64, device=dev)
         ctx.sliced_gemm(torch.from_numpy(A.astype(np.float64)).to(dev), torch.from_numpy(B.astype(np.float64)).to(dev),
                         b_rows=b_rows, slices=10, out=out)
+        got = out.cpu().numpy()
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("b_rows", [True, False])
+def test_integer_operands_bit_exact_over_column_panels(b_rows):
+    """16 slices (136 pairs, digits by the FP64 path) on a 2048 x 8000 output:
+    the FP32 pair slabs exceed the 8 GB workspace cap, so the columns run in
+    two panels of 128-column tiles, the second one ragged."""
+    rng = np.random.default_rng(9)
+    M, Nc, K = 2048, 8000, 300
+    assert 136 * 4 * M * Nc > 8 * 2 ** 30
+    A = rng.integers(-2047, 2048, size=(M, K)).astype(np.int64)
+    Bt = rng.integers(-2047, 2048, size=(Nc, K)).astype(np.int64)
+    ref = (A @ Bt.T).astype(np.float64)
+    B = Bt if b_rows else np.ascontiguousarray(Bt.T)
+    with tiny_ctx() as ctx:
+        out = torch.empty((M, Nc), dtype=torch.float64, device=dev)
+        ctx.sliced_gemm(torch.from_numpy(A.astype(np.float64)).to(dev), torch.from_numpy(B.astype(np.float64)).to(dev),
+                        b_rows=b_rows, slices=16, out=out)
         got = out.cpu().numpy()
     assert np.array_equal(got, ref)
 

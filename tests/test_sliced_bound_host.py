@@ -145,3 +145,50 @@ def test_balancing_keeps_small_norm_states():
     err_bal = float(np.max(np.abs(bal - ref) / row_scale))
     err_f64 = float(np.max(np.abs(A @ B - ref) / row_scale))
     assert err_bal <= max(8 * err_f64, 1e-15) and err_plain > 100 * err_bal
+
+
+def test_block_sparse_product_within_stated_bound():
+    """H X from slices as the block-sparse product splits it: each row of H
+    with one exponent over the columns of its neighbour blocks (at most 4096,
+    one chunk), each state with one exponent over all N entries. The result is
+    within L m_r n_s (2^{-6s}(s + 4) + 6 u) of the exact product, L the row's
+    column count, m_r its largest |entry|, n_s the state's largest |entry| over
+    all of it (so a state that is large away from the row's columns gets a
+    looser but still valid bound)."""
+    rng = np.random.default_rng(12)
+    nb = [5, 7, 4, 6]                                   # a chain of 4 elements, neighbours K-1, K, K+1
+    off = np.concatenate([[0], np.cumsum(nb)])
+    N = int(off[-1])
+    H = np.zeros((N, N))
+    for K in range(4):
+        for Kp in (K - 1, K, K + 1):
+            if 0 <= Kp < 4:
+                H[off[K]:off[K + 1], off[Kp]:off[Kp + 1]] = rng.standard_normal((nb[K], nb[Kp])) * 10.0 ** (K - 2)
+    H = 0.5 * (H + H.T)
+    Ns = 6
+    X = rng.standard_normal((Ns, N)) * np.exp(rng.uniform(-3, 3, (Ns, 1)))
+    X[2, off[3]:] *= 1e6                                # large only on the last element
+    exact = np.array([[float(sum(Fraction(float(H[r, c])) * Fraction(float(X[t, c])) for c in range(N)))
+                       for r in range(N)] for t in range(Ns)])
+    for s in (4, 10):
+        Y = np.zeros((Ns, N))
+        bound = np.zeros((Ns, N))
+        for r in range(N):
+            cols = np.nonzero(H[r])[0]
+            L = len(cols)
+            er = frexp_exp(H[r, cols])
+            qh = np.array([digits(float(H[r, c]), er, s) for c in cols], dtype=np.int64)      # L x s
+            for t_ in range(Ns):
+                es = frexp_exp(X[t_])
+                qx = np.array([digits(float(X[t_, c]), es, s) for c in cols], dtype=np.int64)
+                g = [int(sum(int(qh[:, i] @ qx[:, t - i]) for i in range(t + 1))) for t in range(s)]
+                assert all(abs(int(qh[:, i] @ qx[:, j])) <= 2 ** 24 for i in range(s) for j in range(s - i))
+                h = 0.0
+                for b in range((s + 4) // 5 - 1, -1, -1):
+                    Bv = 0
+                    for t in range(5 * b, 5 * b + 5):
+                        Bv = Bv * 64 + (g[t] if t < s else 0)
+                    h = h * 2.0 ** -30 + float(Bv)
+                Y[t_, r] = np.ldexp(h, er + es - 36)
+                bound[t_, r] = L * np.abs(H[r, cols]).max() * np.abs(X[t_]).max() * (2.0 ** (-6 * s) * (s + 4) + 6 * U)
+        assert np.all(np.abs(Y - exact) <= bound)

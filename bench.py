@@ -115,7 +115,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def profiled_traffic(prec: str, Ns: int, layout: int = -1):
+def profiled_traffic(prec: str, Ns: int, layout: int = -1, order=None):
     """DRAM bytes per launch of the tensor-core filter step from the committed
     ncu summary, if that summary was taken on the current kernel source (its
     recorded source hash matches) for this precision and, when it records one,
@@ -130,6 +130,8 @@ def profiled_traffic(prec: str, Ns: int, layout: int = -1):
         if f"source-sha1 (paper_1606_03416_gb300/csrc/tc_kernel.cuh, first 12): {sha}" not in text:
             continue
         if "unit-shape-layout:" in text and f"unit-shape-layout: {layout}" not in text:
+            continue
+        if "unit-order:" in text and order is not None and f"unit-order: {order}" not in text:
             continue
         for line in text.splitlines():
             key = f"traffic-per-launch-bytes-{prec}-Ns"
@@ -233,6 +235,8 @@ def run_filter_only(args):
         if args.shape:
             G_, T_, L_ = (int(v) for v in args.shape.split(","))
             ctx.set_tile_shape(args.prec, G_, T_, L_)
+        if args.unit_order >= 0 and args.prec != "f64":
+            ctx.set_unit_order(args.prec, args.unit_order)
         for _ in range(args.warmup):
             ctx.filter(X, cfg.m, 10.0, 45.0, -2.0, prec=args.prec, Y=Y)
         torch.cuda.synchronize()
@@ -244,9 +248,11 @@ def run_filter_only(args):
         torch.cuda.synchronize()
         ms = s.elapsed_time(e) / max(args.steps, 1)
         shape = ctx.tile_shape(args.prec) if args.prec != "f64" else None
+        order = ctx.unit_order(args.prec) if args.prec != "f64" else None
     fl = filter_flops(H, cfg.Ns, cfg.m)
     print(json.dumps({"mode": "filter-only", "workload": args.workload, "Ns": cfg.Ns, "m": cfg.m, "prec": args.prec,
-                      "ms_per_filter": ms, "filter_tflops": fl / (ms * 1e-3) / 1e12, "unit_shape": shape}),
+                      "ms_per_filter": ms, "filter_tflops": fl / (ms * 1e-3) / 1e12, "unit_shape": shape,
+                      "unit_order": order}),
           flush=True)
     return 0
 
@@ -616,6 +622,35 @@ def measure_sliced(ctx, X_warm, state, cycle, vd, Ns, N, m, Ne, kT, args, dev, b
     return out
 
 
+def run_sliced_only(args):
+    """One FP64 product from BF16 slices of Gram shape (C = A A^T, A: --ns x --k,
+    seeded Gaussian), timed after one warm-up call: the case the ncu captures
+    of the slice-pair kernel run on."""
+    import torch
+    from paper_1606_03416_gb300 import dgchefsi as D
+    from paper_1606_03416_gb300 import inputs as G
+    dev = torch.device("cuda:0")
+    Hb = G.make_blocks(G.CONFIGS["tiny_2x2x2"])
+    M, K = args.ns or 2048, args.k or 8192
+    A = torch.from_numpy(np.random.default_rng(0).standard_normal((M, K))).to(dev)
+    C = torch.empty((M, M), dtype=torch.float64, device=dev)
+    with D.Context(Hb) as ctx:
+        for _ in range(max(args.warmup, 1)):
+            ctx.sliced_gemm(A, A, slices=args.slices, out=C)
+        torch.cuda.synchronize()
+        s_, e_ = torch.cuda.Event(True), torch.cuda.Event(True)
+        s_.record()
+        for _ in range(args.steps):
+            ctx.sliced_gemm(A, A, slices=args.slices, out=C)
+        e_.record()
+        torch.cuda.synchronize()
+        ms = s_.elapsed_time(e_) / max(args.steps, 1)
+    pairs = args.slices * (args.slices + 1) // 2
+    print(json.dumps({"mode": "sliced-only", "M": M, "K": K, "slices": args.slices, "ms": ms,
+                      "tensor_tflops": pairs * 2.0 * M * M * K / (ms * 1e-3) / 1e12}), flush=True)
+    return 0
+
+
 def run_rr_only(args):
     """One Rayleigh-Ritz step (Alg. 1 steps 3-5) on the workload's BF16x3-filtered
     first block, with --subspace products, bracketed by cudaProfilerStart/Stop
@@ -793,9 +828,14 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--filter-only", action="store_true",
                     help="time only the filter (profiling case); --ns and --m override the workload")
+    ap.add_argument("--sliced-only", action="store_true",
+                    help="one Gram-shaped product from BF16 slices, --ns x --k (profiling case)")
+    ap.add_argument("--k", type=int, default=0)
     ap.add_argument("--ns", type=int, default=0)
     ap.add_argument("--m", type=int, default=0)
     ap.add_argument("--shape", default="", help="filter-only: force the unit shape G,T,layout (default: autotune)")
+    ap.add_argument("--unit-order", type=int, default=-1,
+                    help="filter-only: state tiles per pass over the element groups (default: autotune)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -809,6 +849,8 @@ def main():
         return run_gram_only(args)
     if args.rr_only:
         return run_rr_only(args)
+    if args.sliced_only:
+        return run_sliced_only(args)
 
     import torch
     rank, world, local = dist_env()
@@ -933,7 +975,8 @@ def main():
             rf = {"bound": "tensor", "achieved": mult * step_fl / (ms_launch * 1e-3) / 1e12, "peak": tpeak,
                   "unit": "TFLOP/s"}
     rf["frac"] = rf["achieved"] / rf["peak"]
-    rf["traffic"] = profiled_traffic(args.prec, Ns, ctx.tile_shape(args.prec)[3]) if args.prec != "f64" else None
+    rf["traffic"] = (profiled_traffic(args.prec, Ns, ctx.tile_shape(args.prec)[3], ctx.unit_order(args.prec))
+                     if args.prec != "f64" else None)
     rf["algorithmic_bytes"] = byts
     if args.prec == "f64":
         rf["kernel"] = "k_filter_step_f64"
@@ -941,6 +984,7 @@ def main():
         g_, t_, acc_, lay_ = ctx.tile_shape(args.prec)
         rf["kernel"] = (("k_filter_step_tn" if lay_ >= 1 else "k_filter_step_tc") + f"<{args.prec}, G={g_}, T={t_}"
                         + (", 64-byte slots>" if lay_ == 2 else ">"))
+        rf["unit_order"] = ctx.unit_order(args.prec)
     rf["ms_per_launch"] = ms_launch
     rf["peak_source"] = (F64_PEAK["source"] if args.prec == "f64" else
                          src + (" x 1.1/2.25 (nominal TF32/BF16 ratio)" if args.prec == "tf32" else ""))

@@ -198,6 +198,17 @@ dgchefsi_status dgchefsi_set_tile_shape(dgchefsi_ctx* ctx, int prec, int G, int 
 /* The shape in use (all 0 if not chosen yet) and the accumulator width. */
 dgchefsi_status dgchefsi_get_tile_shape(dgchefsi_ctx* ctx, int prec, int* G, int* T, int* ACC, int* layout);
 
+/* Order in which the persistent tensor-core filter walks its work units: the
+ * state tiles in blocks of tgb, each block visiting every element group
+ * before the next (the Y_k slices one block touches stay in L2, at the price
+ * of reading H once per block), or all state tiles of an element group back
+ * to back (tgb = 0). -1 (default) = the first filter call with a shape times
+ * one step with 0, 2, 4 and 8 and keeps the fastest. Results do not depend on
+ * the order. dgchefsi_get_unit_order reports the order in use (-1 if none was
+ * chosen yet). ERR_ARG for a non-tensor-core precision or tgb < -1. */
+dgchefsi_status dgchefsi_set_unit_order(dgchefsi_ctx* ctx, int prec, int tgb);
+dgchefsi_status dgchefsi_get_unit_order(dgchefsi_ctx* ctx, int prec, int* tgb);
+
 /* Overlap matrix S = Y^T Y of a block (the first product of Cholesky-QR,
  * Alg. 1 step 3), FP64: the tiles on and below the diagonal are computed and
  * mirrored, so S is exactly symmetric.

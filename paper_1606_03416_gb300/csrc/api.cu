@@ -555,6 +555,7 @@ void dgchefsi_destroy(dgchefsi_ctx* ctx) {
   free_buf(ctx->ws_sliced);
   free_buf(ctx->ws_sliced_t);
   free_buf(ctx->ws_sliced_b);
+  free_buf(ctx->ws_pairs);
   for (int i = 0; i < 2; ++i) {
     free_buf(ctx->ws_hin[i]);
     free_buf(ctx->ws_hout[i]);
@@ -816,6 +817,22 @@ dgchefsi_status dgchefsi_get_tile_shape(dgchefsi_ctx* ctx, int prec, int* G, int
   if (!G || !T || !ACC || !layout) return set_error(DGCHEFSI_ERR_ARG, "null output");
   if (prec < DGCHEFSI_TF32 || prec > DGCHEFSI_BF16X3) return set_error(DGCHEFSI_ERR_ARG, "not a tensor-core precision");
   return tc_get_shape(ctx, prec, G, T, ACC, layout);
+}
+
+dgchefsi_status dgchefsi_set_unit_order(dgchefsi_ctx* ctx, int prec, int tgb) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  if (prec < DGCHEFSI_TF32 || prec > DGCHEFSI_BF16X3) return set_error(DGCHEFSI_ERR_ARG, "not a tensor-core precision");
+  if (tgb < -1 || tgb > 65535) return set_error(DGCHEFSI_ERR_ARG, "unit order %d outside -1..65535", tgb);
+  return tc_set_unit_order(ctx, prec, tgb);
+}
+
+dgchefsi_status dgchefsi_get_unit_order(dgchefsi_ctx* ctx, int prec, int* tgb) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  if (prec < DGCHEFSI_TF32 || prec > DGCHEFSI_BF16X3) return set_error(DGCHEFSI_ERR_ARG, "not a tensor-core precision");
+  if (!tgb) return set_error(DGCHEFSI_ERR_ARG, "null output");
+  return tc_get_unit_order(ctx, prec, tgb);
 }
 
 dgchefsi_status dgchefsi_selftest_wait(dgchefsi_ctx* ctx, int64_t limit_ns) {

@@ -60,6 +60,7 @@ struct dgchefsi_ctx {
   dg::DevBuf ws_sliced;
   dg::DevBuf ws_sliced_t;  // transposed left operand of the A^T B form
   dg::DevBuf ws_sliced_b;  // transposed right operand of the A B form
+  dg::DevBuf ws_pairs;     // error word, tensor maps and pair lists of the slice-pair kernel
   int32_t f64_tj = 64;    // column tile of the FP64 filter (set at create)
   // FP64 filter as a CUDA graph: coefficients copied from a pinned mirror at
   // every replay; the graph is captured again when X, Y, N_s, ld, m or the
@@ -118,6 +119,8 @@ dgchefsi_status filter_tc_graph(dgchefsi_ctx* ctx, int prec, const double* X, do
 dgchefsi_status tc_set_shape(dgchefsi_ctx* ctx, int prec, int G, int T, int layout);
 dgchefsi_status tc_get_shape(dgchefsi_ctx* ctx, int prec, int* G, int* T, int* ACC, int* layout);
 dgchefsi_status tc_wait_selftest(dgchefsi_ctx* ctx, int64_t limit_ns);
+dgchefsi_status tc_set_unit_order(dgchefsi_ctx* ctx, int prec, int tgb);
+dgchefsi_status tc_get_unit_order(dgchefsi_ctx* ctx, int prec, int* tgb);
 // Band-energy gradient on the tensor-core filter. Forward: Y_m (FP64, Ns x N
 // compact) from X, keeping FP32 iterate pairs every `stride` steps. Backward
 // (same prec, m, stride, right after the forward): the reverse recurrence from
@@ -157,16 +160,19 @@ cudaError_t slices_of_states(const double* X, int64_t ld, int64_t Ns, int64_t N,
 dgchefsi_status reduce_pair_slabs(const float* Pw, int64_t rows, int64_t cols, const int32_t* Erows,
                                   const int32_t* Ecols, const int32_t* cmap, double* C, int64_t ldc, int s,
                                   cudaStream_t st);
-// The slice-pair products of the dense sliced GEMM on the tensor-core filter's
-// transposed step kernel (tc_filter.cu): for every pair i + j < s,
-// Pw[pair i*s - i(i-1)/2 + j] (M x pn, row-major FP32) = Qa_i[:, k0:k0+kc] times
-// Qb_j[n0:n0+pn, k0:k0+kc]^T, Qa_i = Qa + i*sa (M x K, row stride lqa),
-// Qb_j = Qb + j*sb (Nc x K, row stride lqb), entries k >= K read as zero.
-// Enqueued only; tc_slice_pairs_status synchronises and reports a pipeline timeout.
-dgchefsi_status tc_slice_pairs(dgchefsi_ctx* ctx, const __nv_bfloat16* Qa, int64_t lqa, int64_t sa, int64_t M,
-                               const __nv_bfloat16* Qb, int64_t lqb, int64_t sb, int64_t Nc, int64_t K, int64_t k0,
-                               int64_t kc, int64_t n0, int64_t pn, int s, float* Pw);
-dgchefsi_status tc_slice_pairs_status(dgchefsi_ctx* ctx);
+// The slice-pair products of the dense sliced GEMM (pair_gemm.cu: tcgen05 on
+// pairs of SMs, cta_group::2, all pairs of the chunk in one persistent
+// launch): for every pair i + j < s, Pw[pair i*s - i(i-1)/2 + j] (M x pn,
+// row-major FP32) = Qa_i[:, k0:k0+kc] times Qb_j[n0:n0+pn, k0:k0+kc]^T, with
+// Qa_i = Qa + i*sa (M x K, row stride lqa), Qb_j = Qb + j*sb (Nc x K, row
+// stride lqb), entries k >= K read as zero. Enqueued only.
+// pair_products_begin clears the kernel's error word; pair_products_status
+// synchronises and reports a pipeline timeout.
+dgchefsi_status pair_products_2sm(dgchefsi_ctx* ctx, const __nv_bfloat16* Qa, int64_t lqa, int64_t sa, int64_t M,
+                                  const __nv_bfloat16* Qb, int64_t lqb, int64_t sb, int64_t Nc, int64_t K, int64_t k0,
+                                  int64_t kc, int64_t n0, int64_t pn, int s, float* Pw);
+dgchefsi_status pair_products_begin(dgchefsi_ctx* ctx);
+dgchefsi_status pair_products_status(dgchefsi_ctx* ctx);
 // Y = H X (X, Y: Ns x ld state-major FP64) from s BF16 slices of each operand on
 // the tensor-core filter's step kernel (tc_filter.cu). *used = false when this
 // H does not fit the form (a row longer than 4096 columns, or an element

@@ -14,9 +14,9 @@
 // i + j <= s - 1 are kept; their FP32 results are summed per t = i + j in FP64
 // (exact: integers below 2^53), combined by Horner in 2^{-6}, scaled by
 // 2^{e_r + f_c - 12} and added over the chunks. The slice-pair products run
-// on this library's tcgen05 block-sparse step kernel (the filter's, with
-// 128-row blocks of the right operand as its elements, one pair per launch,
-// FP32 output); splitting and the FP64 reduction are the kernels below.
+// on this library's tcgen05 kernel for pairs of SMs (pair_gemm.cu: 256 x 256
+// tiles, every pair of a chunk in one persistent launch, FP32 slabs);
+// splitting and the FP64 reduction are the kernels below.
 //
 // Error per chunk (row and column maxima m_r, n_c over the chunk): the
 // remainders after s slices and the dropped pairs contribute at most
@@ -355,13 +355,14 @@ dgchefsi_status sliced_gemm(dgchefsi_ctx* ctx, bool b_rows, bool a_lower, int64_
     count_launch();
     DG_CUDA(cudaGetLastError());
   }
+  DG_TRY(pair_products_begin(ctx));
   for (int64_t n0 = 0; n0 < Nc; n0 += P) {
     const int64_t pn = std::min<int64_t>(P, Nc - n0);
     for (int chunk = 0; chunk < nch; ++chunk) {
       const int64_t k0 = (int64_t)chunk * kL;
       const int64_t kc = std::min<int64_t>(kL, K - k0);
       // slab of pair (i, j): M x pn, Qa_i times the panel's rows of Qb_j over this chunk
-      DG_TRY(tc_slice_pairs(ctx, Qa, lqa, sa, M, Qb, lqb, sb, Nc, K, k0, kc, n0, pn, s, Pw));
+      DG_TRY(pair_products_2sm(ctx, Qa, lqa, sa, M, Qb, lqb, sb, Nc, K, k0, kc, n0, pn, s, Pw));
       const int64_t total = M * pn;
       const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
       reduce_kernel(s)<<<grid, 256, 0, st>>>(Pw, M, pn, Ea, Eb, nch, chunk, n0, C, ldc, chunk > 0 ? 1 : 0,
@@ -370,7 +371,7 @@ dgchefsi_status sliced_gemm(dgchefsi_ctx* ctx, bool b_rows, bool a_lower, int64_
       DG_CUDA(cudaGetLastError());
     }
   }
-  return tc_slice_pairs_status(ctx);
+  return pair_products_status(ctx);
 }
 
 // ---------------------------------------------------------------------------

@@ -245,6 +245,7 @@ struct TcState {
   int shapeG[3] = {0, 0, 0}, shapeT[3] = {0, 0, 0}, shapeL[3] = {0, 0, 0};  // chosen per precision
   int forceG[3] = {0, 0, 0}, forceT[3] = {0, 0, 0}, forceL[3] = {0, 0, 0};  // dgchefsi_set_tile_shape
   int tgb[3] = {-1, -1, -1};  // unit order (Params::tgb) chosen per precision; -1 = not tuned yet
+  int force_tgb[3] = {-1, -1, -1};  // dgchefsi_set_unit_order (-1 = tune)
   float tuned_ms[3][NSHAPES] = {};
   // graph form
   cudaStream_t cap_stream = nullptr;
@@ -277,7 +278,6 @@ struct TcState {
     double* coef_d = nullptr;  // {c = 0, alpha = 1, beta = 0}
     Plan plan;
     DevBuf Hs, Xs, Pw, ex;
-    DevBuf dense;  // schedule and element tables of the dense slice-pair products
   } sx;
   float* R[3] = {nullptr, nullptr, nullptr};
   float* WF[2] = {nullptr, nullptr};
@@ -698,19 +698,22 @@ static dgchefsi_status enqueue_filter(dgchefsi_ctx* ctx, TcState& t, int mode, L
 
 // Pick the unit shape for this precision: a forced one, the tuned one, or time
 // step 0 with every candidate whose accumulator width fits and keep the fastest.
+static dgchefsi_status tune_unit_order(dgchefsi_ctx* ctx, TcState& t, int mode, int64_t Ns, int G, int T,
+                                       int layout);
+
 static dgchefsi_status choose_shape(dgchefsi_ctx* ctx, TcState& t, int mode, int64_t Ns, int* G, int* T,
                                     int* layout) {
   if (t.forceG[mode]) {
     *G = t.forceG[mode];
     *T = t.forceT[mode];
     *layout = t.forceL[mode];
-    return DGCHEFSI_OK;
+    return tune_unit_order(ctx, t, mode, Ns, *G, *T, *layout);
   }
   if (t.shapeG[mode]) {
     *G = t.shapeG[mode];
     *T = t.shapeT[mode];
     *layout = t.shapeL[mode];
-    return DGCHEFSI_OK;
+    return tune_unit_order(ctx, t, mode, Ns, *G, *T, *layout);
   }
   cudaStream_t s = ctx->stream;
   cudaEvent_t e0, e1;
@@ -744,38 +747,54 @@ static dgchefsi_status choose_shape(dgchefsi_ctx* ctx, TcState& t, int mode, int
     cudaEventDestroy(e1);
     return set_error(DGCHEFSI_ERR_UNSUPPORTED, "no tensor-core unit shape for accumulator width %d", t.ACC);
   }
-  // unit order of the chosen shape: state tiles in blocks of 2, 4 or 8 per
-  // pass over the element groups (the Y_k slices a pass touches then stay in
-  // L2; H is read once per pass), or all state tiles of a group back to back
-  {
-    Launch L;
-    DG_TRY(prepare_launch(ctx, t, mode, bG, bT, bL, Ns, L));
-    float best_o = 1e30f;
-    int bo = 0;
-    for (int o : {0, 2, 4, 8}) {
-      if (o >= L.p.ntg) continue;
-      L.p.tgb = o;
-      float ms = 0.f;
-      for (int rep = 0; rep < 2; ++rep) {
-        DG_CUDA(cudaEventRecord(e0, s));
-        DG_TRY(launch_step(ctx, t, mode, L, 0, s));
-        DG_CUDA(cudaEventRecord(e1, s));
-        DG_CUDA(cudaEventSynchronize(e1));
-        DG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      }
-      if (ms < best_o) {
-        best_o = ms;
-        bo = o;
-      }
-    }
-    t.tgb[mode] = bo;
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   t.shapeG[mode] = *G = bG;
   t.shapeT[mode] = *T = bT;
   t.shapeL[mode] = *layout = bL;
   clear_error();  // a candidate without a kernel is skipped, not an error
+  return tune_unit_order(ctx, t, mode, Ns, bG, bT, bL);
+}
+
+// Unit order of a shape: state tiles in blocks of 2, 4 or 8 per pass over the
+// element groups (the Y_k slices one pass touches stay in L2; H is read once
+// per pass), or all state tiles of a group back to back (0). A forced order
+// is taken as is; otherwise step 0 is timed with each and the fastest kept.
+static dgchefsi_status tune_unit_order(dgchefsi_ctx* ctx, TcState& t, int mode, int64_t Ns, int G, int T,
+                                       int layout) {
+  if (t.force_tgb[mode] >= 0) {
+    t.tgb[mode] = t.force_tgb[mode];
+    return DGCHEFSI_OK;
+  }
+  if (t.tgb[mode] >= 0) return DGCHEFSI_OK;
+  cudaStream_t s = ctx->stream;
+  cudaEvent_t e0, e1;
+  DG_CUDA(cudaEventCreate(&e0));
+  DG_CUDA(cudaEventCreate(&e1));
+  Launch L;
+  dgchefsi_status st = prepare_launch(ctx, t, mode, G, T, layout, Ns, L);
+  float best = 1e30f;
+  int bo = 0;
+  for (int o : {0, 2, 4, 8}) {
+    if (st != DGCHEFSI_OK || (o > 0 && o >= L.p.ntg)) continue;
+    L.p.tgb = o;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && st == DGCHEFSI_OK; ++rep) {  // the first launch warms caches
+      cudaEventRecord(e0, s);
+      st = launch_step(ctx, t, mode, L, 0, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        st = set_error(DGCHEFSI_ERR_CUDA, "timing the unit order failed");
+    }
+    if (st == DGCHEFSI_OK && ms < best) {
+      best = ms;
+      bo = o;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DGCHEFSI_OK) return st;
+  t.tgb[mode] = bo;
   return DGCHEFSI_OK;
 }
 
@@ -1233,108 +1252,6 @@ dgchefsi_status tc_sliced_matvec(dgchefsi_ctx* ctx, const double* X, int64_t ldx
   return DGCHEFSI_OK;
 }
 
-dgchefsi_status tc_slice_pairs(dgchefsi_ctx* ctx, const __nv_bfloat16* Qa, int64_t lqa, int64_t sa, int64_t M,
-                               const __nv_bfloat16* Qb, int64_t lqb, int64_t sb, int64_t Nc, int64_t K, int64_t k0,
-                               int64_t kc, int64_t n0, int64_t pn, int s, float* Pw) {
-  if (!ctx->tc) ctx->tc = new TcState();
-  TcState& t = *ctx->tc;
-  DG_TRY(ensure_layout(ctx, t));
-  cudaStream_t st = ctx->stream;
-  constexpr int ACC = 128, G = 1, T = 2, W = 64;
-  FilterKernel kern = pick_kernel(MODE_BF16, G, T, ACC, 1);
-  if (!kern) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "no step kernel for the slice-pair products");
-  if (M > 2147483647LL / 2 || pn > 2147483647LL || Nc > 2147483647LL || K > 2147483647LL)
-    return set_error(DGCHEFSI_ERR_UNSUPPORTED, "slice-pair product too large for 32-bit TMA coordinates");
-  // one element per 128 columns of the panel; its schedule walks the chunk's
-  // 64-wide K slices: [K coordinate (both operands), first row of the H-side tile]
-  const int nE = (int)((pn + ACC - 1) / ACC);
-  const int nS = (int)((kc + W - 1) / W);
-  std::vector<int32_t> tab((size_t)nE * 5 + 1 + (size_t)nE * nS * 2);
-  int32_t* grp = tab.data();
-  int32_t* nbv = grp + nE;
-  int32_t* poff = nbv + nE;
-  int32_t* pnb = poff + nE;
-  int32_t* sptr = pnb + nE;       // nE + 1
-  int32_t* sched = sptr + nE + 1;
-  for (int E = 0; E < nE; ++E) {
-    grp[E] = E;
-    nbv[E] = (int32_t)std::min<int64_t>(ACC, pn - (int64_t)E * ACC);
-    poff[E] = E * ACC;
-    pnb[E] = ACC;
-    sptr[E] = E * nS;
-    for (int S = 0; S < nS; ++S) {
-      sched[((size_t)E * nS + S) * 2] = (int32_t)(k0 + (int64_t)S * W);
-      sched[((size_t)E * nS + S) * 2 + 1] = (int32_t)(n0 + (int64_t)E * ACC);
-    }
-  }
-  sptr[nE] = nE * nS;
-  DG_TRY(ensure(ctx, t.sx.dense, sizeof(int32_t) * tab.size(), "slice-pair schedule"));
-  int32_t* d = static_cast<int32_t*>(t.sx.dense.p);
-  DG_CUDA(cudaMemcpyAsync(d, tab.data(), sizeof(int32_t) * tab.size(), cudaMemcpyHostToDevice, st));
-  const int stage_bytes = 128 * SLICE_BYTES + 256 * SLICE_BYTES;
-  const int stages = TN_RING_BYTES / stage_bytes;
-  const int smem = stages * stage_bytes + (2 * stages + 4) * 8 + 2 * nS * (1 + G) * 4 + 1024;
-  DG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  Params p{};
-  p.grp_elem = d;
-  p.nb = d + nE;
-  p.poff = d + 2 * nE;
-  p.pnb = d + 3 * nE;
-  p.sched_ptr = d + 4 * nE;
-  p.sched = d + 5 * nE + 1;
-  p.nsub = nullptr;
-  p.gslots = nullptr;
-  p.hx_sched = 1;
-  p.lo_rows = 0;
-  p.Ns = M;
-  p.ldp = pn;
-  p.W = W;
-  p.mode = MODE_BF16;
-  p.boxn = ACC;
-  p.G = G;
-  p.T = T;
-  p.ACC = ACC;
-  p.NBUF = 2;
-  p.stages = stages;
-  p.ngroups = nE;
-  p.ntg = (int)((M + 255) / 256);
-  p.maxent = nS;
-  p.err = t.err_d;
-  p.step = 0;
-  p.Hout = nullptr;
-  p.Lout = nullptr;
-  if (!t.sx.coef_d) {
-    DG_CUDA(cudaMalloc(&t.sx.coef_d, sizeof(double) * 3));
-    const double coef[3] = {0.0, 1.0, 0.0};
-    DG_CUDA(cudaMemcpy(t.sx.coef_d, coef, sizeof(coef), cudaMemcpyHostToDevice));
-  }
-  p.coef = t.sx.coef_d;
-  DG_CUDA(cudaMemsetAsync(t.err_d, 0, sizeof(int), st));
-  const unsigned grid = (unsigned)std::min<int64_t>((int64_t)nE * p.ntg, t.num_sms);
-  std::vector<CUtensorMap> bmap(s);
-  for (int j = 0; j < s; ++j)
-    DG_TRY(make_map(&bmap[j], const_cast<__nv_bfloat16*>(Qb) + (size_t)j * sb, false, (uint64_t)K, (uint64_t)Nc,
-                    (uint32_t)W, (uint32_t)ACC, false, (uint64_t)lqb));
-  for (int i = 0; i < s; ++i) {
-    CUtensorMap amap;
-    DG_TRY(make_map(&amap, const_cast<__nv_bfloat16*>(Qa) + (size_t)i * sa, false, (uint64_t)K, (uint64_t)M,
-                    (uint32_t)W, 256u, false, (uint64_t)lqa));
-    for (int j = 0; i + j < s; ++j) {
-      p.Fout = Pw + (size_t)(i * s - i * (i - 1) / 2 + j) * (size_t)(M * pn);
-      p.Fprev = p.Fout;
-      kern<<<grid, NTHREADS, smem, st>>>(amap, amap, bmap[j], p);
-      count_launch();
-      DG_CUDA(cudaGetLastError());
-    }
-  }
-  return DGCHEFSI_OK;
-}
-
-dgchefsi_status tc_slice_pairs_status(dgchefsi_ctx* ctx) {
-  if (!ctx->tc) return DGCHEFSI_OK;
-  return check_err(*ctx->tc, ctx->stream);
-}
-
 dgchefsi_status tc_set_shape(dgchefsi_ctx* ctx, int prec, int G, int T, int layout) {
   if (!ctx->tc) ctx->tc = new TcState();
   TcState& t = *ctx->tc;
@@ -1342,6 +1259,7 @@ dgchefsi_status tc_set_shape(dgchefsi_ctx* ctx, int prec, int G, int T, int layo
   const int mode = mode_of(prec);
   if (G == 0 && T == 0) {
     t.forceG[mode] = t.forceT[mode] = t.forceL[mode] = 0;
+    if (t.force_tgb[mode] < 0) t.tgb[mode] = -1;
     return DGCHEFSI_OK;
   }
   if (!pick_kernel(mode, G, T, t.ACC, layout))
@@ -1350,6 +1268,21 @@ dgchefsi_status tc_set_shape(dgchefsi_ctx* ctx, int prec, int G, int T, int layo
   t.forceG[mode] = G;
   t.forceT[mode] = T;
   t.forceL[mode] = layout;
+  t.tgb[mode] = -1;  // a new shape gets its unit order tuned again
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status tc_set_unit_order(dgchefsi_ctx* ctx, int prec, int tgb) {
+  if (!ctx->tc) ctx->tc = new TcState();
+  TcState& t = *ctx->tc;
+  const int mode = mode_of(prec);
+  t.force_tgb[mode] = tgb;
+  t.tgb[mode] = tgb;
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status tc_get_unit_order(dgchefsi_ctx* ctx, int prec, int* tgb) {
+  *tgb = (ctx->tc && ctx->tc->tgb[mode_of(prec)] >= 0) ? ctx->tc->tgb[mode_of(prec)] : -1;
   return DGCHEFSI_OK;
 }
 
@@ -1395,7 +1328,6 @@ void tc_destroy(dgchefsi_ctx* ctx) {
   cudaFree(t.sx.Xs.p);
   cudaFree(t.sx.Pw.p);
   cudaFree(t.sx.ex.p);
-  cudaFree(t.sx.dense.p);
   cudaFree(t.gbuf.p);
   cudaFree(t.coefb_d);
   delete ctx->tc;

@@ -89,10 +89,6 @@ struct Params {
   // zero) and of each element group
   const uint8_t* nsub;
   const int32_t* gslots;
-  // 1: the K coordinate of the H-side tile is the schedule entry's (the dense
-  // slice-pair products, whose H side is a plain row-major matrix); 0: the
-  // operand copy of H, whose tiles start at column 0
-  int hx_sched;
   // unit order: blocks of tgb state tiles, each walking every element group
   // (tgb consecutive units per group) before the next block; 0 = all state
   // tiles of a group back to back (one block)
@@ -627,12 +623,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_expect_tx(fb, (uint32_t)stage_bytes);
             uint8_t* sst = smem + st * stage_bytes;
             const int xo = sub * (SB / ESZ);  // element offset of this K part (16-byte multiple)
-            const int hx = xo + (p.hx_sched ? ent[0] : 0);
 #pragma unroll
             for (int v = 0; v < NA; ++v) {
 #pragma unroll
               for (int g = 0; g < G; ++g)  // H tiles (zero tiles for non-coupling elements)
-                tma_load_2d(smem_u32(sst + v * a_bytes + g * h_bytes), &tmB, hx,
+                tma_load_2d(smem_u32(sst + v * a_bytes + g * h_bytes), &tmB, xo,
                             (int)(ent[1 + g] + (v == 1 ? p.lo_rows : 0)), fb);
               tma_load_2d(smem_u32(sst + NA * a_bytes + v * x_bytes), v == 1 ? &tmA1 : &tmA0, ent[0] + xo, s0, fb);
             }

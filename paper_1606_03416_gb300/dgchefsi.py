@@ -31,7 +31,8 @@ EXPORTS = ["dgchefsi_create", "dgchefsi_destroy", "dgchefsi_set_stream", "dgchef
            "dgchefsi_filter_graph", "dgchefsi_set_tile_shape", "dgchefsi_get_tile_shape",
            "dgchefsi_selftest_wait", "dgchefsi_selftest_fp64_rate", "dgchefsi_set_orthonormalisation", "dgchefsi_density_pattern",
            "dgchefsi_realign", "dgchefsi_filter_host", "dgchefsi_set_subspace_products",
-           "dgchefsi_sliced_gemm", "dgchefsi_sliced_matvec"]
+           "dgchefsi_sliced_gemm", "dgchefsi_sliced_matvec", "dgchefsi_set_unit_order",
+           "dgchefsi_get_unit_order"]
 
 # Orthonormalisations of Alg. 1 step 3 (dgchefsi_set_orthonormalisation).
 ORTHONORMALISATIONS = {"cholqr": 0, "cholqr2": 1, "shifted_cholqr3": 2}
@@ -75,6 +76,8 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_set_subspace_products": (st, [P, C.c_int, C.c_int]),
         "dgchefsi_sliced_gemm": (st, [P, C.c_int, C.c_int, I64, I64, I64, P, I64, P, I64, P, I64, C.c_int]),
         "dgchefsi_sliced_matvec": (st, [P, P, P, I64, I64, C.c_int]),
+        "dgchefsi_set_unit_order": (st, [P, C.c_int, C.c_int]),
+        "dgchefsi_get_unit_order": (st, [P, C.c_int, P]),
         "dgchefsi_density_pattern": (st, [P, P, I64, I64, P, P]),
         "dgchefsi_realign": (st, [P, P, P, P, P, P, I64, I64, P, I64]),
         "dgchefsi_filter_host": (st, [P, C.c_int, P, P, I64, I64, C.c_int, D, D, D, I64]),
@@ -269,6 +272,15 @@ class Context:
 
     def set_tile_shape(self, prec: str, G: int, T: int, layout: int = 0):
         _check(_lib.dgchefsi_set_tile_shape(self._h, PRECISIONS[prec], int(G), int(T), int(layout)))
+
+    def set_unit_order(self, prec: str, tgb: int = -1):
+        """State tiles per pass over the element groups (0: a group's tiles back to back; -1: tune)."""
+        _check(_lib.dgchefsi_set_unit_order(self._h, PRECISIONS[prec], int(tgb)))
+
+    def unit_order(self, prec: str) -> int:
+        v = C.c_int()
+        _check(_lib.dgchefsi_get_unit_order(self._h, PRECISIONS[prec], C.byref(v)))
+        return v.value
 
     def tile_shape(self, prec: str):
         """(G, T, ACC, layout) of the tensor-core filter for this precision."""

@@ -159,6 +159,25 @@ def profiled_gram_traffic(Ns: int):
     return None
 
 
+def profiled_pairs_traffic(Ns: int, N: int):
+    """DRAM bytes of one k_slice_pairs_2sm launch of the Gram-shaped product
+    (Ns x Ns, one 4096-long K chunk) from the committed ncu summary taken on the
+    current kernel source; else None."""
+    import glob
+    import hashlib
+    src = os.path.join(ROOT, "paper_1606_03416_gb300", "csrc", "pair_gemm.cu")
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    for path in glob.glob(os.path.join(ROOT, "profiles", "k_slice_pairs_2sm_*.md")):
+        text = open(path).read()
+        if f"source-sha1 (paper_1606_03416_gb300/csrc/pair_gemm.cu, first 12): {sha}" not in text:
+            continue
+        key = f"traffic-per-launch-bytes-gram-Ns{Ns}:"
+        for line in text.splitlines():
+            if line.startswith(key):
+                return float(line[len(key):])
+    return None
+
+
 def dist_env():
     from paper_1606_03416_gb300.replicas import rank_info
     return rank_info()
@@ -614,8 +633,12 @@ def measure_sliced(ctx, X_warm, state, cycle, vd, Ns, N, m, Ne, kT, args, dev, b
             ts.append(s_.elapsed_time(e_))
         t = statistics.median(ts[1:]) * 1e-3
         tens = pairs * 2.0 * mnk / t / 1e12
+        kms, kn = ctx.sliced_timing()   # device time of the slice-pair kernel launches of the last call
         prods[name] = {"ms": t * 1e3, "fp64_equivalent_tflops": 2.0 * mnk / t / 1e12, "tensor_tflops": tens,
-                       "bound": "tensor", "peak": bf16_peak, "frac": tens / bf16_peak}
+                       "bound": "tensor", "peak": bf16_peak, "frac": tens / bf16_peak,
+                       "slice_pair_kernel": {"kernel": "k_slice_pairs_2sm", "launches": kn, "ms": kms,
+                                             "tensor_tflops": pairs * 2.0 * mnk / (kms * 1e-3) / 1e12,
+                                             "frac": pairs * 2.0 * mnk / (kms * 1e-3) / 1e12 / bf16_peak}}
     out["products"] = prods
     ctx.set_subspace_products("f64", s)
     state["prev"] = warm_prev
@@ -1182,6 +1205,15 @@ def main():
         line["converge"] = conv
     if sliced:
         line["sliced_products"] = sliced
+        g = sliced["products"]["gram"]["slice_pair_kernel"]
+        # the dominant kernel of this library in the timed (sliced) cycle
+        line["roofline_slice_pairs"] = {
+            "bound": "tensor", "achieved": g["tensor_tflops"], "peak": bf16_peak, "unit": "TFLOP/s",
+            "frac": g["frac"], "traffic": profiled_pairs_traffic(Ns, N), "kernel": "k_slice_pairs_2sm",
+            "ms_per_launch": g["ms"] / max(g["launches"], 1),
+            "work": f"{args.slices * (args.slices + 1) // 2} slice pairs x 2 Ns^2 x 4096 per launch (one K chunk of "
+                    "the Gram-shaped product)",
+            "peak_source": src}
     if not args.no_next_rows and args.prec != "f64":
         Xn_rows = torch.from_numpy(X0).to(dev)
         line["next_rows"] = measure_next_rows(ctx, H, Xn_rows, Ns, m, args.prec, dev)

@@ -266,9 +266,9 @@ dgchefsi_status dgchefsi_set_orthonormalisation(dgchefsi_ctx* ctx, int mode);
  * ERR_ARG for another mode or slice count. In the sliced form H Y_hat runs
  * from slices too (dgchefsi_sliced_matvec) when H fits that form, else on the
  * FP64 cores.
- * dgchefsi_energy_grad follows the same setting for its forward products and
- * the dense products of its adjoint (Z = U^{-1} Q, W_m = Z (2 G R^T));
- * dgchefsi_gram always uses FP64 products. */
+ * dgchefsi_energy_grad follows the same setting for its forward products
+ * (H Y_hat included) and the dense products of its adjoint (Z = U^{-1} Q,
+ * W_m = Z (2 G R^T)); dgchefsi_gram always uses FP64 products. */
 #define DGCHEFSI_PRODUCTS_F64 0
 #define DGCHEFSI_PRODUCTS_SLICED_BF16 1
 dgchefsi_status dgchefsi_set_subspace_products(dgchefsi_ctx* ctx, int mode, int slices);
@@ -297,6 +297,13 @@ dgchefsi_status dgchefsi_set_subspace_products(dgchefsi_ctx* ctx, int mode, int 
 dgchefsi_status dgchefsi_sliced_gemm(dgchefsi_ctx* ctx, int b_rows, int a_lower, int64_t M, int64_t Nc, int64_t K,
                                      const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
                                      int64_t ldc, int slices);
+
+/* Measurement aid (no counterpart in the paper): the device time, in ms, of
+ * the slice-pair kernel launches of the last dense product from slices
+ * (dgchefsi_sliced_gemm, or one of the four products of the last sliced
+ * Rayleigh-Ritz step), and their number; CUDA events around each launch on
+ * the context's stream. Either pointer may be NULL. */
+dgchefsi_status dgchefsi_sliced_timing(dgchefsi_ctx* ctx, double* pairs_ms, int64_t* launches);
 
 /* Y = H X in FP64 from exact BF16 slices on the tensor cores: the block-sparse
  * product of Eq. matvec_3 (y_K = sum over K' in N(K) of H_{K;K'} x_{K'}) that

@@ -212,7 +212,9 @@ extern "C" dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, con
   DG_CUDA(zero_strict_upper_f64(S, Ns, Ns, s));  // S now holds L = U^{-T} exactly (lower)
   DG_CUDA(cudaMemcpyAsync(L, S, sizeof(double) * small, cudaMemcpyDeviceToDevice, s));
   DG_TRY(prod_nn(L, Yt, N, N, Yh, N, true));
-  DG_CUDA(filter_step_f64(h, Yh, N, nullptr, HY, N, Ns, 1.0, 0.0, 0.0, s));
+  bool hy_sliced = false;  // H Y_hat from BF16 slices too, when H fits that form
+  if (sl) DG_TRY(tc_sliced_matvec(ctx, Yh, N, HY, N, Ns, nsl, bad, &hy_sliced));
+  if (!hy_sliced) DG_CUDA(filter_step_f64(h, Yh, N, nullptr, HY, N, Ns, 1.0, 0.0, 0.0, s));
   DG_TRY(prod_nt(Yh, HY, S));
   ADJ_SOLVER(cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n, S, n, lam, work, lwork,
                               ctx->info_d + 2));

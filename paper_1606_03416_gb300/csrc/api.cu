@@ -556,6 +556,13 @@ void dgchefsi_destroy(dgchefsi_ctx* ctx) {
   free_buf(ctx->ws_sliced_t);
   free_buf(ctx->ws_sliced_b);
   free_buf(ctx->ws_pairs);
+  if (ctx->s_reduce) cudaStreamSynchronize(ctx->s_reduce);
+  for (int i = 0; i < 2; ++i) {
+    if (ctx->ev_pairs[i]) cudaEventDestroy(ctx->ev_pairs[i]);
+    if (ctx->ev_reduce[i]) cudaEventDestroy(ctx->ev_reduce[i]);
+  }
+  if (ctx->s_reduce) cudaStreamDestroy(ctx->s_reduce);
+  for (cudaEvent_t e : ctx->ev_time) cudaEventDestroy(e);
   for (int i = 0; i < 2; ++i) {
     free_buf(ctx->ws_hin[i]);
     free_buf(ctx->ws_hout[i]);
@@ -799,6 +806,14 @@ dgchefsi_status dgchefsi_sliced_matvec(dgchefsi_ctx* ctx, const double* X, doubl
   DG_CUDA(cudaMemcpyAsync(&bad, ctx->info_d + 3, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   DG_CUDA(cudaStreamSynchronize(ctx->stream));
   if (bad) return set_error(DGCHEFSI_ERR_NONFINITE, "non-finite entry in H or X");
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status dgchefsi_sliced_timing(dgchefsi_ctx* ctx, double* pairs_ms, int64_t* launches) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  if (pairs_ms) *pairs_ms = ctx->pairs_ms;
+  if (launches) *launches = ctx->pairs_launches;
   return DGCHEFSI_OK;
 }
 

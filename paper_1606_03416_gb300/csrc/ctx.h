@@ -61,6 +61,16 @@ struct dgchefsi_ctx {
   dg::DevBuf ws_sliced_t;  // transposed left operand of the A^T B form
   dg::DevBuf ws_sliced_b;  // transposed right operand of the A B form
   dg::DevBuf ws_pairs;     // error word, tensor maps and pair lists of the slice-pair kernel
+  // the slab reduction of the sliced products runs on its own stream, one K
+  // chunk behind the slice-pair kernel (double-buffered slabs)
+  cudaStream_t s_reduce = nullptr;
+  cudaEvent_t ev_pairs[2] = {nullptr, nullptr}, ev_reduce[2] = {nullptr, nullptr};
+  // device time of the slice-pair kernel launches of the last sliced product
+  // (dgchefsi_sliced_timing): timing events around each launch, read back
+  // when the product's status is checked
+  std::vector<cudaEvent_t> ev_time;
+  double pairs_ms = 0.0;
+  int64_t pairs_launches = 0;
   int32_t f64_tj = 64;    // column tile of the FP64 filter (set at create)
   // FP64 filter as a CUDA graph: coefficients copied from a pinned mirror at
   // every replay; the graph is captured again when X, Y, N_s, ld, m or the
@@ -165,12 +175,13 @@ dgchefsi_status reduce_pair_slabs(const float* Pw, int64_t rows, int64_t cols, c
 // launch): for every pair i + j < s, Pw[pair i*s - i(i-1)/2 + j] (M x pn,
 // row-major FP32) = Qa_i[:, k0:k0+kc] times Qb_j[n0:n0+pn, k0:k0+kc]^T, with
 // Qa_i = Qa + i*sa (M x K, row stride lqa), Qb_j = Qb + j*sb (Nc x K, row
-// stride lqb), entries k >= K read as zero. Enqueued only.
+// stride lqb), entries k >= K read as zero; a_lower: A is lower triangular,
+// so a row tile skips the K slices past its last row. Enqueued only.
 // pair_products_begin clears the kernel's error word; pair_products_status
 // synchronises and reports a pipeline timeout.
 dgchefsi_status pair_products_2sm(dgchefsi_ctx* ctx, const __nv_bfloat16* Qa, int64_t lqa, int64_t sa, int64_t M,
                                   const __nv_bfloat16* Qb, int64_t lqb, int64_t sb, int64_t Nc, int64_t K, int64_t k0,
-                                  int64_t kc, int64_t n0, int64_t pn, int s, float* Pw);
+                                  int64_t kc, int64_t n0, int64_t pn, int s, float* Pw, bool a_lower);
 dgchefsi_status pair_products_begin(dgchefsi_ctx* ctx);
 dgchefsi_status pair_products_status(dgchefsi_ctx* ctx);
 // Y = H X (X, Y: Ns x ld state-major FP64) from s BF16 slices of each operand on

@@ -9,10 +9,10 @@
 // read both CTAs' halves, and each CTA's tensor memory holds its 128 rows of
 // the tile. Per SM that is 8 KB of operands per 128-clock MMA, half of what a
 // single-SM 128 x 256 tile reads, which leaves shared-memory bandwidth for the
-// TMA refills. The kernel is persistent over (tile, pair) units, pairs
-// innermost so that consecutive units reuse the tile's slices from L2, and the
-// tensor maps of all slices sit in device memory, so one launch covers every
-// pair of a chunk.
+// TMA refills. The kernel is persistent over (pair, tile) units, the tiles of
+// one pair back to back so that the units in flight read the same two slices
+// from L2, and the tensor maps of all slices sit in device memory, so one
+// launch covers every pair of a chunk.
 //
 // Roles per CTA (320 threads): warp 0 lane 0 loads its halves with TMA into a
 // 6-slot ring and signals the first CTA's "full" barrier (its expect-tx counts
@@ -41,6 +41,7 @@ struct PairJob {
   int64_t pn;       // columns of the slab (rows n0 .. n0 + pn - 1 of B)
   int n0, k0, nk;   // first B row, first K column, 64-wide K slices of the chunk
   int nmt, nnt;     // 256-row tiles along M and along the panel
+  int lower;        // A is lower triangular: a row tile stops at the chunk's last K slice it reaches
   float* Pw;        // slab of pair p at Pw + p * M * pn, row-major M x pn
   int* err;
 };
@@ -92,6 +93,27 @@ __device__ __forceinline__ void commit_pair(uint32_t bar) {
       : "memory");
 }
 
+// Pair and tile of work unit u: pairs outermost (in the table's order, one
+// slice of A with the slices of B in turn), the tiles of one pair back to back
+// (row tiles fastest), so the units in flight share one A slice and one or two
+// B slices, which stay in L2.
+__device__ __forceinline__ void unit_of(const PairJob& J, int64_t u, int& p, int& mt, int& nt) {
+  const int64_t ntiles = (int64_t)J.nmt * J.nnt;
+  p = (int)(u / ntiles);
+  const int64_t tile = u - (int64_t)p * ntiles;
+  mt = (int)(tile % J.nmt);
+  nt = (int)(tile / J.nmt);
+}
+
+// K slices of the chunk that row tile mt needs: all of them, or for a lower
+// triangular A those up to its last row (at least one, so that the tile's
+// accumulator is written).
+__device__ __forceinline__ int slices_of_tile(const PairJob& J, int mt) {
+  if (!J.lower) return J.nk;
+  const int need = (mt * 256 + 256 - J.k0 + 63) / 64;
+  return max(1, min(J.nk, need));
+}
+
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PG_THREADS, 1) k_slice_pairs_2sm(const PairJob J) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -139,14 +161,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PG_THREADS, 1) k_sli
       int c = 0;
       bool ok = true;
       for (int64_t u = cid; u < nunits && ok; u += ncl) {
-        const int64_t tile = u / J.npairs;
-        const int p = (int)(u - tile * J.npairs);
-        const int mt = (int)(tile % J.nmt), nt = (int)(tile / J.nmt);
+        int p, mt, nt;
+        unit_of(J, u, p, mt, nt);
         const CUtensorMap* am = J.maps + J.pair_i[p];
         const CUtensorMap* bm = J.maps + J.s + J.pair_j[p];
         const int ya = mt * 256 + (int)rank * 128;
         const int yb = J.n0 + nt * 256 + (int)rank * 128;
-        for (int ks = 0; ks < J.nk; ++ks) {
+        const int nk = slices_of_tile(J, mt);
+        for (int ks = 0; ks < nk; ++ks) {
           const int st = c % PG_STAGES;
           const uint32_t ph = (uint32_t)(c / PG_STAGES) & 1u;
           if (!mbar_wait(empty0 + 8 * st, ph ^ 1u)) {
@@ -183,7 +205,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PG_THREADS, 1) k_sli
         }
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(buf * 256);
-        for (int ks = 0; ks < J.nk && ok; ++ks) {
+        int p_, mt, nt_;
+        unit_of(J, u, p_, mt, nt_);
+        const int nk = slices_of_tile(J, mt);
+        for (int ks = 0; ks < nk && ok; ++ks) {
           const int st = c % PG_STAGES;
           const uint32_t ph = (uint32_t)(c / PG_STAGES) & 1u;
           if (!mbar_wait(full0 + 8 * st, ph)) {
@@ -224,9 +249,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PG_THREADS, 1) k_sli
         break;
       }
       tc_fence_after();
-      const int64_t tile = u / J.npairs;
-      const int p = (int)(u - tile * J.npairs);
-      const int mt = (int)(tile % J.nmt), nt = (int)(tile / J.nmt);
+      int p, mt, nt;
+      unit_of(J, u, p, mt, nt);
       const int64_t r = (int64_t)mt * 256 + rank * 128 + 32 * q + lane;
       const bool row_ok = r < J.M && *(volatile int*)&abort_sh == 0;
       float* out = J.Pw + (size_t)p * (size_t)(J.M * J.pn) + (size_t)(r < J.M ? r : 0) * (size_t)J.pn;
@@ -296,7 +320,7 @@ dgchefsi_status slice_map(CUtensorMap* map, const __nv_bfloat16* base, uint64_t 
 
 dgchefsi_status pair_products_2sm(dgchefsi_ctx* ctx, const __nv_bfloat16* Qa, int64_t lqa, int64_t sa, int64_t M,
                                   const __nv_bfloat16* Qb, int64_t lqb, int64_t sb, int64_t Nc, int64_t K, int64_t k0,
-                                  int64_t kc, int64_t n0, int64_t pn, int s, float* Pw) {
+                                  int64_t kc, int64_t n0, int64_t pn, int s, float* Pw, bool a_lower) {
   if (M > 2147483647LL - 256 || Nc > 2147483647LL - 256 || K > 2147483647LL)
     return set_error(DGCHEFSI_ERR_UNSUPPORTED, "slice-pair product too large for 32-bit TMA coordinates");
   cudaStream_t st = ctx->stream;
@@ -336,6 +360,7 @@ dgchefsi_status pair_products_2sm(dgchefsi_ctx* ctx, const __nv_bfloat16* Qa, in
   J.nk = (int)((kc + 63) / 64);
   J.nmt = (int)((M + 255) / 256);
   J.nnt = (int)((pn + 255) / 256);
+  J.lower = a_lower ? 1 : 0;
   J.Pw = Pw;
   J.err = static_cast<int*>(tables.p);
   int nsm = 0;

@@ -235,6 +235,58 @@ __global__ void __launch_bounds__(256) k_sliced_reduce(const float* __restrict__
   }
 }
 
+// The same for P % 4 == 0, four consecutive outputs per thread: one 16-byte
+// load per slab instead of four 4-byte ones (same sums, same roundings).
+template <int S>
+__global__ void __launch_bounds__(256) k_sliced_reduce4(const float* __restrict__ Pw, int64_t M, int64_t P,
+                                                        const int32_t* __restrict__ Ea, const int32_t* __restrict__ Eb,
+                                                        int nch, int chunk, int64_t n0, double* __restrict__ C,
+                                                        int64_t ldc, int accumulate, const int32_t* __restrict__ cmap) {
+  constexpr int NB = (S + 4) / 5;
+  const int64_t slab = M * P;
+  const int64_t total4 = slab / 4;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total4;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t idx = 4 * q;
+    int g[4][S];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+      for (int t = 0; t < S; ++t) g[e][t] = 0;
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+      for (int j = 0; j < S - i; ++j) {
+        const float4 v =
+            __ldcs(reinterpret_cast<const float4*>(Pw + (int64_t)(i * S - i * (i - 1) / 2 + j) * slab + idx));
+        g[0][i + j] += __float2int_rn(v.x);
+        g[1][i + j] += __float2int_rn(v.y);
+        g[2][i + j] += __float2int_rn(v.z);
+        g[3][i + j] += __float2int_rn(v.w);
+      }
+    const int64_t r = idx / P;
+    const int64_t c0 = idx - r * P;
+    const int er = Ea[r * nch + chunk];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      double h = 0.0;
+#pragma unroll
+      for (int b = NB - 1; b >= 0; --b) {
+        int64_t B = 0;
+#pragma unroll
+        for (int t = 5 * b; t < 5 * b + 5; ++t) B = B * 64 + (t < S ? (int64_t)g[e][t] : 0);
+        h = h * 0x1p-30 + (double)B;
+      }
+      const int64_t c = c0 + e;
+      const int64_t oc = cmap ? (int64_t)cmap[c] : n0 + c;
+      if (oc < 0) continue;
+      const double v = ldexp(h, er + Eb[(n0 + c) * nch + chunk] - 12 - 24);
+      double* out = C + r * ldc + oc;
+      *out = accumulate ? *out + v : v;
+    }
+  }
+}
+
 typedef void (*ReduceKernel)(const float*, int64_t, int64_t, const int32_t*, const int32_t*, int, int, int64_t,
                              double*, int64_t, int, const int32_t*);
 
@@ -248,6 +300,31 @@ static ReduceKernel reduce_kernel(int s) {
 #undef DG_REDUCE_CASE
     default: return nullptr;
   }
+}
+
+static ReduceKernel reduce_kernel4(int s) {
+  switch (s) {
+#define DG_REDUCE_CASE(n) \
+  case n: return k_sliced_reduce4<n>;
+    DG_REDUCE_CASE(2) DG_REDUCE_CASE(3) DG_REDUCE_CASE(4) DG_REDUCE_CASE(5) DG_REDUCE_CASE(6)
+    DG_REDUCE_CASE(7) DG_REDUCE_CASE(8) DG_REDUCE_CASE(9) DG_REDUCE_CASE(10) DG_REDUCE_CASE(11)
+    DG_REDUCE_CASE(12) DG_REDUCE_CASE(13) DG_REDUCE_CASE(14) DG_REDUCE_CASE(15) DG_REDUCE_CASE(16)
+#undef DG_REDUCE_CASE
+    default: return nullptr;
+  }
+}
+
+// The reduction over slabs of M x P: four outputs per thread when P % 4 == 0.
+static cudaError_t launch_reduce(int s, const float* Pw, int64_t M, int64_t P, const int32_t* Ea, const int32_t* Eb,
+                                 int nch, int chunk, int64_t n0, double* C, int64_t ldc, int accumulate,
+                                 const int32_t* cmap, cudaStream_t st) {
+  const bool v4 = P % 4 == 0;
+  const int64_t work = v4 ? M * P / 4 : M * P;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 152 * 16));
+  (v4 ? reduce_kernel4(s) : reduce_kernel(s))<<<grid, 256, 0, st>>>(Pw, M, P, Ea, Eb, nch, chunk, n0, C, ldc,
+                                                                      accumulate, cmap);
+  count_launch();
+  return cudaGetLastError();
 }
 
 static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -309,11 +386,17 @@ dgchefsi_status sliced_gemm(dgchefsi_ctx* ctx, bool b_rows, bool a_lower, int64_
   const size_t a256 = 256;
   auto up = [&](size_t x) { return (x + a256 - 1) / a256 * a256; };
   // Column panel of the product (a multiple of the kernel's 128-column tiles)
-  // so that the FP32 pair slabs stay under the cap.
-  int64_t P = (int64_t)(kPairBytes / (sizeof(float) * (size_t)pairs * (size_t)M));
+  // so that the FP32 pair slabs stay under the cap; two slab buffers when the
+  // product has more than one (panel, chunk) step, so that the reduction of
+  // one step (on the context's reduction stream) overlaps the next step's
+  // slice pairs.
+  const bool multi = nch > 1 || (int64_t)(kPairBytes / (sizeof(float) * (size_t)pairs * (size_t)M)) < Nc;
+  const int nbuf = multi ? 2 : 1;
+  int64_t P = (int64_t)(kPairBytes / nbuf / (sizeof(float) * (size_t)pairs * (size_t)M));
   P = std::max<int64_t>(128, P / 128 * 128);
   if (P >= Nc) P = Nc;
-  const size_t pw_bytes = sizeof(float) * (size_t)pairs * (size_t)M * (size_t)P;
+  const size_t slab_set = sizeof(float) * (size_t)pairs * (size_t)M * (size_t)P;
+  const size_t pw_bytes = (size_t)nbuf * up(slab_set);
   DG_TRY(ensure(ctx, ctx->ws_sliced,
                 up(qa_bytes) + up(qb_bytes) + up(ea_bytes) + up(eb_bytes) + up(bal_bytes) + up(pw_bytes),
                 "sliced-product workspace"));
@@ -356,22 +439,64 @@ dgchefsi_status sliced_gemm(dgchefsi_ctx* ctx, bool b_rows, bool a_lower, int64_
     DG_CUDA(cudaGetLastError());
   }
   DG_TRY(pair_products_begin(ctx));
+  cudaStream_t sr = st;
+  if (multi) {
+    if (!ctx->s_reduce) {
+      DG_CUDA(cudaStreamCreateWithFlags(&ctx->s_reduce, cudaStreamNonBlocking));
+      for (int i = 0; i < 2; ++i) {
+        DG_CUDA(cudaEventCreateWithFlags(&ctx->ev_pairs[i], cudaEventDisableTiming));
+        DG_CUDA(cudaEventCreateWithFlags(&ctx->ev_reduce[i], cudaEventDisableTiming));
+      }
+    }
+    sr = ctx->s_reduce;
+    // nothing of an earlier call may still read a slab buffer or write C
+    DG_CUDA(cudaEventRecord(ctx->ev_pairs[0], st));
+    DG_CUDA(cudaStreamWaitEvent(sr, ctx->ev_pairs[0], 0));
+    for (int b = 0; b < 2; ++b) DG_CUDA(cudaEventRecord(ctx->ev_reduce[b], sr));
+  }
+  // timing events around every slice-pair launch (read after the status check)
+  const int nsteps = (int)(((Nc + P - 1) / P) * nch);
+  while ((int)ctx->ev_time.size() < 2 * nsteps) {
+    cudaEvent_t e = nullptr;
+    DG_CUDA(cudaEventCreate(&e));
+    ctx->ev_time.push_back(e);
+  }
+  int step = 0;
   for (int64_t n0 = 0; n0 < Nc; n0 += P) {
     const int64_t pn = std::min<int64_t>(P, Nc - n0);
-    for (int chunk = 0; chunk < nch; ++chunk) {
+    for (int chunk = 0; chunk < nch; ++chunk, ++step) {
       const int64_t k0 = (int64_t)chunk * kL;
       const int64_t kc = std::min<int64_t>(kL, K - k0);
-      // slab of pair (i, j): M x pn, Qa_i times the panel's rows of Qb_j over this chunk
-      DG_TRY(pair_products_2sm(ctx, Qa, lqa, sa, M, Qb, lqb, sb, Nc, K, k0, kc, n0, pn, s, Pw));
-      const int64_t total = M * pn;
-      const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
-      reduce_kernel(s)<<<grid, 256, 0, st>>>(Pw, M, pn, Ea, Eb, nch, chunk, n0, C, ldc, chunk > 0 ? 1 : 0,
-                                             nullptr);
-      count_launch();
-      DG_CUDA(cudaGetLastError());
+      const int b = step & 1;
+      float* Pb = reinterpret_cast<float*>(reinterpret_cast<char*>(Pw) + (size_t)b * up(slab_set));
+      // slab of pair (i, j): M x pn, Qa_i times the panel's rows of Qb_j over this chunk,
+      // into buffer b once the reduction that last read it is done
+      if (multi) DG_CUDA(cudaStreamWaitEvent(st, ctx->ev_reduce[b], 0));
+      DG_CUDA(cudaEventRecord(ctx->ev_time[2 * step], st));
+      DG_TRY(pair_products_2sm(ctx, Qa, lqa, sa, M, Qb, lqb, sb, Nc, K, k0, kc, n0, pn, s, Pb, a_lower));
+      DG_CUDA(cudaEventRecord(ctx->ev_time[2 * step + 1], st));
+      if (multi) {
+        DG_CUDA(cudaEventRecord(ctx->ev_pairs[b], st));
+        DG_CUDA(cudaStreamWaitEvent(sr, ctx->ev_pairs[b], 0));
+      }
+      DG_CUDA(launch_reduce(s, Pb, M, pn, Ea, Eb, nch, chunk, n0, C, ldc, chunk > 0 ? 1 : 0, nullptr, sr));
+      if (multi) DG_CUDA(cudaEventRecord(ctx->ev_reduce[b], sr));
     }
   }
-  return pair_products_status(ctx);
+  if (multi) {  // the caller's stream sees C complete
+    DG_CUDA(cudaEventRecord(ctx->ev_reduce[0], sr));
+    DG_CUDA(cudaStreamWaitEvent(st, ctx->ev_reduce[0], 0));
+  }
+  DG_TRY(pair_products_status(ctx));  // synchronises the stream
+  double ms = 0.0;
+  for (int q = 0; q < step; ++q) {
+    float t = 0.f;
+    DG_CUDA(cudaEventElapsedTime(&t, ctx->ev_time[2 * q], ctx->ev_time[2 * q + 1]));
+    ms += t;
+  }
+  ctx->pairs_ms = ms;
+  ctx->pairs_launches = step;
+  return DGCHEFSI_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -538,13 +663,8 @@ cudaError_t slices_of_states(const double* X, int64_t ld, int64_t Ns, int64_t N,
 dgchefsi_status reduce_pair_slabs(const float* Pw, int64_t rows, int64_t cols, const int32_t* Erows,
                                   const int32_t* Ecols, const int32_t* cmap, double* C, int64_t ldc, int s,
                                   cudaStream_t st) {
-  const ReduceKernel k = reduce_kernel(s);
-  if (!k) return set_error(DGCHEFSI_ERR_ARG, "slices = %d outside 2..16", s);
-  const int64_t total = rows * cols;
-  const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
-  k<<<grid, 256, 0, st>>>(Pw, rows, cols, Erows, Ecols, 1, 0, 0, C, ldc, 0, cmap);
-  count_launch();
-  DG_CUDA(cudaGetLastError());
+  if (!reduce_kernel(s)) return set_error(DGCHEFSI_ERR_ARG, "slices = %d outside 2..16", s);
+  DG_CUDA(launch_reduce(s, Pw, rows, cols, Erows, Ecols, 1, 0, 0, C, ldc, 0, cmap, st));
   return DGCHEFSI_OK;
 }
 

@@ -32,7 +32,7 @@ EXPORTS = ["dgchefsi_create", "dgchefsi_destroy", "dgchefsi_set_stream", "dgchef
            "dgchefsi_selftest_wait", "dgchefsi_selftest_fp64_rate", "dgchefsi_set_orthonormalisation", "dgchefsi_density_pattern",
            "dgchefsi_realign", "dgchefsi_filter_host", "dgchefsi_set_subspace_products",
            "dgchefsi_sliced_gemm", "dgchefsi_sliced_matvec", "dgchefsi_set_unit_order",
-           "dgchefsi_get_unit_order"]
+           "dgchefsi_get_unit_order", "dgchefsi_sliced_timing"]
 
 # Orthonormalisations of Alg. 1 step 3 (dgchefsi_set_orthonormalisation).
 ORTHONORMALISATIONS = {"cholqr": 0, "cholqr2": 1, "shifted_cholqr3": 2}
@@ -78,6 +78,7 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_sliced_matvec": (st, [P, P, P, I64, I64, C.c_int]),
         "dgchefsi_set_unit_order": (st, [P, C.c_int, C.c_int]),
         "dgchefsi_get_unit_order": (st, [P, C.c_int, P]),
+        "dgchefsi_sliced_timing": (st, [P, P, P]),
         "dgchefsi_density_pattern": (st, [P, P, I64, I64, P, P]),
         "dgchefsi_realign": (st, [P, P, P, P, P, P, I64, I64, P, I64]),
         "dgchefsi_filter_host": (st, [P, C.c_int, P, P, I64, I64, C.c_int, D, D, D, I64]),
@@ -352,6 +353,12 @@ class Context:
         _check(_lib.dgchefsi_sliced_gemm(self._h, int(b_rows), int(a_lower), M, Nc, K, _ptr(A), A.stride(0),
                                          _ptr(B), B.stride(0), _ptr(out), out.stride(0), int(slices)))
         return out
+
+    def sliced_timing(self):
+        """(ms, launches) of the slice-pair kernel in the last dense sliced product."""
+        ms, n = C.c_double(), C.c_int64()
+        _check(_lib.dgchefsi_sliced_timing(self._h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
 
     def sliced_matvec(self, X: torch.Tensor, Y: torch.Tensor | None = None, slices: int = 10) -> torch.Tensor:
         """Y = H X (Eq. matvec_3) in FP64 from exact BF16 slices on the tensor cores."""

@@ -290,8 +290,12 @@ dgchefsi_status dgchefsi_set_subspace_products(dgchefsi_ctx* ctx, int mode, int 
  * With row maxima m_r of A and column maxima n_c of the product's right
  * operand over each 4096-long chunk of K (length L), the error of C[r, c] is at
  * most the sum over chunks of L m_r n_c (2^{-6 slices} (slices + 4) + (5 + chunks) 2^{-53}).
- * Uses up to ~4 GB of FP32 workspace for the slice
- * products plus the slices (2 bytes x slices per operand entry). Synchronises;
+ * The slice pairs run on this library's tcgen05 kernel on pairs of SMs, all
+ * pairs of a K chunk in one launch; their FP32 results go to up to 8 GB of
+ * workspace (two buffers when there are several chunks or column panels, so
+ * that the FP64 reduction of one runs on a second library stream beside the
+ * next one's pairs), plus the slices (2 bytes x slices per operand entry) and,
+ * for b_rows = 0, a transposed FP64 copy of B. Synchronises;
  * ERR_NONFINITE if A or B holds NaN/Inf (C is then unspecified), ERR_ARG on bad
  * sizes, ERR_UNSUPPORTED when K / 4096 > 65535 or M, Nc > 2^31 - 1. */
 dgchefsi_status dgchefsi_sliced_gemm(dgchefsi_ctx* ctx, int b_rows, int a_lower, int64_t M, int64_t Nc, int64_t K,

@@ -688,6 +688,7 @@ def run_rr_only(args):
     stream = torch.cuda.current_stream()
     with D.Context(H) as ctx:
         ctx.set_subspace_products("sliced_bf16" if args.subspace == "sliced" else "f64", max(args.slices, 2))
+        ctx.set_eigensolver(args.eigensolver)
         b, tmin = ctx.bounds(torch.from_numpy(v0).to(dev), 10)
         X = torch.from_numpy(X0).to(dev)
         Y = ctx.filter(X, cfg.m, tmin + (b - tmin) * Ns / H.N, b, tmin, prec="bf16x3")
@@ -700,8 +701,9 @@ def run_rr_only(args):
         e_.record(stream)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
+        eig = ctx.eigensolver_stats()
     print(json.dumps({"mode": "rr_only", "workload": cfg.name, "subspace": args.subspace, "slices": args.slices,
-                      "ms": s_.elapsed_time(e_)}), flush=True)
+                      "ms": s_.elapsed_time(e_), "eigensolver": eig}), flush=True)
     return 0
 
 
@@ -844,6 +846,8 @@ def main():
     ap.add_argument("--rr-only", action="store_true", help="one Rayleigh-Ritz step (profiling case)")
     ap.add_argument("--subspace", default="sliced", choices=["f64", "sliced"],
                     help="Rayleigh-Ritz products of the timed cycles (and of --rr-only)")
+    ap.add_argument("--eigensolver", default="auto", choices=["auto", "syevd", "refined"],
+                    help="eigensolve of the projected H (auto: refined with sliced products)")
     ap.add_argument("--slices", type=int, default=10,
                     help="BF16 slices of the sliced Rayleigh-Ritz products measured beside the FP64 ones (0: skip)")
     ap.add_argument("--forms", default="",
@@ -900,6 +904,7 @@ def main():
     sliced_timed = args.subspace == "sliced" and args.prec != "f64" and args.slices > 0
     products = "sliced_bf16" if sliced_timed else "f64"
     ctx.set_subspace_products(products, max(args.slices, 2))
+    ctx.set_eigensolver(args.eigensolver)
 
     def cycle(prec, X, Y, timers=None):
         """One CheFSI cycle via the public API; returns (ritz, new X buffer, spare buffer)."""

@@ -273,6 +273,57 @@ dgchefsi_status dgchefsi_set_orthonormalisation(dgchefsi_ctx* ctx, int mode);
 #define DGCHEFSI_PRODUCTS_SLICED_BF16 1
 dgchefsi_status dgchefsi_set_subspace_products(dgchefsi_ctx* ctx, int mode, int slices);
 
+/* Dense symmetric eigensolver of the projected Hamiltonian, H_hat Q = Q D
+ * (Alg. 1 step 4), used by dgchefsi_rayleigh_ritz, dgchefsi_cycle,
+ * dgchefsi_energy_grad and dgchefsi_subspace_eigh. The paper proposes moving
+ * this step onto dense matrix products (Conclusion).
+ *   DGCHEFSI_EIG_AUTO     REFINED when the subspace products are
+ *                         DGCHEFSI_PRODUCTS_SLICED_BF16 and the order is at
+ *                         least 256, else SYEVD (default)
+ *   DGCHEFSI_EIG_SYEVD    cuSOLVER's FP64 divide-and-conquer solver
+ *   DGCHEFSI_EIG_REFINED  FP32 eigenvectors (cuSOLVER's single-precision
+ *                         solver) refined to FP64 accuracy by the iteration of
+ *                         Ogita and Aishima (2018): per step the products
+ *                         T = V H, [G; S] = [V; T] V^T and E^T V (V: one
+ *                         eigenvector per row), each n x n x n, from exact BF16
+ *                         slices on the tensor cores (max(slices, 10) slices,
+ *                         the context's slice count); near-equal eigenvalues
+ *                         whose first-order correction would exceed 1/10 form
+ *                         clusters, each rotated exactly first (Jacobi on the
+ *                         cluster's block); stops after the step whose largest
+ *                         correction is at most 1e-8 (the next would be of its
+ *                         square). Hands over to SYEVD when the FP32 solver
+ *                         fails, a cluster has more than 32 members, a
+ *                         correction is not finite or not below 1, or 10 steps
+ *                         do not converge (dgchefsi_eigensolver_stats says why).
+ * ERR_ARG for another value. */
+#define DGCHEFSI_EIG_AUTO 0
+#define DGCHEFSI_EIG_SYEVD 1
+#define DGCHEFSI_EIG_REFINED 2
+dgchefsi_status dgchefsi_set_eigensolver(dgchefsi_ctx* ctx, int mode);
+
+/* Eigen-decomposition H Q = Q D of a symmetric H with the context's eigensolver:
+ *   A  device row-major n x n (lda >= n): in, the lower triangle holds H (the
+ *      upper one is not read and may be overwritten); out, row i is the unit
+ *      eigenvector of w[i]
+ *   w  device [n] out, ascending; must not overlap A
+ * Synchronises. ERR_NO_CONVERGENCE if the FP64 solver reports a failure,
+ * ERR_NONFINITE on a NaN/Inf eigenvalue, ERR_ARG on bad sizes or pointers. */
+dgchefsi_status dgchefsi_subspace_eigh(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda, double* w);
+
+/* What the context's last eigensolve did (any pointer may be null):
+ *   used         DGCHEFSI_EIG_SYEVD or DGCHEFSI_EIG_REFINED
+ *   steps        refinement steps taken
+ *   max_cluster  largest cluster of near-equal eigenvalues met (1: none)
+ *   fallback     0, or why the refinement handed over to SYEVD: 1 the FP32
+ *                solver failed, 2 too many near-equal pairs, 3 a cluster
+ *                above 32, 4 a correction not finite or not below 1 (or a
+ *                non-finite operand), 5 no convergence in 10 steps
+ *   update       largest |correction| of the last step
+ *   start_ms, refine_ms  host wall time of the FP32 start and of the refinement */
+dgchefsi_status dgchefsi_eigensolver_stats(const dgchefsi_ctx* ctx, int* used, int* steps, int* max_cluster,
+                                           int* fallback, double* update, double* start_ms, double* refine_ms);
+
 /* FP64 matrix product from exact BF16 slices on the tensor cores (the form
  * DGCHEFSI_PRODUCTS_SLICED_BF16 uses; error-free splitting of Ozaki, Ogita,
  * Oishi and Rump 2012, on BF16 tensor cores as Mukunoki et al. 2020 do on

@@ -14,7 +14,8 @@ Sections of arXiv:1606.03416 followed here:
   * Sec. III.A, Algorithm 1 (CheFSI cycle), steps 1-5
   * Sec. III.B.1, Eqs. matvec_1 .. matvec_3          -> ``matvec``
   * Sec. III.B.2 (Cholesky-QR, projection, rotation) -> ``cholesky_qr``,
-    ``rayleigh_ritz``
+    ``rayleigh_ritz``; the dense eigensolve of the projected H alone ->
+    ``subspace_eigh``
   * Sec. II.C, Eqs. densitymatrix / electron_density_from_DM, and the Fermi-Dirac
     occupations of Eq. KS_DG_Energy -> ``fermi_occupations``, ``density_blocks``
 
@@ -292,6 +293,16 @@ def rayleigh_ritz(H: DGHamiltonian, Y_hat: np.ndarray):
     Hh = 0.5 * (Hh + Hh.T)
     D, Q = np.linalg.eigh(Hh)
     return Y_hat @ Q, D, W @ Q
+
+
+def subspace_eigh(A: np.ndarray):
+    """Alg. 1 step 4 on its own: the eigen-decomposition of the symmetric
+    matrix whose lower triangle is held in A (the upper one is not read).
+    Returns (w, V): w ascending, row i of V the unit eigenvector of w[i] (the
+    library's layout). The definition itself: a dense FP64 symmetric eigensolve."""
+    L = np.tril(np.asarray(A, dtype=np.float64))
+    D, Q = np.linalg.eigh(L + np.tril(L, -1).T, UPLO="L")
+    return D, np.ascontiguousarray(Q.T)
 
 
 def _fermi(x: np.ndarray) -> np.ndarray:

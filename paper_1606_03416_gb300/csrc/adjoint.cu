@@ -216,8 +216,7 @@ extern "C" dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, con
   if (sl) DG_TRY(tc_sliced_matvec(ctx, Yh, N, HY, N, Ns, nsl, bad, &hy_sliced));
   if (!hy_sliced) DG_CUDA(filter_step_f64(h, Yh, N, nullptr, HY, N, Ns, 1.0, 0.0, 0.0, s));
   DG_TRY(prod_nt(Yh, HY, S));
-  ADJ_SOLVER(cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n, S, n, lam, work, lwork,
-                              ctx->info_d + 2));
+  DG_TRY(subspace_eigh(ctx, S, Ns, Ns, lam));
   DG_TRY(prod_nn(S, Yh, N, N, XN, N, false));   // X_new^T = Q^T Y_hat^T
   DG_TRY(prod_nn(S, HY, N, N, HXN, N, false));  // (H X_new)^T
   DG_CUDA(occupations_f64(lam, Ns, Ne, kT, f, mu, s));

@@ -380,8 +380,8 @@ static dgchefsi_status rr_impl(dgchefsi_ctx* ctx, double* Y, int64_t Ns, int64_t
     DG_TRY(sliced_gemm(ctx, true, false, Ns, Ns, N, W, N, Y, ld, S, Ns, ctx->products_slices, bad));
   else
     DG_CUDA(gemm_nt_f64(W, N, Y, ld, S, Ns, Ns, Ns, N, true, false, s));
-  DG_SOLVER(cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n, S, n, ritz, work, lwork,
-                             ctx->info_d + 2));
+  // The eigensolver reads the lower triangle (row-major), the one computed.
+  DG_TRY(subspace_eigh(ctx, S, Ns, Ns, ritz));
   // Step 5: X_new^T = Q^T Y_hat^T (column-major Q read row-major is Q^T).
   if (sl)
     DG_TRY(sliced_gemm(ctx, false, false, Ns, N, Ns, S, Ns, W, N, Y, ld, ctx->products_slices, bad));
@@ -556,6 +556,7 @@ void dgchefsi_destroy(dgchefsi_ctx* ctx) {
   free_buf(ctx->ws_sliced_t);
   free_buf(ctx->ws_sliced_b);
   free_buf(ctx->ws_pairs);
+  free_buf(ctx->ws_eig);
   if (ctx->s_reduce) cudaStreamSynchronize(ctx->s_reduce);
   for (int i = 0; i < 2; ++i) {
     if (ctx->ev_pairs[i]) cudaEventDestroy(ctx->ev_pairs[i]);
@@ -814,6 +815,51 @@ dgchefsi_status dgchefsi_sliced_timing(dgchefsi_ctx* ctx, double* pairs_ms, int6
   DG_TRY(check_ctx(ctx));
   if (pairs_ms) *pairs_ms = ctx->pairs_ms;
   if (launches) *launches = ctx->pairs_launches;
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status dgchefsi_set_eigensolver(dgchefsi_ctx* ctx, int mode) {
+  clear_error();
+  if (!ctx) return set_error(DGCHEFSI_ERR_ARG, "null context");
+  if (mode != DGCHEFSI_EIG_AUTO && mode != DGCHEFSI_EIG_SYEVD && mode != DGCHEFSI_EIG_REFINED)
+    return set_error(DGCHEFSI_ERR_ARG, "unknown eigensolver %d", mode);
+  ctx->eig_mode = mode;
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status dgchefsi_subspace_eigh(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda, double* w) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  if (n < 0 || lda < n || (n > 0 && (!A || !w))) return set_error(DGCHEFSI_ERR_ARG, "bad eigensolve arguments");
+  if (n > 0) {
+    const char* a0 = reinterpret_cast<const char*>(A);
+    const char* a1 = a0 + sizeof(double) * (size_t)((n - 1) * lda + n);
+    const char* w0 = reinterpret_cast<const char*>(w);
+    if (w0 < a1 && a0 < w0 + sizeof(double) * (size_t)n) return set_error(DGCHEFSI_ERR_ARG, "w overlaps A");
+  }
+  cudaStream_t s = ctx->stream;
+  DG_CUDA(cudaMemsetAsync(ctx->info_d, 0, 4 * sizeof(int), s));
+  DG_TRY(subspace_eigh(ctx, A, n, lda, w));
+  if (n > 0) DG_CUDA(check_finite_f64(w, n, ctx->info_d + 3, s));
+  int info[4] = {0, 0, 0, 0};
+  DG_CUDA(cudaMemcpyAsync(info, ctx->info_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  if (info[2] != 0) return set_error(DGCHEFSI_ERR_NO_CONVERGENCE, "dense eigensolver failed (info %d)", info[2]);
+  if (info[3] != 0) return set_error(DGCHEFSI_ERR_NONFINITE, "non-finite eigenvalue");
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status dgchefsi_eigensolver_stats(const dgchefsi_ctx* ctx, int* used, int* steps, int* max_cluster,
+                                           int* fallback, double* update, double* start_ms, double* refine_ms) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  if (used) *used = ctx->eig_used;
+  if (steps) *steps = ctx->eig_steps;
+  if (max_cluster) *max_cluster = ctx->eig_max_cluster;
+  if (fallback) *fallback = ctx->eig_fallback;
+  if (update) *update = ctx->eig_update;
+  if (start_ms) *start_ms = ctx->eig_start_ms;
+  if (refine_ms) *refine_ms = ctx->eig_refine_ms;
   return DGCHEFSI_OK;
 }
 

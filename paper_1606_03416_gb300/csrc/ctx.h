@@ -71,6 +71,12 @@ struct dgchefsi_ctx {
   std::vector<cudaEvent_t> ev_time;
   double pairs_ms = 0.0;
   int64_t pairs_launches = 0;
+  // eigensolver of the projected Hamiltonian (DGCHEFSI_EIG_*), its workspace
+  // and what its last call did (dgchefsi_eigensolver_stats)
+  int eig_mode = 0;
+  int eig_used = 0, eig_steps = 0, eig_max_cluster = 0, eig_fallback = 0;
+  double eig_update = 0.0, eig_start_ms = 0.0, eig_refine_ms = 0.0;
+  dg::DevBuf ws_eig;
   int32_t f64_tj = 64;    // column tile of the FP64 filter (set at create)
   // FP64 filter as a CUDA graph: coefficients copied from a pinned mirror at
   // every replay; the graph is captured again when X, Y, N_s, ld, m or the
@@ -190,6 +196,14 @@ dgchefsi_status pair_products_status(dgchefsi_ctx* ctx);
 // larger than 128): the caller then runs the FP64 product.
 dgchefsi_status tc_sliced_matvec(dgchefsi_ctx* ctx, const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t Ns,
                                  int s, int* flag, bool* used);
+
+// Eigen-decomposition of a symmetric A (eig_refine.cu) with the context's
+// eigensolver: on entry the lower triangle (row-major) of A (n x n, lda)
+// holds the matrix, the upper one may be overwritten; on exit row i of A is
+// the eigenvector of w[i], w ascending. cuSOLVER's FP64 solver reports its
+// info in ctx->info_d[2] (checked by the caller); the refined form
+// synchronises and records its statistics in the context.
+dgchefsi_status subspace_eigh(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda, double* w);
 
 // Set-up of dgchefsi_bounds_static for `device` (noalloc.cu), run by
 // dgchefsi_create with that device current: looks up the device address of

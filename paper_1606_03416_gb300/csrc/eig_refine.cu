@@ -1,0 +1,661 @@
+// Eigen-decomposition of the projected Hamiltonian H_hat (Alg. 1 step 4) from
+// dense products. The paper's subspace problem is its largest cost at scale
+// and its Conclusion proposes moving it onto matrix products; here the FP64
+// eigenpairs come from a cheap approximate start improved by iterative
+// refinement whose work is three dense products per step, run on the
+// tensor cores from exact BF16 slices (sliced.cu).
+//
+// Refinement (Ogita and Aishima, "Iterative refinement for symmetric
+// eigenvalue decomposition", Japan J. Indust. Appl. Math. 35, 2018; clustered
+// eigenvalues after their part II, 2019). With X the approximate
+// eigenvectors as columns (here V = X^T, one eigenvector per row):
+//   G = X^T X,  S = X^T A X,  lambda_i = S_ii / G_ii,
+//   e_ii = (1 - G_ii) / 2,
+//   e_ij = (S_ij - lambda_j G_ij) / (lambda_j - lambda_i)        (i != j),
+//   X <- X (I + E).
+// These are the first-order conditions for X (I + E) to be orthonormal
+// (E + E^T = I - G) and to diagonalise A; the error falls quadratically
+// while every |e_ij| stays small. Pairs whose first-order correction would
+// not be small (|lambda_j - lambda_i| <= kappa |S_ij - lambda_j G_ij|, or a
+// gap at the rounding level) are joined into clusters (connected
+// components). The columns of a cluster C are first rotated exactly:
+// X_C <- X_C W with W = (I + R/2) Q, R = I - G_CC and Q the eigenvectors of
+// M = S_CC + (R S_CC + S_CC R) / 2 (first order of G_CC^{-1/2} S_CC G_CC^{-1/2}),
+// found by cyclic Jacobi (Golub and Van Loan, Matrix Computations, 4th ed.,
+// Sec. 8.5). Inside a cluster e_ij = (I - G)_ij / 2 then keeps X orthonormal.
+//
+// Products per step: T = V A, [G; S] = [V; T] V^T (one call, 2n x n) and
+// the update V <- V + E^T V, all n x n x n on the slice-pair kernel.
+
+#include <algorithm>
+#include <cfloat>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "ctx.h"
+
+#define EIG_SOLVER(call)                                                                                   \
+  do {                                                                                                     \
+    cusolverStatus_t s_ = (call);                                                                          \
+    if (s_ != CUSOLVER_STATUS_SUCCESS)                                                                     \
+      return dg::set_error(DGCHEFSI_ERR_CUDA, "%s failed: cuSOLVER status %d", #call, (int)s_);             \
+  } while (0)
+
+namespace dg {
+
+namespace {
+
+constexpr int kMaxCluster = 32;    // largest cluster the Jacobi kernel takes
+constexpr int kMaxSteps = 10;      // refinement steps before the FP64 fallback
+constexpr double kKappa = 100.0;   // cluster when |e_ij| would exceed 1/kappa
+constexpr double kStop = 1e-8;     // last step: the next correction is O(kStop^2)
+constexpr double kNoise = 256.0;   // couplings below kNoise u ||A|| are rounding noise of the products
+
+unsigned grid_for(int64_t n, int t = 256) { return (unsigned)std::min<int64_t>((n + t - 1) / t, 1 << 20); }
+
+// B (FP32, n x n) = A (FP64, lda) with the lower triangle (row-major)
+// mirrored into the upper one.
+__global__ void k_lower_to_f32(const double* __restrict__ A, int64_t lda, int64_t n, float* __restrict__ B) {
+  const int64_t tot = n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / n, j = t % n;
+    B[t] = (float)(j <= i ? A[i * lda + j] : A[j * lda + i]);
+  }
+}
+
+// The upper triangle (row-major) of A is overwritten by the lower one.
+__global__ void k_mirror_lower(double* A, int64_t lda, int64_t n) {
+  const int64_t tot = n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / n, j = t % n;
+    if (j > i) A[i * lda + j] = A[j * lda + i];
+  }
+}
+
+__global__ void k_f32_to_f64(const float* __restrict__ A, int64_t tot, double* __restrict__ B) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
+    B[t] = (double)A[t];
+}
+
+// lam[i] = S[i, i] / G[i, i]  (G, S row-major n x n, ld n)
+__global__ void k_rayleigh(const double* __restrict__ G, const double* __restrict__ S, int64_t n,
+                           double* __restrict__ lam) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    lam[i] = S[i * n + i] / G[i * n + i];
+}
+
+// Symmetrised entries of the 32 x 32 tile (i0, j0) of G and S: the tile
+// itself is read along j by the caller, the mirror tile (j0, i0) is staged
+// here transposed, so Gt[r][c] = G[j0 + c, i0 + r] (likewise St).
+__device__ __forceinline__ void stage_mirror(const double* __restrict__ G, const double* __restrict__ S, int64_t n,
+                                             int64_t i0, int64_t j0, double (*Gt)[33], double (*St)[33]) {
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int64_t j = j0 + r, i = i0 + threadIdx.x;
+    if (j < n && i < n) {
+      Gt[threadIdx.x][r] = G[j * n + i];
+      St[threadIdx.x][r] = S[j * n + i];
+    }
+  }
+}
+
+// Pairs i < j whose first-order correction would not be small,
+// |lambda_j - lambda_i| <= kappa |S_ij - lambda_j G_ij| (G, S symmetrised),
+// or whose gap is at the rounding level: written to pairs[0..cap) (count
+// keeps counting past cap). 32 x 32 tiles on and above the diagonal.
+__global__ void __launch_bounds__(256) k_close_pairs(const double* __restrict__ G, const double* __restrict__ S,
+                                                     int64_t n, const double* __restrict__ lam, double kappa,
+                                                     double floor_gap, int2* __restrict__ pairs, int cap,
+                                                     int* __restrict__ count) {
+  __shared__ double Gt[32][33], St[32][33];
+  if (blockIdx.y > blockIdx.x) return;
+  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  stage_mirror(G, S, n, i0, j0, Gt, St);
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int64_t i = i0 + r, j = j0 + threadIdx.x;
+    if (i < n && j < n && j > i) {
+      const double g = 0.5 * (G[i * n + j] + Gt[r][threadIdx.x]);
+      const double sv = 0.5 * (S[i * n + j] + St[r][threadIdx.x]);
+      const double li = lam[i], lj = lam[j];
+      const double gap = fabs(lj - li);
+      if (gap <= floor_gap || gap <= kappa * fabs(sv - lj * g)) {
+        const int slot = atomicAdd(count, 1);
+        if (slot < cap) pairs[slot] = make_int2((int)i, (int)j);
+      }
+    }
+  }
+}
+
+// One warp per cluster q (members idx[cofs[q] .. cofs[q + 1]), c <= 32):
+// W_q (c x c row-major at Wd + wofs[q]) = (I + R/2) Q with R = I - G_CC and
+// Q the eigenvectors (columns) of M = S_CC + (R S_CC + S_CC R)/2, G_CC and
+// S_CC symmetrised. M is exactly symmetric as computed (the two products
+// take the same terms in the same order), and cyclic Jacobi sweeps run until
+// the off-diagonal part is below 2^-56 of M in the Frobenius norm (at most
+// 50 sweeps). Each rotation zeroes M_pr: tau = (M_rr - M_pp) / (2 M_pr),
+// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c.
+__global__ void __launch_bounds__(32) k_cluster_rotations(const double* __restrict__ G, const double* __restrict__ S,
+                                                         int64_t n, const int* __restrict__ idx,
+                                                         const int* __restrict__ cofs, const int* __restrict__ wofs,
+                                                         int ncl, double* __restrict__ Wd) {
+  __shared__ double Ms[kMaxCluster][kMaxCluster + 1], Qs[kMaxCluster][kMaxCluster + 1];
+  __shared__ double Rs[kMaxCluster][kMaxCluster + 1], Ss[kMaxCluster][kMaxCluster + 1];
+  const int lane = threadIdx.x;
+  for (int q = blockIdx.x; q < ncl; q += gridDim.x) {
+    const int c0 = cofs[q], c = cofs[q + 1] - c0;
+    __syncwarp();
+    if (lane < c) {
+      const int64_t ib = idx[c0 + lane];
+      for (int a = 0; a < c; ++a) {
+        const int64_t ia = idx[c0 + a];
+        Ss[a][lane] = 0.5 * (S[ia * n + ib] + S[ib * n + ia]);
+        Rs[a][lane] = (a == lane ? 1.0 : 0.0) - 0.5 * (G[ia * n + ib] + G[ib * n + ia]);
+        Qs[a][lane] = a == lane ? 1.0 : 0.0;
+      }
+    }
+    __syncwarp();
+    if (lane < c) {
+      for (int b = 0; b < c; ++b) {
+        double rs = 0.0, sr = 0.0;
+        for (int d = 0; d < c; ++d) {
+          rs += Rs[lane][d] * Ss[d][b];
+          sr += Ss[lane][d] * Rs[d][b];
+        }
+        Ms[lane][b] = Ss[lane][b] + 0.5 * (rs + sr);
+      }
+    }
+    __syncwarp();
+    for (int sweep = 0; sweep < 50; ++sweep) {
+      double off = 0.0, tot = 0.0;
+      if (lane < c)
+        for (int b = 0; b < c; ++b) {
+          const double m = Ms[lane][b];
+          tot += m * m;
+          if (b != lane) off += m * m;
+        }
+      for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_xor_sync(0xffffffffu, off, o);
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      }
+      if (!(off > 0x1p-112 * tot)) break;  // also ends on NaN
+      for (int p = 0; p < c - 1; ++p) {
+        for (int r = p + 1; r < c; ++r) {
+          const double apr = Ms[p][r];
+          if (apr == 0.0) continue;
+          const double tau = (Ms[r][r] - Ms[p][p]) / (2.0 * apr);
+          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
+          __syncwarp();
+          if (lane < c) {  // M <- M J, Q <- Q J (columns p, r)
+            const double mp = Ms[lane][p], mr = Ms[lane][r];
+            Ms[lane][p] = cs * mp - sn * mr;
+            Ms[lane][r] = sn * mp + cs * mr;
+            const double qp = Qs[lane][p], qr = Qs[lane][r];
+            Qs[lane][p] = cs * qp - sn * qr;
+            Qs[lane][r] = sn * qp + cs * qr;
+          }
+          __syncwarp();
+          if (lane < c) {  // M <- J^T M (rows p, r)
+            const double mp = Ms[p][lane], mr = Ms[r][lane];
+            Ms[p][lane] = cs * mp - sn * mr;
+            Ms[r][lane] = sn * mp + cs * mr;
+          }
+          __syncwarp();
+        }
+      }
+    }
+    if (lane < c) {
+      double* W = Wd + wofs[q];
+      for (int b = 0; b < c; ++b) {
+        double acc = 0.0;
+        for (int d = 0; d < c; ++d) acc += Rs[lane][d] * Qs[d][b];
+        W[lane * c + b] = Qs[lane][b] + 0.5 * acc;
+      }
+    }
+  }
+}
+
+// Rows of every cluster in up to three matrices (blockIdx.z picks one; null
+// skipped): X[C_b, j] <- sum_a W_ab X[C_a, j] for j < ncols.
+__global__ void __launch_bounds__(256) k_rotate_rows(double* X0, double* X1, double* X2, int64_t ld, int64_t ncols,
+                                                     const int* __restrict__ idx, const int* __restrict__ cofs,
+                                                     const int* __restrict__ wofs, int ncl,
+                                                     const double* __restrict__ Wd) {
+  __shared__ double Ws[kMaxCluster * kMaxCluster];
+  double* X = blockIdx.z == 0 ? X0 : (blockIdx.z == 1 ? X1 : X2);
+  if (X == nullptr) return;
+  for (int q = blockIdx.y; q < ncl; q += gridDim.y) {
+    const int c0 = cofs[q], c = cofs[q + 1] - c0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < c * c; t += blockDim.x) Ws[t] = Wd[wofs[q] + t];
+    __syncthreads();
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < ncols; j += (int64_t)gridDim.x * blockDim.x) {
+      double x[kMaxCluster];
+      for (int a = 0; a < c; ++a) x[a] = X[(int64_t)idx[c0 + a] * ld + j];
+      for (int b = 0; b < c; ++b) {
+        double y = 0.0;
+        for (int a = 0; a < c; ++a) y += Ws[a * c + b] * x[a];
+        X[(int64_t)idx[c0 + b] * ld + j] = y;
+      }
+    }
+  }
+}
+
+// Columns of every cluster in up to two matrices: X[i, C_b] <- sum_a X[i, C_a] W_ab.
+__global__ void __launch_bounds__(256) k_rotate_cols(double* X0, double* X1, int64_t ld, int64_t nrows,
+                                                     const int* __restrict__ idx, const int* __restrict__ cofs,
+                                                     const int* __restrict__ wofs, int ncl,
+                                                     const double* __restrict__ Wd) {
+  __shared__ double Ws[kMaxCluster * kMaxCluster];
+  double* X = blockIdx.z == 0 ? X0 : X1;
+  if (X == nullptr) return;
+  for (int q = blockIdx.y; q < ncl; q += gridDim.y) {
+    const int c0 = cofs[q], c = cofs[q + 1] - c0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < c * c; t += blockDim.x) Ws[t] = Wd[wofs[q] + t];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += (int64_t)gridDim.x * blockDim.x) {
+      double x[kMaxCluster];
+      for (int a = 0; a < c; ++a) x[a] = X[i * ld + idx[c0 + a]];
+      for (int b = 0; b < c; ++b) {
+        double y = 0.0;
+        for (int a = 0; a < c; ++a) y += x[a] * Ws[a * c + b];
+        X[i * ld + idx[c0 + b]] = y;
+      }
+    }
+  }
+}
+
+// F = E^T (row-major n x n): F[j, i] = e_ij with, for G and S symmetrised,
+// nu_ij = S_ij - lambda_j G_ij and D = lambda_j - lambda_i,
+//   e_ii = (1 - G_ii)/2,
+//   e_ij = nu_ij / D, except -G_ij/2 (orthonormalisation only) inside a
+//          cluster (cl[i] == cl[j] >= 0), for |D| at the rounding level
+//          (floor_gap), and for a coupling |S_ij - (lambda_i + lambda_j) G_ij / 2|
+//          at the rounding level of the products (floor_num) whose rotation
+//          would exceed stop (noise over a tiny gap, which a rotation would
+//          only turn into a loss of orthonormality).
+// Both branches are symmetric in (i, j), so E + E^T = I - G. emax (the bits
+// of a non-negative double) = max |e_ij|, +inf on NaN. 32 x 32 tiles: read
+// along j (the mirror tile staged transposed), written transposed.
+__global__ void __launch_bounds__(256) k_update_coeffs(const double* __restrict__ G, const double* __restrict__ S,
+                                                       int64_t n, const double* __restrict__ lam,
+                                                       const int* __restrict__ cl, double floor_gap, double floor_num,
+                                                       double stop, double* __restrict__ F,
+                                                       unsigned long long* emax) {
+  __shared__ double Gt[32][33], St[32][33], tile[32][33];
+  __shared__ double red[8];
+  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  stage_mirror(G, S, n, i0, j0, Gt, St);
+  __syncthreads();
+  double m = 0.0;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int64_t i = i0 + r, j = j0 + threadIdx.x;
+    double e = 0.0;
+    if (i < n && j < n) {
+      const double g = 0.5 * (G[i * n + j] + Gt[r][threadIdx.x]);
+      if (i == j) {
+        e = 0.5 * (1.0 - g);
+      } else {
+        const double sv = 0.5 * (S[i * n + j] + St[r][threadIdx.x]);
+        const double li = lam[i], lj = lam[j], gap = lj - li;
+        const int ci = cl[i];
+        const double cpl = fabs(sv - 0.5 * (li + lj) * g);
+        if ((ci >= 0 && ci == cl[j]) || fabs(gap) <= floor_gap || (cpl <= floor_num && cpl > stop * fabs(gap)))
+          e = -0.5 * g;
+        else
+          e = (sv - lj * g) / gap;
+      }
+      const double ae = fabs(e);
+      m = ae <= DBL_MAX ? fmax(m, ae) : INFINITY;
+    }
+    tile[r][threadIdx.x] = e;
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const int warp = (threadIdx.y * 32 + threadIdx.x) >> 5;
+  if ((threadIdx.x & 31) == 0) red[warp] = m;
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int64_t j = j0 + r, i = i0 + threadIdx.x;
+    if (i < n && j < n) F[j * n + i] = tile[threadIdx.x][r];
+  }
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    double b = red[0];
+    for (int w = 1; w < 8; ++w) b = fmax(b, red[w]);
+    atomicMax(emax, (unsigned long long)__double_as_longlong(b));
+  }
+}
+
+// A[r, :] = V[perm[r], :] (ld n -> lda) and w[r] = lam[perm[r]].
+__global__ void k_gather_rows(const double* __restrict__ V, int64_t n, const int* __restrict__ perm,
+                              const double* __restrict__ lam, double* __restrict__ A, int64_t lda,
+                              double* __restrict__ w) {
+  for (int64_t r = blockIdx.y; r < n; r += gridDim.y) {
+    const int64_t src = perm[r];
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+      A[r * lda + j] = V[src * n + j];
+    if (blockIdx.x == 0 && threadIdx.x == 0) w[r] = lam[src];
+  }
+}
+
+}  // namespace
+
+}  // namespace dg
+
+namespace dg {
+
+namespace {
+
+// cuSOLVER's FP64 divide-and-conquer on the lower triangle (row-major) of A;
+// its info goes to ctx->info_d[2].
+dgchefsi_status eig_syevd(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda, double* w) {
+  if (n > INT32_MAX || lda > INT32_MAX) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "eigensolve of order %lld", (long long)n);
+  EIG_SOLVER(cusolverDnSetStream(ctx->solver, ctx->stream));
+  int lw = 0;
+  EIG_SOLVER(cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)n, A,
+                                        (int)lda, w, &lw));
+  DG_TRY(ensure(ctx, ctx->ws_solver, sizeof(double) * (size_t)lw, "cuSOLVER workspace"));
+  EIG_SOLVER(cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)n, A, (int)lda, w,
+                             static_cast<double*>(ctx->ws_solver.p), (int)(ctx->ws_solver.bytes / sizeof(double)),
+                             ctx->info_d + 2));
+  return DGCHEFSI_OK;
+}
+
+// Layout of the refinement's workspace for order n.
+struct EigWs {
+  float* A32;          // n x n: FP32 copy of A, then the FP32 start's vectors
+  float* w32;          // n
+  double* VT;          // 2n x n: V (rows = vectors), then T = V A
+  double* GS;          // 2n x n: G = V V^T, S = T V^T; rows 0..n-1 reused for E^T V
+  double* F;           // n x n: E^T
+  double* lam;         // n
+  double* Wd;          // cluster rotations (sum of c^2 <= 32 n)
+  int2* pairs;         // cap
+  int* cl;             // n: cluster of each row, -1 for none
+  int* idx;            // n: cluster members
+  int* cofs;           // n + 1
+  int* wofs;           // n + 1
+  int* perm;           // n
+  int* cnt;            // [0] close-pair count, [1] FP32 start info, [2] non-finite operand flag
+  unsigned long long* emax;
+  int cap;
+  size_t bytes;
+};
+
+EigWs eig_layout(int64_t n, char* base) {
+  EigWs w{};
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    const size_t at = o;
+    o += (b + 255) / 256 * 256;
+    return base ? base + at : nullptr;
+  };
+  const size_t nn = (size_t)n * (size_t)n;
+  w.cap = (int)std::min<int64_t>(16 * n, 1 << 24);
+  w.A32 = reinterpret_cast<float*>(take(sizeof(float) * nn));
+  w.w32 = reinterpret_cast<float*>(take(sizeof(float) * (size_t)n));
+  w.VT = reinterpret_cast<double*>(take(sizeof(double) * 2 * nn));
+  w.GS = reinterpret_cast<double*>(take(sizeof(double) * 2 * nn));
+  w.F = reinterpret_cast<double*>(take(sizeof(double) * nn));
+  w.lam = reinterpret_cast<double*>(take(sizeof(double) * (size_t)n));
+  w.Wd = reinterpret_cast<double*>(take(sizeof(double) * (size_t)n * kMaxCluster));
+  w.pairs = reinterpret_cast<int2*>(take(sizeof(int2) * (size_t)w.cap));
+  w.cl = reinterpret_cast<int*>(take(sizeof(int) * (size_t)n));
+  w.idx = reinterpret_cast<int*>(take(sizeof(int) * (size_t)n));
+  w.cofs = reinterpret_cast<int*>(take(sizeof(int) * (size_t)(n + 1)));
+  w.wofs = reinterpret_cast<int*>(take(sizeof(int) * (size_t)(n + 1)));
+  w.perm = reinterpret_cast<int*>(take(sizeof(int) * (size_t)n));
+  w.cnt = reinterpret_cast<int*>(take(sizeof(int) * 4));
+  w.emax = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long)));
+  w.bytes = o;
+  return w;
+}
+
+// Outcome of the refinement other than an error: done, or hand over to the
+// FP64 eigensolver (the reason is recorded in the context's statistics).
+enum class Refine { kDone, kFallback };
+
+int find_root(std::vector<int>& parent, int x) {
+  while (parent[x] != x) {
+    parent[x] = parent[parent[x]];
+    x = parent[x];
+  }
+  return x;
+}
+
+}  // namespace
+
+}  // namespace dg
+
+namespace dg {
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_since(Clock::time_point t) { return std::chrono::duration<double, std::milli>(Clock::now() - t).count(); }
+
+// The refinement. *reason = 0 when A and w hold the result, else the reason
+// for handing over to the FP64 eigensolver (A's lower triangle is then
+// untouched): 1 the FP32 start failed, 2 more close pairs than the table
+// holds, 3 a cluster larger than kMaxCluster, 4 a correction that is not
+// finite or not below 1, 5 no convergence in kMaxSteps steps.
+dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda, double* w, int* reason) {
+  *reason = 0;
+  if (n > INT32_MAX / 2 || lda > INT32_MAX) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "eigensolve of order %lld", (long long)n);
+  cudaStream_t st = ctx->stream;
+  const int s = std::max(ctx->products_slices, 10);
+  EigWs ws = eig_layout(n, nullptr);
+  DG_TRY(ensure(ctx, ctx->ws_eig, ws.bytes, "eigensolver workspace"));
+  ws = eig_layout(n, static_cast<char*>(ctx->ws_eig.p));
+  const int64_t nn = n * n;
+  double* V = ws.VT;
+  double* T = ws.VT + nn;
+  double* Gm = ws.GS;
+  double* Sm = ws.GS + nn;
+  int* bad = ws.cnt + 2;
+  const auto t0 = Clock::now();
+
+  // Start: FP32 eigenvectors of A (cuSOLVER's single-precision solver).
+  k_mirror_lower<<<grid_for(nn), 256, 0, st>>>(A, lda, n);
+  k_lower_to_f32<<<grid_for(nn), 256, 0, st>>>(A, lda, n, ws.A32);
+  count_launch(2);
+  DG_CUDA(cudaGetLastError());
+  EIG_SOLVER(cusolverDnSetStream(ctx->solver, st));
+  int lw = 0;
+  EIG_SOLVER(cusolverDnSsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)n, ws.A32,
+                                         (int)n, ws.w32, &lw));
+  DG_TRY(ensure(ctx, ctx->ws_solver, sizeof(float) * (size_t)lw, "cuSOLVER workspace"));
+  DG_CUDA(cudaMemsetAsync(ws.cnt, 0, 4 * sizeof(int), st));
+  EIG_SOLVER(cusolverDnSsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)n, ws.A32, (int)n,
+                              ws.w32, static_cast<float*>(ctx->ws_solver.p),
+                              (int)(ctx->ws_solver.bytes / sizeof(float)), ws.cnt + 1));
+  // column-major eigenvectors read row-major: one eigenvector per row of V
+  k_f32_to_f64<<<grid_for(nn), 256, 0, st>>>(ws.A32, nn, V);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  std::vector<float> w32(n);
+  int sinfo = 0;
+  DG_CUDA(cudaMemcpyAsync(&sinfo, ws.cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DG_CUDA(cudaMemcpyAsync(w32.data(), ws.w32, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, st));
+  DG_CUDA(cudaStreamSynchronize(st));
+  double norm = 0.0;
+  for (float x : w32) norm = std::max(norm, (double)std::fabs(x));
+  if (sinfo != 0 || !std::isfinite(norm)) {
+    *reason = 1;
+    return DGCHEFSI_OK;
+  }
+  // gaps below this are rounding noise of the FP64 products
+  const double floor_gap = 64.0 * 0x1p-53 * std::max(norm, DBL_MIN);
+  const double floor_num = kNoise * 0x1p-53 * std::max(norm, DBL_MIN);
+  ctx->eig_start_ms = ms_since(t0);
+
+  std::vector<int2> pairs_h;
+  std::vector<int> parent(n), order(n), pos(n), lo(n), hi(n), reach(n), cl_h(n), idx_h(n), cofs_h, wofs_h;
+  std::vector<double> lam_h(n);
+  bool converged = false;
+  for (int step = 0; step < kMaxSteps && !converged; ++step) {
+    DG_TRY(sliced_gemm(ctx, true, false, n, n, n, V, n, A, lda, T, n, s, bad));         // T = V A
+    DG_TRY(sliced_gemm(ctx, true, false, 2 * n, n, n, ws.VT, n, V, n, ws.GS, n, s, bad));  // [G; S] = [V; T] V^T
+    k_rayleigh<<<grid_for(n), 256, 0, st>>>(Gm, Sm, n, ws.lam);
+    DG_CUDA(cudaMemsetAsync(ws.cnt, 0, sizeof(int), st));
+    const unsigned nt = (unsigned)((n + 31) / 32);
+    k_close_pairs<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(Gm, Sm, n, ws.lam, kKappa, floor_gap, ws.pairs, ws.cap,
+                                                        ws.cnt);
+    count_launch(2);
+    DG_CUDA(cudaGetLastError());
+    int npairs = 0;
+    DG_CUDA(cudaMemcpyAsync(&npairs, ws.cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DG_CUDA(cudaMemcpyAsync(lam_h.data(), ws.lam, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    DG_CUDA(cudaStreamSynchronize(st));
+    if (npairs > ws.cap || npairs < 0) {
+      *reason = 2;
+      return DGCHEFSI_OK;
+    }
+    pairs_h.resize(npairs);
+    if (npairs > 0) {
+      DG_CUDA(cudaMemcpyAsync(pairs_h.data(), ws.pairs, sizeof(int2) * (size_t)npairs, cudaMemcpyDeviceToHost, st));
+      DG_CUDA(cudaStreamSynchronize(st));
+    }
+    // Clusters: the connected components of the close pairs, each widened to
+    // the range of Rayleigh quotients it spans (everything in between joins,
+    // and overlapping ranges merge), so a cluster is a run of the sorted order.
+    std::iota(parent.begin(), parent.end(), 0);
+    for (const int2& p : pairs_h) {
+      const int a = find_root(parent, p.x), b = find_root(parent, p.y);
+      if (a != b) parent[std::max(a, b)] = std::min(a, b);
+    }
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lam_h[a] < lam_h[b]; });
+    for (int64_t k = 0; k < n; ++k) pos[order[k]] = (int)k;
+    std::fill(lo.begin(), lo.end(), INT32_MAX);
+    std::fill(hi.begin(), hi.end(), -1);
+    for (int64_t i = 0; i < n; ++i) {
+      const int r = find_root(parent, (int)i);
+      lo[r] = std::min(lo[r], pos[i]);
+      hi[r] = std::max(hi[r], pos[i]);
+    }
+    // reach[k]: the furthest sorted position a range starting at k covers
+    std::fill(reach.begin(), reach.end(), -1);
+    for (int64_t r = 0; r < n; ++r)
+      if (hi[r] > lo[r]) reach[lo[r]] = std::max(reach[lo[r]], hi[r]);
+    int ncl = 0, max_c = 1;
+    cofs_h.assign(1, 0);
+    for (int64_t k = 0; k < n;) {
+      int end = reach[k];
+      if (end <= k) {
+        cl_h[order[k]] = -1;
+        ++k;
+        continue;
+      }
+      for (int64_t t = k; t <= end; ++t) end = std::max(end, reach[t]);
+      for (int64_t t = k; t <= end; ++t) {
+        cl_h[order[t]] = ncl;
+        idx_h[cofs_h.back() + (t - k)] = order[t];
+      }
+      const int c = (int)(end - k + 1);
+      cofs_h.push_back(cofs_h.back() + c);
+      max_c = std::max(max_c, c);
+      ++ncl;
+      k = end + 1;
+    }
+    ctx->eig_max_cluster = std::max(ctx->eig_max_cluster, max_c);
+    if (max_c > kMaxCluster) {
+      *reason = 3;
+      return DGCHEFSI_OK;
+    }
+    DG_CUDA(cudaMemcpyAsync(ws.cl, cl_h.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, st));
+    if (ncl > 0) {
+      wofs_h.assign(ncl + 1, 0);
+      for (int q = 0; q < ncl; ++q) {
+        const int c = cofs_h[q + 1] - cofs_h[q];
+        wofs_h[q + 1] = wofs_h[q] + c * c;
+      }
+      DG_CUDA(cudaMemcpyAsync(ws.idx, idx_h.data(), sizeof(int) * (size_t)cofs_h[ncl], cudaMemcpyHostToDevice, st));
+      DG_CUDA(cudaMemcpyAsync(ws.cofs, cofs_h.data(), sizeof(int) * (size_t)(ncl + 1), cudaMemcpyHostToDevice, st));
+      DG_CUDA(cudaMemcpyAsync(ws.wofs, wofs_h.data(), sizeof(int) * (size_t)(ncl + 1), cudaMemcpyHostToDevice, st));
+      const unsigned gy = (unsigned)std::min(ncl, 65535);
+      k_cluster_rotations<<<(unsigned)std::min(ncl, 4096), 32, 0, st>>>(Gm, Sm, n, ws.idx, ws.cofs, ws.wofs, ncl,
+                                                                        ws.Wd);
+      k_rotate_rows<<<dim3(grid_for(n), gy, 3), 256, 0, st>>>(Gm, Sm, V, n, n, ws.idx, ws.cofs, ws.wofs, ncl, ws.Wd);
+      k_rotate_cols<<<dim3(grid_for(n), gy, 2), 256, 0, st>>>(Gm, Sm, n, n, ws.idx, ws.cofs, ws.wofs, ncl, ws.Wd);
+      k_rayleigh<<<grid_for(n), 256, 0, st>>>(Gm, Sm, n, ws.lam);
+      count_launch(4);
+      DG_CUDA(cudaGetLastError());
+      // host tables must outlive the copies above
+      DG_CUDA(cudaStreamSynchronize(st));
+    }
+    DG_CUDA(cudaMemsetAsync(ws.emax, 0, sizeof(unsigned long long), st));
+    k_update_coeffs<<<dim3((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32)), dim3(32, 8), 0, st>>>(
+        Gm, Sm, n, ws.lam, ws.cl, floor_gap, floor_num, kStop, ws.F, ws.emax);
+    count_launch();
+    DG_CUDA(cudaGetLastError());
+    unsigned long long eb = 0;
+    DG_CUDA(cudaMemcpyAsync(&eb, ws.emax, sizeof(eb), cudaMemcpyDeviceToHost, st));
+    DG_CUDA(cudaStreamSynchronize(st));
+    double emax = 0.0;
+    std::memcpy(&emax, &eb, sizeof(emax));
+    ctx->eig_steps = step + 1;
+    ctx->eig_update = emax;
+    if (!(emax < 1.0)) {
+      *reason = 4;
+      return DGCHEFSI_OK;
+    }
+    DG_TRY(sliced_gemm(ctx, false, false, n, n, n, ws.F, n, V, n, ws.GS, n, s, bad));  // E^T V
+    DG_CUDA(axpby_f64(1.0, ws.GS, 1.0, V, V, nn, st));                                  // V <- V + E^T V
+    converged = emax <= kStop;
+  }
+  if (!converged) {
+    *reason = 5;
+    return DGCHEFSI_OK;
+  }
+  // ascending order: rows of V and their Rayleigh quotients gathered into A and w
+  int nonfinite = 0;
+  DG_CUDA(cudaMemcpyAsync(lam_h.data(), ws.lam, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
+  DG_CUDA(cudaMemcpyAsync(&nonfinite, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DG_CUDA(cudaStreamSynchronize(st));
+  if (nonfinite != 0) {
+    *reason = 4;
+    return DGCHEFSI_OK;
+  }
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lam_h[a] < lam_h[b]; });
+  DG_CUDA(cudaMemcpyAsync(ws.perm, order.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, st));
+  k_gather_rows<<<dim3(grid_for(n), (unsigned)std::min<int64_t>(n, 65535)), 256, 0, st>>>(V, n, ws.perm, ws.lam, A,
+                                                                                        lda, w);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  DG_CUDA(cudaStreamSynchronize(st));
+  ctx->eig_refine_ms = ms_since(t0) - ctx->eig_start_ms;
+  return DGCHEFSI_OK;
+}
+
+}  // namespace
+
+dgchefsi_status subspace_eigh(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda, double* w) {
+  ctx->eig_steps = 0;
+  ctx->eig_max_cluster = 0;
+  ctx->eig_fallback = 0;
+  ctx->eig_update = 0.0;
+  ctx->eig_start_ms = ctx->eig_refine_ms = 0.0;
+  ctx->eig_used = DGCHEFSI_EIG_SYEVD;
+  if (n <= 0) return DGCHEFSI_OK;
+  int mode = ctx->eig_mode;
+  if (mode == DGCHEFSI_EIG_AUTO)
+    mode = ctx->products_mode == DGCHEFSI_PRODUCTS_SLICED_BF16 && n >= 256 ? DGCHEFSI_EIG_REFINED : DGCHEFSI_EIG_SYEVD;
+  if (mode == DGCHEFSI_EIG_REFINED && n >= 2) {
+    int reason = 0;
+    DG_TRY(eig_refined(ctx, A, n, lda, w, &reason));
+    if (reason == 0) {
+      ctx->eig_used = DGCHEFSI_EIG_REFINED;
+      return DGCHEFSI_OK;
+    }
+    ctx->eig_fallback = reason;  // A's lower triangle is intact
+  }
+  return eig_syevd(ctx, A, n, lda, w);
+}
+
+}  // namespace dg

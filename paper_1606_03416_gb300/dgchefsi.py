@@ -32,13 +32,18 @@ EXPORTS = ["dgchefsi_create", "dgchefsi_destroy", "dgchefsi_set_stream", "dgchef
            "dgchefsi_selftest_wait", "dgchefsi_selftest_fp64_rate", "dgchefsi_set_orthonormalisation", "dgchefsi_density_pattern",
            "dgchefsi_realign", "dgchefsi_filter_host", "dgchefsi_set_subspace_products",
            "dgchefsi_sliced_gemm", "dgchefsi_sliced_matvec", "dgchefsi_set_unit_order",
-           "dgchefsi_get_unit_order", "dgchefsi_sliced_timing"]
+           "dgchefsi_get_unit_order", "dgchefsi_sliced_timing", "dgchefsi_set_eigensolver",
+           "dgchefsi_subspace_eigh", "dgchefsi_eigensolver_stats"]
 
 # Orthonormalisations of Alg. 1 step 3 (dgchefsi_set_orthonormalisation).
 ORTHONORMALISATIONS = {"cholqr": 0, "cholqr2": 1, "shifted_cholqr3": 2}
 
 # Arithmetic of the Rayleigh-Ritz products (dgchefsi_set_subspace_products).
 SUBSPACE_PRODUCTS = {"f64": 0, "sliced_bf16": 1}
+
+# Eigensolver of the projected Hamiltonian (dgchefsi_set_eigensolver).
+EIGENSOLVERS = {"auto": 0, "syevd": 1, "refined": 2}
+EIGENSOLVER_NAMES = {v: k for k, v in EIGENSOLVERS.items()}
 
 # Capacity (doubles) of the library's fixed scratch array for bounds_static.
 BOUNDS_STATIC_DOUBLES = 1 << 20
@@ -79,6 +84,9 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_set_unit_order": (st, [P, C.c_int, C.c_int]),
         "dgchefsi_get_unit_order": (st, [P, C.c_int, P]),
         "dgchefsi_sliced_timing": (st, [P, P, P]),
+        "dgchefsi_set_eigensolver": (st, [P, C.c_int]),
+        "dgchefsi_subspace_eigh": (st, [P, P, I64, I64, P]),
+        "dgchefsi_eigensolver_stats": (st, [P, P, P, P, P, P, P, P]),
         "dgchefsi_density_pattern": (st, [P, P, I64, I64, P, P]),
         "dgchefsi_realign": (st, [P, P, P, P, P, P, I64, I64, P, I64]),
         "dgchefsi_filter_host": (st, [P, C.c_int, P, P, I64, I64, C.c_int, D, D, D, I64]),
@@ -353,6 +361,36 @@ class Context:
         _check(_lib.dgchefsi_sliced_gemm(self._h, int(b_rows), int(a_lower), M, Nc, K, _ptr(A), A.stride(0),
                                          _ptr(B), B.stride(0), _ptr(out), out.stride(0), int(slices)))
         return out
+
+    def set_eigensolver(self, mode: str):
+        """"auto", "syevd" (cuSOLVER FP64) or "refined" (FP32 start refined to
+        FP64 by dense sliced products) for the eigensolve of Alg. 1 step 4."""
+        _check(_lib.dgchefsi_set_eigensolver(self._h, EIGENSOLVERS[mode]))
+
+    def subspace_eigh(self, A: torch.Tensor, w: torch.Tensor | None = None):
+        """Eigen-decomposition of the symmetric matrix whose lower triangle is
+        in A (n x n float64 CUDA, rows contiguous), in place: returns (w, A)
+        with w ascending and row i of A the eigenvector of w[i]."""
+        if not (A.is_cuda and A.dtype == torch.float64 and A.dim() == 2 and A.shape[0] == A.shape[1]
+                and A.stride(1) == 1):
+            raise TypeError("A must be a square float64 CUDA tensor with contiguous rows")
+        n = A.shape[0]
+        if w is None:
+            w = torch.empty(n, dtype=torch.float64, device=A.device)
+        if not (w.is_cuda and w.dtype == torch.float64 and w.numel() == n and w.is_contiguous()):
+            raise TypeError("w must be a contiguous float64 CUDA vector of length n")
+        self._sync_stream()
+        _check(_lib.dgchefsi_subspace_eigh(self._h, _ptr(A), n, A.stride(0), _ptr(w)))
+        return w, A
+
+    def eigensolver_stats(self) -> dict:
+        """What the last eigensolve did (see dgchefsi_eigensolver_stats)."""
+        i = [C.c_int() for _ in range(4)]
+        d = [C.c_double() for _ in range(3)]
+        _check(_lib.dgchefsi_eigensolver_stats(self._h, *[C.byref(x) for x in i], *[C.byref(x) for x in d]))
+        return {"used": EIGENSOLVER_NAMES.get(i[0].value, i[0].value), "steps": i[1].value,
+                "max_cluster": i[2].value, "fallback": i[3].value, "update": d[0].value,
+                "start_ms": d[1].value, "refine_ms": d[2].value}
 
     def sliced_timing(self):
         """(ms, launches) of the slice-pair kernel in the last dense sliced product."""

@@ -272,6 +272,28 @@ def make_basis_pair(nb_old, nb_new, nr, delta: float = 0.05, seed: int = 0):
     return V_old, V_new
 
 
+def make_planted_symmetric(lam, seed: int = 0) -> np.ndarray:
+    """A symmetric n x n matrix Q diag(lam) Q^T with Q Haar-orthogonal (QR of a
+    Gaussian, signs fixed), symmetrised exactly as (A + A^T)/2: a stand-in for a
+    projected Hamiltonian with a chosen spectrum (clusters, repeated values)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    rng = np.random.default_rng(seed + 4)
+    Q = _orthonormal_columns(rng, lam.size, lam.size)
+    A = (Q * lam[None, :]) @ Q.T
+    return 0.5 * (A + A.T)
+
+
+def clustered_spectrum(n: int, groups=(), lo: float = -1.3, hi: float = 2.0, seed: int = 0) -> np.ndarray:
+    """n ascending values: n - sum(sizes) uniform on [lo, hi] plus, for each
+    (centre, size, spread) in groups, `size` values centre + spread * Gaussian
+    (spread 0: a value repeated `size` times)."""
+    rng = np.random.default_rng(seed + 5)
+    parts = [rng.uniform(lo, hi, n - sum(g[1] for g in groups))]
+    for centre, size, spread in groups:
+        parts.append(centre + spread * rng.standard_normal(size))
+    return np.sort(np.concatenate(parts))
+
+
 def pack_blocks(blocks) -> np.ndarray:
     """Concatenate row-major blocks into one float64 array (the packed layout
     of the re-alignment call)."""

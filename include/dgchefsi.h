@@ -281,9 +281,15 @@ dgchefsi_status dgchefsi_set_subspace_products(dgchefsi_ctx* ctx, int mode, int 
  *                         DGCHEFSI_PRODUCTS_SLICED_BF16 and the order is at
  *                         least 256, else SYEVD (default)
  *   DGCHEFSI_EIG_SYEVD    cuSOLVER's FP64 divide-and-conquer solver
- *   DGCHEFSI_EIG_REFINED  FP32 eigenvectors (cuSOLVER's single-precision
- *                         solver) refined to FP64 accuracy by the iteration of
- *                         Ogita and Aishima (2018): per step the products
+ *   DGCHEFSI_EIG_REFINED  approximate eigenvectors refined to FP64 accuracy by
+ *                         the iteration of Ogita and Aishima (2018). Start:
+ *                         a row of H whose first-order couplings
+ *                         |H_ij| / |H_jj - H_ii| are all below 1/100 starts
+ *                         from its unit vector (a projected H of converging
+ *                         CheFSI cycles is nearly diagonal); the block of the
+ *                         other rows gets FP32 eigenvectors from cuSOLVER's
+ *                         single-precision solver (the whole matrix when more
+ *                         than half the rows are coupled). Per step the products
  *                         T = V H, [G; S] = [V; T] V^T and E^T V (V: one
  *                         eigenvector per row), each n x n x n, from exact BF16
  *                         slices on the tensor cores (max(slices, 10) slices,
@@ -320,9 +326,13 @@ dgchefsi_status dgchefsi_subspace_eigh(dgchefsi_ctx* ctx, double* A, int64_t n, 
  *                above 32, 4 a correction not finite or not below 1 (or a
  *                non-finite operand), 5 no convergence in 10 steps
  *   update       largest |correction| of the last step
- *   start_ms, refine_ms  host wall time of the FP32 start and of the refinement */
+ *   start_ms, refine_ms  host wall time of the start and of the refinement
+ *   start_order  order of the block solved in FP32 for the start: n (the
+ *                whole matrix), fewer (only the coupled rows), 0 (the
+ *                identity: every first-order coupling below 1/100) */
 dgchefsi_status dgchefsi_eigensolver_stats(const dgchefsi_ctx* ctx, int* used, int* steps, int* max_cluster,
-                                           int* fallback, double* update, double* start_ms, double* refine_ms);
+                                           int* fallback, double* update, double* start_ms, double* refine_ms,
+                                           int64_t* start_order);
 
 /* FP64 matrix product from exact BF16 slices on the tensor cores (the form
  * DGCHEFSI_PRODUCTS_SLICED_BF16 uses; error-free splitting of Ozaki, Ogita,

@@ -76,6 +76,7 @@ struct dgchefsi_ctx {
   int eig_mode = 0;
   int eig_used = 0, eig_steps = 0, eig_max_cluster = 0, eig_fallback = 0;
   double eig_update = 0.0, eig_start_ms = 0.0, eig_refine_ms = 0.0;
+  int64_t eig_start_order = 0;
   dg::DevBuf ws_eig;
   int32_t f64_tj = 64;    // column tile of the FP64 filter (set at create)
   // FP64 filter as a CUDA graph: coefficients copied from a pinned mirror at

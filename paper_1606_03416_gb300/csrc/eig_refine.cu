@@ -329,6 +329,64 @@ __global__ void __launch_bounds__(256) k_update_coeffs(const double* __restrict_
   }
 }
 
+// Start selection. Row i of A (symmetric, both triangles valid) is coupled
+// when some j != i has a first-order correction |A_ij| / |A_jj - A_ii| of at
+// least tau, i.e. |A_ij| >= tau |A_jj - A_ii|, with |A_ij| above the rounding
+// floor: flag[i] = 1 then, else 0. diag[i] = A_ii. One CTA per row.
+__global__ void __launch_bounds__(256) k_row_coupling(const double* __restrict__ A, int64_t lda, int64_t n,
+                                                      double tau, double floor_num, int* __restrict__ flag,
+                                                      double* __restrict__ diag) {
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const double aii = A[i * lda + i];
+    int hit = 0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+      const double aij = fabs(A[i * lda + j]);
+      if (j != i && aij > floor_num && aij >= tau * fabs(A[j * lda + j] - aii)) hit = 1;
+    }
+    const int any = __syncthreads_or(hit);
+    if (threadIdx.x == 0) {
+      flag[i] = any;
+      diag[i] = aii;
+    }
+  }
+}
+
+// B32 (m x m FP32) = A[rows[k], rows[l]].
+__global__ void k_gather_block_f32(const double* __restrict__ A, int64_t lda, const int* __restrict__ rows, int64_t m,
+                                   float* __restrict__ B32) {
+  const int64_t tot = m * m;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
+    B32[t] = (float)A[(int64_t)rows[t / m] * lda + rows[t % m]];
+}
+
+// V = I (n x n).
+__global__ void k_identity(double* __restrict__ V, int64_t n) {
+  const int64_t tot = n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
+    V[t] = (t / n == t % n) ? 1.0 : 0.0;
+}
+
+// Rows rows[k] of V (= I outside them) become the eigenvectors of the
+// gathered block: V[rows[k], rows[l]] = W[k * m + l] (the FP32 solver's
+// column-major eigenvectors read row-major).
+__global__ void k_scatter_block(double* __restrict__ V, int64_t n, const int* __restrict__ rows, int64_t m,
+                                const float* __restrict__ W) {
+  const int64_t tot = m * m;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
+    V[(int64_t)rows[t / m] * n + rows[t % m]] = (double)W[t];
+}
+
+// For V = I: G = I and S = A (the products of a step, without computing them).
+__global__ void k_identity_products(const double* __restrict__ A, int64_t lda, int64_t n, double* __restrict__ G,
+                                    double* __restrict__ S) {
+  const int64_t tot = n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / n, j = t % n;
+    G[t] = i == j ? 1.0 : 0.0;
+    S[t] = A[i * lda + j];
+  }
+}
+
 // A[r, :] = V[perm[r], :] (ld n -> lda) and w[r] = lam[perm[r]].
 __global__ void k_gather_rows(const double* __restrict__ V, int64_t n, const int* __restrict__ perm,
                               const double* __restrict__ lam, double* __restrict__ A, int64_t lda,
@@ -459,32 +517,72 @@ dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda
   int* bad = ws.cnt + 2;
   const auto t0 = Clock::now();
 
-  // Start: FP32 eigenvectors of A (cuSOLVER's single-precision solver).
+  // Start. Rows whose first-order couplings are all below 1/kappa start
+  // from their unit vector; the block of the other rows is solved in FP32
+  // (cuSOLVER's single-precision solver) and its eigenvectors placed on those
+  // rows. When more than half the rows are coupled (a first projected H, a
+  // matrix without structure) the whole matrix is solved in FP32.
   k_mirror_lower<<<grid_for(nn), 256, 0, st>>>(A, lda, n);
-  k_lower_to_f32<<<grid_for(nn), 256, 0, st>>>(A, lda, n, ws.A32);
+  k_row_coupling<<<(unsigned)std::min<int64_t>(n, 1 << 16), 256, 0, st>>>(A, lda, n, 1.0 / kKappa, 0.0, ws.cl,
+                                                                         ws.lam);
   count_launch(2);
   DG_CUDA(cudaGetLastError());
-  EIG_SOLVER(cusolverDnSetStream(ctx->solver, st));
-  int lw = 0;
-  EIG_SOLVER(cusolverDnSsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)n, ws.A32,
-                                         (int)n, ws.w32, &lw));
-  DG_TRY(ensure(ctx, ctx->ws_solver, sizeof(float) * (size_t)lw, "cuSOLVER workspace"));
-  DG_CUDA(cudaMemsetAsync(ws.cnt, 0, 4 * sizeof(int), st));
-  EIG_SOLVER(cusolverDnSsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)n, ws.A32, (int)n,
-                              ws.w32, static_cast<float*>(ctx->ws_solver.p),
-                              (int)(ctx->ws_solver.bytes / sizeof(float)), ws.cnt + 1));
-  // column-major eigenvectors read row-major: one eigenvector per row of V
-  k_f32_to_f64<<<grid_for(nn), 256, 0, st>>>(ws.A32, nn, V);
-  count_launch();
-  DG_CUDA(cudaGetLastError());
-  std::vector<float> w32(n);
-  int sinfo = 0;
-  DG_CUDA(cudaMemcpyAsync(&sinfo, ws.cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-  DG_CUDA(cudaMemcpyAsync(w32.data(), ws.w32, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, st));
+  std::vector<int> flag_h(n);
+  std::vector<double> diag_h(n);
+  DG_CUDA(cudaMemcpyAsync(flag_h.data(), ws.cl, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, st));
+  DG_CUDA(cudaMemcpyAsync(diag_h.data(), ws.lam, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
   DG_CUDA(cudaStreamSynchronize(st));
   double norm = 0.0;
-  for (float x : w32) norm = std::max(norm, (double)std::fabs(x));
-  if (sinfo != 0 || !std::isfinite(norm)) {
+  for (double x : diag_h) norm = std::max(norm, std::fabs(x));
+  std::vector<int> rows;
+  for (int64_t i = 0; i < n; ++i)
+    if (flag_h[i]) rows.push_back((int)i);
+  const bool full = (int64_t)rows.size() * 2 > n;
+  const int64_t m = full ? n : (int64_t)rows.size();
+  ctx->eig_start_order = m;
+  if (m > 0) {
+    if (full) {
+      k_lower_to_f32<<<grid_for(nn), 256, 0, st>>>(A, lda, n, ws.A32);
+    } else {
+      DG_CUDA(cudaMemcpyAsync(ws.idx, rows.data(), sizeof(int) * (size_t)m, cudaMemcpyHostToDevice, st));
+      k_gather_block_f32<<<grid_for(m * m), 256, 0, st>>>(A, lda, ws.idx, m, ws.A32);
+    }
+    count_launch();
+    DG_CUDA(cudaGetLastError());
+    EIG_SOLVER(cusolverDnSetStream(ctx->solver, st));
+    int lw = 0;
+    EIG_SOLVER(cusolverDnSsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)m,
+                                           ws.A32, (int)m, ws.w32, &lw));
+    DG_TRY(ensure(ctx, ctx->ws_solver, sizeof(float) * (size_t)lw, "cuSOLVER workspace"));
+    DG_CUDA(cudaMemsetAsync(ws.cnt, 0, 4 * sizeof(int), st));
+    EIG_SOLVER(cusolverDnSsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)m, ws.A32, (int)m,
+                                ws.w32, static_cast<float*>(ctx->ws_solver.p),
+                                (int)(ctx->ws_solver.bytes / sizeof(float)), ws.cnt + 1));
+    // column-major eigenvectors read row-major: one eigenvector per row
+    if (full) {
+      k_f32_to_f64<<<grid_for(nn), 256, 0, st>>>(ws.A32, nn, V);
+    } else {
+      k_identity<<<grid_for(nn), 256, 0, st>>>(V, n);
+      k_scatter_block<<<grid_for(m * m), 256, 0, st>>>(V, n, ws.idx, m, ws.A32);
+    }
+    count_launch(full ? 1 : 2);
+    DG_CUDA(cudaGetLastError());
+    std::vector<float> w32(m);
+    int sinfo = 0;
+    DG_CUDA(cudaMemcpyAsync(&sinfo, ws.cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DG_CUDA(cudaMemcpyAsync(w32.data(), ws.w32, sizeof(float) * (size_t)m, cudaMemcpyDeviceToHost, st));
+    DG_CUDA(cudaStreamSynchronize(st));
+    for (float x : w32) norm = std::max(norm, (double)std::fabs(x));
+    if (sinfo != 0) {
+      *reason = 1;
+      return DGCHEFSI_OK;
+    }
+  } else {
+    k_identity<<<grid_for(nn), 256, 0, st>>>(V, n);
+    count_launch();
+    DG_CUDA(cudaGetLastError());
+  }
+  if (!std::isfinite(norm)) {
     *reason = 1;
     return DGCHEFSI_OK;
   }
@@ -497,9 +595,16 @@ dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda
   std::vector<int> parent(n), order(n), pos(n), lo(n), hi(n), reach(n), cl_h(n), idx_h(n), cofs_h, wofs_h;
   std::vector<double> lam_h(n);
   bool converged = false;
+  bool unit = m == 0;  // V = I exactly: the step's products are known
   for (int step = 0; step < kMaxSteps && !converged; ++step) {
-    DG_TRY(sliced_gemm(ctx, true, false, n, n, n, V, n, A, lda, T, n, s, bad));         // T = V A
-    DG_TRY(sliced_gemm(ctx, true, false, 2 * n, n, n, ws.VT, n, V, n, ws.GS, n, s, bad));  // [G; S] = [V; T] V^T
+    if (unit) {
+      k_identity_products<<<grid_for(nn), 256, 0, st>>>(A, lda, n, Gm, Sm);
+      count_launch();
+      DG_CUDA(cudaGetLastError());
+    } else {
+      DG_TRY(sliced_gemm(ctx, true, false, n, n, n, V, n, A, lda, T, n, s, bad));         // T = V A
+      DG_TRY(sliced_gemm(ctx, true, false, 2 * n, n, n, ws.VT, n, V, n, ws.GS, n, s, bad));  // [G; S] = [V; T] V^T
+    }
     k_rayleigh<<<grid_for(n), 256, 0, st>>>(Gm, Sm, n, ws.lam);
     DG_CUDA(cudaMemsetAsync(ws.cnt, 0, sizeof(int), st));
     const unsigned nt = (unsigned)((n + 31) / 32);
@@ -604,8 +709,13 @@ dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda
       *reason = 4;
       return DGCHEFSI_OK;
     }
-    DG_TRY(sliced_gemm(ctx, false, false, n, n, n, ws.F, n, V, n, ws.GS, n, s, bad));  // E^T V
-    DG_CUDA(axpby_f64(1.0, ws.GS, 1.0, V, V, nn, st));                                  // V <- V + E^T V
+    if (unit && ncl == 0) {
+      DG_CUDA(axpby_f64(1.0, ws.F, 1.0, V, V, nn, st));  // V <- I + E^T
+    } else {
+      DG_TRY(sliced_gemm(ctx, false, false, n, n, n, ws.F, n, V, n, ws.GS, n, s, bad));  // E^T V
+      DG_CUDA(axpby_f64(1.0, ws.GS, 1.0, V, V, nn, st));                                  // V <- V + E^T V
+    }
+    unit = false;
     converged = emax <= kStop;
   }
   if (!converged) {
@@ -641,6 +751,7 @@ dgchefsi_status subspace_eigh(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t l
   ctx->eig_fallback = 0;
   ctx->eig_update = 0.0;
   ctx->eig_start_ms = ctx->eig_refine_ms = 0.0;
+  ctx->eig_start_order = 0;
   ctx->eig_used = DGCHEFSI_EIG_SYEVD;
   if (n <= 0) return DGCHEFSI_OK;
   int mode = ctx->eig_mode;

@@ -86,7 +86,7 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_sliced_timing": (st, [P, P, P]),
         "dgchefsi_set_eigensolver": (st, [P, C.c_int]),
         "dgchefsi_subspace_eigh": (st, [P, P, I64, I64, P]),
-        "dgchefsi_eigensolver_stats": (st, [P, P, P, P, P, P, P, P]),
+        "dgchefsi_eigensolver_stats": (st, [P, P, P, P, P, P, P, P, P]),
         "dgchefsi_density_pattern": (st, [P, P, I64, I64, P, P]),
         "dgchefsi_realign": (st, [P, P, P, P, P, P, I64, I64, P, I64]),
         "dgchefsi_filter_host": (st, [P, C.c_int, P, P, I64, I64, C.c_int, D, D, D, I64]),
@@ -387,10 +387,12 @@ class Context:
         """What the last eigensolve did (see dgchefsi_eigensolver_stats)."""
         i = [C.c_int() for _ in range(4)]
         d = [C.c_double() for _ in range(3)]
-        _check(_lib.dgchefsi_eigensolver_stats(self._h, *[C.byref(x) for x in i], *[C.byref(x) for x in d]))
+        order = C.c_int64()
+        _check(_lib.dgchefsi_eigensolver_stats(self._h, *[C.byref(x) for x in i], *[C.byref(x) for x in d],
+                                               C.byref(order)))
         return {"used": EIGENSOLVER_NAMES.get(i[0].value, i[0].value), "steps": i[1].value,
                 "max_cluster": i[2].value, "fallback": i[3].value, "update": d[0].value,
-                "start_ms": d[1].value, "refine_ms": d[2].value}
+                "start_ms": d[1].value, "refine_ms": d[2].value, "start_order": order.value}
 
     def sliced_timing(self):
         """(ms, launches) of the slice-pair kernel in the last dense sliced product."""

@@ -294,6 +294,21 @@ def clustered_spectrum(n: int, groups=(), lo: float = -1.3, hi: float = 2.0, see
     return np.sort(np.concatenate(parts))
 
 
+def near_diagonal_symmetric(d, coupling: float, top: int = 0, top_coupling: float = 0.0, seed: int = 0) -> np.ndarray:
+    """diag(d) plus a symmetric Gaussian perturbation of size `coupling`, and
+    of size `top_coupling` among the last `top` rows and columns: the shape of
+    a projected Hamiltonian in the basis of a converging subspace iteration
+    (converged states nearly decoupled, the unconverged top block not)."""
+    d = np.asarray(d, dtype=np.float64)
+    n = d.size
+    rng = np.random.default_rng(seed + 6)
+    P = coupling * rng.standard_normal((n, n))
+    if top > 0:
+        P[n - top:, n - top:] = top_coupling * rng.standard_normal((top, top))
+    A = np.diag(d) + 0.5 * (P + P.T)
+    return 0.5 * (A + A.T)
+
+
 def pack_blocks(blocks) -> np.ndarray:
     """Concatenate row-major blocks into one float64 array (the packed layout
     of the re-alignment call)."""

@@ -133,10 +133,38 @@ def test_auto_follows_subspace_products():
     assert used == {"f64": "syevd", "sliced_bf16": "refined", "forced": "syevd"}
 
 
-def test_rayleigh_ritz_refined_vs_fp64_solver_on_a_projected_hamiltonian():
-    """A CheFSI cycle's own projected H (bulk 5x4x4, N = 5120, N_s = 400) with
-    sliced products: Ritz values and rotated blocks from the refined solver
-    equal those from the FP64 solver, and both match the oracle's cycle."""
+def test_identity_start_for_a_nearly_diagonal_matrix():
+    """Every first-order coupling below 1/100: no FP32 solve, the first step
+    needs no products, and the result is the oracle's."""
+    d = G.clustered_spectrum(1200, seed=31)
+    A = G.near_diagonal_symmetric(d, 1e-9, seed=31)
+    with tiny_ctx() as ctx:
+        ctx.set_eigensolver("refined")
+        w, V, st = solve(ctx, A)
+    ew, eo, er = check_against_oracle(A, w, V)
+    print(f"EIGH identity start: eig {ew:.1e} orth {eo:.1e} resid {er:.1e} {st}")
+    assert st["used"] == "refined" and st["fallback"] == 0 and st["start_order"] == 0
+
+
+def test_partial_start_for_a_coupled_top_block():
+    """Only the last 150 rows are coupled: the FP32 start solves that block
+    alone (its order is reported), the rest starts from unit vectors."""
+    d = G.clustered_spectrum(1100, seed=33)
+    A = G.near_diagonal_symmetric(d, 2e-7, top=150, top_coupling=0.05, seed=33)
+    with tiny_ctx() as ctx:
+        ctx.set_eigensolver("refined")
+        w, V, st = solve(ctx, A, pad=1)
+    ew, eo, er = check_against_oracle(A, w, V)
+    print(f"EIGH partial start: eig {ew:.1e} orth {eo:.1e} resid {er:.1e} {st}")
+    assert st["used"] == "refined" and st["fallback"] == 0 and 150 <= st["start_order"] <= 550
+
+
+def test_cycles_refined_vs_fp64_solver_on_projected_hamiltonians():
+    """The CheFSI cycles' own projected H (bulk 5x4x4, N = 5120, N_s = 400)
+    with sliced products, five cycles from the random start: Ritz values and
+    rotated blocks from the refined solver equal those from the FP64 solver
+    cycle by cycle, the first cycle matches the oracle's, and the later
+    cycles (a converging subspace) start from fewer FP32-solved rows."""
     cfg = G.scaled_copy(G.CONFIGS["bulk3d_8x8x8"], grid=(5, 4, 4), nb=64, Ns=400, m=10, name="bulk5x4x4")
     H, X0, v0, Ns, Ne = G.make_problem(cfg)
     Ho = O.DGHamiltonian.from_blocksparse(H)
@@ -147,20 +175,29 @@ def test_rayleigh_ritz_refined_vs_fp64_solver_on_a_projected_hamiltonian():
         for mode in ("syevd", "refined"):
             ctx.set_eigensolver(mode)
             X = torch.from_numpy(X0).to(dev)
-            res = ctx.cycle(X, cfg.m, Ne, cfg.kT, v0=v)
-            out[mode] = (res["ritz"].cpu().numpy(), X.cpu().numpy(), res["bounds"], ctx.eigensolver_stats())
-    a, b, a0 = out["refined"][2]
+            prev, out[mode] = None, []
+            for cyc in range(5):
+                res = ctx.cycle(X, cfg.m, Ne, cfg.kT, v0=v, prev_ritz=prev)
+                prev = res["ritz"].cpu().numpy()
+                out[mode].append((prev, X.cpu().numpy(), res["bounds"], ctx.eigensolver_stats()))
+    a, b, a0 = out["refined"][0][2]
     ref = O.chefsi_cycle(Ho, X0.T.copy(), cfg.m, Ne, cfg.kT, v0, bounds=(a, b, a0))
     scale = max(abs(a0), abs(b))
-    r_s, X_s = out["syevd"][:2]
-    r_r, X_r, _, st = out["refined"]
-    er = np.abs(r_r - r_s).max() / scale
-    eo = np.abs(r_r - ref["ritz"]).max() / scale
-    # rotated states: same up to sign where the Ritz values are separated
-    gaps = np.minimum(np.diff(r_s, prepend=-np.inf), np.diff(r_s, append=np.inf)) / scale
-    sep = gaps > 1e-6
-    cos = np.abs(np.sum(X_r * X_s, axis=1)) / (np.linalg.norm(X_r, axis=1) * np.linalg.norm(X_s, axis=1))
-    print(f"EIGH cycle: ritz vs syevd {er:.1e}, vs oracle {eo:.1e}, min cos {cos[sep].min():.16f} {st}")
-    assert st["used"] == "refined" and st["fallback"] == 0
-    assert er <= 1e-12 and eo <= 1e-10
-    assert np.all(1.0 - cos[sep] <= 1e-18 / gaps[sep] ** 2 + 1e-13)
+    eo = np.abs(out["refined"][0][0] - ref["ritz"]).max() / scale
+    assert eo <= 1e-10
+    orders = []
+    for cyc in range(5):
+        r_s, X_s = out["syevd"][cyc][:2]
+        r_r, X_r, _, st = out["refined"][cyc]
+        er = np.abs(r_r - r_s).max() / scale
+        # rotated states: same up to sign where the Ritz values are separated
+        gaps = np.minimum(np.diff(r_s, prepend=-np.inf), np.diff(r_s, append=np.inf)) / scale
+        sep = gaps > 1e-6
+        cos = np.abs(np.sum(X_r * X_s, axis=1)) / (np.linalg.norm(X_r, axis=1) * np.linalg.norm(X_s, axis=1))
+        print(f"EIGH cycle {cyc}: ritz vs syevd {er:.1e}, min cos {cos[sep].min():.16f} {st}")
+        assert st["used"] == "refined" and st["fallback"] == 0
+        assert er <= 1e-12
+        assert np.all(1.0 - cos[sep] <= 1e-18 / gaps[sep] ** 2 + 1e-13)
+        orders.append(st["start_order"])
+    print(f"EIGH cycle vs oracle {eo:.1e}, start orders {orders}")
+    assert orders[0] == Ns and orders[-1] < Ns // 2

@@ -676,9 +676,11 @@ def run_sliced_only(args):
 
 def run_rr_only(args):
     """One Rayleigh-Ritz step (Alg. 1 steps 3-5) on the workload's BF16x3-filtered
-    first block, with --subspace products, bracketed by cudaProfilerStart/Stop
-    (profiling case: ncu --profile-from-start off sees only this call). A first
-    call on a copy of the block sets up the workspace outside the bracket."""
+    block, with --subspace products, bracketed by cudaProfilerStart/Stop
+    (profiling case: ncu --profile-from-start off sees only this call). With
+    --rr-cycles K the block is the one filtered after K mixed cycles from the
+    random start (a warm step, as in the timed cycles); K = 0: the first block.
+    A first call on a copy of the block sets up the workspace outside the bracket."""
     import torch
     from paper_1606_03416_gb300 import dgchefsi as D
     from paper_1606_03416_gb300 import inputs as G
@@ -691,7 +693,14 @@ def run_rr_only(args):
         ctx.set_eigensolver(args.eigensolver)
         b, tmin = ctx.bounds(torch.from_numpy(v0).to(dev), 10)
         X = torch.from_numpy(X0).to(dev)
-        Y = ctx.filter(X, cfg.m, tmin + (b - tmin) * Ns / H.N, b, tmin, prec="bf16x3")
+        a, a0 = tmin + (b - tmin) * Ns / H.N, tmin
+        prev = None
+        for _ in range(args.rr_cycles):
+            prev = ctx.cycle(X, cfg.m, Ne, cfg.kT, v0=torch.from_numpy(v0).to(dev), prec="bf16x3",
+                             prev_ritz=prev)["ritz"].cpu().numpy()
+        if prev is not None:
+            a, a0 = float(prev[-1]), float(prev[0])
+        Y = ctx.filter(X, cfg.m, a, b, a0, prec="bf16x3")
         ctx.rayleigh_ritz(Y.clone())
         s_, e_ = torch.cuda.Event(True), torch.cuda.Event(True)
         torch.cuda.synchronize()
@@ -703,7 +712,7 @@ def run_rr_only(args):
         torch.cuda.profiler.stop()
         eig = ctx.eigensolver_stats()
     print(json.dumps({"mode": "rr_only", "workload": cfg.name, "subspace": args.subspace, "slices": args.slices,
-                      "ms": s_.elapsed_time(e_), "eigensolver": eig}), flush=True)
+                      "warm_cycles": args.rr_cycles, "ms": s_.elapsed_time(e_), "eigensolver": eig}), flush=True)
     return 0
 
 
@@ -844,6 +853,7 @@ def main():
     ap.add_argument("--converge-cycles", type=int, default=8, help="cycle limit of those runs")
     ap.add_argument("--gram-only", action="store_true", help="time one FP64 Gram (profiling case)")
     ap.add_argument("--rr-only", action="store_true", help="one Rayleigh-Ritz step (profiling case)")
+    ap.add_argument("--rr-cycles", type=int, default=0, help="--rr-only: mixed cycles run before the profiled step")
     ap.add_argument("--subspace", default="sliced", choices=["f64", "sliced"],
                     help="Rayleigh-Ritz products of the timed cycles (and of --rr-only)")
     ap.add_argument("--eigensolver", default="auto", choices=["auto", "syevd", "refined"],
@@ -948,6 +958,7 @@ def main():
             _, X, Y = cycle(args.prec, X, Y, fl_t[i])
         t1.record(stream)
         barrier()
+    eig_timed = ctx.eigensolver_stats()  # the last timed cycle's eigensolve
     launches = D.launch_count() - n0
     X_warm = X.clone()  # the block the timed cycles left (later measurements reuse X and Y)
     ms_step = t0.elapsed_time(t1) / args.steps
@@ -1205,6 +1216,7 @@ def main():
         "roofline": rf, "roofline_gram_f64": roof_gram, "fp64_peak": F64_PEAK,
         "filter_tflops_other_precisions": other,
         "e2e": e2e, "e2e_cycle": e2e_cycle, "gpu_launches": launches, "clocks": clocks,
+        "eigensolver_timed_cycle": eig_timed,
     }
     if conv:
         line["converge"] = conv

@@ -344,6 +344,11 @@ dgchefsi_status dgchefsi_eigensolver_stats(const dgchefsi_ctx* ctx, int* used, i
  *      are taken as zero and not read
  *   C  device out, row-major M x Nc (ldc >= Nc); must not overlap A or B
  *   slices  2..16
+ *   tri  0: every entry of C; > 0: only the entries C[r, c] with
+ *        c <= r mod tri are computed, the others keep their values (the lower
+ *        triangle of a symmetric product, or of each of M / tri stacked ones:
+ *        the slice-pair kernel skips the 256 x 256 tiles above that line and
+ *        the reduction skips their entries)
  * For b_rows = 0 every K index k is first balanced exactly: row k of B times
  * 2^{-s_k}, column k of A times 2^{s_k}, s_k the exponent of max_c |B[k, c]|
  * (rows of B with very different norms would otherwise share one column
@@ -361,7 +366,7 @@ dgchefsi_status dgchefsi_eigensolver_stats(const dgchefsi_ctx* ctx, int* used, i
  * sizes, ERR_UNSUPPORTED when K / 4096 > 65535 or M, Nc > 2^31 - 1. */
 dgchefsi_status dgchefsi_sliced_gemm(dgchefsi_ctx* ctx, int b_rows, int a_lower, int64_t M, int64_t Nc, int64_t K,
                                      const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
-                                     int64_t ldc, int slices);
+                                     int64_t ldc, int slices, int64_t tri);
 
 /* Measurement aid (no counterpart in the paper): the device time, in ms, of
  * the slice-pair kernel launches of the last dense product from slices

@@ -174,8 +174,10 @@ extern "C" dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, con
   const bool sl = ctx->products_mode == DGCHEFSI_PRODUCTS_SLICED_BF16;
   const int nsl = ctx->products_slices;
   int* bad = ctx->info_d + 3;
-  auto prod_nt = [&](const double* A_, const double* B_, double* C_) -> dgchefsi_status {  // C = A B^T, K = N
-    if (sl) return sliced_gemm(ctx, true, false, Ns, Ns, N, A_, N, B_, N, C_, Ns, nsl, bad);
+  // C = A B^T, K = N, for a symmetric C of which only the lower triangle is
+  // read (the Cholesky factorisation and the eigensolver)
+  auto prod_nt = [&](const double* A_, const double* B_, double* C_) -> dgchefsi_status {
+    if (sl) return sliced_gemm(ctx, true, false, Ns, Ns, N, A_, N, B_, N, C_, Ns, nsl, bad, Ns);
     DG_CUDA(gemm_nt_f64(A_, N, B_, N, C_, Ns, Ns, Ns, N, true, false, s));
     return DGCHEFSI_OK;
   };

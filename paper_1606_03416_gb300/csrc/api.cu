@@ -341,7 +341,7 @@ static dgchefsi_status rr_impl(dgchefsi_ctx* ctx, double* Y, int64_t Ns, int64_t
     double* outp = pass == 0 ? W : Y;
     const int64_t ldo = pass == 0 ? N : ld;
     if (sl)
-      DG_TRY(sliced_gemm(ctx, true, false, Ns, Ns, N, in, ldi, in, ldi, S, Ns, ctx->products_slices, bad));
+      DG_TRY(sliced_gemm(ctx, true, false, Ns, Ns, N, in, ldi, in, ldi, S, Ns, ctx->products_slices, bad, Ns));
     else
       DG_CUDA(gemm_nt_f64(in, ldi, in, ldi, S, Ns, Ns, Ns, N, true, false, s));
     if (pass == 0 && ctx->orth_mode == DGCHEFSI_ORTH_SHIFTED_CHOLQR3)
@@ -377,7 +377,7 @@ static dgchefsi_status rr_impl(dgchefsi_ctx* ctx, double* Y, int64_t Ns, int64_t
   if (sl) DG_TRY(tc_sliced_matvec(ctx, W, N, Y, ld, Ns, ctx->products_slices, bad, &hx_sliced));
   if (!hx_sliced) DG_CUDA(filter_step_f64(ctx->view(), W, N, nullptr, Y, ld, Ns, 1.0, 0.0, 0.0, s));
   if (sl)
-    DG_TRY(sliced_gemm(ctx, true, false, Ns, Ns, N, W, N, Y, ld, S, Ns, ctx->products_slices, bad));
+    DG_TRY(sliced_gemm(ctx, true, false, Ns, Ns, N, W, N, Y, ld, S, Ns, ctx->products_slices, bad, Ns));
   else
     DG_CUDA(gemm_nt_f64(W, N, Y, ld, S, Ns, Ns, Ns, N, true, false, s));
   // The eigensolver reads the lower triangle (row-major), the one computed.
@@ -556,6 +556,7 @@ void dgchefsi_destroy(dgchefsi_ctx* ctx) {
   free_buf(ctx->ws_sliced_t);
   free_buf(ctx->ws_sliced_b);
   free_buf(ctx->ws_pairs);
+  free_buf(ctx->ws_pairs_err);
   free_buf(ctx->ws_eig);
   if (ctx->s_reduce) cudaStreamSynchronize(ctx->s_reduce);
   for (int i = 0; i < 2; ++i) {
@@ -766,10 +767,10 @@ dgchefsi_status dgchefsi_set_subspace_products(dgchefsi_ctx* ctx, int mode, int 
 
 dgchefsi_status dgchefsi_sliced_gemm(dgchefsi_ctx* ctx, int b_rows, int a_lower, int64_t M, int64_t Nc, int64_t K,
                                      const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
-                                     int64_t ldc, int slices) {
+                                     int64_t ldc, int slices, int64_t tri) {
   clear_error();
   DG_TRY(check_ctx(ctx));
-  if (M < 0 || Nc < 0 || K < 0) return set_error(DGCHEFSI_ERR_ARG, "negative size");
+  if (M < 0 || Nc < 0 || K < 0 || tri < 0) return set_error(DGCHEFSI_ERR_ARG, "negative size");
   if (slices < 2 || slices > 16) return set_error(DGCHEFSI_ERR_ARG, "slices = %d outside 2..16", slices);
   if (M == 0 || Nc == 0) return DGCHEFSI_OK;
   if (!C || (K > 0 && (!A || !B))) return set_error(DGCHEFSI_ERR_ARG, "null matrix pointer");
@@ -778,7 +779,8 @@ dgchefsi_status dgchefsi_sliced_gemm(dgchefsi_ctx* ctx, int b_rows, int a_lower,
   if ((K + 4095) / 4096 > 65535 || M > 0x7fffffff || Nc > 0x7fffffff)
     return set_error(DGCHEFSI_ERR_UNSUPPORTED, "sizes beyond this build's grid limits");
   DG_CUDA(cudaMemsetAsync(ctx->info_d + 3, 0, sizeof(int), ctx->stream));
-  DG_TRY(sliced_gemm(ctx, b_rows != 0, a_lower != 0, M, Nc, K, A, lda, B, ldb, C, ldc, slices, ctx->info_d + 3));
+  DG_TRY(sliced_gemm(ctx, b_rows != 0, a_lower != 0, M, Nc, K, A, lda, B, ldb, C, ldc, slices, ctx->info_d + 3,
+                     tri));
   int bad = 0;
   DG_CUDA(cudaMemcpyAsync(&bad, ctx->info_d + 3, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   DG_CUDA(cudaStreamSynchronize(ctx->stream));

@@ -60,7 +60,8 @@ struct dgchefsi_ctx {
   dg::DevBuf ws_sliced;
   dg::DevBuf ws_sliced_t;  // transposed left operand of the A^T B form
   dg::DevBuf ws_sliced_b;  // transposed right operand of the A B form
-  dg::DevBuf ws_pairs;     // error word, tensor maps and pair lists of the slice-pair kernel
+  dg::DevBuf ws_pairs;     // tensor maps, pair and tile lists of the slice-pair kernel (regrown as needed)
+  dg::DevBuf ws_pairs_err; // the slice-pair kernel's error word (its own buffer: never regrown mid-product)
   // the slab reduction of the sliced products runs on its own stream, one K
   // chunk behind the slice-pair kernel (double-buffered slabs)
   cudaStream_t s_reduce = nullptr;
@@ -153,9 +154,12 @@ void tc_destroy(dgchefsi_ctx* ctx);
 // A (M x K, lda) row-major, all FP64, computed from s exact BF16 slices per
 // operand on the tensor cores (sliced.cu). a_lower: entries k > r of A are
 // zero and not read. flag (device int) gets 1 if an operand is not finite.
+// tri > 0: only the entries C[r, c] with c <= r mod tri are computed (the lower
+// triangle of a symmetric result, or of each of M / tri stacked ones); the
+// others are left as they were.
 dgchefsi_status sliced_gemm(dgchefsi_ctx* ctx, bool b_rows, bool a_lower, int64_t M, int64_t Nc, int64_t K,
                             const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int s,
-                            int* flag);
+                            int* flag, int64_t tri = 0);
 // C (M x Nc) = A^T B with A (K x M, lda) and B (K x Nc, ldb) row-major: A is
 // transposed into a library buffer, then the A B form above.
 dgchefsi_status sliced_gemm_tn(dgchefsi_ctx* ctx, int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda,
@@ -188,7 +192,8 @@ dgchefsi_status reduce_pair_slabs(const float* Pw, int64_t rows, int64_t cols, c
 // synchronises and reports a pipeline timeout.
 dgchefsi_status pair_products_2sm(dgchefsi_ctx* ctx, const __nv_bfloat16* Qa, int64_t lqa, int64_t sa, int64_t M,
                                   const __nv_bfloat16* Qb, int64_t lqb, int64_t sb, int64_t Nc, int64_t K, int64_t k0,
-                                  int64_t kc, int64_t n0, int64_t pn, int s, float* Pw, bool a_lower);
+                                  int64_t kc, int64_t n0, int64_t pn, int s, float* Pw, bool a_lower,
+                                  int64_t tri = 0);
 dgchefsi_status pair_products_begin(dgchefsi_ctx* ctx);
 dgchefsi_status pair_products_status(dgchefsi_ctx* ctx);
 // Y = H X (X, Y: Ns x ld state-major FP64) from s BF16 slices of each operand on

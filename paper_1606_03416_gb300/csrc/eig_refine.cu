@@ -602,8 +602,13 @@ dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda
       count_launch();
       DG_CUDA(cudaGetLastError());
     } else {
-      DG_TRY(sliced_gemm(ctx, true, false, n, n, n, V, n, A, lda, T, n, s, bad));         // T = V A
-      DG_TRY(sliced_gemm(ctx, true, false, 2 * n, n, n, ws.VT, n, V, n, ws.GS, n, s, bad));  // [G; S] = [V; T] V^T
+      DG_TRY(sliced_gemm(ctx, true, false, n, n, n, V, n, A, lda, T, n, s, bad));  // T = V A
+      // [G; S] = [V; T] V^T, both symmetric: lower triangles, then mirrored
+      DG_TRY(sliced_gemm(ctx, true, false, 2 * n, n, n, ws.VT, n, V, n, ws.GS, n, s, bad, n));
+      k_mirror_lower<<<grid_for(nn), 256, 0, st>>>(Gm, n, n);
+      k_mirror_lower<<<grid_for(nn), 256, 0, st>>>(Sm, n, n);
+      count_launch(2);
+      DG_CUDA(cudaGetLastError());
     }
     k_rayleigh<<<grid_for(n), 256, 0, st>>>(Gm, Sm, n, ws.lam);
     DG_CUDA(cudaMemsetAsync(ws.cnt, 0, sizeof(int), st));

@@ -22,6 +22,10 @@
 // (double-buffered, 2 x 256 columns) and report to the first CTA's "empty"
 // accumulator barrier. Every wait is bounded; on expiry the CTA records an
 // error word and both CTAs still meet at the final cluster barrier.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
 #include "tc_kernel.cuh"
 
 namespace dg {
@@ -42,6 +46,8 @@ struct PairJob {
   int n0, k0, nk;   // first B row, first K column, 64-wide K slices of the chunk
   int nmt, nnt;     // 256-row tiles along M and along the panel
   int lower;        // A is lower triangular: a row tile stops at the chunk's last K slice it reaches
+  const int2* tiles;  // null: every (row tile, column tile); else the ntl tiles to compute
+  int ntl;
   float* Pw;        // slab of pair p at Pw + p * M * pn, row-major M x pn
   int* err;
 };
@@ -98,6 +104,13 @@ __device__ __forceinline__ void commit_pair(uint32_t bar) {
 // (row tiles fastest), so the units in flight share one A slice and one or two
 // B slices, which stay in L2.
 __device__ __forceinline__ void unit_of(const PairJob& J, int64_t u, int& p, int& mt, int& nt) {
+  if (J.tiles) {
+    p = (int)(u / J.ntl);
+    const int2 t = J.tiles[u - (int64_t)p * J.ntl];
+    mt = t.x;
+    nt = t.y;
+    return;
+  }
   const int64_t ntiles = (int64_t)J.nmt * J.nnt;
   p = (int)(u / ntiles);
   const int64_t tile = u - (int64_t)p * ntiles;
@@ -125,7 +138,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PG_THREADS, 1) k_sli
   const bool leader = rank == 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
-  const int64_t nunits = (int64_t)J.nmt * J.nnt * J.npairs;
+  const int64_t nunits = (J.tiles ? (int64_t)J.ntl : (int64_t)J.nmt * J.nnt) * J.npairs;
   const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * PG_STAGES;
   const uint32_t accf0 = empty0 + 8 * PG_STAGES, acce0 = accf0 + 16;
 
@@ -320,14 +333,31 @@ dgchefsi_status slice_map(CUtensorMap* map, const __nv_bfloat16* base, uint64_t 
 
 dgchefsi_status pair_products_2sm(dgchefsi_ctx* ctx, const __nv_bfloat16* Qa, int64_t lqa, int64_t sa, int64_t M,
                                   const __nv_bfloat16* Qb, int64_t lqb, int64_t sb, int64_t Nc, int64_t K, int64_t k0,
-                                  int64_t kc, int64_t n0, int64_t pn, int s, float* Pw, bool a_lower) {
+                                  int64_t kc, int64_t n0, int64_t pn, int s, float* Pw, bool a_lower, int64_t tri) {
   if (M > 2147483647LL - 256 || Nc > 2147483647LL - 256 || K > 2147483647LL)
     return set_error(DGCHEFSI_ERR_UNSUPPORTED, "slice-pair product too large for 32-bit TMA coordinates");
   cudaStream_t st = ctx->stream;
   const int npairs = s * (s + 1) / 2;
-  // tables: 2s tensor maps (64-byte aligned), then the pair lists
+  const int nmt = (int)((M + 255) / 256), nnt = (int)((pn + 255) / 256);
+  // tri > 0: only entries (r, n0 + c) with n0 + c <= r mod tri are wanted (the
+  // lower triangle of a symmetric product, or of each of several stacked
+  // ones); tiles entirely above it are left out.
+  std::vector<int2> tl;
+  if (tri > 0) {
+    for (int nt = 0; nt < nnt; ++nt)
+      for (int mt = 0; mt < nmt; ++mt) {
+        const int64_t r0 = (int64_t)mt * 256, r1 = std::min<int64_t>(r0 + 256, M) - 1;
+        const int64_t c0 = n0 + (int64_t)nt * 256;
+        const bool wrap = r0 / tri != r1 / tri;
+        if (wrap || c0 <= r1 % tri) tl.push_back(make_int2(mt, nt));
+      }
+    if (tl.empty()) return DGCHEFSI_OK;
+  }
+  // tables: 2s tensor maps (64-byte aligned), then the pair lists, then the tile list
   const size_t maps_bytes = sizeof(CUtensorMap) * (size_t)(2 * s);
-  std::vector<uint8_t> host(maps_bytes + sizeof(int32_t) * (size_t)(2 * npairs));
+  const size_t pairs_bytes = sizeof(int32_t) * (size_t)(2 * npairs);
+  const size_t tiles_at = (maps_bytes + pairs_bytes + 15) / 16 * 16;
+  std::vector<uint8_t> host(tiles_at + sizeof(int2) * tl.size());
   CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(host.data());
   for (int i = 0; i < s; ++i) {
     DG_TRY(slice_map(&maps[i], Qa + (size_t)i * sa, (uint64_t)K, (uint64_t)M, (uint64_t)lqa));
@@ -341,10 +371,11 @@ dgchefsi_status pair_products_2sm(dgchefsi_ctx* ctx, const __nv_bfloat16* Qa, in
       pi[n] = i;
       pj[n] = j;
     }
-  // the context's table buffer: the error word, then (at 256 bytes) the maps and pair lists
+  if (!tl.empty()) std::memcpy(host.data() + tiles_at, tl.data(), sizeof(int2) * tl.size());
+  // the context's table buffer (may be regrown here: it holds no state across launches)
   DevBuf& tables = ctx->ws_pairs;
-  DG_TRY(ensure(ctx, tables, 256 + host.size(), "slice-pair tensor maps"));
-  uint8_t* tab = static_cast<uint8_t*>(tables.p) + 256;
+  DG_TRY(ensure(ctx, tables, host.size(), "slice-pair tensor maps"));
+  uint8_t* tab = static_cast<uint8_t*>(tables.p);
   DG_CUDA(cudaMemcpyAsync(tab, host.data(), host.size(), cudaMemcpyHostToDevice, st));
   // the pageable copy above has been staged before it returns, so `host` may go
   PairJob J{};
@@ -358,14 +389,17 @@ dgchefsi_status pair_products_2sm(dgchefsi_ctx* ctx, const __nv_bfloat16* Qa, in
   J.n0 = (int)n0;
   J.k0 = (int)k0;
   J.nk = (int)((kc + 63) / 64);
-  J.nmt = (int)((M + 255) / 256);
-  J.nnt = (int)((pn + 255) / 256);
+  J.nmt = nmt;
+  J.nnt = nnt;
   J.lower = a_lower ? 1 : 0;
+  J.tiles = tl.empty() ? nullptr : reinterpret_cast<const int2*>(tab + tiles_at);
+  J.ntl = (int)tl.size();
   J.Pw = Pw;
-  J.err = static_cast<int*>(tables.p);
+  if (!ctx->ws_pairs_err.p) return set_error(DGCHEFSI_ERR_CUDA, "slice-pair products not begun");
+  J.err = static_cast<int*>(ctx->ws_pairs_err.p);
   int nsm = 0;
   DG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
-  const int64_t units = (int64_t)J.nmt * J.nnt * npairs;
+  const int64_t units = (J.tiles ? (int64_t)J.ntl : (int64_t)J.nmt * J.nnt) * npairs;
   const int clusters = (int)std::min<int64_t>(units, std::max(nsm / 2, 1));
   const int smem = PG_STAGES * PG_STAGE + (2 * PG_STAGES + 4) * 8 + 1024;
   DG_CUDA(cudaFuncSetAttribute(k_slice_pairs_2sm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -376,15 +410,15 @@ dgchefsi_status pair_products_2sm(dgchefsi_ctx* ctx, const __nv_bfloat16* Qa, in
 }
 
 dgchefsi_status pair_products_begin(dgchefsi_ctx* ctx) {
-  DG_TRY(ensure(ctx, ctx->ws_pairs, 256, "slice-pair tensor maps"));
-  DG_CUDA(cudaMemsetAsync(ctx->ws_pairs.p, 0, sizeof(int), ctx->stream));
+  DG_TRY(ensure(ctx, ctx->ws_pairs_err, 256, "slice-pair error word"));
+  DG_CUDA(cudaMemsetAsync(ctx->ws_pairs_err.p, 0, sizeof(int), ctx->stream));
   return DGCHEFSI_OK;
 }
 
 dgchefsi_status pair_products_status(dgchefsi_ctx* ctx) {
-  if (!ctx->ws_pairs.p) return DGCHEFSI_OK;
+  if (!ctx->ws_pairs_err.p) return DGCHEFSI_OK;
   int err = 0;
-  DG_CUDA(cudaMemcpyAsync(&err, ctx->ws_pairs.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  DG_CUDA(cudaMemcpyAsync(&err, ctx->ws_pairs_err.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   DG_CUDA(cudaStreamSynchronize(ctx->stream));
   if (err) return set_error(DGCHEFSI_ERR_TIMEOUT, "a slice-pair CTA gave up waiting on a pipeline barrier");
   return DGCHEFSI_OK;

@@ -198,16 +198,20 @@ __global__ void __launch_bounds__(256) k_row_exponents(const double* __restrict_
 // before any use, so the kernel streams Pw at memory speed.
 // cmap (may be null): column c of the slabs goes to column cmap[c] of C, and
 // is skipped when cmap[c] < 0 (the padding columns of the element-padded layout).
+// tri > 0: only the entries with n0 + c <= r mod tri are formed (the slice-pair
+// kernel left the tiles above that line out); the others are not read or written.
 template <int S>
 __global__ void __launch_bounds__(256) k_sliced_reduce(const float* __restrict__ Pw, int64_t M, int64_t P,
                                                        const int32_t* __restrict__ Ea, const int32_t* __restrict__ Eb,
                                                        int nch, int chunk, int64_t n0, double* __restrict__ C,
-                                                       int64_t ldc, int accumulate, const int32_t* __restrict__ cmap) {
+                                                       int64_t ldc, int accumulate, const int32_t* __restrict__ cmap,
+                                                       int64_t tri) {
   constexpr int NB = (S + 4) / 5;  // blocks of five t
   const int64_t total = M * P;
   const int64_t slab = M * P;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
+    if (tri > 0 && n0 + idx % P > (idx / P) % tri) continue;
     int g[S];
 #pragma unroll
     for (int t = 0; t < S; ++t) g[t] = 0;
@@ -241,13 +245,18 @@ template <int S>
 __global__ void __launch_bounds__(256) k_sliced_reduce4(const float* __restrict__ Pw, int64_t M, int64_t P,
                                                         const int32_t* __restrict__ Ea, const int32_t* __restrict__ Eb,
                                                         int nch, int chunk, int64_t n0, double* __restrict__ C,
-                                                        int64_t ldc, int accumulate, const int32_t* __restrict__ cmap) {
+                                                        int64_t ldc, int accumulate, const int32_t* __restrict__ cmap,
+                                                        int64_t tri) {
   constexpr int NB = (S + 4) / 5;
   const int64_t slab = M * P;
   const int64_t total4 = slab / 4;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total4;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t idx = 4 * q;
+    // the four entries share a row and a 256-column tile: when the first is
+    // above the line all are, and otherwise the tile was computed
+    const int64_t rdiag = tri > 0 ? (idx / P) % tri : 0;
+    if (tri > 0 && n0 + idx % P > rdiag) continue;
     int g[4][S];
 #pragma unroll
     for (int e = 0; e < 4; ++e)
@@ -279,7 +288,7 @@ __global__ void __launch_bounds__(256) k_sliced_reduce4(const float* __restrict_
       }
       const int64_t c = c0 + e;
       const int64_t oc = cmap ? (int64_t)cmap[c] : n0 + c;
-      if (oc < 0) continue;
+      if (oc < 0 || (tri > 0 && n0 + c > rdiag)) continue;
       const double v = ldexp(h, er + Eb[(n0 + c) * nch + chunk] - 12 - 24);
       double* out = C + r * ldc + oc;
       *out = accumulate ? *out + v : v;
@@ -288,7 +297,7 @@ __global__ void __launch_bounds__(256) k_sliced_reduce4(const float* __restrict_
 }
 
 typedef void (*ReduceKernel)(const float*, int64_t, int64_t, const int32_t*, const int32_t*, int, int, int64_t,
-                             double*, int64_t, int, const int32_t*);
+                             double*, int64_t, int, const int32_t*, int64_t);
 
 static ReduceKernel reduce_kernel(int s) {
   switch (s) {
@@ -317,12 +326,12 @@ static ReduceKernel reduce_kernel4(int s) {
 // The reduction over slabs of M x P: four outputs per thread when P % 4 == 0.
 static cudaError_t launch_reduce(int s, const float* Pw, int64_t M, int64_t P, const int32_t* Ea, const int32_t* Eb,
                                  int nch, int chunk, int64_t n0, double* C, int64_t ldc, int accumulate,
-                                 const int32_t* cmap, cudaStream_t st) {
+                                 const int32_t* cmap, cudaStream_t st, int64_t tri = 0) {
   const bool v4 = P % 4 == 0;
   const int64_t work = v4 ? M * P / 4 : M * P;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 152 * 16));
   (v4 ? reduce_kernel4(s) : reduce_kernel(s))<<<grid, 256, 0, st>>>(Pw, M, P, Ea, Eb, nch, chunk, n0, C, ldc,
-                                                                      accumulate, cmap);
+                                                                      accumulate, cmap, tri);
   count_launch();
   return cudaGetLastError();
 }
@@ -361,7 +370,7 @@ static dgchefsi_status transpose_f64(const double* X, int64_t ldx, int64_t rows,
 
 dgchefsi_status sliced_gemm(dgchefsi_ctx* ctx, bool b_rows, bool a_lower, int64_t M, int64_t Nc, int64_t K,
                             const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int s,
-                            int* flag) {
+                            int* flag, int64_t tri) {
   if (M <= 0 || Nc <= 0) return DGCHEFSI_OK;
   if (!reduce_kernel(s)) return set_error(DGCHEFSI_ERR_ARG, "slices = %d outside 2..16", s);
   cudaStream_t st = ctx->stream;
@@ -473,13 +482,13 @@ dgchefsi_status sliced_gemm(dgchefsi_ctx* ctx, bool b_rows, bool a_lower, int64_
       // into buffer b once the reduction that last read it is done
       if (multi) DG_CUDA(cudaStreamWaitEvent(st, ctx->ev_reduce[b], 0));
       DG_CUDA(cudaEventRecord(ctx->ev_time[2 * step], st));
-      DG_TRY(pair_products_2sm(ctx, Qa, lqa, sa, M, Qb, lqb, sb, Nc, K, k0, kc, n0, pn, s, Pb, a_lower));
+      DG_TRY(pair_products_2sm(ctx, Qa, lqa, sa, M, Qb, lqb, sb, Nc, K, k0, kc, n0, pn, s, Pb, a_lower, tri));
       DG_CUDA(cudaEventRecord(ctx->ev_time[2 * step + 1], st));
       if (multi) {
         DG_CUDA(cudaEventRecord(ctx->ev_pairs[b], st));
         DG_CUDA(cudaStreamWaitEvent(sr, ctx->ev_pairs[b], 0));
       }
-      DG_CUDA(launch_reduce(s, Pb, M, pn, Ea, Eb, nch, chunk, n0, C, ldc, chunk > 0 ? 1 : 0, nullptr, sr));
+      DG_CUDA(launch_reduce(s, Pb, M, pn, Ea, Eb, nch, chunk, n0, C, ldc, chunk > 0 ? 1 : 0, nullptr, sr, tri));
       if (multi) DG_CUDA(cudaEventRecord(ctx->ev_reduce[b], sr));
     }
   }

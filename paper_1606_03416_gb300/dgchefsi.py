@@ -79,7 +79,7 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_selftest_fp64_rate": (st, [P, C.c_int, P]),
         "dgchefsi_set_orthonormalisation": (st, [P, C.c_int]),
         "dgchefsi_set_subspace_products": (st, [P, C.c_int, C.c_int]),
-        "dgchefsi_sliced_gemm": (st, [P, C.c_int, C.c_int, I64, I64, I64, P, I64, P, I64, P, I64, C.c_int]),
+        "dgchefsi_sliced_gemm": (st, [P, C.c_int, C.c_int, I64, I64, I64, P, I64, P, I64, P, I64, C.c_int, I64]),
         "dgchefsi_sliced_matvec": (st, [P, P, P, I64, I64, C.c_int]),
         "dgchefsi_set_unit_order": (st, [P, C.c_int, C.c_int]),
         "dgchefsi_get_unit_order": (st, [P, C.c_int, P]),
@@ -343,9 +343,10 @@ class Context:
         _check(_lib.dgchefsi_set_subspace_products(self._h, SUBSPACE_PRODUCTS[mode], int(slices)))
 
     def sliced_gemm(self, A: torch.Tensor, B: torch.Tensor, b_rows: bool = True, a_lower: bool = False,
-                    slices: int = 10, out: torch.Tensor | None = None) -> torch.Tensor:
+                    slices: int = 10, out: torch.Tensor | None = None, tri: int = 0) -> torch.Tensor:
         """A @ B.T (b_rows) or A @ B in FP64 from exact BF16 slices. A, B: 2-D
-        float64 CUDA tensors, rows contiguous; a_lower treats A as lower triangular."""
+        float64 CUDA tensors, rows contiguous; a_lower treats A as lower
+        triangular; tri > 0 computes only the entries (r, c) with c <= r % tri."""
         for name, T in (("A", A), ("B", B)):
             if not (T.is_cuda and T.dtype == torch.float64 and T.dim() == 2 and T.stride(1) == 1):
                 raise TypeError(f"{name} must be a 2-D float64 CUDA tensor with contiguous rows")
@@ -359,7 +360,7 @@ class Context:
             raise TypeError("out must be a float64 CUDA tensor of shape (M, Nc) with contiguous rows")
         self._sync_stream()
         _check(_lib.dgchefsi_sliced_gemm(self._h, int(b_rows), int(a_lower), M, Nc, K, _ptr(A), A.stride(0),
-                                         _ptr(B), B.stride(0), _ptr(out), out.stride(0), int(slices)))
+                                         _ptr(B), B.stride(0), _ptr(out), out.stride(0), int(slices), int(tri)))
         return out
 
     def set_eigensolver(self, mode: str):

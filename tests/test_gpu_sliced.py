@@ -62,6 +62,47 @@ def test_integer_operands_bit_exact(b_rows, a_lower, slices):
     assert np.all(got[:, Nc:] == -1.0)
 
 
+@pytest.mark.parametrize("case", ["gram_same", "gram_two", "stacked", "panels"])
+def test_lower_triangle_only_bit_exact(case):
+    """tri > 0: only the entries C[r, c] with c <= r mod tri are formed, bit
+    for bit the exact integer product, and every other entry keeps its value.
+    A symmetric Gram with A == B (one slice set) and with two operands, two
+    stacked symmetric products (tri = M / 2, the refinement's [G; S] form),
+    both over ragged tiles and K chunks, and a product wide enough (16 slices)
+    to run in column panels, where the line is followed across panels."""
+    rng = np.random.default_rng(21)
+    slices = 10
+    if case == "panels":
+        M = Nc = 4500
+        K, slices, tri = 300, 16, 4500
+        assert 136 * 4 * M * Nc > 8 * 2 ** 30
+    elif case == "stacked":
+        M, Nc, K, tri = 1200, 600, 5000, 600
+    else:
+        M = Nc = 700
+        K, tri = 2 * L_CHUNK + 900, 700
+    A = rng.integers(-2047, 2048, size=(M, K)).astype(np.int64)
+    if case == "stacked":
+        A[:Nc] = rng.integers(-2047, 2048, size=(Nc, K))
+        Bt = A[:Nc].copy()
+    elif case in ("gram_same", "panels"):
+        Bt = A
+    else:
+        Bt = rng.integers(-2047, 2048, size=(Nc, K)).astype(np.int64)
+    ref = (A @ Bt.T).astype(np.float64)
+    r = np.arange(M)[:, None]
+    c = np.arange(Nc)[None, :]
+    want = c <= r % tri
+    with tiny_ctx() as ctx:
+        At = torch.from_numpy(A.astype(np.float64)).to(dev)
+        Bd = At if case in ("gram_same", "panels") else torch.from_numpy(Bt.astype(np.float64)).to(dev)
+        out = torch.full((M, Nc), -1.0, dtype=torch.float64, device=dev)
+        ctx.sliced_gemm(At, Bd, b_rows=True, slices=slices, out=out, tri=tri)
+        got = out.cpu().numpy()
+    assert np.array_equal(got[want], ref[want])
+    assert np.all(got[~want] == -1.0)
+
+
 @pytest.mark.parametrize("b_rows", [True, False])
 def test_pair_sums_at_the_fp32_limit_bit_exact(b_rows):
     """One full K chunk (4096) of same-sign operands whose digits reach their

@@ -691,6 +691,7 @@ def run_rr_only(args):
     with D.Context(H) as ctx:
         ctx.set_subspace_products("sliced_bf16" if args.subspace == "sliced" else "f64", max(args.slices, 2))
         ctx.set_eigensolver(args.eigensolver)
+        ctx.set_cholesky(args.cholesky)
         b, tmin = ctx.bounds(torch.from_numpy(v0).to(dev), 10)
         X = torch.from_numpy(X0).to(dev)
         a, a0 = tmin + (b - tmin) * Ns / H.N, tmin
@@ -712,7 +713,8 @@ def run_rr_only(args):
         torch.cuda.profiler.stop()
         eig = ctx.eigensolver_stats()
     print(json.dumps({"mode": "rr_only", "workload": cfg.name, "subspace": args.subspace, "slices": args.slices,
-                      "warm_cycles": args.rr_cycles, "ms": s_.elapsed_time(e_), "eigensolver": eig}), flush=True)
+                      "warm_cycles": args.rr_cycles, "cholesky": args.cholesky, "ms": s_.elapsed_time(e_),
+                      "eigensolver": eig}), flush=True)
     return 0
 
 
@@ -858,6 +860,8 @@ def main():
                     help="Rayleigh-Ritz products of the timed cycles (and of --rr-only)")
     ap.add_argument("--eigensolver", default="auto", choices=["auto", "syevd", "refined"],
                     help="eigensolve of the projected H (auto: refined with sliced products)")
+    ap.add_argument("--cholesky", default="auto", choices=["auto", "cusolver", "products"],
+                    help="Cholesky factorisation of step 3 (auto: recursive on products with sliced products)")
     ap.add_argument("--slices", type=int, default=10,
                     help="BF16 slices of the sliced Rayleigh-Ritz products measured beside the FP64 ones (0: skip)")
     ap.add_argument("--forms", default="",
@@ -915,6 +919,7 @@ def main():
     products = "sliced_bf16" if sliced_timed else "f64"
     ctx.set_subspace_products(products, max(args.slices, 2))
     ctx.set_eigensolver(args.eigensolver)
+    ctx.set_cholesky(args.cholesky)
 
     def cycle(prec, X, Y, timers=None):
         """One CheFSI cycle via the public API; returns (ritz, new X buffer, spare buffer)."""

@@ -273,6 +273,38 @@ dgchefsi_status dgchefsi_set_orthonormalisation(dgchefsi_ctx* ctx, int mode);
 #define DGCHEFSI_PRODUCTS_SLICED_BF16 1
 dgchefsi_status dgchefsi_set_subspace_products(dgchefsi_ctx* ctx, int mode, int slices);
 
+/* Cholesky factorisation of Alg. 1 step 3 (S = U^T U and U^{-1}) in
+ * dgchefsi_rayleigh_ritz, dgchefsi_cycle, dgchefsi_energy_grad and
+ * dgchefsi_cholesky_inverse. The paper names it, with the eigensolve, as the
+ * part of the subspace problem to move onto dense matrix products
+ * (Conclusion).
+ *   DGCHEFSI_CHOL_AUTO      PRODUCTS when the subspace products are
+ *                           DGCHEFSI_PRODUCTS_SLICED_BF16, else CUSOLVER (default)
+ *   DGCHEFSI_CHOL_CUSOLVER  cuSOLVER potrf and trtri (FP64)
+ *   DGCHEFSI_CHOL_PRODUCTS  recursive blocked factorisation that forms the
+ *                           factor and its inverse together: per level
+ *                           L21 = S21 L11^{-T}, S22 -= L21 L21^T, and
+ *                           (L^{-1})21 = -L22^{-1} L21 L11^{-1}; blocks of at
+ *                           most 64 rows in one CTA's shared memory; products
+ *                           with every side >= 512 from exact BF16 slices on
+ *                           the tensor cores (max(slices, 10) slices), smaller
+ *                           ones on the FP64 cores
+ * ERR_ARG for another value. */
+#define DGCHEFSI_CHOL_AUTO 0
+#define DGCHEFSI_CHOL_CUSOLVER 1
+#define DGCHEFSI_CHOL_PRODUCTS 2
+dgchefsi_status dgchefsi_set_cholesky(dgchefsi_ctx* ctx, int mode);
+
+/* S = U^T U (row-major lower view: S = L L^T, L = U^T) with the context's
+ * Cholesky form, and the inverse factor:
+ *   S  device row-major n x n (lda >= n): in, the lower triangle holds the
+ *      symmetric positive definite S (the upper one is not read); out, the
+ *      lower triangle holds L^{-1} = U^{-T}, the strict upper part unspecified
+ * Synchronises. ERR_NOT_SPD (with the 1-based column) when a pivot is not
+ * positive, ERR_NONFINITE on a NaN/Inf operand of a sliced product, ERR_ARG
+ * on bad sizes. */
+dgchefsi_status dgchefsi_cholesky_inverse(dgchefsi_ctx* ctx, double* S, int64_t n, int64_t lda);
+
 /* Dense symmetric eigensolver of the projected Hamiltonian, H_hat Q = Q D
  * (Alg. 1 step 4), used by dgchefsi_rayleigh_ritz, dgchefsi_cycle,
  * dgchefsi_energy_grad and dgchefsi_subspace_eigh. The paper proposes moving

@@ -15,7 +15,8 @@ Sections of arXiv:1606.03416 followed here:
   * Sec. III.B.1, Eqs. matvec_1 .. matvec_3          -> ``matvec``
   * Sec. III.B.2 (Cholesky-QR, projection, rotation) -> ``cholesky_qr``,
     ``rayleigh_ritz``; the dense eigensolve of the projected H alone ->
-    ``subspace_eigh``
+    ``subspace_eigh``; the Cholesky factor and its inverse alone ->
+    ``cholesky_inverse``
   * Sec. II.C, Eqs. densitymatrix / electron_density_from_DM, and the Fermi-Dirac
     occupations of Eq. KS_DG_Energy -> ``fermi_occupations``, ``density_blocks``
 
@@ -283,6 +284,19 @@ def cholesky_qr(Y: np.ndarray):
     U = np.linalg.cholesky(S).T  # numpy gives lower L with S = L L^T
     Y_hat = sla.solve_triangular(U, Y.T, trans="T", lower=False).T
     return Y_hat, U, S
+
+
+def cholesky_inverse(S: np.ndarray):
+    """The factor of Alg. 1 step 3 on its own: S = L L^T (L lower, positive
+    diagonal; L = U^T for the paper's S = U^T U) from the lower triangle of S
+    (the upper one is not read), and L^{-1}, the factor Y_hat^T = L^{-1} Y^T
+    applies. Raises ``np.linalg.LinAlgError`` if S is not positive definite.
+    The definition: a library Cholesky factorisation and a triangular solve
+    against the identity."""
+    Lo = np.tril(np.asarray(S, dtype=np.float64))
+    L = np.linalg.cholesky(Lo + np.tril(Lo, -1).T)
+    Li = sla.solve_triangular(L, np.eye(L.shape[0]), lower=True)
+    return L, Li
 
 
 def rayleigh_ritz(H: DGHamiltonian, Y_hat: np.ndarray):

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgchefsi.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "f64_kernels.cu", "tc_filter.cu", "tc_tf32.cu", "tc_bf16.cu", "tc_bf16x3.cu", "noalloc.cu",
-           "adjoint.cu", "realign.cu", "sliced.cu", "pair_gemm.cu", "eig_refine.cu"]
+           "adjoint.cu", "realign.cu", "sliced.cu", "pair_gemm.cu", "eig_refine.cu", "chol.cu"]
 
 
 def nvcc() -> str:

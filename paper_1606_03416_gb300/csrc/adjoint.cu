@@ -203,14 +203,20 @@ extern "C" dgchefsi_status dgchefsi_energy_grad(dgchefsi_ctx* ctx, int prec, con
   if (ctx->solver_host.size() < lw_tr_h) ctx->solver_host.resize(lw_tr_h);
   double* work = static_cast<double*>(ctx->ws_solver.p);
   const int lwork = (int)(ctx->ws_solver.bytes / sizeof(double));
-  ADJ_SOLVER(cusolverDnDpotrf(ctx->solver, CUBLAS_FILL_MODE_UPPER, n, S, n, work, lwork, ctx->info_d));
+  const bool own_chol = use_own_cholesky(ctx);
+  if (own_chol)
+    DG_TRY(cholesky_inverse(ctx, S, Ns, Ns, ctx->info_d, bad));
+  else
+    ADJ_SOLVER(cusolverDnDpotrf(ctx->solver, CUBLAS_FILL_MODE_UPPER, n, S, n, work, lwork, ctx->info_d));
   int info[4] = {0, 0, 0, 0};
   DG_CUDA(cudaMemcpyAsync(info, ctx->info_d, sizeof(int), cudaMemcpyDeviceToHost, s));
   DG_CUDA(cudaStreamSynchronize(s));
   if (info[0] != 0) return set_error(DGCHEFSI_ERR_NOT_SPD, "Cholesky of S = Y^T Y failed at column %d", info[0]);
-  ADJ_SOLVER(cusolverDnXtrtri(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, Ns, CUDA_R_64F, S, Ns, work,
-                              ctx->ws_solver.bytes, ctx->solver_host.empty() ? nullptr : ctx->solver_host.data(),
-                              lw_tr_h, ctx->info_d + 1));
+  if (!own_chol)
+    ADJ_SOLVER(cusolverDnXtrtri(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, Ns, CUDA_R_64F, S, Ns,
+                                work, ctx->ws_solver.bytes,
+                                ctx->solver_host.empty() ? nullptr : ctx->solver_host.data(), lw_tr_h,
+                                ctx->info_d + 1));
   DG_CUDA(zero_strict_upper_f64(S, Ns, Ns, s));  // S now holds L = U^{-T} exactly (lower)
   DG_CUDA(cudaMemcpyAsync(L, S, sizeof(double) * small, cudaMemcpyDeviceToDevice, s));
   DG_TRY(prod_nn(L, Yt, N, N, Yh, N, true));

@@ -328,6 +328,7 @@ static dgchefsi_status rr_impl(dgchefsi_ctx* ctx, double* Y, int64_t Ns, int64_t
   // Products on the FP64 cores, or from exact BF16 slices on the tensor cores
   // (non-finite operands there raise info[3], like a non-finite Ritz value).
   const bool sl = ctx->products_mode == DGCHEFSI_PRODUCTS_SLICED_BF16;
+  const bool own_chol = use_own_cholesky(ctx);
   int* bad = ctx->info_d + 3;
   // Step 3: S = Y^T Y (lower tiles, mirrored), S = U^T U, Y_hat = Y U^{-1}.
   // CholeskyQR2 repeats the pass on Y_hat; shifted CholeskyQR3 factors
@@ -347,17 +348,24 @@ static dgchefsi_status rr_impl(dgchefsi_ctx* ctx, double* Y, int64_t Ns, int64_t
     if (pass == 0 && ctx->orth_mode == DGCHEFSI_ORTH_SHIFTED_CHOLQR3)
       DG_CUDA(shift_diagonal_by_trace_f64(S, Ns, 11.0 * ((double)N * (double)Ns + (double)Ns * (double)(Ns + 1)) *
                                                      0x1p-53, s));
-    DG_SOLVER(cusolverDnDpotrf(ctx->solver, CUBLAS_FILL_MODE_UPPER, n, S, n, work, lwork, ctx->info_d));
+    // S = U^T U and U^{-1}: column-major U^{-1} read row-major is U^{-T} (lower),
+    // which the recursive form writes directly.
+    if (own_chol) {
+      DG_TRY(cholesky_inverse(ctx, S, Ns, Ns, ctx->info_d, bad));
+    } else {
+      DG_SOLVER(cusolverDnDpotrf(ctx->solver, CUBLAS_FILL_MODE_UPPER, n, S, n, work, lwork, ctx->info_d));
+    }
     DG_CUDA(cudaMemcpyAsync(info, ctx->info_d, sizeof(int), cudaMemcpyDeviceToHost, s));
     DG_CUDA(cudaStreamSynchronize(s));
     if (info[0] != 0)
       return set_error(DGCHEFSI_ERR_NOT_SPD,
                        "Cholesky of S = Y^T Y failed at column %d (S not positive definite; orthonormalisation pass %d)",
                        info[0], pass + 1);
-    // U^{-1} in place. Column-major U^{-1} read row-major is U^{-T} (lower).
-    DG_SOLVER(cusolverDnXtrtri(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, Ns, CUDA_R_64F, S, Ns, work,
-                               ctx->ws_solver.bytes, ctx->solver_host.empty() ? nullptr : ctx->solver_host.data(),
-                               lw_trtri_h, ctx->info_d + 1));
+    if (!own_chol)
+      DG_SOLVER(cusolverDnXtrtri(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, Ns, CUDA_R_64F, S, Ns,
+                                 work, ctx->ws_solver.bytes,
+                                 ctx->solver_host.empty() ? nullptr : ctx->solver_host.data(), lw_trtri_h,
+                                 ctx->info_d + 1));
     // Y_hat^T = U^{-T} Y^T
     if (sl)
       DG_TRY(sliced_gemm(ctx, false, true, Ns, N, Ns, S, Ns, in, ldi, outp, ldo, ctx->products_slices, bad));
@@ -558,6 +566,7 @@ void dgchefsi_destroy(dgchefsi_ctx* ctx) {
   free_buf(ctx->ws_pairs);
   free_buf(ctx->ws_pairs_err);
   free_buf(ctx->ws_eig);
+  free_buf(ctx->ws_chol);
   if (ctx->s_reduce) cudaStreamSynchronize(ctx->s_reduce);
   for (int i = 0; i < 2; ++i) {
     if (ctx->ev_pairs[i]) cudaEventDestroy(ctx->ev_pairs[i]);
@@ -817,6 +826,54 @@ dgchefsi_status dgchefsi_sliced_timing(dgchefsi_ctx* ctx, double* pairs_ms, int6
   DG_TRY(check_ctx(ctx));
   if (pairs_ms) *pairs_ms = ctx->pairs_ms;
   if (launches) *launches = ctx->pairs_launches;
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status dgchefsi_set_cholesky(dgchefsi_ctx* ctx, int mode) {
+  clear_error();
+  if (!ctx) return set_error(DGCHEFSI_ERR_ARG, "null context");
+  if (mode != DGCHEFSI_CHOL_AUTO && mode != DGCHEFSI_CHOL_CUSOLVER && mode != DGCHEFSI_CHOL_PRODUCTS)
+    return set_error(DGCHEFSI_ERR_ARG, "unknown Cholesky form %d", mode);
+  ctx->chol_mode = mode;
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status dgchefsi_cholesky_inverse(dgchefsi_ctx* ctx, double* S, int64_t n, int64_t lda) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  if (n < 0 || lda < n || (n > 0 && !S)) return set_error(DGCHEFSI_ERR_ARG, "bad Cholesky arguments");
+  if (n == 0) return DGCHEFSI_OK;
+  cudaStream_t s = ctx->stream;
+  DG_CUDA(cudaMemsetAsync(ctx->info_d, 0, 4 * sizeof(int), s));
+  if (use_own_cholesky(ctx)) {
+    DG_TRY(cholesky_inverse(ctx, S, n, lda, ctx->info_d, ctx->info_d + 3));
+  } else {
+    if (n > INT32_MAX || lda > INT32_MAX) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "order beyond cuSOLVER's int");
+    DG_SOLVER(cusolverDnSetStream(ctx->solver, s));
+    int lw = 0;
+    size_t lw_d = 0, lw_h = 0;
+    DG_SOLVER(cusolverDnDpotrf_bufferSize(ctx->solver, CUBLAS_FILL_MODE_UPPER, (int)n, S, (int)lda, &lw));
+    DG_SOLVER(cusolverDnXtrtri_bufferSize(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, n, CUDA_R_64F, S,
+                                          lda, &lw_d, &lw_h));
+    DG_TRY(ensure(ctx, ctx->ws_solver, std::max(sizeof(double) * (size_t)lw, lw_d), "cuSOLVER workspace"));
+    if (ctx->solver_host.size() < lw_h) ctx->solver_host.resize(lw_h);
+    DG_SOLVER(cusolverDnDpotrf(ctx->solver, CUBLAS_FILL_MODE_UPPER, (int)n, S, (int)lda,
+                               static_cast<double*>(ctx->ws_solver.p), (int)(ctx->ws_solver.bytes / sizeof(double)),
+                               ctx->info_d));
+    int f = 0;
+    DG_CUDA(cudaMemcpyAsync(&f, ctx->info_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaStreamSynchronize(s));
+    if (f != 0) return set_error(DGCHEFSI_ERR_NOT_SPD, "Cholesky failed at column %d", f);
+    DG_SOLVER(cusolverDnXtrtri(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, n, CUDA_R_64F, S, lda,
+                               ctx->ws_solver.p, ctx->ws_solver.bytes,
+                               ctx->solver_host.empty() ? nullptr : ctx->solver_host.data(), lw_h, ctx->info_d + 1));
+  }
+  int info[4] = {0, 0, 0, 0};
+  DG_CUDA(cudaMemcpyAsync(info, ctx->info_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  if (info[0] != 0) return set_error(DGCHEFSI_ERR_NOT_SPD, "Cholesky failed at column %d", info[0]);
+  if (info[1] != 0) return set_error(DGCHEFSI_ERR_NOT_SPD, "triangular inverse failed (info %d)", info[1]);
+  if (info[3] != 0) return set_error(DGCHEFSI_ERR_NONFINITE, "non-finite entry in S");
   return DGCHEFSI_OK;
 }
 

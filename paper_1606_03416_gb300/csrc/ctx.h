@@ -79,6 +79,10 @@ struct dgchefsi_ctx {
   double eig_update = 0.0, eig_start_ms = 0.0, eig_refine_ms = 0.0;
   int64_t eig_start_order = 0;
   dg::DevBuf ws_eig;
+  // Cholesky factorisation of step 3 (DGCHEFSI_CHOL_*) and the recursive
+  // form's workspace (L^{-1} and two scratch blocks, 3 N_s^2 doubles)
+  int chol_mode = 0;
+  dg::DevBuf ws_chol;
   int32_t f64_tj = 64;    // column tile of the FP64 filter (set at create)
   // FP64 filter as a CUDA graph: coefficients copied from a pinned mirror at
   // every replay; the graph is captured again when X, Y, N_s, ld, m or the
@@ -210,6 +214,21 @@ dgchefsi_status tc_sliced_matvec(dgchefsi_ctx* ctx, const double* X, int64_t ldx
 // info in ctx->info_d[2] (checked by the caller); the refined form
 // synchronises and records its statistics in the context.
 dgchefsi_status subspace_eigh(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda, double* w);
+
+// S = L L^T (lower triangle of S, row-major n x n, lda) factored by the
+// recursive blocked form whose work is dense products (chol.cu); on return
+// the lower triangle of S holds L^{-1} (= U^{-T} for S = U^T U) and the
+// strict upper part is unspecified. A pivot that is not positive sets
+// *info (device) to its 1-based column; a non-finite operand of a sliced
+// product sets *bad. Enqueued on the context's stream (sliced products
+// synchronise).
+dgchefsi_status cholesky_inverse(dgchefsi_ctx* ctx, double* S, int64_t n, int64_t lda, int* info, int* bad);
+// The recursive form for the context's setting: DGCHEFSI_CHOL_PRODUCTS, or
+// DGCHEFSI_CHOL_AUTO with sliced subspace products.
+inline bool use_own_cholesky(const dgchefsi_ctx* ctx) {
+  return ctx->chol_mode == DGCHEFSI_CHOL_PRODUCTS ||
+         (ctx->chol_mode == DGCHEFSI_CHOL_AUTO && ctx->products_mode == DGCHEFSI_PRODUCTS_SLICED_BF16);
+}
 
 // Set-up of dgchefsi_bounds_static for `device` (noalloc.cu), run by
 // dgchefsi_create with that device current: looks up the device address of

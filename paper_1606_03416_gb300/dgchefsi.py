@@ -33,7 +33,8 @@ EXPORTS = ["dgchefsi_create", "dgchefsi_destroy", "dgchefsi_set_stream", "dgchef
            "dgchefsi_realign", "dgchefsi_filter_host", "dgchefsi_set_subspace_products",
            "dgchefsi_sliced_gemm", "dgchefsi_sliced_matvec", "dgchefsi_set_unit_order",
            "dgchefsi_get_unit_order", "dgchefsi_sliced_timing", "dgchefsi_set_eigensolver",
-           "dgchefsi_subspace_eigh", "dgchefsi_eigensolver_stats"]
+           "dgchefsi_subspace_eigh", "dgchefsi_eigensolver_stats", "dgchefsi_set_cholesky",
+           "dgchefsi_cholesky_inverse"]
 
 # Orthonormalisations of Alg. 1 step 3 (dgchefsi_set_orthonormalisation).
 ORTHONORMALISATIONS = {"cholqr": 0, "cholqr2": 1, "shifted_cholqr3": 2}
@@ -44,6 +45,9 @@ SUBSPACE_PRODUCTS = {"f64": 0, "sliced_bf16": 1}
 # Eigensolver of the projected Hamiltonian (dgchefsi_set_eigensolver).
 EIGENSOLVERS = {"auto": 0, "syevd": 1, "refined": 2}
 EIGENSOLVER_NAMES = {v: k for k, v in EIGENSOLVERS.items()}
+
+# Cholesky form of Alg. 1 step 3 (dgchefsi_set_cholesky).
+CHOLESKY_FORMS = {"auto": 0, "cusolver": 1, "products": 2}
 
 # Capacity (doubles) of the library's fixed scratch array for bounds_static.
 BOUNDS_STATIC_DOUBLES = 1 << 20
@@ -85,6 +89,8 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_get_unit_order": (st, [P, C.c_int, P]),
         "dgchefsi_sliced_timing": (st, [P, P, P]),
         "dgchefsi_set_eigensolver": (st, [P, C.c_int]),
+        "dgchefsi_set_cholesky": (st, [P, C.c_int]),
+        "dgchefsi_cholesky_inverse": (st, [P, P, I64, I64]),
         "dgchefsi_subspace_eigh": (st, [P, P, I64, I64, P]),
         "dgchefsi_eigensolver_stats": (st, [P, P, P, P, P, P, P, P, P]),
         "dgchefsi_density_pattern": (st, [P, P, I64, I64, P, P]),
@@ -362,6 +368,22 @@ class Context:
         _check(_lib.dgchefsi_sliced_gemm(self._h, int(b_rows), int(a_lower), M, Nc, K, _ptr(A), A.stride(0),
                                          _ptr(B), B.stride(0), _ptr(out), out.stride(0), int(slices), int(tri)))
         return out
+
+    def set_cholesky(self, mode: str):
+        """"auto", "cusolver" (potrf + trtri) or "products" (recursive blocked
+        form on dense products) for the Cholesky factorisation of Alg. 1 step 3."""
+        _check(_lib.dgchefsi_set_cholesky(self._h, CHOLESKY_FORMS[mode]))
+
+    def cholesky_inverse(self, S: torch.Tensor) -> torch.Tensor:
+        """In place: the lower triangle of S (n x n float64 CUDA, rows
+        contiguous, symmetric positive definite) is replaced by L^{-1} for
+        S = L L^T; returns S."""
+        if not (S.is_cuda and S.dtype == torch.float64 and S.dim() == 2 and S.shape[0] == S.shape[1]
+                and S.stride(1) == 1):
+            raise TypeError("S must be a square float64 CUDA tensor with contiguous rows")
+        self._sync_stream()
+        _check(_lib.dgchefsi_cholesky_inverse(self._h, _ptr(S), S.shape[0], S.stride(0)))
+        return S
 
     def set_eigensolver(self, mode: str):
         """"auto", "syevd" (cuSOLVER FP64) or "refined" (FP32 start refined to

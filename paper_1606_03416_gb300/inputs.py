@@ -309,6 +309,22 @@ def near_diagonal_symmetric(d, coupling: float, top: int = 0, top_coupling: floa
     return 0.5 * (A + A.T)
 
 
+def planted_cholesky(n: int, cond: float = 1e3, negative_at: int = -1, seed: int = 0):
+    """(S, L): S = L D L^T with L lower triangular, unit-scale Gaussian below
+    the diagonal and a positive diagonal spread log-uniformly over [1, sqrt(cond)],
+    D = I except D[negative_at] = -1 (then S is indefinite and its Cholesky
+    factorisation meets its first non-positive pivot at that row). S is
+    symmetrised exactly."""
+    rng = np.random.default_rng(seed + 7)
+    L = np.tril(rng.standard_normal((n, n)), -1) / np.sqrt(max(n, 1))
+    L[np.diag_indices(n)] = np.exp(rng.uniform(0.0, 0.5 * np.log(cond), n))
+    d = np.ones(n)
+    if negative_at >= 0:
+        d[negative_at] = -1.0
+    S = (L * d[None, :]) @ L.T
+    return 0.5 * (S + S.T), L
+
+
 def pack_blocks(blocks) -> np.ndarray:
     """Concatenate row-major blocks into one float64 array (the packed layout
     of the re-alignment call)."""

@@ -77,3 +77,31 @@ def test_clustered_spectrum_generator(groups):
     assert lam.shape == (120,) and np.all(np.diff(lam) >= 0)
     for centre, size, spread in groups:
         assert np.sum(np.abs(lam - centre) <= 10 * spread) >= size
+
+
+# ---- the Cholesky factor and its inverse (Alg. 1 step 3), oracle.cholesky_inverse
+
+def test_cholesky_two_by_two_closed_form():
+    a, b, c = 4.0, 2.0, 5.0          # S = [[4, 2], [2, 5]] = L L^T, L = [[2, 0], [1, 2]]
+    L, Li = O.cholesky_inverse(np.array([[a, -7.0], [b, c]]))
+    assert np.allclose(L, [[2.0, 0.0], [1.0, 2.0]], rtol=0, atol=1e-15)
+    assert np.allclose(Li, [[0.5, 0.0], [-0.25, 0.5]], rtol=0, atol=1e-15)
+
+
+def test_cholesky_recovers_the_planted_factor():
+    S, Lp = G.planted_cholesky(300, cond=1e4, seed=2)
+    L, Li = O.cholesky_inverse(S)
+    # the factor with a positive diagonal is unique
+    assert np.abs(L - Lp).max() <= 1e-10 * np.abs(Lp).max()
+    assert np.abs(Li @ L - np.eye(300)).max() <= 1e-12
+    assert np.array_equal(np.triu(Li, 1), np.zeros((300, 300)))
+
+
+def test_cholesky_rejects_an_indefinite_matrix():
+    S, _ = G.planted_cholesky(50, negative_at=17, seed=3)
+    with pytest.raises(np.linalg.LinAlgError):
+        O.cholesky_inverse(S)
+    # the leading 17 x 17 block is still positive definite, the 18 x 18 one is not
+    O.cholesky_inverse(S[:17, :17])
+    with pytest.raises(np.linalg.LinAlgError):
+        O.cholesky_inverse(S[:18, :18])

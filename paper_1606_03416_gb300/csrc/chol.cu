@@ -14,10 +14,11 @@
 //   (L^{-1})21 = -L22^{-1} (L21 L11^{-1}),
 // (Golub and Van Loan, Matrix Computations, 4th ed., Sec. 4.2 for the block
 // Cholesky; the block form of the triangular inverse is the one of Sec. 3.1).
-// Blocks of at most 64 rows are factored and inverted in shared memory by
-// one CTA (the unblocked outer-product Cholesky and forward substitution of
-// the unit vectors). Products with every side at least 512 run from exact
-// BF16 slices on the tensor cores (sliced.cu), smaller ones on the FP64 cores.
+// Blocks of at most 64 rows are factored and inverted by one CTA (the
+// unblocked outer-product Cholesky, then Gauss-Jordan elimination of the
+// identity, with the block's entries held in registers). Products with every
+// side at least 512 run from exact BF16 slices on the tensor cores
+// (sliced.cu), smaller ones on the FP64 cores as split-K tiles over the whole GPU.
 // S is first equilibrated by powers of two (see k_equilibrate).
 #include <algorithm>
 #include <cmath>
@@ -28,63 +29,166 @@ namespace dg {
 
 namespace {
 
-constexpr int kLeaf = 64;        // rows of a block factored by one CTA
+// rows of a block factored by one CTA. A leaf runs on one SM, which does two
+// FP64 multiply-adds per clock, and its ~2 kLeaf^3 / 3 of them are serial
+// across the leaves: 64 keeps that near 3 ms at n = 4096 (128 took 4 ms per
+// leaf), the levels above run over the whole GPU
+constexpr int kLeaf = 64;
 constexpr int64_t kSliced = 512;  // smallest product side run from slices
+constexpr int kLeafThreads = 256;
+constexpr int64_t kPartial = int64_t(1) << 20;  // doubles of partial tiles for the split-K products
+constexpr int kOwn = (kLeaf * (kLeaf + 1) / 2 + kLeafThreads - 1) / kLeafThreads;  // entries per thread
 
 // One CTA factors the n x n block (n <= 64) whose lower triangle is at A
 // (lda): L (lower) replaces it, the strict upper part is left as it was, and
-// Li (ldl) receives L^{-1} with its strict upper part zeroed. A pivot that is
-// not positive and finite stops the block: *info = col0 + j + 1 (1-based
-// column of the whole matrix) if *info was 0.
-__global__ void __launch_bounds__(256) k_chol_leaf(double* __restrict__ A, int64_t lda, double* __restrict__ Li,
-                                                   int64_t ldl, int n, int64_t col0, int* __restrict__ info) {
-  __shared__ double M[kLeaf][kLeaf + 1];
-  __shared__ int bad;
+// Li (ldl) receives L^{-1} with its strict upper part zeroed. Each thread owns
+// up to kOwn entries of the lower triangle in registers (entry e = i(i+1)/2 + k
+// belongs to thread e mod 256). Step j of the factorisation publishes column
+// j to shared memory, and every owner of (i, k), j < k <= i, subtracts
+// M_ij M_kj / M_jj; column j is then divided by sqrt(M_jj). L^{-1} follows by
+// Gauss-Jordan elimination of W = I: step j publishes row j of W and column j
+// of L, row j is divided by L_jj, and rows i > j lose L_ij times it. The
+// shared rows and columns alternate between two buffers, so each step needs
+// one barrier. A pivot that is not positive and finite stops the block:
+// *info = col0 + j + 1 (1-based column of the whole matrix) if *info was 0.
+__global__ void __launch_bounds__(kLeafThreads, 1) k_chol_leaf(double* __restrict__ A, int64_t lda,
+                                                              double* __restrict__ Li, int64_t ldl, int n,
+                                                              int64_t col0, int* __restrict__ info) {
+  __shared__ double col[2][kLeaf], row[2][kLeaf];
+  __shared__ double sc[2][4];  // the pivot, its square root and their reciprocals (one thread computes them)
   const int t = threadIdx.x;
-  if (t == 0) bad = 0;
-  for (int e = t; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    M[i][j] = j <= i ? A[(int64_t)i * lda + j] : 0.0;
+  const int tot = n * (n + 1) / 2;
+  double v[kOwn], w[kOwn];
+  int rc[kOwn];  // (row << 8) | column of the entry, -1 for none
+#pragma unroll
+  for (int q = 0; q < kOwn; ++q) {
+    const int e = t + kLeafThreads * q;
+    int i = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    while (i * (i + 1) / 2 > e) --i;
+    const int k = e - i * (i + 1) / 2;
+    const bool ok = e < tot;
+    rc[q] = ok ? (i << 8) | k : -1;
+    v[q] = ok ? A[(int64_t)i * lda + k] : 0.0;
+    w[q] = (ok && i == k) ? 1.0 : 0.0;
   }
-  __syncthreads();
   for (int j = 0; j < n; ++j) {
-    if (t == 0) {
-      const double d = M[j][j];
-      if (!(d > 0.0) || !isfinite(d)) {
-        bad = 1;
-        atomicCAS(info, 0, (int)(col0 + j + 1));
-      } else {
-        M[j][j] = sqrt(d);
+    const int b = j & 1;
+#pragma unroll
+    for (int q = 0; q < kOwn; ++q)
+      if (rc[q] >= 0 && (rc[q] & 255) == j) {
+        col[b][rc[q] >> 8] = v[q];
+        if ((rc[q] >> 8) == j) {  // the pivot's owner
+          const double pv = v[q], sq = sqrt(pv);
+          sc[b][0] = pv;
+          sc[b][1] = sq;
+          sc[b][2] = 1.0 / sq;
+          sc[b][3] = 1.0 / pv;
+        }
       }
+    __syncthreads();
+    const double p = sc[b][0];
+    if (!(p > 0.0) || !isfinite(p)) {  // the same value in every thread: all leave together
+      if (t == 0) atomicCAS(info, 0, (int)(col0 + j + 1));
+      return;
+    }
+    const double ljj = sc[b][1], rl = sc[b][2], rp = sc[b][3];
+#pragma unroll
+    for (int q = 0; q < kOwn; ++q) {
+      if (rc[q] < 0) continue;
+      const int i = rc[q] >> 8, k = rc[q] & 255;
+      if (k == j)
+        v[q] = i == j ? ljj : v[q] * rl;
+      else if (k > j)
+        v[q] -= col[b][i] * (col[b][k] * rp);
+    }
+  }
+  __syncthreads();  // the last factorisation step's readers are done with its buffer
+  for (int j = 0; j < n; ++j) {
+    const int b = j & 1;
+#pragma unroll
+    for (int q = 0; q < kOwn; ++q) {
+      if (rc[q] < 0) continue;
+      const int i = rc[q] >> 8, k = rc[q] & 255;
+      if (k == j) col[b][i] = v[q];  // column j of L (L_jj included)
+      if (i == j) row[b][k] = w[q];  // row j of W, before its division
+      if (i == j && k == j) sc[b][0] = 1.0 / v[q];
     }
     __syncthreads();
-    if (bad) break;
-    const double ljj = M[j][j];
-    for (int i = j + 1 + t; i < n; i += blockDim.x) M[i][j] /= ljj;
+    const double rl = sc[b][0];
+#pragma unroll
+    for (int q = 0; q < kOwn; ++q) {
+      if (rc[q] < 0) continue;
+      const int i = rc[q] >> 8, k = rc[q] & 255;
+      if (i == j)
+        w[q] *= rl;
+      else if (i > j && k <= j)
+        w[q] -= col[b][i] * (row[b][k] * rl);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kOwn; ++q) {
+    if (rc[q] < 0) continue;
+    const int i = rc[q] >> 8, k = rc[q] & 255;
+    A[(int64_t)i * lda + k] = v[q];
+    Li[(int64_t)i * ldl + k] = w[q];
+  }
+  for (int e = t; e < n * n; e += kLeafThreads) {
+    const int i = e / n, k = e % n;
+    if (k > i) Li[(int64_t)i * ldl + k] = 0.0;
+  }
+}
+
+// Small FP64 products on the CUDA cores, spread over the whole GPU: 32 x 32
+// output tiles, the K range split into `splits` parts (one CTA per tile and
+// part) whose partial tiles go to P, then summed in a fixed order
+// (deterministic). C = X op(Z): op(Z)[k, c] = Z[c, k] (zt, the X Z^T form)
+// or Z[k, c]; x_lower: X[r, k] = 0 for k > r. One SM does two FP64 FMAs per
+// clock, so a product of a few million multiply-adds needs many CTAs.
+template <bool ZT, bool XLOWER>
+__global__ void __launch_bounds__(256) k_small_gemm_part(const double* __restrict__ X, int64_t ldx,
+                                                         const double* __restrict__ Z, int64_t ldz,
+                                                         double* __restrict__ P, int64_t rows, int64_t cols,
+                                                         int64_t K, int64_t kc) {
+  __shared__ double Xs[32][33], Zs[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  const int64_t k0 = (int64_t)blockIdx.z * kc, k1 = K < k0 + kc ? K : k0 + kc;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t kk = k0; kk < k1; kk += 32) {
+    for (int u = ty; u < 32; u += 8) {
+      const int64_t r = r0 + u, k = kk + tx;
+      Xs[u][tx] = (r < rows && k < k1 && (!XLOWER || k <= r)) ? X[r * ldx + k] : 0.0;
+      const int64_t kz = kk + u, c = c0 + tx;
+      Zs[u][tx] = (kz < k1 && c < cols) ? (ZT ? Z[c * ldz + kz] : Z[kz * ldz + c]) : 0.0;
+    }
     __syncthreads();
-    // trailing update of the lower triangle: M[i][k] -= M[i][j] M[k][j], j < k <= i
-    const int m = n - j - 1;
-    for (int e = t; e < m * m; e += blockDim.x) {
-      const int i = j + 1 + e / m, k = j + 1 + e % m;
-      if (k <= i) M[i][k] -= M[i][j] * M[k][j];
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) {
+      const double z = Zs[i][tx];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] += Xs[ty + 8 * u][i] * z;
     }
     __syncthreads();
   }
-  if (bad) return;
-  for (int e = t; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    if (j <= i) A[(int64_t)i * lda + j] = M[i][j];
+  double* Pp = P + (int64_t)blockIdx.z * rows * cols;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t r = r0 + ty + 8 * u, c = c0 + tx;
+    if (r < rows && c < cols) Pp[r * cols + c] = acc[u];
   }
-  // column c of L^{-1}: forward substitution of e_c (entries above c are zero)
-  for (int c = t; c < n; c += blockDim.x) {
-    double x[kLeaf];
-    for (int i = 0; i < c; ++i) Li[(int64_t)i * ldl + c] = 0.0;
-    for (int i = c; i < n; ++i) {
-      double acc = i == c ? 1.0 : 0.0;
-      for (int k = c; k < i; ++k) acc -= M[i][k] * x[k];
-      x[i] = acc / M[i][i];
-      Li[(int64_t)i * ldl + c] = x[i];
-    }
+}
+
+// C[r, c] = sum_s P[s, r, c] in the order s = 0, 1, ...; tri: only c <= r.
+__global__ void k_small_gemm_sum(const double* __restrict__ P, int splits, int64_t rows, int64_t cols,
+                                 double* __restrict__ C, int64_t ldc, int tri) {
+  const int64_t tot = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, c = e % cols;
+    if (tri && c > r) continue;
+    double sum = 0.0;
+    for (int sp = 0; sp < splits; ++sp) sum += P[(int64_t)sp * tot + e];
+    C[r * ldc + c] = sum;
   }
 }
 
@@ -146,28 +250,44 @@ struct Chol {
   double* Li;    // L^{-1}, n x n, row stride n (strict upper zero)
   double* T;     // scratch, n x n, row stride n
   double* T2;    // scratch, n x n, row stride n
+  double* P;     // partial tiles of the small products (kPartial doubles)
   int64_t n;
   int* info;     // device
   int* bad;      // device non-finite flag of the sliced products
   int slices;
   cudaStream_t st;
 
+  // Split-K FP64 product on the CUDA cores for the small levels.
+  template <bool ZT, bool XLOWER>
+  dgchefsi_status small(const double* X, int64_t ldx, const double* Z, int64_t ldz, double* C, int64_t ldc,
+                        int64_t rows, int64_t cols, int64_t K, bool tri) {
+    const int64_t tiles = ((rows + 31) / 32) * ((cols + 31) / 32);
+    int64_t splits = std::max<int64_t>(1, std::min<int64_t>((2 * 152 + tiles - 1) / tiles, (K + 31) / 32));
+    splits = std::max<int64_t>(1, std::min<int64_t>(splits, kPartial / (rows * cols)));
+    const int64_t kc = ((K + splits - 1) / splits + 31) / 32 * 32;
+    splits = (K + kc - 1) / kc;
+    k_small_gemm_part<ZT, XLOWER><<<dim3((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32), (unsigned)splits),
+                                     256, 0, st>>>(X, ldx, Z, ldz, P, rows, cols, K, kc);
+    k_small_gemm_sum<<<grid_2d(rows * cols), 256, 0, st>>>(P, (int)splits, rows, cols, C, ldc, tri ? 1 : 0);
+    count_launch(2);
+    DG_CUDA(cudaGetLastError());
+    return DGCHEFSI_OK;
+  }
   // C (rows x cols, ldc) = X Z^T with X rows x K (ldx), Z cols x K (ldz);
   // tri: only the lower triangle (rows == cols).
   dgchefsi_status prod_nt(const double* X, int64_t ldx, const double* Z, int64_t ldz, double* C, int64_t ldc,
                           int64_t rows, int64_t cols, int64_t K, bool tri) {
     if (std::min(std::min(rows, cols), K) >= kSliced)
       return sliced_gemm(ctx, true, false, rows, cols, K, X, ldx, Z, ldz, C, ldc, slices, bad, tri ? rows : 0);
-    DG_CUDA(gemm_nt_f64(X, ldx, Z, ldz, C, ldc, rows, cols, K, tri, false, st));
-    return DGCHEFSI_OK;
+    return small<true, false>(X, ldx, Z, ldz, C, ldc, rows, cols, K, tri);
   }
   // C = X Z with X rows x K (x_lower: lower triangular), Z K x cols.
   dgchefsi_status prod_nn(const double* X, int64_t ldx, const double* Z, int64_t ldz, double* C, int64_t ldc,
                           int64_t rows, int64_t cols, int64_t K, bool x_lower) {
     if (std::min(std::min(rows, cols), K) >= kSliced)
       return sliced_gemm(ctx, false, x_lower, rows, cols, K, X, ldx, Z, ldz, C, ldc, slices, bad);
-    DG_CUDA(gemm_nn_f64(X, ldx, Z, ldz, C, ldc, rows, cols, K, x_lower, st));
-    return DGCHEFSI_OK;
+    return x_lower ? small<false, true>(X, ldx, Z, ldz, C, ldc, rows, cols, K, false)
+                   : small<false, false>(X, ldx, Z, ldz, C, ldc, rows, cols, K, false);
   }
   dgchefsi_status axpby(double alpha, const double* X, int64_t ldx, double beta, double* Y, int64_t ldy,
                         int64_t rows, int64_t cols, bool lower) {
@@ -182,13 +302,13 @@ struct Chol {
     double* a = A + i0 * lda + i0;
     double* li = Li + i0 * n + i0;
     if (m <= kLeaf) {
-      k_chol_leaf<<<1, 256, 0, st>>>(a, lda, li, n, (int)m, i0, info);
+      k_chol_leaf<<<1, kLeafThreads, 0, st>>>(a, lda, li, n, (int)m, i0, info);
       count_launch();
       DG_CUDA(cudaGetLastError());
       return DGCHEFSI_OK;
     }
     // split on a multiple of the leaf (of 256 once blocks are large), near the middle
-    const int64_t q = m >= 1024 ? 256 : kLeaf;
+    const int64_t q = m >= 1024 ? 256 : 64;
     const int64_t m1 = std::max<int64_t>(q, (m / 2 + q / 2) / q * q);
     const int64_t m2 = m - m1;
     DG_TRY(block(i0, m1));
@@ -217,10 +337,11 @@ struct Chol {
 dgchefsi_status cholesky_inverse(dgchefsi_ctx* ctx, double* S, int64_t n, int64_t lda, int* info, int* bad) {
   if (n <= 0) return DGCHEFSI_OK;
   const size_t nn = (size_t)n * (size_t)n;
-  DG_TRY(ensure(ctx, ctx->ws_chol, sizeof(double) * (3 * nn + (size_t)n), "Cholesky workspace"));
+  DG_TRY(ensure(ctx, ctx->ws_chol, sizeof(double) * (3 * nn + (size_t)kPartial + (size_t)n), "Cholesky workspace"));
   double* Li = static_cast<double*>(ctx->ws_chol.p);
-  double* d = Li + 3 * nn;
-  Chol c{ctx, S, lda, Li, Li + nn, Li + 2 * nn, n, info, bad, std::max(ctx->products_slices, 10), ctx->stream};
+  double* d = Li + 3 * nn + kPartial;
+  Chol c{ctx, S, lda, Li, Li + nn, Li + 2 * nn, Li + 3 * nn, n, info, bad, std::max(ctx->products_slices, 10),
+         ctx->stream};
   DG_CUDA(cudaMemsetAsync(Li, 0, sizeof(double) * nn, c.st));
   k_equilibrate<<<dim3((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)std::min<int64_t>(n, 65535)), 256,
                   0, c.st>>>(S, lda, n, d);

@@ -52,6 +52,7 @@ constexpr int kMaxCluster = 32;    // largest cluster the Jacobi kernel takes
 constexpr int kMaxSteps = 10;      // refinement steps before the FP64 fallback
 constexpr double kKappa = 100.0;   // cluster when |e_ij| would exceed 1/kappa
 constexpr double kStop = 1e-8;     // last step: the next correction is O(kStop^2)
+constexpr double kPredict = 1e-15; // or when the next correction is predicted below this
 constexpr double kNoise = 256.0;   // couplings below kNoise u ||A|| are rounding noise of the products
 
 unsigned grid_for(int64_t n, int t = 256) { return (unsigned)std::min<int64_t>((n + t - 1) / t, 1 << 20); }
@@ -376,6 +377,57 @@ __global__ void k_scatter_block(double* __restrict__ V, int64_t n, const int* __
     V[(int64_t)rows[t / m] * n + rows[t % m]] = (double)W[t];
 }
 
+// Block-structured V (the identity outside the rows and columns rows[0..m)):
+// gathers and scatters of those rows and columns.
+// R (m x ncols) = X[rows[k], :]
+__global__ void k_gather_rows_of(const double* __restrict__ X, int64_t ldx, const int* __restrict__ rows, int64_t m,
+                                 int64_t ncols, double* __restrict__ R) {
+  const int64_t tot = m * ncols;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
+    R[t] = X[(int64_t)rows[t / ncols] * ldx + t % ncols];
+}
+// X[rows[k], :] = R (m x ncols)
+__global__ void k_scatter_rows_of(double* __restrict__ X, int64_t ldx, const int* __restrict__ rows, int64_t m,
+                                  int64_t ncols, const double* __restrict__ R) {
+  const int64_t tot = m * ncols;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
+    X[(int64_t)rows[t / ncols] * ldx + t % ncols] = R[t];
+}
+// R (nrows x m) = X[:, cols[k]]
+__global__ void k_gather_cols_of(const double* __restrict__ X, int64_t ldx, const int* __restrict__ cols, int64_t m,
+                                 int64_t nrows, double* __restrict__ R) {
+  const int64_t tot = m * nrows;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
+    R[t] = X[(t / m) * ldx + cols[t % m]];
+}
+// X[i, cols[k]] = R[i, k] + (pos[i] >= 0 ? B[pos[i], k] : 0) for every row i
+// (R nrows x m; B m x m, may be null)
+__global__ void k_scatter_cols_of(double* __restrict__ X, int64_t ldx, const int* __restrict__ cols, int64_t m,
+                                  int64_t nrows, const double* __restrict__ R, const int* __restrict__ pos,
+                                  const double* __restrict__ B) {
+  const int64_t tot = m * nrows;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / m, k = t % m;
+    double v = R[t];
+    if (B && pos[i] >= 0) v += B[(int64_t)pos[i] * m + k];
+    X[i * ldx + cols[k]] = v;
+  }
+}
+// X[rows[k], rows[l]] = B[k, l]  (B m x m)
+__global__ void k_scatter_block_of(double* __restrict__ X, int64_t ldx, const int* __restrict__ rows, int64_t m,
+                                   const double* __restrict__ B) {
+  const int64_t tot = m * m;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
+    X[(int64_t)rows[t / m] * ldx + rows[t % m]] = B[t];
+}
+// B (m x m) = X[rows[k], rows[l]]
+__global__ void k_gather_block_of(const double* __restrict__ X, int64_t ldx, const int* __restrict__ rows, int64_t m,
+                                  double* __restrict__ B) {
+  const int64_t tot = m * m;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
+    B[t] = X[(int64_t)rows[t / m] * ldx + rows[t % m]];
+}
+
 // For V = I: G = I and S = A (the products of a step, without computing them).
 __global__ void k_identity_products(const double* __restrict__ A, int64_t lda, int64_t n, double* __restrict__ G,
                                     double* __restrict__ S) {
@@ -436,7 +488,8 @@ struct EigWs {
   int* idx;            // n: cluster members
   int* cofs;           // n + 1
   int* wofs;           // n + 1
-  int* perm;           // n
+  int* perm;           // n: the block's rows in the first step, the final order at the end
+  int* posb;           // n: position of a row in the block, -1 outside
   int* cnt;            // [0] close-pair count, [1] FP32 start info, [2] non-finite operand flag
   unsigned long long* emax;
   int cap;
@@ -466,6 +519,7 @@ EigWs eig_layout(int64_t n, char* base) {
   w.cofs = reinterpret_cast<int*>(take(sizeof(int) * (size_t)(n + 1)));
   w.wofs = reinterpret_cast<int*>(take(sizeof(int) * (size_t)(n + 1)));
   w.perm = reinterpret_cast<int*>(take(sizeof(int) * (size_t)n));
+  w.posb = reinterpret_cast<int*>(take(sizeof(int) * (size_t)n));
   w.cnt = reinterpret_cast<int*>(take(sizeof(int) * 4));
   w.emax = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long)));
   w.bytes = o;
@@ -545,6 +599,7 @@ dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda
       k_lower_to_f32<<<grid_for(nn), 256, 0, st>>>(A, lda, n, ws.A32);
     } else {
       DG_CUDA(cudaMemcpyAsync(ws.idx, rows.data(), sizeof(int) * (size_t)m, cudaMemcpyHostToDevice, st));
+      DG_CUDA(cudaMemcpyAsync(ws.perm, rows.data(), sizeof(int) * (size_t)m, cudaMemcpyHostToDevice, st));
       k_gather_block_f32<<<grid_for(m * m), 256, 0, st>>>(A, lda, ws.idx, m, ws.A32);
     }
     count_launch();
@@ -594,11 +649,37 @@ dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda
   std::vector<int2> pairs_h;
   std::vector<int> parent(n), order(n), pos(n), lo(n), hi(n), reach(n), cl_h(n), idx_h(n), cofs_h, wofs_h;
   std::vector<double> lam_h(n);
+  std::vector<int> blk_h, pos_h(n);
   bool converged = false;
   bool unit = m == 0;  // V = I exactly: the step's products are known
+  // V = I outside a small block (rows[] in ws.perm): the first step's products
+  // and update come from products of the block's rows and columns alone
+  bool block = m > 0 && !full && 8 * m <= n;
+  double prev = -1.0;
   for (int step = 0; step < kMaxSteps && !converged; ++step) {
     if (unit) {
       k_identity_products<<<grid_for(nn), 256, 0, st>>>(A, lda, n, Gm, Sm);
+      count_launch();
+      DG_CUDA(cudaGetLastError());
+    } else if (block) {
+      // S = V A V^T: rows B become W A[B, :], then columns B become S[:, B] W^T;
+      // G = V V^T: I outside B, W W^T on B x B (W: the block's eigenvectors, rows)
+      double* Wb = T;             // m x m
+      double* R1 = T + m * m;     // m x n, then n x m, then m x m
+      double* R2 = R1 + m * n;    // m x n, then n x m
+      k_f32_to_f64<<<grid_for(m * m), 256, 0, st>>>(ws.A32, m * m, Wb);
+      k_identity_products<<<grid_for(nn), 256, 0, st>>>(A, lda, n, Gm, Sm);
+      k_gather_rows_of<<<grid_for(m * n), 256, 0, st>>>(A, lda, ws.perm, m, n, R1);
+      count_launch(3);
+      DG_CUDA(gemm_nn_f64(Wb, m, R1, n, R2, n, m, n, m, false, st));
+      k_scatter_rows_of<<<grid_for(m * n), 256, 0, st>>>(Sm, n, ws.perm, m, n, R2);
+      k_gather_cols_of<<<grid_for(m * n), 256, 0, st>>>(Sm, n, ws.perm, m, n, R1);
+      count_launch(2);
+      DG_CUDA(gemm_nt_f64(R1, m, Wb, m, R2, m, n, m, m, false, false, st));
+      k_scatter_cols_of<<<grid_for(m * n), 256, 0, st>>>(Sm, n, ws.perm, m, n, R2, nullptr, nullptr);
+      count_launch();
+      DG_CUDA(gemm_nt_f64(Wb, m, Wb, m, R1, m, m, m, m, false, false, st));
+      k_scatter_block_of<<<grid_for(m * m), 256, 0, st>>>(Gm, n, ws.perm, m, R1);
       count_launch();
       DG_CUDA(cudaGetLastError());
     } else {
@@ -714,14 +795,51 @@ dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda
       *reason = 4;
       return DGCHEFSI_OK;
     }
+    // the block of V that differs from I: the first step's block and this
+    // step's cluster rows (the rotations mixed only those rows)
+    int64_t mb = 0;
+    if (block && !unit) {
+      std::vector<char> in(n, 0);
+      for (int r : rows) in[r] = 1;
+      for (int q = 0; q < cofs_h[ncl]; ++q) in[idx_h[q]] = 1;
+      blk_h.clear();
+      for (int64_t i = 0; i < n; ++i)
+        if (in[i]) blk_h.push_back((int)i);
+      mb = (int64_t)blk_h.size();
+      if (4 * mb > n) mb = 0;
+    }
     if (unit && ncl == 0) {
       DG_CUDA(axpby_f64(1.0, ws.F, 1.0, V, V, nn, st));  // V <- I + E^T
+    } else if (mb > 0) {
+      // V <- V + E^T V: outside the block's columns E^T V = E^T; on them
+      // E^T[:, B] V[B, B], and V[:, B] is zero outside the rows B
+      std::fill(pos_h.begin(), pos_h.end(), -1);
+      for (int64_t k = 0; k < mb; ++k) pos_h[blk_h[k]] = (int)k;
+      DG_CUDA(cudaMemcpyAsync(ws.perm, blk_h.data(), sizeof(int) * (size_t)mb, cudaMemcpyHostToDevice, st));
+      DG_CUDA(cudaMemcpyAsync(ws.posb, pos_h.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, st));
+      double* VB = T;            // mb x mb
+      double* FB = T + mb * mb;  // n x mb
+      double* FV = FB + n * mb;  // n x mb
+      k_gather_block_of<<<grid_for(mb * mb), 256, 0, st>>>(V, n, ws.perm, mb, VB);
+      k_gather_cols_of<<<grid_for(mb * n), 256, 0, st>>>(ws.F, n, ws.perm, mb, n, FB);
+      count_launch(2);
+      DG_CUDA(gemm_nn_f64(FB, mb, VB, mb, FV, mb, n, mb, mb, false, st));
+      DG_CUDA(axpby_f64(1.0, ws.F, 1.0, V, V, nn, st));
+      k_scatter_cols_of<<<grid_for(mb * n), 256, 0, st>>>(V, n, ws.perm, mb, n, FV, ws.posb, VB);
+      count_launch();
+      DG_CUDA(cudaGetLastError());
+      DG_CUDA(cudaStreamSynchronize(st));  // the host tables above are pageable copies' sources
     } else {
       DG_TRY(sliced_gemm(ctx, false, false, n, n, n, ws.F, n, V, n, ws.GS, n, s, bad));  // E^T V
       DG_CUDA(axpby_f64(1.0, ws.GS, 1.0, V, V, nn, st));                                  // V <- V + E^T V
     }
     unit = false;
-    converged = emax <= kStop;
+    block = false;
+    // stop when this correction is small, or when the quadratic rate seen
+    // over the last two steps puts the next one below kPredict
+    const double rate = prev > 0.0 ? std::max(1.0, emax / (prev * prev)) : 0.0;
+    converged = emax <= kStop || (prev > 0.0 && rate * emax * emax <= kPredict);
+    prev = emax;
   }
   if (!converged) {
     *reason = 5;

@@ -146,17 +146,28 @@ def test_identity_start_for_a_nearly_diagonal_matrix():
     assert st["used"] == "refined" and st["fallback"] == 0 and st["start_order"] == 0
 
 
-def test_partial_start_for_a_coupled_top_block():
-    """Only the last 150 rows are coupled: the FP32 start solves that block
-    alone (its order is reported), the rest starts from unit vectors."""
-    d = G.clustered_spectrum(1100, seed=33)
-    A = G.near_diagonal_symmetric(d, 2e-7, top=150, top_coupling=0.05, seed=33)
+@pytest.mark.parametrize("n,top,repeats", [(1100, 150, 0), (1600, 150, 0), (1600, 150, 3)])
+def test_partial_start_for_a_coupled_top_block(n, top, repeats):
+    """Only the last `top` rows are coupled: the FP32 start solves that block
+    alone (its order is reported), the rest starts from unit vectors. With a
+    block of at most n/8 rows the first step's products and update come from
+    the block's rows and columns; `repeats` pairs of exactly equal, mutually
+    uncoupled diagonal entries outside the block form clusters in that step,
+    whose rows join the block of the update."""
+    d = G.clustered_spectrum(n, seed=33)
+    A = G.near_diagonal_symmetric(d, 2e-7, top=top, top_coupling=0.05, seed=33)
+    for r in range(repeats):
+        i, j = 100 + 40 * r, 101 + 40 * r
+        A[j, j] = A[i, i]
+        A[i, j] = A[j, i] = 0.0
     with tiny_ctx() as ctx:
         ctx.set_eigensolver("refined")
         w, V, st = solve(ctx, A, pad=1)
     ew, eo, er = check_against_oracle(A, w, V)
-    print(f"EIGH partial start: eig {ew:.1e} orth {eo:.1e} resid {er:.1e} {st}")
-    assert st["used"] == "refined" and st["fallback"] == 0 and 150 <= st["start_order"] <= 550
+    print(f"EIGH partial start n={n} repeats={repeats}: eig {ew:.1e} orth {eo:.1e} resid {er:.1e} {st}")
+    assert st["used"] == "refined" and st["fallback"] == 0 and top <= st["start_order"] <= n // 2
+    if repeats:
+        assert st["max_cluster"] >= 2
 
 
 def test_cycles_refined_vs_fp64_solver_on_projected_hamiltonians():

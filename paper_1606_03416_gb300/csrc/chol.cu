@@ -41,36 +41,42 @@ constexpr int kOwn = (kLeaf * (kLeaf + 1) / 2 + kLeafThreads - 1) / kLeafThreads
 
 // One CTA factors the n x n block (n <= 64) whose lower triangle is at A
 // (lda): L (lower) replaces it, the strict upper part is left as it was, and
-// Li (ldl) receives L^{-1} with its strict upper part zeroed. Each thread owns
-// up to kOwn entries of the lower triangle in registers (entry e = i(i+1)/2 + k
-// belongs to thread e mod 256). Step j of the factorisation publishes column
-// j to shared memory, and every owner of (i, k), j < k <= i, subtracts
-// M_ij M_kj / M_jj; column j is then divided by sqrt(M_jj). L^{-1} follows by
-// Gauss-Jordan elimination of W = I: step j publishes row j of W and column j
-// of L, row j is divided by L_jj, and rows i > j lose L_ij times it. The
-// shared rows and columns alternate between two buffers, so each step needs
-// one barrier. A pivot that is not positive and finite stops the block:
+// Li (ldl) receives L^{-1} with its strict upper part zeroed.
+// Factorisation: each thread owns up to kOwn entries of the lower triangle in
+// registers, numbered by column from the last one (entry e of column k, row
+// i, is e = (n-1-k)(n-k)/2 + i - k; thread e mod 256 owns it), so the
+// entries a step updates (columns after j) are a prefix of the numbering and
+// fill whole warps; one FP64 warp instruction occupies the SM's FP64 pipe for
+// many clocks, so half-empty warps cost as much as full ones. Step j
+// publishes column j, the pivot's owner also its root and reciprocals, and
+// every owner of (i, k), j < k <= i, subtracts M_ij M_kj / M_jj; column j is
+// then divided by sqrt(M_jj).
+// Inverse: L goes to shared memory, and W = L^{-1} follows by Gauss-Jordan
+// elimination of I with the entries of W owned by rows (e = i(i+1)/2 + k): step
+// j publishes row j of W, row j is divided by L_jj, rows i > j lose L_ij times
+// it. The shared rows and columns alternate between two buffers, so each step
+// needs one barrier. A pivot that is not positive and finite stops the block:
 // *info = col0 + j + 1 (1-based column of the whole matrix) if *info was 0.
 __global__ void __launch_bounds__(kLeafThreads, 1) k_chol_leaf(double* __restrict__ A, int64_t lda,
                                                               double* __restrict__ Li, int64_t ldl, int n,
                                                               int64_t col0, int* __restrict__ info) {
-  __shared__ double col[2][kLeaf], row[2][kLeaf];
+  __shared__ double col[2][kLeaf], row[2][kLeaf], rd[kLeaf];
+  __shared__ double Ls[kLeaf][kLeaf + 1];
   __shared__ double sc[2][4];  // the pivot, its square root and their reciprocals (one thread computes them)
   const int t = threadIdx.x;
   const int tot = n * (n + 1) / 2;
-  double v[kOwn], w[kOwn];
+  double v[kOwn];
   int rc[kOwn];  // (row << 8) | column of the entry, -1 for none
 #pragma unroll
   for (int q = 0; q < kOwn; ++q) {
     const int e = t + kLeafThreads * q;
-    int i = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-    while ((i + 1) * (i + 2) / 2 <= e) ++i;
-    while (i * (i + 1) / 2 > e) --i;
-    const int k = e - i * (i + 1) / 2;
+    int m = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);  // columns after this one: m = n - 1 - k
+    while ((m + 1) * (m + 2) / 2 <= e) ++m;
+    while (m * (m + 1) / 2 > e) --m;
+    const int k = n - 1 - m, i = k + (e - m * (m + 1) / 2);
     const bool ok = e < tot;
     rc[q] = ok ? (i << 8) | k : -1;
     v[q] = ok ? A[(int64_t)i * lda + k] : 0.0;
-    w[q] = (ok && i == k) ? 1.0 : 0.0;
   }
   for (int j = 0; j < n; ++j) {
     const int b = j & 1;
@@ -103,19 +109,37 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_chol_leaf(double* __restric
         v[q] -= col[b][i] * (col[b][k] * rp);
     }
   }
-  __syncthreads();  // the last factorisation step's readers are done with its buffer
+  // L to A and to shared memory; the reciprocals of its diagonal
+#pragma unroll
+  for (int q = 0; q < kOwn; ++q) {
+    if (rc[q] < 0) continue;
+    const int i = rc[q] >> 8, k = rc[q] & 255;
+    A[(int64_t)i * lda + k] = v[q];
+    Ls[i][k] = v[q];
+  }
+  __syncthreads();
+  if (t < n) rd[t] = 1.0 / Ls[t][t];
+  // W by rows: entry e = i(i+1)/2 + k
+  double w[kOwn];
+#pragma unroll
+  for (int q = 0; q < kOwn; ++q) {
+    const int e = t + kLeafThreads * q;
+    int i = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    while (i * (i + 1) / 2 > e) --i;
+    const int k = e - i * (i + 1) / 2;
+    const bool ok = e < tot;
+    rc[q] = ok ? (i << 8) | k : -1;
+    w[q] = (ok && i == k) ? 1.0 : 0.0;
+  }
+  __syncthreads();
   for (int j = 0; j < n; ++j) {
     const int b = j & 1;
 #pragma unroll
-    for (int q = 0; q < kOwn; ++q) {
-      if (rc[q] < 0) continue;
-      const int i = rc[q] >> 8, k = rc[q] & 255;
-      if (k == j) col[b][i] = v[q];  // column j of L (L_jj included)
-      if (i == j) row[b][k] = w[q];  // row j of W, before its division
-      if (i == j && k == j) sc[b][0] = 1.0 / v[q];
-    }
+    for (int q = 0; q < kOwn; ++q)
+      if (rc[q] >= 0 && (rc[q] >> 8) == j) row[b][rc[q] & 255] = w[q];  // row j of W, before its division
     __syncthreads();
-    const double rl = sc[b][0];
+    const double rl = rd[j];
 #pragma unroll
     for (int q = 0; q < kOwn; ++q) {
       if (rc[q] < 0) continue;
@@ -123,15 +147,13 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_chol_leaf(double* __restric
       if (i == j)
         w[q] *= rl;
       else if (i > j && k <= j)
-        w[q] -= col[b][i] * (row[b][k] * rl);
+        w[q] -= Ls[i][j] * (row[b][k] * rl);
     }
   }
 #pragma unroll
   for (int q = 0; q < kOwn; ++q) {
     if (rc[q] < 0) continue;
-    const int i = rc[q] >> 8, k = rc[q] & 255;
-    A[(int64_t)i * lda + k] = v[q];
-    Li[(int64_t)i * ldl + k] = w[q];
+    Li[(int64_t)(rc[q] >> 8) * ldl + (rc[q] & 255)] = w[q];
   }
   for (int e = t; e < n * n; e += kLeafThreads) {
     const int i = e / n, k = e % n;

@@ -692,6 +692,7 @@ def run_rr_only(args):
         ctx.set_subspace_products("sliced_bf16" if args.subspace == "sliced" else "f64", max(args.slices, 2))
         ctx.set_eigensolver(args.eigensolver)
         ctx.set_cholesky(args.cholesky)
+        ctx.set_refinement_start(args.start_coupling)
         b, tmin = ctx.bounds(torch.from_numpy(v0).to(dev), 10)
         X = torch.from_numpy(X0).to(dev)
         a, a0 = tmin + (b - tmin) * Ns / H.N, tmin
@@ -856,6 +857,8 @@ def main():
     ap.add_argument("--gram-only", action="store_true", help="time one FP64 Gram (profiling case)")
     ap.add_argument("--rr-only", action="store_true", help="one Rayleigh-Ritz step (profiling case)")
     ap.add_argument("--rr-cycles", type=int, default=0, help="--rr-only: mixed cycles run before the profiled step")
+    ap.add_argument("--start-coupling", type=float, default=0.001,
+                    help="first-order coupling that puts a row in the refined eigensolve's FP32 start block")
     ap.add_argument("--subspace", default="sliced", choices=["f64", "sliced"],
                     help="Rayleigh-Ritz products of the timed cycles (and of --rr-only)")
     ap.add_argument("--eigensolver", default="auto", choices=["auto", "syevd", "refined"],
@@ -920,6 +923,7 @@ def main():
     ctx.set_subspace_products(products, max(args.slices, 2))
     ctx.set_eigensolver(args.eigensolver)
     ctx.set_cholesky(args.cholesky)
+    ctx.set_refinement_start(args.start_coupling)
 
     def cycle(prec, X, Y, timers=None):
         """One CheFSI cycle via the public API; returns (ritz, new X buffer, spare buffer)."""

@@ -316,7 +316,8 @@ dgchefsi_status dgchefsi_cholesky_inverse(dgchefsi_ctx* ctx, double* S, int64_t 
  *   DGCHEFSI_EIG_REFINED  approximate eigenvectors refined to FP64 accuracy by
  *                         the iteration of Ogita and Aishima (2018). Start:
  *                         a row of H whose first-order couplings
- *                         |H_ij| / |H_jj - H_ii| are all below 1/100 starts
+ *                         |H_ij| / |H_jj - H_ii| are all below 1/1000 (see
+ *                         dgchefsi_set_refinement_start) starts
  *                         from its unit vector (a projected H of converging
  *                         CheFSI cycles is nearly diagonal); the block of the
  *                         other rows gets FP32 eigenvectors from cuSOLVER's
@@ -349,6 +350,20 @@ dgchefsi_status dgchefsi_set_eigensolver(dgchefsi_ctx* ctx, int mode);
  * ERR_NONFINITE on a NaN/Inf eigenvalue, ERR_ARG on bad sizes or pointers. */
 dgchefsi_status dgchefsi_subspace_eigh(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda, double* w);
 
+/* Start of the refined eigensolve: rows whose largest first-order coupling
+ * |H_ij| / |H_jj - H_ii| reaches `coupling` get FP32 eigenvectors of their
+ * block (cuSOLVER's single-precision solver) as the start, the others their
+ * unit vectors. 0 < coupling <= 1; default 0.001. A smaller value solves a
+ * larger block in FP32 and starts the rest closer to convergence (on the
+ * 8x8x8 CheFSI cycles 0.001 takes 3 steps where 0.01 takes 4). ERR_ARG
+ * outside (0, 1]. */
+dgchefsi_status dgchefsi_set_refinement_start(dgchefsi_ctx* ctx, double coupling);
+
+/* The largest correction of each step of the last refined eigensolve:
+ * corrections[0 .. min(count, cap)) (may be null), *count = the steps taken
+ * (at most 16 are kept). */
+dgchefsi_status dgchefsi_eigensolver_history(const dgchefsi_ctx* ctx, double* corrections, int cap, int* count);
+
 /* What the context's last eigensolve did (any pointer may be null):
  *   used         DGCHEFSI_EIG_SYEVD or DGCHEFSI_EIG_REFINED
  *   steps        refinement steps taken
@@ -361,7 +376,8 @@ dgchefsi_status dgchefsi_subspace_eigh(dgchefsi_ctx* ctx, double* A, int64_t n, 
  *   start_ms, refine_ms  host wall time of the start and of the refinement
  *   start_order  order of the block solved in FP32 for the start: n (the
  *                whole matrix), fewer (only the coupled rows), 0 (the
- *                identity: every first-order coupling below 1/100) */
+ *                identity: every first-order coupling below the start
+ *                threshold, dgchefsi_set_refinement_start) */
 dgchefsi_status dgchefsi_eigensolver_stats(const dgchefsi_ctx* ctx, int* used, int* steps, int* max_cluster,
                                            int* fallback, double* update, double* start_ms, double* refine_ms,
                                            int64_t* start_order);

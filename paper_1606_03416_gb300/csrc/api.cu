@@ -829,6 +829,23 @@ dgchefsi_status dgchefsi_sliced_timing(dgchefsi_ctx* ctx, double* pairs_ms, int6
   return DGCHEFSI_OK;
 }
 
+dgchefsi_status dgchefsi_set_refinement_start(dgchefsi_ctx* ctx, double coupling) {
+  clear_error();
+  if (!ctx) return set_error(DGCHEFSI_ERR_ARG, "null context");
+  if (!(coupling > 0.0 && coupling <= 1.0)) return set_error(DGCHEFSI_ERR_ARG, "coupling threshold outside (0, 1]");
+  ctx->eig_start_coupling = coupling;
+  return DGCHEFSI_OK;
+}
+
+dgchefsi_status dgchefsi_eigensolver_history(const dgchefsi_ctx* ctx, double* corrections, int cap, int* count) {
+  clear_error();
+  DG_TRY(check_ctx(ctx));
+  const int k = std::min(ctx->eig_steps, 16);
+  if (count) *count = k;
+  for (int i = 0; corrections && i < std::min(k, cap); ++i) corrections[i] = ctx->eig_history[i];
+  return DGCHEFSI_OK;
+}
+
 dgchefsi_status dgchefsi_set_cholesky(dgchefsi_ctx* ctx, int mode) {
   clear_error();
   if (!ctx) return set_error(DGCHEFSI_ERR_ARG, "null context");

@@ -78,6 +78,8 @@ struct dgchefsi_ctx {
   int eig_used = 0, eig_steps = 0, eig_max_cluster = 0, eig_fallback = 0;
   double eig_update = 0.0, eig_start_ms = 0.0, eig_refine_ms = 0.0;
   int64_t eig_start_order = 0;
+  double eig_history[16] = {};  // largest correction of each refinement step
+  double eig_start_coupling = 0.001;  // first-order coupling that puts a row in the FP32 start block
   dg::DevBuf ws_eig;
   // Cholesky factorisation of step 3 (DGCHEFSI_CHOL_*) and the recursive
   // form's workspace (L^{-1} and two scratch blocks, 3 N_s^2 doubles)

@@ -571,13 +571,13 @@ dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda
   int* bad = ws.cnt + 2;
   const auto t0 = Clock::now();
 
-  // Start. Rows whose first-order couplings are all below 1/kappa start
-  // from their unit vector; the block of the other rows is solved in FP32
+  // Start. Rows whose first-order couplings are all below the context's start
+  // threshold (0.001 by default) start from their unit vector; the block of the other rows is solved in FP32
   // (cuSOLVER's single-precision solver) and its eigenvectors placed on those
   // rows. When more than half the rows are coupled (a first projected H, a
   // matrix without structure) the whole matrix is solved in FP32.
   k_mirror_lower<<<grid_for(nn), 256, 0, st>>>(A, lda, n);
-  k_row_coupling<<<(unsigned)std::min<int64_t>(n, 1 << 16), 256, 0, st>>>(A, lda, n, 1.0 / kKappa, 0.0, ws.cl,
+  k_row_coupling<<<(unsigned)std::min<int64_t>(n, 1 << 16), 256, 0, st>>>(A, lda, n, ctx->eig_start_coupling, 0.0, ws.cl,
                                                                          ws.lam);
   count_launch(2);
   DG_CUDA(cudaGetLastError());
@@ -791,6 +791,7 @@ dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda
     std::memcpy(&emax, &eb, sizeof(emax));
     ctx->eig_steps = step + 1;
     ctx->eig_update = emax;
+    if (step < 16) ctx->eig_history[step] = emax;
     if (!(emax < 1.0)) {
       *reason = 4;
       return DGCHEFSI_OK;
@@ -875,6 +876,7 @@ dgchefsi_status subspace_eigh(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t l
   ctx->eig_update = 0.0;
   ctx->eig_start_ms = ctx->eig_refine_ms = 0.0;
   ctx->eig_start_order = 0;
+  for (double& h : ctx->eig_history) h = 0.0;
   ctx->eig_used = DGCHEFSI_EIG_SYEVD;
   if (n <= 0) return DGCHEFSI_OK;
   int mode = ctx->eig_mode;

@@ -34,7 +34,7 @@ EXPORTS = ["dgchefsi_create", "dgchefsi_destroy", "dgchefsi_set_stream", "dgchef
            "dgchefsi_sliced_gemm", "dgchefsi_sliced_matvec", "dgchefsi_set_unit_order",
            "dgchefsi_get_unit_order", "dgchefsi_sliced_timing", "dgchefsi_set_eigensolver",
            "dgchefsi_subspace_eigh", "dgchefsi_eigensolver_stats", "dgchefsi_set_cholesky",
-           "dgchefsi_cholesky_inverse"]
+           "dgchefsi_cholesky_inverse", "dgchefsi_set_refinement_start", "dgchefsi_eigensolver_history"]
 
 # Orthonormalisations of Alg. 1 step 3 (dgchefsi_set_orthonormalisation).
 ORTHONORMALISATIONS = {"cholqr": 0, "cholqr2": 1, "shifted_cholqr3": 2}
@@ -90,6 +90,8 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_sliced_timing": (st, [P, P, P]),
         "dgchefsi_set_eigensolver": (st, [P, C.c_int]),
         "dgchefsi_set_cholesky": (st, [P, C.c_int]),
+        "dgchefsi_set_refinement_start": (st, [P, D]),
+        "dgchefsi_eigensolver_history": (st, [P, P, C.c_int, P]),
         "dgchefsi_cholesky_inverse": (st, [P, P, I64, I64]),
         "dgchefsi_subspace_eigh": (st, [P, P, I64, I64, P]),
         "dgchefsi_eigensolver_stats": (st, [P, P, P, P, P, P, P, P, P]),
@@ -413,9 +415,18 @@ class Context:
         order = C.c_int64()
         _check(_lib.dgchefsi_eigensolver_stats(self._h, *[C.byref(x) for x in i], *[C.byref(x) for x in d],
                                                C.byref(order)))
+        hist = (C.c_double * 16)()
+        cnt = C.c_int()
+        _check(_lib.dgchefsi_eigensolver_history(self._h, hist, 16, C.byref(cnt)))
         return {"used": EIGENSOLVER_NAMES.get(i[0].value, i[0].value), "steps": i[1].value,
                 "max_cluster": i[2].value, "fallback": i[3].value, "update": d[0].value,
-                "start_ms": d[1].value, "refine_ms": d[2].value, "start_order": order.value}
+                "start_ms": d[1].value, "refine_ms": d[2].value, "start_order": order.value,
+                "history": [hist[k] for k in range(cnt.value)]}
+
+    def set_refinement_start(self, coupling: float = 0.001):
+        """First-order coupling at which a row joins the FP32 start block of
+        the refined eigensolve (default 0.001)."""
+        _check(_lib.dgchefsi_set_refinement_start(self._h, float(coupling)))
 
     def sliced_timing(self):
         """(ms, launches) of the slice-pair kernel in the last dense sliced product."""

@@ -134,10 +134,10 @@ def test_auto_follows_subspace_products():
 
 
 def test_identity_start_for_a_nearly_diagonal_matrix():
-    """Every first-order coupling below 1/100: no FP32 solve, the first step
+    """Every first-order coupling below 1/1000: no FP32 solve, the first step
     needs no products, and the result is the oracle's."""
     d = G.clustered_spectrum(1200, seed=31)
-    A = G.near_diagonal_symmetric(d, 1e-9, seed=31)
+    A = G.near_diagonal_symmetric(d, 1e-10, seed=31)
     with tiny_ctx() as ctx:
         ctx.set_eigensolver("refined")
         w, V, st = solve(ctx, A)
@@ -148,6 +148,8 @@ def test_identity_start_for_a_nearly_diagonal_matrix():
 
 @pytest.mark.parametrize("n,top,repeats", [(1100, 150, 0), (1600, 150, 0), (1600, 150, 3)])
 def test_partial_start_for_a_coupled_top_block(n, top, repeats):
+    # with 2e-8 background coupling 156 (n = 1100) and 160 (n = 1600) rows reach
+    # the default start threshold: the full and the block-structured first step
     """Only the last `top` rows are coupled: the FP32 start solves that block
     alone (its order is reported), the rest starts from unit vectors. With a
     block of at most n/8 rows the first step's products and update come from
@@ -155,7 +157,7 @@ def test_partial_start_for_a_coupled_top_block(n, top, repeats):
     uncoupled diagonal entries outside the block form clusters in that step,
     whose rows join the block of the update."""
     d = G.clustered_spectrum(n, seed=33)
-    A = G.near_diagonal_symmetric(d, 2e-7, top=top, top_coupling=0.05, seed=33)
+    A = G.near_diagonal_symmetric(d, 2e-8, top=top, top_coupling=0.05, seed=33)
     for r in range(repeats):
         i, j = 100 + 40 * r, 101 + 40 * r
         A[j, j] = A[i, i]

@@ -295,7 +295,8 @@ dgchefsi_status dgchefsi_set_subspace_products(dgchefsi_ctx* ctx, int mode, int 
 #define DGCHEFSI_CHOL_PRODUCTS 2
 dgchefsi_status dgchefsi_set_cholesky(dgchefsi_ctx* ctx, int mode);
 
-/* S = U^T U (row-major lower view: S = L L^T, L = U^T) with the context's
+/* S = U^T U (Alg. 1 step 3, Sec. III.B.2: the Cholesky factor of the Gram
+ * matrix; row-major lower view: S = L L^T, L = U^T) with the context's
  * Cholesky form, and the inverse factor:
  *   S  device row-major n x n (lda >= n): in, the lower triangle holds the
  *      symmetric positive definite S (the upper one is not read); out, the
@@ -341,7 +342,8 @@ dgchefsi_status dgchefsi_cholesky_inverse(dgchefsi_ctx* ctx, double* S, int64_t 
 #define DGCHEFSI_EIG_REFINED 2
 dgchefsi_status dgchefsi_set_eigensolver(dgchefsi_ctx* ctx, int mode);
 
-/* Eigen-decomposition H Q = Q D of a symmetric H with the context's eigensolver:
+/* Eigen-decomposition H Q = Q D of a symmetric H (Alg. 1 step 4, the dense
+ * eigensolve of the projected Hamiltonian) with the context's eigensolver:
  *   A  device row-major n x n (lda >= n): in, the lower triangle holds H (the
  *      upper one is not read and may be overwritten); out, row i is the unit
  *      eigenvector of w[i]
@@ -350,18 +352,18 @@ dgchefsi_status dgchefsi_set_eigensolver(dgchefsi_ctx* ctx, int mode);
  * ERR_NONFINITE on a NaN/Inf eigenvalue, ERR_ARG on bad sizes or pointers. */
 dgchefsi_status dgchefsi_subspace_eigh(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda, double* w);
 
-/* Start of the refined eigensolve: rows whose largest first-order coupling
- * |H_ij| / |H_jj - H_ii| reaches `coupling` get FP32 eigenvectors of their
- * block (cuSOLVER's single-precision solver) as the start, the others their
- * unit vectors. 0 < coupling <= 1; default 0.001. A smaller value solves a
+/* Start of the refined eigensolve (Alg. 1 step 4): rows whose largest
+ * first-order coupling |H_ij| / |H_jj - H_ii| reaches `coupling` get FP32
+ * eigenvectors of their block (cuSOLVER's single-precision solver) as the
+ * start, the others their unit vectors. 0 < coupling <= 1; default 0.001. A smaller value solves a
  * larger block in FP32 and starts the rest closer to convergence (on the
  * 8x8x8 CheFSI cycles 0.001 takes 3 steps where 0.01 takes 4). ERR_ARG
  * outside (0, 1]. */
 dgchefsi_status dgchefsi_set_refinement_start(dgchefsi_ctx* ctx, double coupling);
 
-/* The largest correction of each step of the last refined eigensolve:
- * corrections[0 .. min(count, cap)) (may be null), *count = the steps taken
- * (at most 16 are kept). */
+/* The largest correction of each step of the last refined eigensolve
+ * (Alg. 1 step 4): corrections[0 .. min(count, cap)) (may be null), *count =
+ * the steps taken (at most 16 are kept). */
 dgchefsi_status dgchefsi_eigensolver_history(const dgchefsi_ctx* ctx, double* corrections, int cap, int* count);
 
 /* What the context's last eigensolve did (any pointer may be null):

@@ -15,17 +15,33 @@
 //   X <- X (I + E).
 // These are the first-order conditions for X (I + E) to be orthonormal
 // (E + E^T = I - G) and to diagonalise A; the error falls quadratically
-// while every |e_ij| stays small. Pairs whose first-order correction would
-// not be small (|lambda_j - lambda_i| <= kappa |S_ij - lambda_j G_ij|, or a
-// gap at the rounding level) are joined into clusters (connected
-// components). The columns of a cluster C are first rotated exactly:
-// X_C <- X_C W with W = (I + R/2) Q, R = I - G_CC and Q the eigenvectors of
-// M = S_CC + (R S_CC + S_CC R) / 2 (first order of G_CC^{-1/2} S_CC G_CC^{-1/2}),
-// found by cyclic Jacobi (Golub and Van Loan, Matrix Computations, 4th ed.,
-// Sec. 8.5). Inside a cluster e_ij = (I - G)_ij / 2 then keeps X orthonormal.
+// while every |e_ij| stays small. The coefficients are formed from the
+// symmetrised G and S, so E + E^T = I - G holds over any gap; a coupling at
+// the rounding level of the products (below kNoise u ||A||) over a gap too
+// small to rotate safely gets only the orthonormalisation term.
+// Pairs whose first-order correction would not be small
+// (|lambda_j - lambda_i| <= kappa |S_ij - lambda_j G_ij|, or a gap at the
+// rounding level) are joined into clusters: connected components, widened to
+// the range of Rayleigh quotients they span. The columns of a cluster C are
+// first rotated exactly: X_C <- X_C W with W = (I + R/2) Q, R = I - G_CC and
+// Q the eigenvectors of M = S_CC + (R S_CC + S_CC R) / 2 (first order of
+// G_CC^{-1/2} S_CC G_CC^{-1/2}), found by cyclic Jacobi (Golub and Van Loan,
+// Matrix Computations, 4th ed., Sec. 8.5). Inside a cluster
+// e_ij = (I - G)_ij / 2 then keeps X orthonormal.
 //
-// Products per step: T = V A, [G; S] = [V; T] V^T (one call, 2n x n) and
-// the update V <- V + E^T V, all n x n x n on the slice-pair kernel.
+// Start: a row of A whose first-order couplings |A_ij| / |A_jj - A_ii| all
+// stay below the context's start threshold begins as its unit vector (a
+// projected H of converging CheFSI cycles is nearly diagonal); the block of
+// the other rows gets FP32 eigenvectors (cuSOLVER's single-precision solver),
+// the whole matrix when more than half the rows are in it. With V = I the
+// first step needs no products; with V = I outside a block of at most n/8
+// rows, only small FP64 products on the block's rows and columns.
+//
+// Products per later step: T = V A, [G; S] = [V; T] V^T (one call, 2n x n,
+// lower triangles) and the update V <- V + E^T V, all n x n x n on the
+// slice-pair kernel. Stop after the step whose largest correction is at most
+// kStop, or whose correction, at the quadratic rate seen over the last two
+// steps, predicts the next one below kPredict.
 
 #include <algorithm>
 #include <cfloat>
@@ -462,7 +478,8 @@ namespace {
 // cuSOLVER's FP64 divide-and-conquer on the lower triangle (row-major) of A;
 // its info goes to ctx->info_d[2].
 dgchefsi_status eig_syevd(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda, double* w) {
-  if (n > INT32_MAX || lda > INT32_MAX) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "eigensolve of order %lld", (long long)n);
+  if (n > INT32_MAX || lda > INT32_MAX)
+    return set_error(DGCHEFSI_ERR_UNSUPPORTED, "eigensolve of order %lld", (long long)n);
   EIG_SOLVER(cusolverDnSetStream(ctx->solver, ctx->stream));
   int lw = 0;
   EIG_SOLVER(cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)n, A,
@@ -557,7 +574,8 @@ double ms_since(Clock::time_point t) { return std::chrono::duration<double, std:
 // finite or not below 1, 5 no convergence in kMaxSteps steps.
 dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda, double* w, int* reason) {
   *reason = 0;
-  if (n > INT32_MAX / 2 || lda > INT32_MAX) return set_error(DGCHEFSI_ERR_UNSUPPORTED, "eigensolve of order %lld", (long long)n);
+  if (n > INT32_MAX / 2 || lda > INT32_MAX)
+    return set_error(DGCHEFSI_ERR_UNSUPPORTED, "eigensolve of order %lld", (long long)n);
   cudaStream_t st = ctx->stream;
   const int s = std::max(ctx->products_slices, 10);
   EigWs ws = eig_layout(n, nullptr);
@@ -571,14 +589,15 @@ dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda
   int* bad = ws.cnt + 2;
   const auto t0 = Clock::now();
 
-  // Start. Rows whose first-order couplings are all below the context's start
-  // threshold (0.001 by default) start from their unit vector; the block of the other rows is solved in FP32
-  // (cuSOLVER's single-precision solver) and its eigenvectors placed on those
-  // rows. When more than half the rows are coupled (a first projected H, a
-  // matrix without structure) the whole matrix is solved in FP32.
+  // Start. Rows whose first-order couplings are all below the context's
+  // start threshold (0.001 by default) start from their unit vector; the
+  // block of the other rows is solved in FP32 (cuSOLVER's single-precision
+  // solver) and its eigenvectors placed on those rows. When more than half
+  // the rows are coupled (a first projected H, a matrix without structure)
+  // the whole matrix is solved in FP32.
   k_mirror_lower<<<grid_for(nn), 256, 0, st>>>(A, lda, n);
-  k_row_coupling<<<(unsigned)std::min<int64_t>(n, 1 << 16), 256, 0, st>>>(A, lda, n, ctx->eig_start_coupling, 0.0, ws.cl,
-                                                                         ws.lam);
+  k_row_coupling<<<(unsigned)std::min<int64_t>(n, 1 << 16), 256, 0, st>>>(A, lda, n, ctx->eig_start_coupling, 0.0,
+                                                                         ws.cl, ws.lam);
   count_launch(2);
   DG_CUDA(cudaGetLastError());
   std::vector<int> flag_h(n);

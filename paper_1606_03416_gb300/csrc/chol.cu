@@ -32,7 +32,9 @@ namespace {
 // rows of a block factored by one CTA. A leaf runs on one SM, which does two
 // FP64 multiply-adds per clock, and its ~2 kLeaf^3 / 3 of them are serial
 // across the leaves: 64 keeps that near 3 ms at n = 4096 (128 took 4 ms per
-// leaf), the levels above run over the whole GPU
+// leaf; 32 gave the same Rayleigh-Ritz time as 64, the extra level of small
+// products taking what the smaller leaves save), the levels above run over
+// the whole GPU
 constexpr int kLeaf = 64;
 constexpr int64_t kSliced = 512;  // smallest product side run from slices
 constexpr int kLeafThreads = 256;
@@ -330,7 +332,7 @@ struct Chol {
       return DGCHEFSI_OK;
     }
     // split on a multiple of the leaf (of 256 once blocks are large), near the middle
-    const int64_t q = m >= 1024 ? 256 : 64;
+    const int64_t q = m >= 1024 ? 256 : kLeaf;
     const int64_t m1 = std::max<int64_t>(q, (m / 2 + q / 2) / q * q);
     const int64_t m2 = m - m1;
     DG_TRY(block(i0, m1));

@@ -927,7 +927,7 @@ dgchefsi_status dgchefsi_subspace_eigh(dgchefsi_ctx* ctx, double* A, int64_t n, 
 
 dgchefsi_status dgchefsi_eigensolver_stats(const dgchefsi_ctx* ctx, int* used, int* steps, int* max_cluster,
                                            int* fallback, double* update, double* start_ms, double* refine_ms,
-                                           int64_t* start_order) {
+                                           int64_t* start_order, int* start_solver) {
   clear_error();
   DG_TRY(check_ctx(ctx));
   if (used) *used = ctx->eig_used;
@@ -938,6 +938,7 @@ dgchefsi_status dgchefsi_eigensolver_stats(const dgchefsi_ctx* ctx, int* used, i
   if (start_ms) *start_ms = ctx->eig_start_ms;
   if (refine_ms) *refine_ms = ctx->eig_refine_ms;
   if (start_order) *start_order = ctx->eig_start_order;
+  if (start_solver) *start_solver = ctx->eig_start_solver;
   return DGCHEFSI_OK;
 }
 

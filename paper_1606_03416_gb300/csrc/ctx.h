@@ -78,6 +78,7 @@ struct dgchefsi_ctx {
   int eig_used = 0, eig_steps = 0, eig_max_cluster = 0, eig_fallback = 0;
   double eig_update = 0.0, eig_start_ms = 0.0, eig_refine_ms = 0.0;
   int64_t eig_start_order = 0;
+  int eig_start_solver = 0;  // 0 none (identity start), 1 this library's Jacobi kernel, 2 cuSOLVER FP32
   double eig_history[16] = {};  // largest correction of each refinement step
   double eig_start_coupling = 0.001;  // first-order coupling that puts a row in the FP32 start block
   dg::DevBuf ws_eig;

@@ -346,6 +346,172 @@ __global__ void __launch_bounds__(256) k_update_coeffs(const double* __restrict_
   }
 }
 
+// FP32 eigenvectors of a small symmetric block by cyclic Jacobi (Golub and
+// Van Loan, Matrix Computations, 4th ed., Sec. 8.5.5: the parallel ordering).
+// B (m x m, m <= kJacobiMax, in: the block; the lower triangle is read); W
+// (m x m, out) the eigenvectors as rows (W[k * m + l]: component l of vector
+// k, the layout the scatter into V expects); w[k] the eigenvalues
+// (unordered). Each round rotates M/2 disjoint index pairs at once, the
+// round-robin tournament over M = m rounded up to even indices (index m, when
+// m is odd, is idle): pairs (pos_k, pos_{M-1-k}) with pos_0 = 0, pos_i = 1 +
+// (i - 1 + r) mod (M - 1). A rotation zeroes B_pq: tau = (B_qq - B_pp) /
+// (2 B_pq), t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2),
+// s = t c; B <- R^T B R and W <- R^T W with columns p, q of R equal to
+// (c e_p - s e_q, s e_p + c e_q). Because the pairs of a round are disjoint,
+// the 2 x 2 block of B on rows of pair k and columns of pair l receives
+// exactly the column rotation of l and then the row rotation of k, so one
+// pass over the blocks applies the whole round; only the blocks with l >= k
+// are computed, each written with its mirror. After each sweep (M - 1
+// rounds) the off-diagonal part is measured; the sweeps stop once its squared
+// Frobenius norm is below 2^-32 of the whole (2^-16 in norm: near FP32
+// rounding, a start for the FP64 refinement) or after 40.
+// Every CTA of the grid runs the same iteration on its own copy of B (the
+// arithmetic and its order are identical, so are the rotations) and keeps
+// components [c0, c0 + cw) of the vectors, cw = ceil(m / gridDim.x), in
+// shared memory: B and a slab of W fit one SM's shared memory up to m = 224.
+constexpr int kJacobiMax = 224;
+constexpr int kJacobiThreads = 1024;
+constexpr int kJacobiCtas = 8;
+constexpr int kJacobiChunks = (kJacobiMax / 2 + 31) / 32;  // 32-wide chunks of the pair index
+
+__global__ void __launch_bounds__(kJacobiThreads, 1) k_block_jacobi(const float* __restrict__ B, int m,
+                                                                    float* __restrict__ W, float* __restrict__ w) {
+  extern __shared__ float sm_j[];
+  __shared__ float cs[kJacobiMax / 2], sn[kJacobiMax / 2];
+  __shared__ int pp[kJacobiMax / 2], qq[kJacobiMax / 2];
+  __shared__ float red[2][kJacobiThreads / 32];
+  __shared__ int done;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+  const int cw = (m + (int)gridDim.x - 1) / (int)gridDim.x, c0 = (int)blockIdx.x * cw;
+  const int ld = m | 1;       // odd: the mirrored (column) writes spread over the banks
+  float* As = sm_j;           // m x ld, row-major
+  float* Ws = sm_j + m * ld;  // m x cw: components c0 .. c0 + cw - 1 of every vector
+  const int M = m + (m & 1), half = M / 2;
+  for (int i = warp; i < m; i += nw) {
+    for (int j = lane; j < m; j += 32) As[i * ld + j] = j <= i ? B[i * m + j] : B[j * m + i];
+    for (int j = lane; j < cw; j += 32) Ws[i * cw + j] = c0 + j == i ? 1.0f : 0.0f;
+  }
+  if (t == 0) done = 0;
+  __syncthreads();
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    for (int r = 0; r < M - 1; ++r) {
+      if (t < half) {  // pair t of this round and its rotation
+        const int pa = t == 0 ? 0 : 1 + (t - 1 + r) % (M - 1);
+        const int k2 = M - 1 - t;
+        const int pb = k2 == 0 ? 0 : 1 + (k2 - 1 + r) % (M - 1);
+        const int p = min(pa, pb), q = max(pa, pb);
+        float c = 1.0f, sv = 0.0f;
+        if (q < m) {
+          const float apq = As[q * ld + p];
+          if (apq != 0.0f) {
+            const float tau = (As[q * ld + q] - As[p * ld + p]) / (2.0f * apq);
+            const float tt = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+            c = 1.0f / sqrtf(1.0f + tt * tt);
+            sv = tt * c;
+          }
+        }
+        pp[t] = p;
+        qq[t] = q < m ? q : p;  // a pair with the idle index rotates nothing
+        cs[t] = c;
+        sn[t] = q < m ? sv : 0.0f;
+      }
+      __syncthreads();
+      // block (k, l), l >= k: rows pp[k], qq[k] x columns pp[l], qq[l],
+      // written with its mirror (B stays exactly symmetric); warp w takes
+      // k = w, w + nw, ... and lane j the l = 32 c + j of chunk c, whose
+      // pair values it holds in registers for the whole round
+      int pl[kJacobiChunks], ql[kJacobiChunks];
+      float cl[kJacobiChunks], sl[kJacobiChunks];
+#pragma unroll
+      for (int c = 0; c < kJacobiChunks; ++c) {
+        const int l = c * 32 + lane;
+        const bool on = l < half;
+        pl[c] = on ? pp[l] : 0;
+        ql[c] = on ? qq[l] : 0;
+        cl[c] = on ? cs[l] : 1.0f;
+        sl[c] = on ? sn[l] : 0.0f;
+      }
+      for (int k = warp; k < half; k += nw) {
+        const int pk = pp[k], qk = qq[k];
+        const float ck = cs[k], sk = sn[k];
+        const bool krot = qk != pk;
+#pragma unroll
+        for (int c = 0; c < kJacobiChunks; ++c) {
+          const int l = c * 32 + lane;
+          if (l < k || l >= half) continue;
+          const bool lrot = ql[c] != pl[c];
+          const float a = As[pk * ld + pl[c]], b = As[pk * ld + ql[c]];
+          const float d = As[qk * ld + pl[c]], e = As[qk * ld + ql[c]];
+          const float a1 = cl[c] * a - sl[c] * b, b1 = sl[c] * a + cl[c] * b;
+          const float d1 = cl[c] * d - sl[c] * e, e1 = sl[c] * d + cl[c] * e;
+          const float a2 = ck * a1 - sk * d1, b2 = ck * b1 - sk * e1;
+          const float d2 = sk * a1 + ck * d1, e2 = sk * b1 + ck * e1;
+          if (l == k) {  // the pair's own 2 x 2 block
+            As[pk * ld + pk] = a2;
+            if (krot) {
+              As[pk * ld + qk] = b2;
+              As[qk * ld + pk] = b2;
+              As[qk * ld + qk] = e2;
+            }
+            continue;
+          }
+          As[pk * ld + pl[c]] = a2;
+          As[pl[c] * ld + pk] = a2;
+          if (lrot) {
+            As[pk * ld + ql[c]] = b2;
+            As[ql[c] * ld + pk] = b2;
+          }
+          if (krot) {
+            As[qk * ld + pl[c]] = d2;
+            As[pl[c] * ld + qk] = d2;
+            if (lrot) {
+              As[qk * ld + ql[c]] = e2;
+              As[ql[c] * ld + qk] = e2;
+            }
+          }
+        }
+        if (krot)  // rows pk, qk of the W slab
+          for (int j = lane; j < cw; j += 32) {
+            const float vp = Ws[pk * cw + j], vq = Ws[qk * cw + j];
+            Ws[pk * cw + j] = ck * vp - sk * vq;
+            Ws[qk * cw + j] = sk * vp + ck * vq;
+          }
+      }
+      __syncthreads();
+    }
+    float off = 0.0f, tot = 0.0f;
+    for (int i = warp; i < m; i += nw)
+      for (int j = lane; j < m; j += 32) {
+        const float a = As[i * ld + j];
+        tot += a * a;
+        if (i != j) off += a * a;
+      }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if (lane == 0) {
+      red[0][warp] = off;
+      red[1][warp] = tot;
+    }
+    __syncthreads();
+    if (t == 0) {
+      float so = 0.0f, st = 0.0f;
+      for (int k = 0; k < nw; ++k) {
+        so += red[0][k];
+        st += red[1][k];
+      }
+      done = !(so > 0x1p-32f * st);  // also ends on NaN
+    }
+    __syncthreads();
+    if (done) break;
+  }
+  if (blockIdx.x == 0)
+    for (int i = t; i < m; i += blockDim.x) w[i] = As[i * ld + i];
+  for (int i = warp; i < m; i += nw)
+    for (int j = lane; j < cw && c0 + j < m; j += 32) W[(int64_t)i * m + c0 + j] = Ws[i * cw + j];
+}
+
 // Start selection. Row i of A (symmetric, both triangles valid) is coupled
 // when some j != i has a first-order correction |A_ij| / |A_jj - A_ii| of at
 // least tau, i.e. |A_ij| >= tau |A_jj - A_ii|, with |A_ij| above the rounding
@@ -612,6 +778,7 @@ dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda
     if (flag_h[i]) rows.push_back((int)i);
   const bool full = (int64_t)rows.size() * 2 > n;
   const int64_t m = full ? n : (int64_t)rows.size();
+  float* W32 = ws.A32;  // the start block's FP32 eigenvectors, one per row
   ctx->eig_start_order = m;
   if (m > 0) {
     if (full) {
@@ -623,21 +790,36 @@ dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda
     }
     count_launch();
     DG_CUDA(cudaGetLastError());
-    EIG_SOLVER(cusolverDnSetStream(ctx->solver, st));
-    int lw = 0;
-    EIG_SOLVER(cusolverDnSsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)m,
-                                           ws.A32, (int)m, ws.w32, &lw));
-    DG_TRY(ensure(ctx, ctx->ws_solver, sizeof(float) * (size_t)lw, "cuSOLVER workspace"));
     DG_CUDA(cudaMemsetAsync(ws.cnt, 0, 4 * sizeof(int), st));
-    EIG_SOLVER(cusolverDnSsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)m, ws.A32, (int)m,
-                                ws.w32, static_cast<float*>(ctx->ws_solver.p),
-                                (int)(ctx->ws_solver.bytes / sizeof(float)), ws.cnt + 1));
-    // column-major eigenvectors read row-major: one eigenvector per row
+    if (!full && m <= kJacobiMax) {
+      // a small block: this library's Jacobi kernel, eigenvectors after the block
+      W32 = ws.A32 + m * m;
+      const int ctas = (int)std::min<int64_t>(kJacobiCtas, m);
+      const int64_t cw = (m + ctas - 1) / ctas;
+      const int smem = (int)(sizeof(float) * (m * (m | 1) + m * cw));
+      DG_CUDA(cudaFuncSetAttribute(k_block_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      k_block_jacobi<<<ctas, kJacobiThreads, smem, st>>>(ws.A32, (int)m, W32, ws.w32);
+      count_launch();
+      DG_CUDA(cudaGetLastError());
+      ctx->eig_start_solver = 1;
+    } else {
+      EIG_SOLVER(cusolverDnSetStream(ctx->solver, st));
+      int lw = 0;
+      EIG_SOLVER(cusolverDnSsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)m,
+                                             ws.A32, (int)m, ws.w32, &lw));
+      DG_TRY(ensure(ctx, ctx->ws_solver, sizeof(float) * (size_t)lw, "cuSOLVER workspace"));
+      EIG_SOLVER(cusolverDnSsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)m, ws.A32,
+                                  (int)m, ws.w32, static_cast<float*>(ctx->ws_solver.p),
+                                  (int)(ctx->ws_solver.bytes / sizeof(float)), ws.cnt + 1));
+      ctx->eig_start_solver = 2;
+    }
+    // column-major eigenvectors read row-major (the Jacobi kernel writes rows):
+    // one eigenvector per row
     if (full) {
       k_f32_to_f64<<<grid_for(nn), 256, 0, st>>>(ws.A32, nn, V);
     } else {
       k_identity<<<grid_for(nn), 256, 0, st>>>(V, n);
-      k_scatter_block<<<grid_for(m * m), 256, 0, st>>>(V, n, ws.idx, m, ws.A32);
+      k_scatter_block<<<grid_for(m * m), 256, 0, st>>>(V, n, ws.idx, m, W32);
     }
     count_launch(full ? 1 : 2);
     DG_CUDA(cudaGetLastError());
@@ -686,7 +868,7 @@ dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda
       double* Wb = T;             // m x m
       double* R1 = T + m * m;     // m x n, then n x m, then m x m
       double* R2 = R1 + m * n;    // m x n, then n x m
-      k_f32_to_f64<<<grid_for(m * m), 256, 0, st>>>(ws.A32, m * m, Wb);
+      k_f32_to_f64<<<grid_for(m * m), 256, 0, st>>>(W32, m * m, Wb);
       k_identity_products<<<grid_for(nn), 256, 0, st>>>(A, lda, n, Gm, Sm);
       k_gather_rows_of<<<grid_for(m * n), 256, 0, st>>>(A, lda, ws.perm, m, n, R1);
       count_launch(3);
@@ -895,6 +1077,7 @@ dgchefsi_status subspace_eigh(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t l
   ctx->eig_update = 0.0;
   ctx->eig_start_ms = ctx->eig_refine_ms = 0.0;
   ctx->eig_start_order = 0;
+  ctx->eig_start_solver = 0;
   for (double& h : ctx->eig_history) h = 0.0;
   ctx->eig_used = DGCHEFSI_EIG_SYEVD;
   if (n <= 0) return DGCHEFSI_OK;

@@ -94,7 +94,7 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_eigensolver_history": (st, [P, P, C.c_int, P]),
         "dgchefsi_cholesky_inverse": (st, [P, P, I64, I64]),
         "dgchefsi_subspace_eigh": (st, [P, P, I64, I64, P]),
-        "dgchefsi_eigensolver_stats": (st, [P, P, P, P, P, P, P, P, P]),
+        "dgchefsi_eigensolver_stats": (st, [P, P, P, P, P, P, P, P, P, P]),
         "dgchefsi_density_pattern": (st, [P, P, I64, I64, P, P]),
         "dgchefsi_realign": (st, [P, P, P, P, P, P, I64, I64, P, I64]),
         "dgchefsi_filter_host": (st, [P, C.c_int, P, P, I64, I64, C.c_int, D, D, D, I64]),
@@ -413,14 +413,16 @@ class Context:
         i = [C.c_int() for _ in range(4)]
         d = [C.c_double() for _ in range(3)]
         order = C.c_int64()
+        solver = C.c_int()
         _check(_lib.dgchefsi_eigensolver_stats(self._h, *[C.byref(x) for x in i], *[C.byref(x) for x in d],
-                                               C.byref(order)))
+                                               C.byref(order), C.byref(solver)))
         hist = (C.c_double * 16)()
         cnt = C.c_int()
         _check(_lib.dgchefsi_eigensolver_history(self._h, hist, 16, C.byref(cnt)))
         return {"used": EIGENSOLVER_NAMES.get(i[0].value, i[0].value), "steps": i[1].value,
                 "max_cluster": i[2].value, "fallback": i[3].value, "update": d[0].value,
                 "start_ms": d[1].value, "refine_ms": d[2].value, "start_order": order.value,
+                "start_solver": {0: "none", 1: "jacobi", 2: "cusolver_fp32"}.get(solver.value, solver.value),
                 "history": [hist[k] for k in range(cnt.value)]}
 
     def set_refinement_start(self, coupling: float = 0.001):

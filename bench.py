@@ -964,8 +964,11 @@ def main():
         barrier()
         torch.cuda.profiler.start()  # a launch-list capture with --profile-from-start off sees the timed cycles
         t0.record(stream)
+        eig_cycles = []  # per timed cycle: the eigensolve's start block and steps (host fields, no device work)
         for i in range(args.steps):
             _, X, Y = cycle(args.prec, X, Y, fl_t[i])
+            st_ = ctx.eigensolver_stats()
+            eig_cycles.append({k: st_[k] for k in ("start_order", "start_solver", "steps", "used")})
         t1.record(stream)
         barrier()
         torch.cuda.profiler.stop()
@@ -1231,6 +1234,7 @@ def main():
         "filter_tflops_other_precisions": other,
         "e2e": e2e, "e2e_cycle": e2e_cycle, "gpu_launches": launches, "clocks": clocks,
         "eigensolver_timed_cycle": eig_timed,
+        "eigensolver_timed_cycles": eig_cycles,
     }
     if conv:
         line["converge"] = conv

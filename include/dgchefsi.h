@@ -322,7 +322,7 @@ dgchefsi_status dgchefsi_cholesky_inverse(dgchefsi_ctx* ctx, double* S, int64_t 
  *                         from its unit vector (a projected H of converging
  *                         CheFSI cycles is nearly diagonal); the block of the
  *                         other rows gets FP32 eigenvectors, from this
- *                         library's cyclic Jacobi kernel up to 224 rows, else
+ *                         library's cyclic Jacobi kernel up to 320 rows, else
  *                         from cuSOLVER's single-precision solver (the whole
  *                         matrix when more than half the rows are coupled).
  *                         Per step the products
@@ -357,7 +357,7 @@ dgchefsi_status dgchefsi_subspace_eigh(dgchefsi_ctx* ctx, double* A, int64_t n, 
 /* Start of the refined eigensolve (Alg. 1 step 4): rows whose largest
  * first-order coupling |H_ij| / |H_jj - H_ii| reaches `coupling` get FP32
  * eigenvectors of their block (cuSOLVER's single-precision solver) as the
- * start (a cyclic Jacobi kernel up to 224 rows, else cuSOLVER's
+ * start (a cyclic Jacobi kernel up to 320 rows, else cuSOLVER's
  * single-precision solver), the others their unit vectors. 0 < coupling <= 1; default 0.001. A smaller value solves a
  * larger block in FP32 and starts the rest closer to convergence (on the
  * 8x8x8 CheFSI cycles 0.001 takes 3 steps where 0.01 takes 4). ERR_ARG
@@ -380,7 +380,7 @@ dgchefsi_status dgchefsi_eigensolver_history(const dgchefsi_ctx* ctx, double* co
  *   update       largest |correction| of the last step
  *   start_ms, refine_ms  host wall time of the start and of the refinement
  *   start_solver 0 none (identity start), 1 this library's cyclic Jacobi
- *                kernel (a block of at most 224 rows), 2 cuSOLVER's
+ *                kernel (a block of at most 320 rows), 2 cuSOLVER's
  *                single-precision solver (larger blocks, the whole matrix)
  *   start_order  order of the block solved in FP32 for the start: n (the
  *                whole matrix), fewer (only the coupled rows), 0 (the

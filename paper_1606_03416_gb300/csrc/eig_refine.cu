@@ -360,19 +360,33 @@ __global__ void __launch_bounds__(256) k_update_coeffs(const double* __restrict_
 // (c e_p - s e_q, s e_p + c e_q). Because the pairs of a round are disjoint,
 // the 2 x 2 block of B on rows of pair k and columns of pair l receives
 // exactly the column rotation of l and then the row rotation of k, so one
-// pass over the blocks applies the whole round; only the blocks with l >= k
-// are computed, each written with its mirror. After each sweep (M - 1
-// rounds) the off-diagonal part is measured; the sweeps stop once its squared
-// Frobenius norm is below 2^-32 of the whole (2^-16 in norm: near FP32
-// rounding, a start for the FP64 refinement) or after 40.
-// Every CTA of the grid runs the same iteration on its own copy of B (the
-// arithmetic and its order are identical, so are the rotations) and keeps
-// components [c0, c0 + cw) of the vectors, cw = ceil(m / gridDim.x), in
-// shared memory: B and a slab of W fit one SM's shared memory up to m = 224.
-constexpr int kJacobiMax = 224;
+// pass over the blocks with l >= k applies the whole round. After each sweep
+// (M - 1 rounds) the off-diagonal part is measured; the sweeps stop once its
+// squared Frobenius norm is below 2^-32 of the whole (2^-16 in norm: near
+// FP32 rounding, a start for the FP64 refinement) or after 40.
+// B is held once per entry (jacobi_slot), so a block of 320 rows takes
+// ~207 KB of shared memory. Every CTA of the grid runs the same iteration on
+// its own copy of B (the arithmetic and its order are identical, so are the
+// rotations) and keeps components [c0, c0 + cw) of the vectors, cw =
+// ceil(m / gridDim.x), in shared memory.
+constexpr int kJacobiMax = 320;
 constexpr int kJacobiThreads = 1024;
-constexpr int kJacobiCtas = 8;
+constexpr int kJacobiCtas = 32;
 constexpr int kJacobiChunks = (kJacobiMax / 2 + 31) / 32;  // 32-wide chunks of the pair index
+
+// Slot of entry {i, j} (i, j < m) in the wrapped half storage of a symmetric
+// matrix: with the odd modulus Mo = m | 1 and d = (j - i) mod Mo, exactly one
+// of d and Mo - d is at most (Mo - 1) / 2; the entry is column d of row i in
+// the first case, column Mo - d of row j in the second (column 0: the
+// diagonal). Rows have ld >= (Mo + 1) / 2 columns, ld even: 32 consecutive
+// j then fall on distinct banks in either case (strides 1 and ld - 1).
+__device__ __forceinline__ int jacobi_slot(int i, int j, int Mo, int ld) {
+  int d = j - i;
+  d += d < 0 ? Mo : 0;
+  return d <= (Mo >> 1) ? i * ld + d : j * ld + (Mo - d);
+}
+
+__host__ __device__ constexpr int jacobi_ld(int m) { return (((m | 1) + 1) / 2 + 1) & ~1; }
 
 __global__ void __launch_bounds__(kJacobiThreads, 1) k_block_jacobi(const float* __restrict__ B, int m,
                                                                     float* __restrict__ W, float* __restrict__ w) {
@@ -383,12 +397,16 @@ __global__ void __launch_bounds__(kJacobiThreads, 1) k_block_jacobi(const float*
   __shared__ int done;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
   const int cw = (m + (int)gridDim.x - 1) / (int)gridDim.x, c0 = (int)blockIdx.x * cw;
-  const int ld = m | 1;       // odd: the mirrored (column) writes spread over the banks
-  float* As = sm_j;           // m x ld, row-major
+  const int Mo = m | 1, ld = jacobi_ld(m), ncol = (Mo + 1) / 2;
+  float* As = sm_j;           // m x ld, wrapped half storage
   float* Ws = sm_j + m * ld;  // m x cw: components c0 .. c0 + cw - 1 of every vector
   const int M = m + (m & 1), half = M / 2;
   for (int i = warp; i < m; i += nw) {
-    for (int j = lane; j < m; j += 32) As[i * ld + j] = j <= i ? B[i * m + j] : B[j * m + i];
+    for (int d = lane; d < ld; d += 32) {
+      int j = i + d;
+      j -= j >= Mo ? Mo : 0;
+      As[i * ld + d] = d < ncol && j < m ? B[(int64_t)max(i, j) * m + min(i, j)] : 0.0f;
+    }
     for (int j = lane; j < cw; j += 32) Ws[i * cw + j] = c0 + j == i ? 1.0f : 0.0f;
   }
   if (t == 0) done = 0;
@@ -402,9 +420,9 @@ __global__ void __launch_bounds__(kJacobiThreads, 1) k_block_jacobi(const float*
         const int p = min(pa, pb), q = max(pa, pb);
         float c = 1.0f, sv = 0.0f;
         if (q < m) {
-          const float apq = As[q * ld + p];
+          const float apq = As[jacobi_slot(q, p, Mo, ld)];
           if (apq != 0.0f) {
-            const float tau = (As[q * ld + q] - As[p * ld + p]) / (2.0f * apq);
+            const float tau = (As[q * ld] - As[p * ld]) / (2.0f * apq);
             const float tt = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
             c = 1.0f / sqrtf(1.0f + tt * tt);
             sv = tt * c;
@@ -416,10 +434,10 @@ __global__ void __launch_bounds__(kJacobiThreads, 1) k_block_jacobi(const float*
         sn[t] = q < m ? sv : 0.0f;
       }
       __syncthreads();
-      // block (k, l), l >= k: rows pp[k], qq[k] x columns pp[l], qq[l],
-      // written with its mirror (B stays exactly symmetric); warp w takes
-      // k = w, w + nw, ... and lane j the l = 32 c + j of chunk c, whose
-      // pair values it holds in registers for the whole round
+      // block (k, l), l >= k: rows pp[k], qq[k] x columns pp[l], qq[l]; each
+      // entry is in exactly one such block. Warp w takes k = w, w + nw, ...
+      // and lane j the l = 32 c + j of chunk c, whose pair values it holds in
+      // registers for the whole round.
       int pl[kJacobiChunks], ql[kJacobiChunks];
       float cl[kJacobiChunks], sl[kJacobiChunks];
 #pragma unroll
@@ -440,34 +458,24 @@ __global__ void __launch_bounds__(kJacobiThreads, 1) k_block_jacobi(const float*
           const int l = c * 32 + lane;
           if (l < k || l >= half) continue;
           const bool lrot = ql[c] != pl[c];
-          const float a = As[pk * ld + pl[c]], b = As[pk * ld + ql[c]];
-          const float d = As[qk * ld + pl[c]], e = As[qk * ld + ql[c]];
+          // on the pair's own block (l == k) slots sb and sd coincide
+          const int sa = jacobi_slot(pk, pl[c], Mo, ld), sb = jacobi_slot(pk, ql[c], Mo, ld);
+          const int sd = jacobi_slot(qk, pl[c], Mo, ld), se = jacobi_slot(qk, ql[c], Mo, ld);
+          const float a = As[sa], b = As[sb], d = As[sd], e = As[se];
           const float a1 = cl[c] * a - sl[c] * b, b1 = sl[c] * a + cl[c] * b;
           const float d1 = cl[c] * d - sl[c] * e, e1 = sl[c] * d + cl[c] * e;
-          const float a2 = ck * a1 - sk * d1, b2 = ck * b1 - sk * e1;
-          const float d2 = sk * a1 + ck * d1, e2 = sk * b1 + ck * e1;
-          if (l == k) {  // the pair's own 2 x 2 block
-            As[pk * ld + pk] = a2;
+          As[sa] = ck * a1 - sk * d1;
+          if (l == k) {
             if (krot) {
-              As[pk * ld + qk] = b2;
-              As[qk * ld + pk] = b2;
-              As[qk * ld + qk] = e2;
+              As[sb] = ck * b1 - sk * e1;
+              As[se] = sk * b1 + ck * e1;
             }
             continue;
           }
-          As[pk * ld + pl[c]] = a2;
-          As[pl[c] * ld + pk] = a2;
-          if (lrot) {
-            As[pk * ld + ql[c]] = b2;
-            As[ql[c] * ld + pk] = b2;
-          }
+          if (lrot) As[sb] = ck * b1 - sk * e1;
           if (krot) {
-            As[qk * ld + pl[c]] = d2;
-            As[pl[c] * ld + qk] = d2;
-            if (lrot) {
-              As[qk * ld + ql[c]] = e2;
-              As[ql[c] * ld + qk] = e2;
-            }
+            As[sd] = sk * a1 + ck * d1;
+            if (lrot) As[se] = sk * b1 + ck * e1;
           }
         }
         if (krot)  // rows pk, qk of the W slab
@@ -481,10 +489,14 @@ __global__ void __launch_bounds__(kJacobiThreads, 1) k_block_jacobi(const float*
     }
     float off = 0.0f, tot = 0.0f;
     for (int i = warp; i < m; i += nw)
-      for (int j = lane; j < m; j += 32) {
-        const float a = As[i * ld + j];
-        tot += a * a;
-        if (i != j) off += a * a;
+      for (int d = lane; d < ncol; d += 32) {
+        int j = i + d;
+        j -= j >= Mo ? Mo : 0;
+        if (j >= m) continue;
+        const float a = As[i * ld + d];
+        const float a2 = d == 0 ? a * a : 2.0f * a * a;  // an off-diagonal slot holds two entries
+        tot += a2;
+        if (d != 0) off += a2;
       }
     for (int o = 16; o > 0; o >>= 1) {
       off += __shfl_xor_sync(0xffffffffu, off, o);
@@ -507,7 +519,7 @@ __global__ void __launch_bounds__(kJacobiThreads, 1) k_block_jacobi(const float*
     if (done) break;
   }
   if (blockIdx.x == 0)
-    for (int i = t; i < m; i += blockDim.x) w[i] = As[i * ld + i];
+    for (int i = t; i < m; i += blockDim.x) w[i] = As[i * ld];
   for (int i = warp; i < m; i += nw)
     for (int j = lane; j < cw && c0 + j < m; j += 32) W[(int64_t)i * m + c0 + j] = Ws[i * cw + j];
 }
@@ -796,7 +808,7 @@ dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda
       W32 = ws.A32 + m * m;
       const int ctas = (int)std::min<int64_t>(kJacobiCtas, m);
       const int64_t cw = (m + ctas - 1) / ctas;
-      const int smem = (int)(sizeof(float) * (m * (m | 1) + m * cw));
+      const int smem = (int)(sizeof(float) * (m * jacobi_ld((int)m) + m * cw));
       DG_CUDA(cudaFuncSetAttribute(k_block_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
       k_block_jacobi<<<ctas, kJacobiThreads, smem, st>>>(ws.A32, (int)m, W32, ws.w32);
       count_launch();

@@ -149,21 +149,21 @@ def test_identity_start_for_a_nearly_diagonal_matrix():
 @pytest.mark.parametrize(
     "n,top,repeats",
     [(600, 7, 0), (700, 37, 0), (900, 61, 0), (1100, 150, 0), (1300, 213, 0), (1600, 150, 0), (1600, 150, 3),
-     (1600, 300, 0)],
+     (1600, 300, 0), (1600, 311, 0), (1600, 312, 0), (1600, 400, 0)],
 )
 def test_partial_start_for_a_coupled_top_block(n, top, repeats):
     # with 2e-8 background coupling 13, 41, 63 (odd orders: the Jacobi
-    # tournament has an idle index), 156, 224 (the Jacobi kernel's largest
-    # order) and 160 rows reach the default start threshold: the full and the
-    # block-structured first step
+    # tournament has an idle index), 156, 224, 160, 308, 319 and 320 (the
+    # Jacobi kernel's largest order) and 406 rows reach the default start
+    # threshold: the full and the block-structured first step
     """Only the last `top` rows are coupled: the FP32 start solves that block
     alone (its order is reported), the rest starts from unit vectors. With a
     block of at most n/8 rows the first step's products and update come from
     the block's rows and columns; `repeats` pairs of exactly equal, mutually
     uncoupled diagonal entries outside the block form clusters in that step,
-    whose rows join the block of the update. Blocks up to 224 rows get their
-    FP32 start from the library's one-CTA Jacobi kernel (n = 1600 with a
-    300-row coupled block still takes cuSOLVER's)."""
+    whose rows join the block of the update. Blocks up to 320 rows get their
+    FP32 start from the library's cyclic Jacobi kernel (a 406-row coupled
+    block still takes cuSOLVER's)."""
     d = G.clustered_spectrum(n, seed=33)
     A = G.near_diagonal_symmetric(d, 2e-8, top=top, top_coupling=0.05, seed=33)
     for r in range(repeats):
@@ -176,8 +176,8 @@ def test_partial_start_for_a_coupled_top_block(n, top, repeats):
     ew, eo, er = check_against_oracle(A, w, V)
     print(f"EIGH partial start n={n} repeats={repeats}: eig {ew:.1e} orth {eo:.1e} resid {er:.1e} {st}")
     assert st["used"] == "refined" and st["fallback"] == 0 and top <= st["start_order"] <= n // 2
-    # blocks up to 224 rows start from this library's Jacobi kernel, larger ones from cuSOLVER
-    assert st["start_solver"] == ("jacobi" if st["start_order"] <= 224 else "cusolver_fp32")
+    # blocks up to 320 rows start from this library's Jacobi kernel, larger ones from cuSOLVER
+    assert st["start_solver"] == ("jacobi" if st["start_order"] <= 320 else "cusolver_fp32")
     if repeats:
         assert st["max_cluster"] >= 2
 

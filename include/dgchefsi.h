@@ -356,18 +356,25 @@ dgchefsi_status dgchefsi_subspace_eigh(dgchefsi_ctx* ctx, double* A, int64_t n, 
 
 /* Start of the refined eigensolve (Alg. 1 step 4): rows whose largest
  * first-order coupling |H_ij| / |H_jj - H_ii| reaches `coupling` get FP32
- * eigenvectors of their block (cuSOLVER's single-precision solver) as the
- * start (a cyclic Jacobi kernel up to 320 rows, else cuSOLVER's
- * single-precision solver), the others their unit vectors. 0 < coupling <= 1; default 0.001. A smaller value solves a
+ * eigenvectors of their block as the start (a cyclic Jacobi kernel up to 320
+ * rows, else cuSOLVER's single-precision solver), the others their unit
+ * vectors. 0 < coupling <= 1; default 0.001. A smaller value solves a
  * larger block in FP32 and starts the rest closer to convergence (on the
  * 8x8x8 CheFSI cycles 0.001 takes 3 steps where 0.01 takes 4). ERR_ARG
  * outside (0, 1]. */
 dgchefsi_status dgchefsi_set_refinement_start(dgchefsi_ctx* ctx, double coupling);
 
-/* The largest correction of each step of the last refined eigensolve
- * (Alg. 1 step 4): corrections[0 .. min(count, cap)) (may be null), *count =
- * the steps taken (at most 16 are kept). */
-dgchefsi_status dgchefsi_eigensolver_history(const dgchefsi_ctx* ctx, double* corrections, int cap, int* count);
+/* Each step of the last refined eigensolve (Alg. 1 step 4), entries
+ * [0 .. min(count, cap)) of each array (either may be null):
+ *   corrections  the step's largest correction max|E|
+ *   slices       BF16 slices of the step's update product E^T V: the fewest
+ *                whose splitting error, 2 L max|E| 2^(-6 s) (s + 4) per K
+ *                chunk of length L, stays below 2^-53 L, at most the
+ *                products' slice count; 0 when the step's update needed no
+ *                full product (an identity or block-structured step)
+ * *count = the steps taken (at most 16 are kept). */
+dgchefsi_status dgchefsi_eigensolver_history(const dgchefsi_ctx* ctx, double* corrections, int* slices, int cap,
+                                             int* count);
 
 /* What the context's last eigensolve did (any pointer may be null):
  *   used         DGCHEFSI_EIG_SYEVD or DGCHEFSI_EIG_REFINED

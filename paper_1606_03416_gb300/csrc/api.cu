@@ -837,12 +837,14 @@ dgchefsi_status dgchefsi_set_refinement_start(dgchefsi_ctx* ctx, double coupling
   return DGCHEFSI_OK;
 }
 
-dgchefsi_status dgchefsi_eigensolver_history(const dgchefsi_ctx* ctx, double* corrections, int cap, int* count) {
+dgchefsi_status dgchefsi_eigensolver_history(const dgchefsi_ctx* ctx, double* corrections, int* slices, int cap,
+                                             int* count) {
   clear_error();
   DG_TRY(check_ctx(ctx));
   const int k = std::min(ctx->eig_steps, 16);
   if (count) *count = k;
   for (int i = 0; corrections && i < std::min(k, cap); ++i) corrections[i] = ctx->eig_history[i];
+  for (int i = 0; slices && i < std::min(k, cap); ++i) slices[i] = ctx->eig_slices_history[i];
   return DGCHEFSI_OK;
 }
 

@@ -79,7 +79,8 @@ struct dgchefsi_ctx {
   double eig_update = 0.0, eig_start_ms = 0.0, eig_refine_ms = 0.0;
   int64_t eig_start_order = 0;
   int eig_start_solver = 0;  // 0 none (identity start), 1 this library's Jacobi kernel, 2 cuSOLVER FP32
-  double eig_history[16] = {};  // largest correction of each refinement step
+  double eig_history[16] = {};     // largest correction of each refinement step
+  int eig_slices_history[16] = {};  // slices of each step's update product (0: no full product)
   double eig_start_coupling = 0.001;  // first-order coupling that puts a row in the FP32 start block
   dg::DevBuf ws_eig;
   // Cholesky factorisation of step 3 (DGCHEFSI_CHOL_*) and the recursive

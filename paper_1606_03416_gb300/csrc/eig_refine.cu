@@ -32,14 +32,16 @@
 // Start: a row of A whose first-order couplings |A_ij| / |A_jj - A_ii| all
 // stay below the context's start threshold begins as its unit vector (a
 // projected H of converging CheFSI cycles is nearly diagonal); the block of
-// the other rows gets FP32 eigenvectors (cuSOLVER's single-precision solver),
-// the whole matrix when more than half the rows are in it. With V = I the
+// the other rows gets FP32 eigenvectors (this library's Jacobi kernel up to
+// kJacobiMax rows, else cuSOLVER's single-precision solver), the whole matrix
+// when more than half the rows are in it. With V = I the
 // first step needs no products; with V = I outside a block of at most n/8
 // rows, only small FP64 products on the block's rows and columns.
 //
 // Products per later step: T = V A, [G; S] = [V; T] V^T (one call, 2n x n,
 // lower triangles) and the update V <- V + E^T V, all n x n x n on the
-// slice-pair kernel. Stop after the step whose largest correction is at most
+// slice-pair kernel; the update takes only the slices that the size of E
+// needs (update_slices), fewer as the corrections shrink. Stop after the step whose largest correction is at most
 // kStop, or whose correction, at the quadratic rate seen over the last two
 // steps, predicts the next one below kPredict.
 
@@ -750,6 +752,15 @@ double ms_since(Clock::time_point t) { return std::chrono::duration<double, std:
 // untouched): 1 the FP32 start failed, 2 more close pairs than the table
 // holds, 3 a cluster larger than kMaxCluster, 4 a correction that is not
 // finite or not below 1, 5 no convergence in kMaxSteps steps.
+// Fewest slices s' in [2, smax] of the refinement's update product E^T V
+// whose splitting error, 2 L emax 2^{-6s'} (s' + 4) per K chunk, stays below
+// u L = 2^-53 L; smax when none does.
+static int update_slices(double emax, int smax) {
+  for (int sp = 2; sp < smax; ++sp)
+    if (2.0 * std::ldexp((double)(sp + 4), -6 * sp) * emax <= 0x1p-53) return sp;
+  return smax;
+}
+
 dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda, double* w, int* reason) {
   *reason = 0;
   if (n > INT32_MAX / 2 || lda > INT32_MAX)
@@ -1044,8 +1055,14 @@ dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda
       DG_CUDA(cudaGetLastError());
       DG_CUDA(cudaStreamSynchronize(st));  // the host tables above are pageable copies' sources
     } else {
-      DG_TRY(sliced_gemm(ctx, false, false, n, n, n, ws.F, n, V, n, ws.GS, n, s, bad));  // E^T V
-      DG_CUDA(axpby_f64(1.0, ws.GS, 1.0, V, V, nn, st));                                  // V <- V + E^T V
+      // E^T V with the slices its size needs: the splitting error is at most
+      // L max|F| max|V| 2^{-6s'} (s' + 4) per K chunk of length L (sliced.cu),
+      // max|F| = emax and max|V| < 2, so 2^{-6s'} (s' + 4) 2 emax <= 2^-53
+      // keeps it below u L, FP64's own bound for a product of V's size
+      const int su = update_slices(emax, s);
+      if (step < 16) ctx->eig_slices_history[step] = su;
+      DG_TRY(sliced_gemm(ctx, false, false, n, n, n, ws.F, n, V, n, ws.GS, n, su, bad));  // E^T V
+      DG_CUDA(axpby_f64(1.0, ws.GS, 1.0, V, V, nn, st));                                   // V <- V + E^T V
     }
     unit = false;
     block = false;
@@ -1091,6 +1108,7 @@ dgchefsi_status subspace_eigh(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t l
   ctx->eig_start_order = 0;
   ctx->eig_start_solver = 0;
   for (double& h : ctx->eig_history) h = 0.0;
+  for (int& h : ctx->eig_slices_history) h = 0;
   ctx->eig_used = DGCHEFSI_EIG_SYEVD;
   if (n <= 0) return DGCHEFSI_OK;
   int mode = ctx->eig_mode;

@@ -91,7 +91,7 @@ def load_library(path: str = _LIBPATH) -> C.CDLL:
         "dgchefsi_set_eigensolver": (st, [P, C.c_int]),
         "dgchefsi_set_cholesky": (st, [P, C.c_int]),
         "dgchefsi_set_refinement_start": (st, [P, D]),
-        "dgchefsi_eigensolver_history": (st, [P, P, C.c_int, P]),
+        "dgchefsi_eigensolver_history": (st, [P, P, P, C.c_int, P]),
         "dgchefsi_cholesky_inverse": (st, [P, P, I64, I64]),
         "dgchefsi_subspace_eigh": (st, [P, P, I64, I64, P]),
         "dgchefsi_eigensolver_stats": (st, [P, P, P, P, P, P, P, P, P, P]),
@@ -418,12 +418,14 @@ class Context:
                                                C.byref(order), C.byref(solver)))
         hist = (C.c_double * 16)()
         cnt = C.c_int()
-        _check(_lib.dgchefsi_eigensolver_history(self._h, hist, 16, C.byref(cnt)))
+        sl = (C.c_int * 16)()
+        _check(_lib.dgchefsi_eigensolver_history(self._h, hist, sl, 16, C.byref(cnt)))
         return {"used": EIGENSOLVER_NAMES.get(i[0].value, i[0].value), "steps": i[1].value,
                 "max_cluster": i[2].value, "fallback": i[3].value, "update": d[0].value,
                 "start_ms": d[1].value, "refine_ms": d[2].value, "start_order": order.value,
                 "start_solver": {0: "none", 1: "jacobi", 2: "cusolver_fp32"}.get(solver.value, solver.value),
-                "history": [hist[k] for k in range(cnt.value)]}
+                "history": [hist[k] for k in range(cnt.value)],
+                "update_slices": [sl[k] for k in range(cnt.value)]}
 
     def set_refinement_start(self, coupling: float = 0.001):
         """First-order coupling at which a row joins the FP32 start block of

@@ -16,6 +16,8 @@ Clusters of repeated values are resolved (statistics show them), a cluster
 above 32 members hands over to the FP64 solver with the same results, and the
 context's choice of solver follows DGCHEFSI_EIG_AUTO.
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -79,6 +81,12 @@ def test_refined_matches_oracle(n):
     ew, eo, er = check_against_oracle(A, w, V)
     print(f"EIGH refined n={n}: eig {ew:.1e} orth {eo:.1e} resid {er:.1e} {st}")
     assert st["used"] == "refined" and st["fallback"] == 0 and 1 <= st["steps"] <= 5
+    # from a whole-matrix start every step's update is a full product; it takes
+    # the fewest slices whose splitting error 2 L max|E| 2^(-6s) (s + 4) stays
+    # below 2^-53 L (the parity above holds with them)
+    expect = [next((k for k in range(2, 10) if 2 * math.ldexp(k + 4, -6 * k) * e <= 2.0**-53), 10)
+              for e in st["history"]]
+    assert st["update_slices"] == expect and expect[-1] < 10
 
 
 def test_refined_resolves_repeated_and_close_eigenvalues():

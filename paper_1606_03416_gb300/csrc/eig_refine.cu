@@ -780,10 +780,11 @@ dgchefsi_status eig_refined(dgchefsi_ctx* ctx, double* A, int64_t n, int64_t lda
 
   // Start. Rows whose first-order couplings are all below the context's
   // start threshold (0.001 by default) start from their unit vector; the
-  // block of the other rows is solved in FP32 (cuSOLVER's single-precision
-  // solver) and its eigenvectors placed on those rows. When more than half
-  // the rows are coupled (a first projected H, a matrix without structure)
-  // the whole matrix is solved in FP32.
+  // block of the other rows is solved in FP32 (k_block_jacobi up to
+  // kJacobiMax rows, else cuSOLVER's single-precision solver) and its
+  // eigenvectors placed on those rows. When more than half the rows are
+  // coupled (a first projected H, a matrix without structure) the whole
+  // matrix is solved in FP32 by cuSOLVER.
   k_mirror_lower<<<grid_for(nn), 256, 0, st>>>(A, lda, n);
   k_row_coupling<<<(unsigned)std::min<int64_t>(n, 1 << 16), 256, 0, st>>>(A, lda, n, ctx->eig_start_coupling, 0.0,
                                                                          ws.cl, ws.lam);

@@ -968,7 +968,8 @@ def main():
         for i in range(args.steps):
             _, X, Y = cycle(args.prec, X, Y, fl_t[i])
             st_ = ctx.eigensolver_stats()
-            eig_cycles.append({k: st_[k] for k in ("start_order", "start_solver", "steps", "used")})
+            eig_cycles.append({k: st_[k] for k in ("start_order", "start_solver", "steps", "used", "history",
+                                                   "update_slices")})
         t1.record(stream)
         barrier()
         torch.cuda.profiler.stop()
